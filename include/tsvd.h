@@ -1,0 +1,152 @@
+/*
+ * tsvd.h -- C ABI of libtsvd: tensor singular value thresholding (t-SVT) and the two ADMM
+ * solvers built on it, from Zhang, Ely, Aeron, Hao and Kilmer, "Novel methods for
+ * multilinear data completion and de-noising based on tensor-SVD" (arXiv:1407.1785).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Tensors.  A real tensor of order 3 (n1 x n2 x n3) or 4 (n1 x n2 x n3 x n4) is a dense FP32
+ *   array in MATLAB column-major order: entry (i1, i2, i3[, i4]) (0-based) lives at
+ *   i1 + n1*(i2 + n2*(i3 + n3*i4)).  `order` is 3 or 4 and `dims` points to `order` int64
+ *   extents, each >= 1.  The transformed modes are 3 (and 4): the Fourier slices of Sec. 2
+ *   are taken along them (Algorithm 1, "fft along modes 3..N").
+ * Memory.  Every tensor pointer may be either a device pointer (on the context's device) or
+ *   host memory (pinned or pageable); the library asks the CUDA runtime which it is.  Device
+ *   tensors are used in place and the call returns as soon as the work is queued on the
+ *   context's stream (results are ready when that stream reaches them).  Host tensors are
+ *   copied to and from library-owned device buffers on the stream and the call returns after
+ *   the stream has finished.  The caller owns all tensors; the library keeps no pointer
+ *   after a call returns.  Small outputs (`multirank`, `tnn`, `stats`) are host pointers; a
+ *   call that fills one of them waits for its stream.
+ * Errors.  Every call returns a tsvd_status and never aborts; tsvd_last_error() holds a
+ *   one-line reason for the last failure on that context.  TSVD_EINVAL: a null required
+ *   pointer, order not 3 or 4, an extent < 1, a non-finite observed entry or a bad scalar.
+ *   TSVD_EUNSUPPORTED: a shape the kernels do not handle (reported before any work).
+ *   TSVD_ECUDA: a CUDA runtime error.  TSVD_ENOTCONV: a tsvt() call whose Jacobi SVD of some
+ *   Fourier slice reached max_sweeps (the result is still written); inside the ADMM solvers
+ *   such slices are only counted in tsvd_stats.
+ * Threads.  A context is not thread-safe; calls on one context run in order on its stream.
+ *   Distinct contexts are independent.
+ */
+#ifndef TSVD_H
+#define TSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsvd_ctx tsvd_ctx;
+
+typedef enum tsvd_status {
+  TSVD_OK = 0,
+  TSVD_EINVAL = 1,
+  TSVD_ENOMEM = 2,
+  TSVD_ECUDA = 3,
+  TSVD_ENOTCONV = 4,
+  TSVD_ETIMEOUT = 5,
+  TSVD_EUNSUPPORTED = 6
+} tsvd_status;
+
+/* Precision of the slice SVDs.  Only TSVD_PRECISION_FP32 (one-sided Jacobi in FP32) is
+ * implemented; the other values are rejected with TSVD_EUNSUPPORTED. */
+enum { TSVD_PRECISION_FP32 = 0, TSVD_PRECISION_TF32 = 1, TSVD_PRECISION_BF16 = 2,
+       TSVD_PRECISION_3XTF32 = 3 };
+
+/* Sparse penalty of tensor RPCA: entrywise l1 (soft threshold at lambda/rho) or the
+ * tube-wise l_{1,1,2} norm of Sec. 5 (eq. sparse2; for order 4 the group is S(i,j,:,:)). */
+enum { TSVD_SPARSE_ENTRY = 0, TSVD_SPARSE_TUBE = 1 };
+
+/* Threshold of the ADMM low-rank step for penalty rho.  AVG: tau = 1/rho applied to the
+ * singular values of the unnormalised DFT slices, i.e. eq. shrink as printed (the prox of
+ * TNN/P in the original domain, P = number of Fourier slices).  SUM: tau = P/rho, the prox
+ * of the TNN exactly as defined in Thm 2.4.1 (sum over all Fourier slices). */
+enum { TSVD_SCALE_AVG = 0, TSVD_SCALE_SUM = 1 };
+
+typedef struct tsvd_opts {
+  int precision;      /* TSVD_PRECISION_*; default FP32 */
+  int sparse_mode;    /* TSVD_SPARSE_*; default ENTRY */
+  int tnn_scale;      /* TSVD_SCALE_*; default AVG */
+  double rho0;        /* initial ADMM penalty; default 1e-2 */
+  double mu;          /* penalty growth per iteration, rho <- min(mu*rho, rho_max); 1.1 */
+  double rho_max;     /* penalty cap; default 1e10 */
+  int max_sweeps;     /* Jacobi sweep cap per slice SVD; default 40 */
+  float jacobi_tol;   /* rotate a pair while |x^H y| > tol ||x|| ||y||; default 1e-6 */
+  int timing;         /* 1: time every kernel launch with CUDA events on the context's stream
+                         and report the totals in tsvd_stats; default 0 */
+} tsvd_opts;
+
+/* Counters of one ADMM solve (host struct). */
+typedef struct tsvd_stats {
+  int iters;                    /* ADMM iterations run */
+  int max_sweeps_used;          /* most Jacobi sweeps taken by any slice SVD */
+  int64_t total_sweeps;         /* Jacobi sweeps summed over all slice SVDs */
+  int64_t nonconverged;         /* slice SVDs stopped by max_sweeps */
+  int64_t slice_svds;           /* slice SVDs run */
+  double rho_final;             /* penalty after the last iteration */
+  double tnn_last;              /* TNN (sum form) of the last t-SVT input */
+  int rank_last_max;            /* largest Fourier-slice rank of the last t-SVT result */
+  int64_t launches;             /* kernels launched by the call */
+  int64_t slice_launches;       /* of which slice-SVT launches */
+  double slice_ms;              /* summed device time of the slice-SVT launches (timing=1) */
+  double tube_ms;               /* summed device time of the tube-pass launches (timing=1) */
+} tsvd_stats;
+
+/* Fill *opts with the defaults listed above. */
+void tsvd_default_opts(tsvd_opts* opts);
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  `opts` may be NULL for the defaults and
+ * is copied.  On success *out owns device workspaces that grow on demand; free it with
+ * tsvd_destroy().  Errors: EINVAL (out == NULL, bad opts), ECUDA (device unusable). */
+tsvd_status tsvd_create(tsvd_ctx** out, int device, void* cuda_stream, const tsvd_opts* opts);
+
+/* Wait for the context's stream, release every buffer the context owns and free it.
+ * NULL is accepted. */
+tsvd_status tsvd_destroy(tsvd_ctx* ctx);
+
+/* One-line description of the last failure on ctx (static string for ctx == NULL). */
+const char* tsvd_last_error(const tsvd_ctx* ctx);
+
+/* t-SVT: Z = prox of tau*TNN-per-slice, i.e. for every Fourier slice Yhat^(k) (DFT along
+ * modes 3..order) Zhat^(k) = D_tau(Yhat^(k)) = U diag((sigma_i - tau)_+) V^H, then the
+ * inverse DFT (Lemma and eq. shrink2 of Sec. 4.1, Algorithm 1).  tau applies to the singular
+ * values of the unnormalised DFT slices.  Y and Z: dims-shaped tensors (may alias).  Unlike
+ * the solvers, tsvt() always waits for its stream before returning (it reports ENOTCONV).
+ * multirank (nullable, host): receives the rank of every Fourier slice of Z, prod(dims[2..])
+ * int32 in column-major (k3[, k4]) order.  tnn (nullable, host): receives the TNN of Y, the
+ * sum of the singular values of all Fourier slices (Thm 2.4.1).  Errors: EINVAL (tau < 0 or
+ * not finite), EUNSUPPORTED, ENOTCONV. */
+tsvd_status tsvt(tsvd_ctx* ctx, const float* Y, float* Z, int order, const int64_t* dims,
+                 float tau, int32_t* multirank, double* tnn);
+
+/* TNN tensor completion (Sec. 4: min ||X||_TNN s.t. P_Omega(X) = P_Omega(M), eq.
+ * originalTNN) by the ADMM of eq. proj / eq. shrink / dual ascent with scaled dual Q and
+ * penalty schedule rho_{k+1} = min(mu rho_k, rho_max) from opts:
+ *   X = P_Omega(M) + P_Omega^c(Z - Q);  Z = tSVT(X + Q, tau(rho));  Q = (Q + X - Z) rho_k/rho_{k+1}.
+ * M_obs: dims-shaped tensor whose entries are read only where omega is nonzero (they must be
+ * finite there).  omega: uint8 per entry (nonzero = observed).  iters >= 0 ADMM iterations.
+ * X_out: receives X of the last iteration (it agrees with M_obs on Omega).  Z_out
+ * (nullable): receives Z of the last iteration.  stats (nullable, host).  Errors: EINVAL,
+ * EUNSUPPORTED. */
+tsvd_status tnn_complete(tsvd_ctx* ctx, const float* M_obs, const uint8_t* omega, int order,
+                         const int64_t* dims, int iters, float* X_out, float* Z_out,
+                         tsvd_stats* stats);
+
+/* Tensor robust PCA (Sec. 5: min ||L||_TNN + lambda ||S||, s.t. M = L + S, eq. tensor_PCA)
+ * by the ADMM of eq. low_rank / eq. sparse / eq. dual with scaled dual W:
+ *   L = tSVT(M - S - W, tau(rho));  S = shrink(M - W - L, lambda/rho);
+ *   W = (W + L + S - M) rho_k/rho_{k+1}.
+ * The shrink is opts.sparse_mode (entrywise, or tube-wise eq. sparse2).  M: dims-shaped,
+ * finite.  lambda > 0.  L_out, S_out: receive L and S of the last iteration.  stats
+ * (nullable, host).  Errors: EINVAL, EUNSUPPORTED. */
+tsvd_status trpca(tsvd_ctx* ctx, const float* M, int order, const int64_t* dims, float lambda,
+                  int iters, float* L_out, float* S_out, tsvd_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSVD_H */

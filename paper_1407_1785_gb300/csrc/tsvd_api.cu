@@ -1,0 +1,696 @@
+// tsvd_api.cu -- the C ABI of libtsvd (include/tsvd.h): argument checks, device workspaces,
+// host/device staging and the order of kernel launches of the t-SVT and of the two ADMM
+// solvers.  All arithmetic runs in the kernels of tube_pass.cu and slice_svt.cu; this file
+// only computes the scalar penalty schedule rho_k (Sec. 4 / Sec. 5) on the host.
+#include "tsvd.h"
+#include "tsvd_internal.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace tsvd;
+
+struct tsvd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  tsvd_opts opts{};
+  std::string err;
+  char* ws = nullptr;        // device workspace
+  size_t ws_cap = 0;
+  std::vector<float2> twid_host;   // kept alive while copies may be in flight
+  std::vector<int> slices_host;
+  std::vector<SliceStat> stat_host;
+  // launch accounting of the current call
+  int64_t launches = 0;
+  int64_t slice_launches = 0;
+  // opts.timing: event pairs around launches; kind 0 = slice SVT, 1 = tube pass
+  std::vector<cudaEvent_t> events;
+  std::vector<int> event_kind;
+  size_t events_used = 0;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+tsvd_status fail(tsvd_ctx* c, tsvd_status st, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return st;
+}
+
+#define TSVD_CUDA(ctx, expr)                                                              \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail((ctx), TSVD_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));             \
+  } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// 0 = device-accessible on `dev`, 1 = host memory, -1 = device memory of another device.
+int pointer_kind(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (at.type == cudaMemoryTypeDevice) return at.device == dev ? 0 : -1;
+  if (at.type == cudaMemoryTypeManaged) return 0;
+  return 1;
+}
+
+// Problem geometry shared by every entry point.
+struct Problem {
+  int order = 0;
+  int64_t n1 = 0, n2 = 0, n3 = 0, n4 = 1;
+  int64_t N = 0;       // entries
+  int64_t nslices = 0; // Fourier slices of the full spectrum (n3 or n3*n4)
+  TubeGeom g{};
+};
+
+tsvd_status make_problem(tsvd_ctx* c, int order, const int64_t* dims, Problem& p) {
+  if (!dims) return fail(c, TSVD_EINVAL, "dims is NULL");
+  if (order != 3 && order != 4) return fail(c, TSVD_EINVAL, "order must be 3 or 4 (got %d)", order);
+  for (int d = 0; d < order; ++d)
+    if (dims[d] < 1) return fail(c, TSVD_EINVAL, "dims[%d] = %lld < 1", d, (long long)dims[d]);
+  p.order = order;
+  p.n1 = dims[0];
+  p.n2 = dims[1];
+  p.n3 = dims[2];
+  p.n4 = order == 4 ? dims[3] : 1;
+  if (p.n1 > (1 << 30) || p.n2 > (1 << 30) || p.n3 > (1 << 20) || p.n4 > (1 << 20))
+    return fail(c, TSVD_EUNSUPPORTED, "extent too large");
+  p.nslices = p.n3 * p.n4;
+  p.N = p.n1 * p.n2 * p.nslices;
+  p.g.N12 = p.n1 * p.n2;
+  if (order == 3) {
+    p.g.nf = 1;
+    p.g.nh = (int)p.n3;
+  } else {
+    p.g.nf = (int)p.n3;
+    p.g.nh = (int)p.n4;
+  }
+  p.g.hh = p.g.nh / 2 + 1;
+  p.g.nstore = p.g.nf * p.g.hh;
+  if (!tube_pass_supported(p.g))
+    return fail(c, TSVD_EUNSUPPORTED, "tube of %lld entries exceeds the tube-pass limit",
+                (long long)p.nslices);
+  if (!jacobi_svt_supported((int)p.n1, (int)p.n2))
+    return fail(c, TSVD_EUNSUPPORTED,
+                "a %lld x %lld complex slice does not fit one SM's shared memory",
+                (long long)p.n1, (long long)p.n2);
+  return TSVD_OK;
+}
+
+// Stored slice (kf, kh) is computed by the t-SVT unless it is the conjugate partner of an
+// earlier stored slice: only possible on the self-conjugate columns kh = 0, nh/2.
+bool slice_is_distinct(const TubeGeom& g, int kf, int kh) {
+  const bool selfcol = (kh == 0) || (2 * kh == g.nh);
+  return !(selfcol && 2 * kf > g.nf);
+}
+
+// Stored slice that holds full-spectrum slice (kf, kfull) itself or its conjugate.
+int stored_slice_of(const TubeGeom& g, int kf, int kfull) {
+  int f = kf, h = kfull;
+  if (h >= g.hh) {  // conjugate partner (-kf, -kh)
+    f = (g.nf - kf) % g.nf;
+    h = g.nh - kfull;
+  }
+  if (!slice_is_distinct(g, f, h)) f = g.nf - f;
+  return f + g.nf * h;
+}
+
+// Number of full-spectrum slices a distinct stored slice stands for (1 or 2).
+int slice_weight(const TubeGeom& g, int kf, int kh) {
+  const bool selfcol = (kh == 0) || (2 * kh == g.nh);
+  const bool selfrow = (kf == 0) || (2 * kf == g.nf);
+  return (selfcol && selfrow) ? 1 : 2;
+}
+
+// Device workspace carved from one allocation.
+struct Workspace {
+  float2* spec_a = nullptr;
+  float2* spec_b = nullptr;
+  float* state = nullptr;
+  float* yn = nullptr;
+  float* stage_in = nullptr;
+  uint8_t* stage_om = nullptr;
+  float* stage_out0 = nullptr;
+  float* stage_out1 = nullptr;
+  float2* twid = nullptr;
+  int* slices = nullptr;
+  SliceStat* stat = nullptr;
+  SweepAccum* acc = nullptr;
+  int* bad = nullptr;
+  int ndistinct = 0;
+};
+
+struct WsRequest {
+  bool state = false, yn = false, stage_in = false, stage_om = false, stage_out0 = false,
+       stage_out1 = false;
+};
+
+tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq, Workspace& w) {
+  const TubeGeom& g = p.g;
+  const size_t spec = align_up((size_t)g.nstore * g.N12 * sizeof(float2));
+  const size_t real = align_up((size_t)p.N * sizeof(float));
+  size_t off[13], total = 0;
+  auto take = [&](int i, size_t bytes) { off[i] = total; total += align_up(bytes); };
+  take(0, spec);
+  take(1, spec);
+  take(2, rq.state ? real : 0);
+  take(3, rq.yn ? real : 0);
+  take(4, rq.stage_in ? real : 0);
+  take(5, rq.stage_om ? (size_t)p.N : 0);
+  take(6, rq.stage_out0 ? real : 0);
+  take(7, rq.stage_out1 ? real : 0);
+  take(8, (size_t)(g.nh + g.nf) * sizeof(float2));
+  take(9, (size_t)g.nstore * sizeof(int));
+  take(10, (size_t)g.nstore * sizeof(SliceStat));
+  take(11, sizeof(SweepAccum));
+  take(12, sizeof(int));
+  if (total > c->ws_cap) {
+    if (c->ws) {
+      TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+      cudaFree(c->ws);
+      c->ws = nullptr;
+      c->ws_cap = 0;
+    }
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, TSVD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", total, cudaGetErrorString(e));
+    }
+    c->ws = static_cast<char*>(ptr);
+    c->ws_cap = total;
+  }
+  char* b = c->ws;
+  w.spec_a = reinterpret_cast<float2*>(b + off[0]);
+  w.spec_b = reinterpret_cast<float2*>(b + off[1]);
+  w.state = rq.state ? reinterpret_cast<float*>(b + off[2]) : nullptr;
+  w.yn = rq.yn ? reinterpret_cast<float*>(b + off[3]) : nullptr;
+  w.stage_in = rq.stage_in ? reinterpret_cast<float*>(b + off[4]) : nullptr;
+  w.stage_om = rq.stage_om ? reinterpret_cast<uint8_t*>(b + off[5]) : nullptr;
+  w.stage_out0 = rq.stage_out0 ? reinterpret_cast<float*>(b + off[6]) : nullptr;
+  w.stage_out1 = rq.stage_out1 ? reinterpret_cast<float*>(b + off[7]) : nullptr;
+  w.twid = reinterpret_cast<float2*>(b + off[8]);
+  w.slices = reinterpret_cast<int*>(b + off[9]);
+  w.stat = reinterpret_cast<SliceStat*>(b + off[10]);
+  w.acc = reinterpret_cast<SweepAccum*>(b + off[11]);
+  w.bad = reinterpret_cast<int*>(b + off[12]);
+
+  // twiddles (cos, sin)(2 pi m / n) in FP64, exact at the quarter points
+  auto table = [](int n, float2* dst) {
+    for (int m = 0; m < n; ++m) {
+      double cr, sr;
+      if (m == 0) { cr = 1; sr = 0; }
+      else if (2 * m == n) { cr = -1; sr = 0; }
+      else if (4 * m == n) { cr = 0; sr = 1; }
+      else if (4 * m == 3 * n) { cr = 0; sr = -1; }
+      else {
+        const double a = 2.0 * M_PI * (double)m / (double)n;
+        cr = std::cos(a);
+        sr = std::sin(a);
+      }
+      dst[m] = make_float2((float)cr, (float)sr);
+    }
+  };
+  c->twid_host.resize((size_t)(g.nh + g.nf));
+  table(g.nh, c->twid_host.data());
+  table(g.nf, c->twid_host.data() + g.nh);
+  c->slices_host.clear();
+  for (int kh = 0; kh < g.hh; ++kh)
+    for (int kf = 0; kf < g.nf; ++kf)
+      if (slice_is_distinct(g, kf, kh)) c->slices_host.push_back(kf + g.nf * kh);
+  w.ndistinct = (int)c->slices_host.size();
+  TSVD_CUDA(c, cudaMemcpyAsync(w.twid, c->twid_host.data(), c->twid_host.size() * sizeof(float2),
+                               cudaMemcpyHostToDevice, c->stream));
+  TSVD_CUDA(c, cudaMemcpyAsync(w.slices, c->slices_host.data(),
+                               c->slices_host.size() * sizeof(int), cudaMemcpyHostToDevice,
+                               c->stream));
+  TSVD_CUDA(c, cudaMemsetAsync(w.acc, 0, sizeof(SweepAccum), c->stream));
+  TSVD_CUDA(c, cudaMemsetAsync(w.stat, 0, (size_t)g.nstore * sizeof(SliceStat), c->stream));
+  TSVD_CUDA(c, cudaMemsetAsync(w.bad, 0, sizeof(int), c->stream));
+  // The host tables above are pageable; cudaMemcpyAsync from pageable memory returns only
+  // after the source has been consumed, so they may change on the next call.
+  return TSVD_OK;
+}
+
+TubeArgs tube_args(const Problem& p, const Workspace& w, int mode) {
+  TubeArgs a{};
+  a.g = p.g;
+  a.mode = mode;
+  a.twid_h = w.twid;
+  a.twid_f = w.twid + p.g.nh;
+  a.ratio = 1.f;
+  return a;
+}
+
+SliceArgs slice_args(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau) {
+  SliceArgs s{};
+  s.ahat = w.spec_a;
+  s.zhat = w.spec_b;
+  s.slices = w.slices;
+  s.nslices = w.ndistinct;
+  s.n1 = (int)p.n1;
+  s.n2 = (int)p.n2;
+  s.N12 = p.g.N12;
+  s.tau = tau;
+  s.tol = c->opts.jacobi_tol;
+  s.max_sweeps = c->opts.max_sweeps;
+  s.stat = w.stat;
+  s.acc = w.acc;
+  return s;
+}
+
+double threshold_scale(tsvd_ctx* c, const Problem& p) {
+  return c->opts.tnn_scale == TSVD_SCALE_SUM ? (double)p.nslices : 1.0;
+}
+
+tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
+  if (o.precision != TSVD_PRECISION_FP32)
+    return fail(c, TSVD_EUNSUPPORTED, "precision %d is not implemented (FP32 only)", o.precision);
+  if (o.sparse_mode != TSVD_SPARSE_ENTRY && o.sparse_mode != TSVD_SPARSE_TUBE)
+    return fail(c, TSVD_EINVAL, "bad sparse_mode %d", o.sparse_mode);
+  if (o.tnn_scale != TSVD_SCALE_AVG && o.tnn_scale != TSVD_SCALE_SUM)
+    return fail(c, TSVD_EINVAL, "bad tnn_scale %d", o.tnn_scale);
+  if (!(o.rho0 > 0) || !std::isfinite(o.rho0) || !(o.mu >= 1) || !std::isfinite(o.mu) ||
+      !(o.rho_max >= o.rho0))
+    return fail(c, TSVD_EINVAL, "bad penalty schedule (rho0 > 0, mu >= 1, rho_max >= rho0)");
+  if (o.max_sweeps < 1) return fail(c, TSVD_EINVAL, "max_sweeps must be >= 1");
+  if (!(o.jacobi_tol > 0) || !std::isfinite(o.jacobi_tol))
+    return fail(c, TSVD_EINVAL, "jacobi_tol must be positive");
+  return TSVD_OK;
+}
+
+// Fill host-side result summaries from the per-slice stats of the last t-SVT.
+tsvd_status read_slice_stats(tsvd_ctx* c, const Problem& p, const Workspace& w, int32_t* multirank,
+                             double* tnn, int* rank_max, bool* all_converged) {
+  const TubeGeom& g = p.g;
+  c->stat_host.resize((size_t)g.nstore);
+  TSVD_CUDA(c, cudaMemcpyAsync(c->stat_host.data(), w.stat, (size_t)g.nstore * sizeof(SliceStat),
+                               cudaMemcpyDeviceToHost, c->stream));
+  TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+  double t = 0;
+  int rmax = 0;
+  bool conv = true;
+  for (int kh = 0; kh < g.hh; ++kh)
+    for (int kf = 0; kf < g.nf; ++kf) {
+      if (!slice_is_distinct(g, kf, kh)) continue;
+      const SliceStat& st = c->stat_host[(size_t)(kf + g.nf * kh)];
+      t += slice_weight(g, kf, kh) * st.nuc;
+      if (st.rank > rmax) rmax = st.rank;
+      if (!st.converged) conv = false;
+    }
+  if (multirank) {
+    for (int kfull = 0; kfull < g.nh; ++kfull)
+      for (int kf = 0; kf < g.nf; ++kf)
+        multirank[kf + g.nf * kfull] = c->stat_host[(size_t)stored_slice_of(g, kf, kfull)].rank;
+  }
+  if (tnn) *tnn = t;
+  if (rank_max) *rank_max = rmax;
+  if (all_converged) *all_converged = conv;
+  return TSVD_OK;
+}
+
+tsvd_status launch(tsvd_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaErrorInvalidValue)
+    return fail(c, TSVD_EUNSUPPORTED, "%s: shape not supported by the kernel", what);
+  if (e != cudaSuccess) return fail(c, TSVD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  ++c->launches;
+  return TSVD_OK;
+}
+
+#define TSVD_TRY(expr)                 \
+  do {                                 \
+    tsvd_status s_ = (expr);           \
+    if (s_ != TSVD_OK) return s_;      \
+  } while (0)
+
+void begin_call(tsvd_ctx* c) {
+  c->err.clear();
+  c->launches = 0;
+  c->slice_launches = 0;
+  c->events_used = 0;
+}
+
+// Records one event of a timed pair (opts.timing); kind 0 = slice SVT, 1 = tube pass.
+tsvd_status record_event(tsvd_ctx* c, int kind) {
+  if (!c->opts.timing) return TSVD_OK;
+  if (c->events_used == c->events.size()) {
+    cudaEvent_t ev;
+    TSVD_CUDA(c, cudaEventCreate(&ev));
+    c->events.push_back(ev);
+    c->event_kind.push_back(kind);
+  }
+  c->event_kind[c->events_used] = kind;
+  TSVD_CUDA(c, cudaEventRecord(c->events[c->events_used++], c->stream));
+  return TSVD_OK;
+}
+
+tsvd_status run_tube(tsvd_ctx* c, const TubeArgs& a, const char* what) {
+  TSVD_TRY(record_event(c, 1));
+  TSVD_TRY(launch(c, launch_tube_pass(a, c->stream), what));
+  return record_event(c, 1);
+}
+
+tsvd_status run_slice(tsvd_ctx* c, const SliceArgs& a) {
+  TSVD_TRY(record_event(c, 0));
+  TSVD_TRY(launch(c, launch_jacobi_svt(a, c->stream), "slice SVT"));
+  ++c->slice_launches;
+  return record_event(c, 0);
+}
+
+// Sum of the timed pairs per kind (waits for the stream).
+tsvd_status timed_totals(tsvd_ctx* c, double* slice_ms, double* tube_ms) {
+  *slice_ms = *tube_ms = 0.0;
+  if (!c->opts.timing || c->events_used == 0) return TSVD_OK;
+  TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i + 1 < c->events_used; i += 2) {
+    float ms = 0.f;
+    TSVD_CUDA(c, cudaEventElapsedTime(&ms, c->events[i], c->events[i + 1]));
+    if (c->event_kind[i] == 0) *slice_ms += ms;
+    else *tube_ms += ms;
+  }
+  return TSVD_OK;
+}
+
+tsvd_status fill_stats(tsvd_ctx* c, const Problem& p, const Workspace& w, int iters, double rho,
+                       tsvd_stats* stats) {
+  if (!stats) return TSVD_OK;
+  std::memset(stats, 0, sizeof *stats);
+  stats->iters = iters;
+  stats->rho_final = rho;
+  stats->launches = c->launches;
+  stats->slice_launches = c->slice_launches;
+  TSVD_TRY(timed_totals(c, &stats->slice_ms, &stats->tube_ms));
+  if (iters <= 0) return TSVD_OK;
+  SweepAccum acc;
+  TSVD_CUDA(c, cudaMemcpyAsync(&acc, w.acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+  int rmax = 0;
+  double tnn = 0;
+  TSVD_TRY(read_slice_stats(c, p, w, nullptr, &tnn, &rmax, nullptr));
+  stats->max_sweeps_used = acc.max_sweeps;
+  stats->total_sweeps = (int64_t)acc.total_sweeps;
+  stats->nonconverged = (int64_t)acc.nonconverged;
+  stats->slice_svds = (int64_t)iters * w.ndistinct;
+  stats->tnn_last = tnn;
+  stats->rank_last_max = rmax;
+  return TSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tsvd_default_opts(tsvd_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->precision = TSVD_PRECISION_FP32;
+  o->sparse_mode = TSVD_SPARSE_ENTRY;
+  o->tnn_scale = TSVD_SCALE_AVG;
+  o->rho0 = 1e-2;
+  o->mu = 1.1;
+  o->rho_max = 1e10;
+  o->max_sweeps = 40;
+  o->jacobi_tol = 1e-6f;
+}
+
+tsvd_status tsvd_create(tsvd_ctx** out, int device, void* cuda_stream, const tsvd_opts* opts) {
+  if (!out) return TSVD_EINVAL;
+  *out = nullptr;
+  tsvd_ctx* c = new (std::nothrow) tsvd_ctx();
+  if (!c) return TSVD_ENOMEM;
+  if (opts) c->opts = *opts;
+  else tsvd_default_opts(&c->opts);
+  tsvd_status st = check_opts(c, c->opts);
+  if (st != TSVD_OK) {
+    delete c;
+    return st;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    delete c;
+    return TSVD_ECUDA;
+  }
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  *out = c;
+  return TSVD_OK;
+}
+
+tsvd_status tsvd_destroy(tsvd_ctx* c) {
+  if (!c) return TSVD_OK;
+  DeviceGuard dg(c->device);
+  tsvd_status st = TSVD_OK;
+  if (c->ws) {
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) st = TSVD_ECUDA;
+    cudaFree(c->ws);
+  }
+  for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
+  delete c;
+  return st;
+}
+
+const char* tsvd_last_error(const tsvd_ctx* c) {
+  if (!c) return "no context";
+  return c->err.c_str();
+}
+
+tsvd_status tsvt(tsvd_ctx* c, const float* Y, float* Z, int order, const int64_t* dims,
+                 float tau, int32_t* multirank, double* tnn) {
+  if (!c) return TSVD_EINVAL;
+  begin_call(c);
+  if (!Y || !Z) return fail(c, TSVD_EINVAL, "Y and Z must not be NULL");
+  if (!(tau >= 0.f) || !std::isfinite(tau)) return fail(c, TSVD_EINVAL, "tau must be finite and >= 0");
+  Problem p;
+  TSVD_TRY(make_problem(c, order, dims, p));
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
+  const int ky = pointer_kind(Y, c->device), kz = pointer_kind(Z, c->device);
+  if (ky < 0 || kz < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
+  WsRequest rq;
+  rq.stage_in = ky == 1;
+  rq.stage_out0 = kz == 1;
+  Workspace w;
+  TSVD_TRY(prepare_workspace(c, p, rq, w));
+  const size_t bytes = (size_t)p.N * sizeof(float);
+  const float* y = Y;
+  float* z = Z;
+  if (ky == 1) {
+    TSVD_CUDA(c, cudaMemcpyAsync(w.stage_in, Y, bytes, cudaMemcpyHostToDevice, c->stream));
+    y = w.stage_in;
+  }
+  if (kz == 1) z = w.stage_out0;
+
+  TubeArgs f = tube_args(p, w, TUBE_FWD);
+  f.in = y;
+  f.spec_out = w.spec_a;
+  TSVD_TRY(run_tube(c, f, "tube pass (forward)"));
+  SliceArgs s = slice_args(c, p, w, tau);
+  TSVD_TRY(run_slice(c, s));
+  TubeArgs inv = tube_args(p, w, TUBE_INV);
+  inv.spec_in = w.spec_b;
+  inv.out0 = z;
+  TSVD_TRY(run_tube(c, inv, "tube pass (inverse)"));
+  if (kz == 1)
+    TSVD_CUDA(c, cudaMemcpyAsync(Z, w.stage_out0, bytes, cudaMemcpyDeviceToHost, c->stream));
+  bool conv = true;
+  TSVD_TRY(read_slice_stats(c, p, w, multirank, tnn, nullptr, &conv));
+  if (!conv) return fail(c, TSVD_ENOTCONV, "a slice SVD reached max_sweeps = %d", c->opts.max_sweeps);
+  return TSVD_OK;
+}
+
+tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, int order,
+                         const int64_t* dims, int iters, float* X_out, float* Z_out,
+                         tsvd_stats* stats) {
+  if (!c) return TSVD_EINVAL;
+  begin_call(c);
+  if (!M_obs || !omega || !X_out) return fail(c, TSVD_EINVAL, "M_obs, omega and X_out must not be NULL");
+  if (iters < 0) return fail(c, TSVD_EINVAL, "iters must be >= 0");
+  Problem p;
+  TSVD_TRY(make_problem(c, order, dims, p));
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
+  const int km = pointer_kind(M_obs, c->device), ko = pointer_kind(omega, c->device);
+  const int kx = pointer_kind(X_out, c->device);
+  const int kzz = Z_out ? pointer_kind(Z_out, c->device) : 0;
+  if (km < 0 || ko < 0 || kx < 0 || kzz < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
+  WsRequest rq;
+  rq.state = rq.yn = true;
+  rq.stage_in = km == 1;
+  rq.stage_om = ko == 1;
+  rq.stage_out0 = kx == 1;
+  rq.stage_out1 = Z_out && kzz == 1;
+  Workspace w;
+  TSVD_TRY(prepare_workspace(c, p, rq, w));
+  const size_t bytes = (size_t)p.N * sizeof(float);
+  const float* m = M_obs;
+  const uint8_t* om = omega;
+  if (km == 1) {
+    TSVD_CUDA(c, cudaMemcpyAsync(w.stage_in, M_obs, bytes, cudaMemcpyHostToDevice, c->stream));
+    m = w.stage_in;
+  }
+  if (ko == 1) {
+    TSVD_CUDA(c, cudaMemcpyAsync(w.stage_om, omega, (size_t)p.N, cudaMemcpyHostToDevice, c->stream));
+    om = w.stage_om;
+  }
+  float* x = kx == 1 ? w.stage_out0 : X_out;
+  float* z = Z_out ? (kzz == 1 ? w.stage_out1 : Z_out) : nullptr;
+
+  TSVD_TRY(launch(c, launch_encode_observed(m, om, w.yn, p.N, w.bad, c->stream), "encode observed"));
+  int bad = 0;
+  TSVD_CUDA(c, cudaMemcpyAsync(&bad, w.bad, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+  TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (bad) return fail(c, TSVD_EINVAL, "%d observed entries are not finite", bad);
+
+  const double scale = threshold_scale(c, p);
+  double rho = c->opts.rho0;
+  if (iters == 0) {
+    TSVD_TRY(launch(c, launch_project_observed(m, om, x, p.N, c->stream), "project"));
+    if (z) TSVD_CUDA(c, cudaMemsetAsync(z, 0, bytes, c->stream));
+  } else {
+    // iteration 0: X = P_Omega(M), Q = 0, V = X + Q
+    TubeArgs t0 = tube_args(p, w, TUBE_COMPLETE);
+    t0.in = w.yn;
+    t0.state = w.state;
+    t0.spec_out = w.spec_a;
+    t0.first = 1;
+    t0.write_out = iters == 1;
+    t0.out0 = x;
+    TSVD_TRY(run_tube(c, t0, "completion pass"));
+    for (int k = 0; k < iters; ++k) {
+      const float tau = (float)(scale / rho);
+      SliceArgs s = slice_args(c, p, w, tau);
+      TSVD_TRY(run_slice(c, s));
+      const double rho_next = std::fmin(c->opts.mu * rho, c->opts.rho_max);
+      if (k + 1 < iters) {
+        TubeArgs t = tube_args(p, w, TUBE_COMPLETE);
+        t.in = w.yn;
+        t.state = w.state;
+        t.spec_in = w.spec_b;
+        t.spec_out = w.spec_a;
+        t.ratio = (float)(rho / rho_next);
+        t.write_out = (k + 2 == iters);
+        t.out0 = x;
+        TSVD_TRY(run_tube(c, t, "completion pass"));
+      }
+      rho = rho_next;
+    }
+    if (z) {
+      TubeArgs inv = tube_args(p, w, TUBE_INV);
+      inv.spec_in = w.spec_b;
+      inv.out0 = z;
+      TSVD_TRY(run_tube(c, inv, "tube pass (inverse)"));
+    }
+  }
+  if (kx == 1) TSVD_CUDA(c, cudaMemcpyAsync(X_out, x, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (z && kzz == 1) TSVD_CUDA(c, cudaMemcpyAsync(Z_out, z, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (kx == 1 || (z && kzz == 1)) TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+  TSVD_TRY(fill_stats(c, p, w, iters, rho, stats));
+  TSVD_CUDA(c, cudaGetLastError());
+  return TSVD_OK;
+}
+
+tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, float lambda,
+                  int iters, float* L_out, float* S_out, tsvd_stats* stats) {
+  if (!c) return TSVD_EINVAL;
+  begin_call(c);
+  if (!M || !L_out || !S_out) return fail(c, TSVD_EINVAL, "M, L_out and S_out must not be NULL");
+  if (iters < 0) return fail(c, TSVD_EINVAL, "iters must be >= 0");
+  if (!(lambda > 0.f) || !std::isfinite(lambda)) return fail(c, TSVD_EINVAL, "lambda must be finite and > 0");
+  Problem p;
+  TSVD_TRY(make_problem(c, order, dims, p));
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
+  const int km = pointer_kind(M, c->device), kl = pointer_kind(L_out, c->device);
+  const int ks = pointer_kind(S_out, c->device);
+  if (km < 0 || kl < 0 || ks < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
+  WsRequest rq;
+  rq.state = true;
+  rq.stage_in = km == 1;
+  rq.stage_out0 = kl == 1;
+  rq.stage_out1 = ks == 1;
+  Workspace w;
+  TSVD_TRY(prepare_workspace(c, p, rq, w));
+  const size_t bytes = (size_t)p.N * sizeof(float);
+  const float* m = M;
+  if (km == 1) {
+    TSVD_CUDA(c, cudaMemcpyAsync(w.stage_in, M, bytes, cudaMemcpyHostToDevice, c->stream));
+    m = w.stage_in;
+  }
+  float* l = kl == 1 ? w.stage_out0 : L_out;
+  float* sp = ks == 1 ? w.stage_out1 : S_out;
+  TSVD_TRY(launch(c, launch_count_nonfinite(m, p.N, w.bad, c->stream), "check input"));
+  int bad = 0;
+  TSVD_CUDA(c, cudaMemcpyAsync(&bad, w.bad, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+  TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (bad) return fail(c, TSVD_EINVAL, "%d entries of M are not finite", bad);
+
+  const double scale = threshold_scale(c, p);
+  double rho = c->opts.rho0;
+  if (iters == 0) {
+    TSVD_CUDA(c, cudaMemsetAsync(l, 0, bytes, c->stream));
+    TSVD_CUDA(c, cudaMemsetAsync(sp, 0, bytes, c->stream));
+  } else {
+    // iteration 0: S = W = 0, so the t-SVT input is M itself
+    TubeArgs t0 = tube_args(p, w, TUBE_FWD);
+    t0.in = m;
+    t0.spec_out = w.spec_a;
+    TSVD_TRY(run_tube(c, t0, "tube pass (forward)"));
+    for (int k = 0; k < iters; ++k) {
+      const float tau = (float)(scale / rho);
+      SliceArgs s = slice_args(c, p, w, tau);
+      TSVD_TRY(run_slice(c, s));
+      const double rho_next = std::fmin(c->opts.mu * rho, c->opts.rho_max);
+      TubeArgs t = tube_args(p, w, TUBE_RPCA);
+      t.in = m;
+      t.state = w.state;
+      t.spec_in = w.spec_b;
+      t.spec_out = w.spec_a;
+      t.ratio = (float)(rho / rho_next);
+      t.kappa = (float)((double)lambda / rho);
+      t.first = k == 0;
+      t.last = k + 1 == iters;
+      t.out0 = l;
+      t.out1 = sp;
+      t.tube_sparse = c->opts.sparse_mode == TSVD_SPARSE_TUBE;
+      TSVD_TRY(run_tube(c, t, "RPCA pass"));
+      rho = rho_next;
+    }
+  }
+  if (kl == 1) TSVD_CUDA(c, cudaMemcpyAsync(L_out, l, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (ks == 1) TSVD_CUDA(c, cudaMemcpyAsync(S_out, sp, bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (kl == 1 || ks == 1) TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+  TSVD_TRY(fill_stats(c, p, w, iters, rho, stats));
+  TSVD_CUDA(c, cudaGetLastError());
+  return TSVD_OK;
+}
+
+}  // extern "C"

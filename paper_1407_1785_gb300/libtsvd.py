@@ -1,0 +1,201 @@
+"""Thin ctypes binding of libtsvd (include/tsvd.h).
+
+Only argument marshalling lives here: every step of the t-SVT and of the ADMM solvers runs
+in the CUDA kernels of ``libtsvd.so``.  There is no CPU fallback; if the shared library is
+missing or fails to load, importing this module raises.
+
+Tensors are passed as 1-D contiguous buffers in MATLAB column-major order (see
+``synth.to_colmajor``): CUDA tensors (torch) are used in place on the context's stream,
+host tensors (numpy arrays or CPU torch tensors, pinned or not) are staged by the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+TSVD_OK, TSVD_EINVAL, TSVD_ENOMEM, TSVD_ECUDA, TSVD_ENOTCONV = 0, 1, 2, 3, 4
+TSVD_ETIMEOUT, TSVD_EUNSUPPORTED = 5, 6
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT",
+                6: "EUNSUPPORTED"}
+PRECISION_FP32, PRECISION_TF32, PRECISION_BF16, PRECISION_3XTF32 = 0, 1, 2, 3
+SPARSE_ENTRY, SPARSE_TUBE = 0, 1
+SCALE_AVG, SCALE_SUM = 0, 1
+
+# Every symbol include/tsvd.h declares.
+EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_last_error",
+                    "tsvt", "tnn_complete", "trpca")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("sparse_mode", ctypes.c_int),
+                ("tnn_scale", ctypes.c_int), ("rho0", ctypes.c_double),
+                ("mu", ctypes.c_double), ("rho_max", ctypes.c_double),
+                ("max_sweeps", ctypes.c_int), ("jacobi_tol", ctypes.c_float),
+                ("timing", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("max_sweeps_used", ctypes.c_int),
+                ("total_sweeps", ctypes.c_int64), ("nonconverged", ctypes.c_int64),
+                ("slice_svds", ctypes.c_int64), ("rho_final", ctypes.c_double),
+                ("tnn_last", ctypes.c_double), ("rank_last_max", ctypes.c_int),
+                ("launches", ctypes.c_int64), ("slice_launches", ctypes.c_int64),
+                ("slice_ms", ctypes.c_double), ("tube_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class TsvdError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn} failed: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libtsvd.so (building it first if it is missing and nvcc is available)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB_PATH):
+        if not build_if_missing:
+            raise ImportError(f"libtsvd.so not found at {_build.LIB_PATH}")
+        _build.build()
+    L = ctypes.CDLL(_build.LIB_PATH)
+    P = ctypes.c_void_p
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.tsvd_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.tsvd_default_opts.restype = None
+    L.tsvd_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P, ctypes.POINTER(Opts)]
+    L.tsvd_create.restype = ctypes.c_int
+    L.tsvd_destroy.argtypes = [P]
+    L.tsvd_destroy.restype = ctypes.c_int
+    L.tsvd_last_error.argtypes = [P]
+    L.tsvd_last_error.restype = ctypes.c_char_p
+    L.tsvt.argtypes = [P, P, P, ctypes.c_int, i64p, ctypes.c_float, P, P]
+    L.tsvt.restype = ctypes.c_int
+    L.tnn_complete.argtypes = [P, P, P, ctypes.c_int, i64p, ctypes.c_int, P, P,
+                               ctypes.POINTER(Stats)]
+    L.tnn_complete.restype = ctypes.c_int
+    L.trpca.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_float, ctypes.c_int, P, P,
+                        ctypes.POINTER(Stats)]
+    L.trpca.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    load().tsvd_default_opts(ctypes.byref(o))
+    return o
+
+
+def _ptr(x) -> Optional[int]:
+    """Raw address of a tensor / array buffer (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):          # torch.Tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _dims(dims: Sequence[int]):
+    return (ctypes.c_int64 * len(dims))(*[int(d) for d in dims])
+
+
+class Context:
+    """A libtsvd context bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None, **opts):
+        L = load()
+        o = default_opts()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        h = ctypes.c_void_p()
+        st = L.tsvd_create(ctypes.byref(h), int(device), ctypes.c_void_p(stream or 0),
+                           ctypes.byref(o))
+        if st != TSVD_OK:
+            raise TsvdError("tsvd_create", st, "cannot create context")
+        self._h = h
+        self._L = L
+        self.opts = o
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.tsvd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def last_error(self) -> str:
+        return self._L.tsvd_last_error(self._h).decode()
+
+    def _check(self, fn: str, st: int, allow=(TSVD_OK,)) -> int:
+        if st not in allow:
+            raise TsvdError(fn, st, self.last_error())
+        return st
+
+    def tsvt(self, Y, Z, dims: Sequence[int], tau: float, multirank=None, with_tnn=False,
+             allow_notconv: bool = False):
+        """t-SVT of Y into Z.  Returns (status, tnn or None)."""
+        tnn = ctypes.c_double(0.0)
+        st = self._L.tsvt(self._h, _ptr(Y), _ptr(Z), len(dims), _dims(dims), float(tau),
+                          _ptr(multirank), ctypes.byref(tnn) if with_tnn else None)
+        allow = (TSVD_OK, TSVD_ENOTCONV) if allow_notconv else (TSVD_OK,)
+        self._check("tsvt", st, allow)
+        return st, (tnn.value if with_tnn else None)
+
+    def tnn_complete(self, M_obs, omega, dims: Sequence[int], iters: int, X_out, Z_out=None,
+                     stats: bool = False):
+        s = Stats()
+        st = self._L.tnn_complete(self._h, _ptr(M_obs), _ptr(omega), len(dims), _dims(dims),
+                                  int(iters), _ptr(X_out), _ptr(Z_out),
+                                  ctypes.byref(s) if stats else None)
+        self._check("tnn_complete", st)
+        return s.as_dict() if stats else None
+
+    def trpca(self, M, dims: Sequence[int], lam: float, iters: int, L_out, S_out,
+              stats: bool = False):
+        s = Stats()
+        st = self._L.trpca(self._h, _ptr(M), len(dims), _dims(dims), float(lam), int(iters),
+                           _ptr(L_out), _ptr(S_out), ctypes.byref(s) if stats else None)
+        self._check("trpca", st)
+        return s.as_dict() if stats else None
+
+    # raw status variants (for error-path tests)
+    def raw_tnn_complete(self, M_obs, omega, order, dims, iters, X_out, Z_out=None) -> int:
+        return self._L.tnn_complete(self._h, _ptr(M_obs), _ptr(omega), int(order),
+                                    _dims(dims) if dims is not None else None, int(iters),
+                                    _ptr(X_out), _ptr(Z_out), None)

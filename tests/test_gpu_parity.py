@@ -1,0 +1,298 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Tolerances:
+  * one t-SVT call: relative Frobenius error <= 2e-5, normalised by
+    max(||Z_oracle||_F, 1e-3 ||Y||_F) (early ADMM thresholds can zero almost everything);
+  * an ADMM run: final tensor within 1e-3 relative of the oracle's, and a recovery error
+    against the ground truth within 1% (+1e-5) of the oracle's;
+  * masks and the observed entries of X: bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import colmajor, relerr, uncolmajor
+
+import oracle
+from paper_1407_1785_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TSVT_TOL = 2e-5
+ADMM_TOL = 1e-3
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dev(x, dtype=np.float32):
+    torch = _torch()
+    return torch.from_numpy(colmajor(x, dtype)).cuda()
+
+
+def host(t, shape):
+    torch = _torch()
+    torch.cuda.synchronize()
+    return uncolmajor(t.cpu().numpy(), shape)
+
+
+def gpu_tsvt(ctx, Y, tau, allow_notconv=False):
+    y = dev(Y)
+    z = _torch().empty_like(y)
+    ns = int(np.prod(Y.shape[2:]))
+    mr = np.zeros(ns, np.int32)
+    st, tnn = ctx.tsvt(y, z, Y.shape, tau, multirank=mr, with_tnn=True,
+                       allow_notconv=allow_notconv)
+    return host(z, Y.shape), uncolmajor(mr, Y.shape[2:]), tnn
+
+
+def slice_singular_values(Y):
+    axes = tuple(range(2, Y.ndim))
+    Yh = np.fft.fftn(np.asarray(Y, np.float64), axes=axes)
+    out = {}
+    for idx in np.ndindex(*Y.shape[2:]):
+        out[idx] = np.linalg.svd(Yh[(slice(None), slice(None)) + idx], compute_uv=False)
+    return out
+
+
+def check_tsvt(ctx, Y, tau):
+    Y32 = np.asarray(Y, np.float32)
+    Zo, rko, tnno = oracle.tsvt(Y32.astype(np.float64), tau, with_info=True)
+    Zg, rkg, tnng = gpu_tsvt(ctx, Y32, tau)
+    floor = 1e-3 * np.linalg.norm(Y32.astype(np.float64).ravel())
+    err = relerr(Zg, Zo, floor=floor)
+    assert err <= TSVT_TOL, f"t-SVT relative error {err:.3e}"
+    assert abs(tnng - tnno) <= 1e-5 * max(tnno, 1e-30)
+    # multi-rank: exact wherever no singular value sits within 1e-4 sigma_max of tau
+    sv = slice_singular_values(Y32)
+    smax = max(s.max() for s in sv.values()) if sv else 0.0
+    for idx, s in sv.items():
+        if s.size and np.min(np.abs(s - tau)) > 1e-4 * max(smax, 1e-30):
+            assert rkg[idx] == rko[idx], (idx, rkg[idx], rko[idx])
+    return err
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 16), (33, 17, 7), (17, 33, 8), (40, 24, 1),
+                                   (5, 64, 2), (1, 9, 5), (9, 1, 4), (64, 48, 13), (3, 130, 6),
+                                   (150, 20, 9)])
+def test_tsvt_parity_3d(gpu_ctx, shape):
+    Y = synth.normal(11, 0, int(np.prod(shape))).reshape(shape, order="F")
+    sv = slice_singular_values(Y.astype(np.float32))
+    allsv = np.sort(np.concatenate([s for s in sv.values()]))
+    for q in (0.0, 0.3, 0.7):
+        tau = float(np.quantile(allsv, q)) * (0.999 if q else 0.0)
+        check_tsvt(gpu_ctx, Y, tau)
+    # above the largest singular value everything is thresholded away
+    Zg, rk, _ = gpu_tsvt(gpu_ctx, Y.astype(np.float32), float(allsv[-1]) * 1.01)
+    assert np.abs(Zg).max() == 0.0 and rk.max() == 0
+
+
+@pytest.mark.parametrize("shape", [(9, 7, 3, 6), (16, 12, 3, 5), (8, 8, 4, 4), (6, 10, 5, 1),
+                                   (7, 5, 1, 6)])
+def test_tsvt_parity_4d(gpu_ctx, shape):
+    Y = synth.normal(12, 0, int(np.prod(shape))).reshape(shape, order="F")
+    sv = slice_singular_values(Y.astype(np.float32))
+    allsv = np.sort(np.concatenate([s for s in sv.values()]))
+    for q in (0.0, 0.5):
+        tau = float(np.quantile(allsv, q)) * (0.999 if q else 0.0)
+        check_tsvt(gpu_ctx, Y, tau)
+
+
+def test_tsvt_lowrank_input(gpu_ctx):
+    X = synth.lowrank_tensor(48, 40, 12, 3, seed=3)
+    for tau in (0.0, 1.0, 30.0):
+        check_tsvt(gpu_ctx, X, tau)
+
+
+def test_tsvt_video_full_size(gpu_ctx):
+    """The 144 x 176 x 100 video at the sizes the benchmark runs, one t-SVT per threshold."""
+    X, om = synth.workload_video_completion(seed=1)
+    Y = (X * om).astype(np.float32)
+    for tau in (100.0, 1.0, 1e-3):
+        check_tsvt(gpu_ctx, Y, tau)
+
+
+def test_tsvt_deterministic_and_host_path(gpu_ctx):
+    Y = synth.normal(5, 0, 30 * 20 * 9).reshape((30, 20, 9), order="F").astype(np.float32)
+    Z1, _, _ = gpu_tsvt(gpu_ctx, Y, 0.8)
+    Z2, _, _ = gpu_tsvt(gpu_ctx, Y, 0.8)
+    assert np.array_equal(Z1, Z2)
+    yh = colmajor(Y)
+    zh = np.zeros_like(yh)
+    gpu_ctx.tsvt(yh, zh, Y.shape, 0.8)                    # host buffers, staged by the library
+    assert np.array_equal(uncolmajor(zh, Y.shape), Z1)
+
+
+# ------------------------------------------------------------------------ completion (Sec. 4)
+
+def gpu_complete(ctx, Mobs, om, iters, stats=False):
+    torch = _torch()
+    m = dev(Mobs)
+    o = torch.from_numpy(colmajor(om, np.uint8)).cuda()
+    x = torch.empty_like(m)
+    z = torch.empty_like(m)
+    st = ctx.tnn_complete(m, o, Mobs.shape, iters, x, z, stats=stats)
+    return host(x, Mobs.shape), host(z, Mobs.shape), st
+
+
+def test_completion_lowrank_parity(gpu_ctx):
+    X, om = synth.workload_lowrank_completion(seed=1)
+    Mobs = (X * om).astype(np.float32)
+    Xo, Zo = oracle.tnn_complete(Mobs.astype(np.float64), om, 100)
+    Xg, Zg, st = gpu_complete(gpu_ctx, Mobs, om, 100, stats=True)
+    assert np.array_equal(Xg[om == 1], Mobs[om == 1])              # observed entries exact
+    assert relerr(Xg, Xo) <= ADMM_TOL
+    assert relerr(Zg, Zo) <= ADMM_TOL
+    e_g = relerr(Xg, X)
+    e_o = relerr(Xo, X)
+    assert abs(e_g - e_o) <= 0.01 * e_o + 1e-5, (e_g, e_o)
+    assert st["iters"] == 100 and st["nonconverged"] == 0
+    assert st["slice_svds"] == 100 * 9
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2, 5])
+def test_completion_short_runs_match_oracle(gpu_ctx, iters):
+    X, om = synth.workload_lowrank_completion(seed=4, n1=21, n2=35, n3=9, rank=4, p=0.4)
+    Mobs = (X * om).astype(np.float32)
+    Xo, Zo = oracle.tnn_complete(Mobs.astype(np.float64), om, iters)
+    Xg, Zg, _ = gpu_complete(gpu_ctx, Mobs, om, iters)
+    assert relerr(Xg, Xo, floor=1e-6) <= ADMM_TOL
+    assert relerr(Zg, Zo, floor=1e-3 * np.linalg.norm(Mobs)) <= ADMM_TOL
+    assert np.array_equal(Xg[om == 1], Mobs[om == 1])
+
+
+def test_completion_4d_parity(gpu_ctx):
+    shape = (20, 18, 3, 8)
+    X = np.empty(shape)
+    for c in range(3):
+        X[:, :, c, :] = synth.translating_texture(20, 18, 8, seed=2, channel=c)
+    om = synth.sampling_mask(shape, 0.3, seed=2)
+    Mobs = (X * om).astype(np.float32)
+    Xo, Zo = oracle.tnn_complete(Mobs.astype(np.float64), om, 40)
+    Xg, Zg, _ = gpu_complete(gpu_ctx, Mobs, om, 40)
+    assert relerr(Xg, Xo) <= ADMM_TOL
+    assert np.array_equal(Xg[om == 1], Mobs[om == 1])
+    e_g, e_o = relerr(Xg, X), relerr(Xo, X)
+    assert abs(e_g - e_o) <= 0.01 * e_o + 1e-5
+
+
+def test_completion_video_full_size_short(gpu_ctx):
+    """Full benchmark size, first iterations compared entry by entry with the oracle."""
+    X, om = synth.workload_video_completion(seed=1)
+    Mobs = (X * om).astype(np.float32)
+    Xo, Zo = oracle.tnn_complete(Mobs.astype(np.float64), om, 3)
+    Xg, Zg, _ = gpu_complete(gpu_ctx, Mobs, om, 3)
+    assert relerr(Xg, Xo) <= ADMM_TOL
+    assert relerr(Zg, Zo, floor=1e-3 * np.linalg.norm(Mobs)) <= ADMM_TOL
+
+
+def test_completion_video_full_run_properties(gpu_ctx):
+    """The full 150-iteration benchmark run: properties that hold at any size."""
+    X, om = synth.workload_video_completion(seed=1)
+    Mobs = (X * om).astype(np.float32)
+    Xg, Zg, st = gpu_complete(gpu_ctx, Mobs, om, 150, stats=True)
+    assert np.all(np.isfinite(Xg))
+    assert np.array_equal(Xg[om == 1], Mobs[om == 1])
+    assert st["nonconverged"] == 0
+    # the penalty grew as min(1.1^k rho0, rho_max)
+    assert st["rho_final"] == pytest.approx(1e-2 * 1.1 ** 150, rel=1e-9)
+    # completion beats the zero fill by a wide margin on the unobserved entries
+    un = om == 0
+    e_fill = np.linalg.norm(X[un])
+    e_rec = np.linalg.norm((Xg - X)[un])
+    assert e_rec < 0.2 * e_fill
+    # X and Z agree at convergence (primal residual)
+    assert relerr(Xg, Zg) < 0.05
+
+
+# ------------------------------------------------------------------------ RPCA (Sec. 5)
+
+def gpu_rpca(ctx, M, lam, iters, stats=False):
+    torch = _torch()
+    m = dev(M)
+    l = torch.empty_like(m)
+    s = torch.empty_like(m)
+    st = ctx.trpca(m, M.shape, lam, iters, l, s, stats=stats)
+    return host(l, M.shape), host(s, M.shape), st
+
+
+@pytest.mark.parametrize("iters", [0, 1, 3, 60])
+def test_rpca_entry_parity(gpu_ctx, iters):
+    L0 = synth.lowrank_tensor(24, 20, 8, 2, seed=9)
+    S0, _ = synth.sparse_corruption(L0.shape, 0.1, seed=9)
+    M = (L0 + S0).astype(np.float32)
+    lam = 1.0 / math.sqrt(24 * 8)
+    Lo, So = oracle.trpca(M.astype(np.float64), lam, iters)
+    Lg, Sg, _ = gpu_rpca(gpu_ctx, M, lam, iters)
+    assert relerr(Lg, Lo, floor=1e-6) <= ADMM_TOL
+    assert relerr(Sg, So, floor=1e-3 * np.linalg.norm(M)) <= ADMM_TOL
+    mism = np.count_nonzero((Sg != 0) != (So != 0))
+    assert mism <= 1e-3 * M.size
+
+
+@pytest.mark.parametrize("iters", [1, 40])
+def test_rpca_tube_mode_parity(iters):
+    from paper_1407_1785_gb300 import libtsvd
+    torch = _torch()
+    ctx = libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
+                          sparse_mode=libtsvd.SPARSE_TUBE)
+    try:
+        L0 = synth.lowrank_tensor(22, 18, 10, 2, seed=10)
+        S0, _ = synth.tube_corruption(L0.shape, 0.08, seed=10, block=5, std=3.0)
+        M = (L0 + S0).astype(np.float32)
+        lam = 1.0 / math.sqrt(22)
+        Lo, So = oracle.trpca(M.astype(np.float64), lam, iters, sparse_mode=oracle.SPARSE_TUBE)
+        Lg, Sg, _ = gpu_rpca(ctx, M, lam, iters)
+        assert relerr(Lg, Lo) <= ADMM_TOL
+        assert relerr(Sg, So, floor=1e-3 * np.linalg.norm(M)) <= ADMM_TOL
+        tg = np.linalg.norm(Sg, axis=2) > 0
+        to = np.linalg.norm(So, axis=2) > 0
+        assert np.count_nonzero(tg != to) <= 2
+    finally:
+        ctx.close()
+
+
+def test_rpca_4d_parity(gpu_ctx):
+    shape = (12, 10, 3, 6)
+    L0 = synth.normal(13, 0, int(np.prod(shape))).reshape(shape, order="F")
+    L0 = oracle.tsvt(L0, 4.0)                       # a low multi-rank 4-way tensor
+    S0, _ = synth.sparse_corruption(shape, 0.1, seed=13)
+    M = (L0 + S0).astype(np.float32)
+    lam = 1.0 / math.sqrt(12 * 18)
+    Lo, So = oracle.trpca(M.astype(np.float64), lam, 30)
+    Lg, Sg, _ = gpu_rpca(gpu_ctx, M, lam, 30)
+    assert relerr(Lg, Lo) <= ADMM_TOL
+
+
+# ------------------------------------------------------------------------ error paths
+
+def test_invalid_arguments(gpu_ctx):
+    from paper_1407_1785_gb300 import libtsvd
+    torch = _torch()
+    m = torch.zeros(4 * 4 * 4, device="cuda")
+    om = torch.ones(4 * 4 * 4, dtype=torch.uint8, device="cuda")
+    x = torch.empty_like(m)
+    assert gpu_ctx.raw_tnn_complete(m, om, 5, (4, 4, 4, 1, 1), 3, x) == libtsvd.TSVD_EINVAL
+    assert gpu_ctx.raw_tnn_complete(m, om, 3, (4, 0, 4), 3, x) == libtsvd.TSVD_EINVAL
+    assert gpu_ctx.raw_tnn_complete(m, om, 3, (4, 4, 4), -1, x) == libtsvd.TSVD_EINVAL
+    m[5] = float("nan")
+    assert gpu_ctx.raw_tnn_complete(m, om, 3, (4, 4, 4), 3, x) == libtsvd.TSVD_EINVAL
+    assert "not finite" in gpu_ctx.last_error()
+    om[5] = 0                                   # a NaN at an unobserved entry is ignored
+    assert gpu_ctx.raw_tnn_complete(m, om, 3, (4, 4, 4), 3, x) == libtsvd.TSVD_OK
+    with pytest.raises(libtsvd.TsvdError):
+        gpu_ctx.tsvt(m, x, (4, 4, 4), -1.0)
+
+
+def test_unsupported_slice_is_reported(gpu_ctx):
+    from paper_1407_1785_gb300 import libtsvd
+    torch = _torch()
+    shape = (600, 700, 2)
+    m = torch.zeros(int(np.prod(shape)), device="cuda")
+    z = torch.empty_like(m)
+    with pytest.raises(libtsvd.TsvdError) as ei:
+        gpu_ctx.tsvt(m, z, shape, 1.0)
+    assert ei.value.status == libtsvd.TSVD_EUNSUPPORTED
