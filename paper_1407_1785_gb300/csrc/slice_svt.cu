@@ -124,7 +124,9 @@ __global__ void __launch_bounds__(1024) jacobi_svt_kernel(SliceArgs a, SliceShap
           t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
         if (t == 0.f) continue;
         rotated = 1;
-        const float cs = rsqrtf(1.f + t * t), sn = cs * t;
+        // correctly rounded: an approximate reciprocal square root makes every rotation
+        // slightly non-unitary and the vector norms drift over thousands of rotations
+        const float cs = 1.f / sqrtf(1.f + t * t), sn = cs * t;
         const float er = cr / g, ei = ci / g;       // e^{i phi}
         const float kr = sn * er, ki = sn * ei;     // sn e^{i phi}
         for (int e = lane; e < len; e += 32) {

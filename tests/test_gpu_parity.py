@@ -65,7 +65,9 @@ def check_tsvt(ctx, Y, tau):
     floor = 1e-3 * np.linalg.norm(Y32.astype(np.float64).ravel())
     err = relerr(Zg, Zo, floor=floor)
     assert err <= TSVT_TOL, f"t-SVT relative error {err:.3e}"
-    assert abs(tnng - tnno) <= 1e-5 * max(tnno, 1e-30)
+    # the TNN sums every singular value, including thousands at the FP32 floor, each with an
+    # absolute error of order eps_32 * ||Yhat_k||_2, so the sum is compared at 1e-4
+    assert abs(tnng - tnno) <= 1e-4 * max(tnno, 1e-30)
     # multi-rank: exact wherever no singular value sits within 1e-4 sigma_max of tau
     sv = slice_singular_values(Y32)
     smax = max(s.max() for s in sv.values()) if sv else 0.0
@@ -73,6 +75,17 @@ def check_tsvt(ctx, Y, tau):
         if s.size and np.min(np.abs(s - tau)) > 1e-4 * max(smax, 1e-30):
             assert rkg[idx] == rko[idx], (idx, rkg[idx], rko[idx])
     return err
+
+
+def gap_threshold(allsv, q):
+    """A threshold at quantile q of the singular values, placed in the middle of the gap
+    between two consecutive distinct values (a threshold within rounding distance of a
+    singular value makes the result ill-conditioned in any precision)."""
+    if q == 0.0:
+        return 0.0
+    u = np.unique(allsv)
+    i = min(max(int(q * len(u)), 1), len(u) - 1)
+    return float(0.5 * (u[i - 1] + u[i]))
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 16), (33, 17, 7), (17, 33, 8), (40, 24, 1),
@@ -83,8 +96,7 @@ def test_tsvt_parity_3d(gpu_ctx, shape):
     sv = slice_singular_values(Y.astype(np.float32))
     allsv = np.sort(np.concatenate([s for s in sv.values()]))
     for q in (0.0, 0.3, 0.7):
-        tau = float(np.quantile(allsv, q)) * (0.999 if q else 0.0)
-        check_tsvt(gpu_ctx, Y, tau)
+        check_tsvt(gpu_ctx, Y, gap_threshold(allsv, q))
     # above the largest singular value everything is thresholded away
     Zg, rk, _ = gpu_tsvt(gpu_ctx, Y.astype(np.float32), float(allsv[-1]) * 1.01)
     assert np.abs(Zg).max() == 0.0 and rk.max() == 0
@@ -97,8 +109,7 @@ def test_tsvt_parity_4d(gpu_ctx, shape):
     sv = slice_singular_values(Y.astype(np.float32))
     allsv = np.sort(np.concatenate([s for s in sv.values()]))
     for q in (0.0, 0.5):
-        tau = float(np.quantile(allsv, q)) * (0.999 if q else 0.0)
-        check_tsvt(gpu_ctx, Y, tau)
+        check_tsvt(gpu_ctx, Y, gap_threshold(allsv, q))
 
 
 def test_tsvt_lowrank_input(gpu_ctx):
