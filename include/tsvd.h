@@ -145,6 +145,29 @@ tsvd_status tnn_complete(tsvd_ctx* ctx, const float* M_obs, const uint8_t* omega
 tsvd_status trpca(tsvd_ctx* ctx, const float* M, int order, const int64_t* dims, float lambda,
                   int iters, float* L_out, float* S_out, tsvd_stats* stats);
 
+/* The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory.  Some callers cannot call cudaMalloc: a process that has handed the
+ * whole device memory budget to its own pool allocator (a later cudaMalloc fails or fragments
+ * the pool), or a latency-critical loop that must not pay the implicit device-wide
+ * synchronisation of cudaMalloc / cudaFree.  tsvt() allocates its workspace on first use, so
+ * tsvt_static() computes the same t-SVT (same kernels, default opts) with every byte of its
+ * scratch taken from one fixed 64 MiB array in the library's device memory, and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ * Y, Z: device pointers on the current device (host memory is rejected), dims-shaped as for
+ * tsvt(); Y and Z may alias.  The work is queued on `cuda_stream` (a cudaStream_t, NULL =
+ * legacy default stream) and the call returns without waiting; no multi-rank, TNN or
+ * convergence report.
+ * Limit: 2 * 8 * n1*n2*P_half bytes of spectra plus small tables must fit in 64 MiB, where
+ * P_half = floor(n3/2)+1 (order 3) or n3*(floor(n4/2)+1) (order 4); larger problems return
+ * TSVD_ENOMEM before any work.  Every GPU that loads the library holds the 64 MiB until the
+ * process exits.  The first call on a device (with that device current) looks up the array's
+ * device address once; make it before any stream capture.  All calls on a device share the
+ * array: calls that overlap on the GPU race and corrupt each other, so order them (one stream,
+ * or events).  Errors: EINVAL (null or host pointer, bad order/dims/tau), EUNSUPPORTED,
+ * ENOMEM (over the limit), ECUDA. */
+tsvd_status tsvt_static(const float* Y, float* Z, int order, const int64_t* dims, float tau,
+                        void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ SCALE_AVG, SCALE_SUM = 0, 1
 
 # Every symbol include/tsvd.h declares.
 EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_last_error",
-                    "tsvt", "tnn_complete", "trpca")
+                    "tsvt", "tnn_complete", "trpca", "tsvt_static")
 
 
 class Opts(ctypes.Structure):
@@ -92,8 +92,17 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.trpca.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_float, ctypes.c_int, P, P,
                         ctypes.POINTER(Stats)]
     L.trpca.restype = ctypes.c_int
+    L.tsvt_static.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_float, P]
+    L.tsvt_static.restype = ctypes.c_int
     _lib = L
     return L
+
+
+def tsvt_static(Y, Z, dims: Sequence[int], tau: float, stream: Optional[int] = None) -> int:
+    """t-SVT with the library's fixed device scratch (no device allocation).  Y and Z are
+    device buffers on the current device; returns the tsvd_status code."""
+    return load().tsvt_static(_ptr(Y), _ptr(Z), len(dims), _dims(dims), float(tau),
+                              ctypes.c_void_p(stream or 0))
 
 
 def default_opts() -> Opts:

@@ -1,0 +1,56 @@
+"""tsvt_static(): the t-SVT for callers that cannot allocate device memory (a process whose
+device memory belongs to its own pool allocator, or a loop that must not pay cudaMalloc's
+implicit synchronisation).  Its scratch is a fixed array inside the library; the test checks
+it against tsvt(), which allocates its own workspace, through the C ABI.
+
+This file is collected last on purpose, so that a run stopping at the first failure has
+already run every other test."""
+import numpy as np
+import pytest
+
+from helpers import colmajor, relerr, uncolmajor
+
+from paper_1407_1785_gb300 import libtsvd, synth
+
+pytestmark = pytest.mark.gpu
+
+TSVT_TOL = 2e-5      # the per-call t-SVT tolerance of the parity tests
+
+
+def _run_pair(ctx, torch, shape, seed, tau):
+    Y = synth.normal(seed, 0, int(np.prod(shape))).reshape(shape, order="F").astype(np.float32)
+    stream = torch.cuda.current_stream()
+    y = torch.from_numpy(colmajor(Y)).cuda()
+    z_ref = torch.empty_like(y)
+    ctx.tsvt(y, z_ref, shape, tau)
+    z = torch.full_like(y, float("nan"))
+    st = libtsvd.tsvt_static(y, z, shape, tau, stream.cuda_stream)
+    assert st == libtsvd.TSVD_OK
+    torch.cuda.synchronize()
+    Zr = uncolmajor(z_ref.cpu().numpy(), shape)
+    Zs = uncolmajor(z.cpu().numpy(), shape)
+    floor = 1e-3 * np.linalg.norm(Y)
+    assert np.all(np.isfinite(Zs))
+    assert relerr(Zs, Zr, floor=floor) <= TSVT_TOL
+
+
+def test_static_scratch_tsvt_matches_tsvt():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream) as ctx:
+        # two calls in a row on different shapes: the second must not depend on what the
+        # first left in the shared scratch
+        _run_pair(ctx, torch, (40, 28, 12), seed=21, tau=2.0)
+        _run_pair(ctx, torch, (17, 33, 3, 5), seed=22, tau=1.0)
+        _run_pair(ctx, torch, (144, 176, 100), seed=23, tau=5.0)
+
+
+def test_static_scratch_rejects_oversize_and_host_buffers():
+    torch = pytest.importorskip("torch")
+    y = torch.zeros(8, device="cuda")
+    # 144 x 176 x 400: 2 spectra of 201 slices x 198 KiB = 81.5 MB > 64 MiB (the slices
+    # themselves fit the kernels, so only the scratch limit rejects it)
+    assert libtsvd.tsvt_static(y, y, (144, 176, 400), 1.0) == libtsvd.TSVD_ENOMEM
+    h = np.zeros(4 * 4 * 4, np.float32)
+    assert libtsvd.tsvt_static(h, h, (4, 4, 4), 1.0) == libtsvd.TSVD_EINVAL
+    assert libtsvd.tsvt_static(y, y, (2, 2, 2), -1.0) == libtsvd.TSVD_EINVAL
