@@ -76,6 +76,11 @@ typedef struct tsvd_opts {
   float jacobi_tol;   /* rotate a pair while |x^H y| > tol ||x|| ||y||; default 1e-6 */
   int timing;         /* 1: time every kernel launch with CUDA events on the context's stream
                          and report the totals in tsvd_stats; default 0 */
+  int ctas_per_slice; /* CTAs (one thread-block cluster) per Fourier slice SVD: 1, 2, 4 or 8;
+                         0 (default) = chosen from the slice shape and count */
+  int accumulate_v;   /* 1: also rotate V during the Jacobi sweeps and rebuild each slice as
+                         W diag((s - tau)/s) V^H instead of U diag((s - tau)/s) U^H A;
+                         default 0 */
 } tsvd_opts;
 
 /* Counters of one ADMM solve (host struct). */

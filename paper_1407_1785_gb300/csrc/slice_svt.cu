@@ -3,42 +3,79 @@
 // L-step of tensor RPCA, eq. low_rank), solved by the Lemma of Sec. 4.1:
 //     D_tau(A) = U diag((sigma_i - tau)_+) V^H.
 //
-// One CTA owns one complex n1 x n2 slice, held entirely in shared memory.  The SVD is a
-// one-sided (Hestenes) Jacobi iteration on the nv = min(n1, n2) "vectors" of the slice
-// (its columns when n1 >= n2, otherwise its rows, i.e. the columns of A^T, since
-// D_tau(A^T) = D_tau(A)^T).  A sweep visits every vector pair once in the round-robin
-// (circle) order: each of the P-1 rounds holds P/2 disjoint pairs (P = nv rounded up to
-// even), which the warps process concurrently; one warp rotates one pair, with the three
-// inner products reduced by warp shuffles.  The plane rotation of a pair diagonalises its
-// 2x2 Gram matrix [[a, c], [c*, b]]:
+// The SVD is a one-sided (Hestenes) Jacobi iteration on the nv = min(n1, n2) "vectors" of
+// the slice (its columns when n1 >= n2, otherwise its rows, i.e. the columns of A^T, since
+// D_tau(A^T) = D_tau(A)^T).  The plane rotation of a pair diagonalises its 2x2 Gram matrix
+// [[a, c], [c*, b]]:
 //     c = |c| e^{i phi},  zeta = (b - a) / (2|c|),  t = sign(zeta) / (|zeta| + sqrt(1+zeta^2)),
 //     cs = 1/sqrt(1+t^2), sn = cs t,
 //     x <- cs x - sn e^{-i phi} y,   y <- sn e^{i phi} x + cs y.
 // A pair is rotated while |c| > tol sqrt(a b); sweeps stop when a whole sweep rotates
-// nothing (or at max_sweeps).  The converged vectors are U diag(sigma); with
-// u_i = w_i / sigma_i the thresholded slice is rebuilt without V as
-//     D_tau(B) = sum_{sigma_i > tau} ((sigma_i - tau)/sigma_i) u_i (u_i^H B),
-// re-reading the original slice B from global memory (it is L2 resident) in chunks.
+// nothing (or at max_sweeps).  The converged vectors are W = B V = U diag(sigma).
+//
+// Rebuild.  Two forms:
+//   U form (default):  D_tau(B) = sum_{sigma_i > tau} ((sigma_i - tau)/sigma_i) u_i (u_i^H B),
+//            u_i = w_i / sigma_i, re-reading the original slice B from global memory (L2);
+//   V form (opt-in):   the rotations are also applied to V (stored after each vector, V = I
+//            at the start) and D_tau(B) = sum_{sigma_i > tau} ((sigma_i - tau)/sigma_i) w_i v_i^H.
+// The V form costs one more rotation of an nv-vector per pair and halves the rebuild.
+//
+// Rounding.  Each rotation is applied as x + (cs - 1) x - conj(k) y with cs - 1 computed to
+// full relative precision: in FP32, cs rounds to exactly 1 for small angles while sn = t
+// does not, so the textbook form makes every late rotation slightly norm-increasing and the
+// singular values drift upward over the thousands of rotations a vector takes.
+//
+// Work split.  A slice is owned by a thread-block cluster of C CTAs (C = 1, 2, 4, 8).  Its
+// vectors form nb = 2C blocks of bs vectors (zero vectors pad the last block); a sweep is a
+// round-robin tournament of the blocks: in block round r CTA c holds the pair of blocks of
+// slot c of the circle method.  Round 0 rotates every vector pair inside the two blocks,
+// later rounds only the bs x bs cross pairs, so each vector pair meets once per sweep.
+// Inside a CTA the pairs of a local round are disjoint and run concurrently, G lanes per
+// pair (32/G pairs per warp), with the inner products reduced by shuffles inside the group.
+// Between block rounds the CTAs trade blocks through a double-buffered global buffer (one
+// cluster barrier per exchange).  Each CTA then rebuilds the part of D_tau(B) spanned by its
+// own kept vectors; the C partial slices are summed in a fixed order (deterministic).
+//
+// Shared memory holds a CTA's 2 bs vectors in planar form: a real plane and an imaginary
+// plane, rows of pitch rowp floats (the vector's ld entries, then in the V form its ldv V
+// entries; pitches are multiples of 4, zero padded).  A lane moves 4 consecutive entries of
+// a plane with one 128-bit access and does the complex arithmetic of two entries at a time
+// with packed FP32x2 instructions (__ffma2_rn / __fmul2_rn).  A pair's vector entries stay
+// in registers between the inner products and the rotation; V entries are streamed.
 //
 // A slice whose matrix is exactly real (the self-conjugate Fourier slices) stays exactly
 // real: every inner product then has a zero imaginary part and every rotation is real.
 #include "tsvd_internal.h"
 
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
 namespace tsvd {
 namespace {
 
-constexpr int kNC = 8;            // rebuild chunk width (vectors of B per chunk)
+constexpr int kNC = 8;            // rebuild chunk width (columns of B per chunk)
 constexpr int kMinWarps = 4;
+constexpr int kMinBlock = 16;     // fewest vectors per block before a slice is split further
+constexpr int kSMs = 152;
 constexpr size_t kStaticSmemReserve = 1024;   // static __shared__ of the kernel, with margin
 
-__device__ __forceinline__ float warp_sum(float v) {
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 lo(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 f4(const float2& a, const float2& b) {
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Pair (p, q) of slot `slot` in round r of the circle method over P players.
-__device__ __forceinline__ void round_robin_pair(int r, int slot, int P, int& p, int& q) {
+// Pair (p, q) of slot `slot` in round r of the circle method over P (even) players.
+__host__ __device__ inline void round_robin_pair(int r, int slot, int P, int& p, int& q) {
   if (slot == 0) {
     p = P - 1;
     q = r;
@@ -49,108 +86,336 @@ __device__ __forceinline__ void round_robin_pair(int r, int slot, int P, int& p,
 }
 
 struct SliceShape {
-  int nv;    // number of vectors
-  int len;   // vector length
-  int ld;    // shared-memory pitch of a vector (odd, in float2)
-  int rows;  // 1: vectors are the rows of the slice
-  int nc;    // rebuild chunk width
+  int nv;     // number of vectors
+  int len;    // vector length
+  int ld;     // pitch of the vector entries in a row (floats, multiple of 4)
+  int ldv;    // V form: pitch of the V entries (multiple of 4); 0 in the U form
+  int rowp;   // row pitch = ld + ldv
+  int rows;   // 1: vectors are the rows of the slice
+  int nc;     // rebuild chunk width
+  int G;      // lanes per pair
+  int cpl;    // 4-entry chunks per lane
+  int vform;  // 1: V form rebuild
+  int C;      // CTAs per slice (cluster size)
+  int nb;     // vector blocks = 2C
+  int bs;     // vectors per block
+  size_t xbuf_floats;   // exchange buffer per slice (floats)
 };
 
 __host__ __device__ inline size_t slice_smem_bytes(const SliceShape& sh) {
-  return (size_t)sh.nv * sh.ld * sizeof(float2) + (size_t)sh.len * sh.nc * sizeof(float2) +
-         (size_t)sh.nv * sh.nc * sizeof(float2) + (size_t)sh.nv * (2 * sizeof(float) + sizeof(int));
+  const size_t nl = 2 * (size_t)sh.bs;   // vectors held by one CTA
+  return 2 * nl * sh.rowp * sizeof(float) + (size_t)sh.len * sh.nc * sizeof(float2) +
+         nl * sh.nc * sizeof(float2) + nl * (2 * sizeof(float) + sizeof(int));
 }
 
-__global__ void __launch_bounds__(1024) jacobi_svt_kernel(SliceArgs a, SliceShape sh) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nv = sh.nv, len = sh.len, ld = sh.ld, nc = sh.nc;
-  float2* W = reinterpret_cast<float2*>(smem_raw);
-  float2* Bc = W + (size_t)nv * ld;
-  float2* Cc = Bc + (size_t)len * nc;
-  float* sig = reinterpret_cast<float*>(Cc + (size_t)nv * nc);
-  float* dsc = sig + nv;
-  int* keep = reinterpret_cast<int*>(dsc + nv);
-  __shared__ int s_rank;
+// x' = x + (cs-1) x - conj(k) y ;  y' = y + (cs-1) y + k x on two entries of each plane
+// (planar re / im).  CM = cs - 1 is carried separately: cs itself rounds to 1 in FP32 for
+// small angles while sn does not, which made every late rotation slightly norm-increasing.
+__device__ __forceinline__ void rotate2(const float2 CM, const float2 KR, const float2 KI,
+                                        const float2 NKR, const float2 NKI, float2& xr,
+                                        float2& xi, float2& yr, float2& yi) {
+  const float2 nxr = __ffma2_rn(NKI, yi, __ffma2_rn(NKR, yr, __ffma2_rn(CM, xr, xr)));
+  const float2 nxi = __ffma2_rn(KI, yr, __ffma2_rn(NKR, yi, __ffma2_rn(CM, xi, xi)));
+  const float2 nyr = __ffma2_rn(NKI, xi, __ffma2_rn(KR, xr, __ffma2_rn(CM, yr, yr)));
+  const float2 nyi = __ffma2_rn(KI, xr, __ffma2_rn(KR, xi, __ffma2_rn(CM, yi, yi)));
+  xr = nxr;
+  xi = nxi;
+  yr = nyr;
+  yi = nyi;
+}
 
-  const int s = a.slices ? a.slices[blockIdx.x] : (int)blockIdx.x;
+__device__ __forceinline__ void rotate4(const float2 CS, const float2 KR, const float2 KI,
+                                        const float2 NKR, const float2 NKI, float4& xr,
+                                        float4& xi, float4& yr, float4& yi) {
+  float2 xr0 = lo(xr), xr1 = hi(xr), xi0 = lo(xi), xi1 = hi(xi);
+  float2 yr0 = lo(yr), yr1 = hi(yr), yi0 = lo(yi), yi1 = hi(yi);
+  rotate2(CS, KR, KI, NKR, NKI, xr0, xi0, yr0, yi0);
+  rotate2(CS, KR, KI, NKR, NKI, xr1, xi1, yr1, yi1);
+  xr = f4(xr0, xr1);
+  xi = f4(xi0, xi1);
+  yr = f4(yr0, yr1);
+  yi = f4(yi0, yi1);
+}
+
+// Rotate local vectors p and q if they are not yet orthogonal.  All G lanes of the group
+// call it with the same (p, q); returns whether a rotation was applied.  nchunk = vector
+// chunks (inner products and rotation), nchunkv = V chunks (rotation only) that follow.
+template <int G, int CPL>
+__device__ __forceinline__ bool jacobi_pair(float* __restrict__ Wr, float* __restrict__ Wi,
+                                            int rowp, int nchunk, int nchunkv, int p, int q,
+                                            int gl, float tol) {
+  float4* xr4 = reinterpret_cast<float4*>(Wr + (size_t)p * rowp);
+  float4* xi4 = reinterpret_cast<float4*>(Wi + (size_t)p * rowp);
+  float4* yr4 = reinterpret_cast<float4*>(Wr + (size_t)q * rowp);
+  float4* yi4 = reinterpret_cast<float4*>(Wi + (size_t)q * rowp);
+  float4 xr[CPL], xi[CPL], yr[CPL], yi[CPL];
+  float2 a0 = f2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0, r0 = a0, r1 = a0, g1 = a0, g2 = a0;
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) {
+    const int c = gl + G * u;
+    if (c < nchunk) {
+      xr[u] = xr4[c];
+      xi[u] = xi4[c];
+      yr[u] = yr4[c];
+      yi[u] = yi4[c];
+    } else {
+      xr[u] = xi[u] = yr[u] = yi[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    a0 = __ffma2_rn(lo(xr[u]), lo(xr[u]), a0);
+    a1 = __ffma2_rn(hi(xr[u]), hi(xr[u]), a1);
+    a0 = __ffma2_rn(lo(xi[u]), lo(xi[u]), a0);
+    a1 = __ffma2_rn(hi(xi[u]), hi(xi[u]), a1);
+    b0 = __ffma2_rn(lo(yr[u]), lo(yr[u]), b0);
+    b1 = __ffma2_rn(hi(yr[u]), hi(yr[u]), b1);
+    b0 = __ffma2_rn(lo(yi[u]), lo(yi[u]), b0);
+    b1 = __ffma2_rn(hi(yi[u]), hi(yi[u]), b1);
+    r0 = __ffma2_rn(lo(xr[u]), lo(yr[u]), r0);     // Re(x^H y) = xr.yr + xi.yi
+    r1 = __ffma2_rn(hi(xr[u]), hi(yr[u]), r1);
+    r0 = __ffma2_rn(lo(xi[u]), lo(yi[u]), r0);
+    r1 = __ffma2_rn(hi(xi[u]), hi(yi[u]), r1);
+    g1 = __ffma2_rn(lo(xr[u]), lo(yi[u]), g1);     // Im(x^H y) = xr.yi - xi.yr
+    g1 = __ffma2_rn(hi(xr[u]), hi(yi[u]), g1);
+    g2 = __ffma2_rn(lo(xi[u]), lo(yr[u]), g2);
+    g2 = __ffma2_rn(hi(xi[u]), hi(yr[u]), g2);
+  }
+  const float al = group_sum<G>((a0.x + a0.y) + (a1.x + a1.y));
+  const float be = group_sum<G>((b0.x + b0.y) + (b1.x + b1.y));
+  const float cr = group_sum<G>((r0.x + r0.y) + (r1.x + r1.y));
+  const float ci = group_sum<G>((g1.x + g1.y) - (g2.x + g2.y));
+  const float g = sqrtf(cr * cr + ci * ci);
+  if (!(g > tol * sqrtf(al) * sqrtf(be))) return false;
+  const float zeta = (be - al) / (2.f * g);
+  float t;
+  if (fabsf(zeta) > 1e18f)
+    t = 0.5f / zeta;
+  else
+    t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  if (t == 0.f) return false;
+  // cs = 1/r, sn = t/r with r = sqrt(1 + t^2), and cs - 1 = -t^2 / (r (1 + r)) to full
+  // relative precision, all correctly rounded: the rotation stays unitary to rounding, so
+  // the vector norms do not drift over thousands of rotations
+  const float r = sqrtf(1.f + t * t);
+  const float cm = -(t * t) / (r * (1.f + r)), sn = t / r;
+  const float kr = sn * (cr / g), ki = sn * (ci / g);     // k = sn e^{i phi}
+  const float2 CS = f2(cm, cm), KR = f2(kr, kr), KI = f2(ki, ki), NKR = f2(-kr, -kr),
+               NKI = f2(-ki, -ki);
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) {
+    const int c = gl + G * u;
+    if (c < nchunk) {
+      rotate4(CS, KR, KI, NKR, NKI, xr[u], xi[u], yr[u], yi[u]);
+      xr4[c] = xr[u];
+      xi4[c] = xi[u];
+      yr4[c] = yr[u];
+      yi4[c] = yi[u];
+    }
+  }
+  for (int c = nchunk + gl; c < nchunk + nchunkv; c += G) {
+    float4 vxr = xr4[c], vxi = xi4[c], vyr = yr4[c], vyi = yi4[c];
+    rotate4(CS, KR, KI, NKR, NKI, vxr, vxi, vyr, vyi);
+    xr4[c] = vxr;
+    xi4[c] = vxi;
+    yr4[c] = vyr;
+    yi4[c] = vyi;
+  }
+  return true;
+}
+
+// Largest CTA for a chunk count: the pair registers (16 floats per chunk) must fit.
+__host__ __device__ constexpr int max_warps_for(int cpl) {
+  return cpl <= 1 ? 32 : cpl == 2 ? 24 : cpl == 3 ? 18 : cpl == 4 ? 16 : cpl <= 6 ? 14 : 12;
+}
+
+// Copy block `blk` of the slice (vectors blk*bs .. blk*bs+bs-1, zero past nv) into local
+// slot `slot`; in the V form the V entries of vector g start as the unit vector e_g.
+__device__ void load_block_from_slice(float* Wr, float* Wi, const float2* __restrict__ A,
+                                      const SliceShape& sh, int n1, int blk, int slot) {
+  const int bs = sh.bs, len = sh.len, rowp = sh.rowp;
+  const int v0 = blk * bs;
+  const int nvalid = max(0, min(bs, sh.nv - v0));
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  float* r0 = Wr + (size_t)slot * bs * rowp;
+  float* i0 = Wi + (size_t)slot * bs * rowp;
+  // zero everything the slice does not cover: the tail of each row and padding vectors
+  const int tail = rowp - len;
+  for (int idx = tid; idx < nvalid * tail; idx += nthr) {
+    const int k = idx / tail, p = len + idx % tail;
+    r0[(size_t)k * rowp + p] = 0.f;
+    i0[(size_t)k * rowp + p] = 0.f;
+  }
+  for (int idx = tid; idx < (bs - nvalid) * rowp; idx += nthr) {
+    const int k = nvalid + idx / rowp, p = idx % rowp;
+    r0[(size_t)k * rowp + p] = 0.f;
+    i0[(size_t)k * rowp + p] = 0.f;
+  }
+  __syncthreads();
+  if (sh.vform)
+    for (int k = tid; k < nvalid; k += nthr) r0[(size_t)k * rowp + sh.ld + v0 + k] = 1.f;
+  if (!sh.rows) {
+    // vector v = column v0 + k: entries A[p + n1 (v0 + k)], contiguous in p
+    for (int idx = tid; idx < nvalid * len; idx += nthr) {
+      const int k = idx / len, p = idx % len;
+      const float2 x = A[(size_t)p + (size_t)n1 * (v0 + k)];
+      r0[(size_t)k * rowp + p] = x.x;
+      i0[(size_t)k * rowp + p] = x.y;
+    }
+  } else {
+    // vector v = row v0 + k: entries A[(v0 + k) + n1 p]; k fastest across threads
+    for (int idx = tid; idx < nvalid * len; idx += nthr) {
+      const int k = idx % nvalid, p = idx / nvalid;
+      const float2 x = A[(size_t)(v0 + k) + (size_t)n1 * p];
+      r0[(size_t)k * rowp + p] = x.x;
+      i0[(size_t)k * rowp + p] = x.y;
+    }
+  }
+}
+
+// Exchange buffer of one slice: [parity][block][plane][bs][rowp] floats.
+__device__ __forceinline__ float* xblock(float* xbuf, const SliceShape& sh, int par, int blk,
+                                         int plane) {
+  return xbuf + (((size_t)par * sh.nb + blk) * 2 + plane) * (size_t)sh.bs * sh.rowp;
+}
+
+__device__ void copy_floats4(float* __restrict__ dst, const float* __restrict__ src, size_t n) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (size_t i = threadIdx.x; i < n / 4; i += blockDim.x) d4[i] = s4[i];
+}
+
+// Global index of entry p of column c of B (the slice in vector orientation).
+__device__ __forceinline__ size_t b_index(const SliceShape& sh, int n1, int p, int c) {
+  return sh.rows ? (size_t)c + (size_t)n1 * p : (size_t)p + (size_t)n1 * c;
+}
+
+template <int G, int CPL>
+__global__ void __launch_bounds__(max_warps_for(CPL) * 32)
+    jacobi_svt_kernel(SliceArgs a, SliceShape sh) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int len = sh.len, ld = sh.ld, rowp = sh.rowp, nc = sh.nc, bs = sh.bs, nb = sh.nb;
+  const int C = sh.C;
+  const int nl = 2 * bs;
+  float* Wr = reinterpret_cast<float*>(smem_raw);
+  float* Wi = Wr + (size_t)nl * rowp;
+  float2* Bc = reinterpret_cast<float2*>(Wi + (size_t)nl * rowp);
+  float2* Cc = Bc + (size_t)len * nc;
+  float* sig = reinterpret_cast<float*>(Cc + (size_t)nl * nc);
+  float* dsc = sig + nl;
+  int* keep = reinterpret_cast<int*>(dsc + nl);
+  __shared__ int s_flag[2];
+  __shared__ int s_rank;
+  __shared__ double s_nuc;
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = C > 1 ? (int)cluster.block_rank() : 0;
+  const int so = blockIdx.x / C;     // slice ordinal in this launch
+  const int s = a.slices ? a.slices[so] : so;
   const int n1 = a.n1;
   const int64_t N12 = a.N12;
   const float2* __restrict__ A = a.ahat + (size_t)s * N12;
   float2* __restrict__ Z = a.zhat + (size_t)s * N12;
+  char* scr = static_cast<char*>(a.scratch);
+  const size_t xbytes = sh.xbuf_floats * sizeof(float);
+  const size_t pbytes = (size_t)C * N12 * sizeof(float2);
+  float* xbuf = C > 1 ? reinterpret_cast<float*>(scr + (size_t)so * (xbytes + pbytes)) : nullptr;
+  float2* part = C > 1 ? reinterpret_cast<float2*>(scr + (size_t)so * (xbytes + pbytes) + xbytes)
+                       : nullptr;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
 
-  // ---- load the slice: vector v, element p  <->  A(i, j) at i + n1*j
-  for (int64_t idx = tid; idx < N12; idx += nthr) {
-    const int i = (int)(idx % n1), j = (int)(idx / n1);
-    const int v = sh.rows ? i : j, p = sh.rows ? j : i;
-    W[(size_t)v * ld + p] = A[idx];
-  }
+  // ---- initial blocks: slot 0 / slot 1 hold the blocks of circle slot `crank`, round 0
+  int bx, by;
+  round_robin_pair(0, crank, nb, bx, by);
+  load_block_from_slice(Wr, Wi, A, sh, n1, bx, 0);
+  load_block_from_slice(Wr, Wi, A, sh, n1, by, 1);
   __syncthreads();
 
-  // ---- one-sided Jacobi sweeps in round-robin order
-  const int P = nv + (nv & 1);
-  const int npairs = P / 2;
+  // ---- Jacobi sweeps
+  const int gpw = 32 / G;                    // groups per warp
+  const int group = warp * gpw + lane / G;   // group index in the CTA
+  const int ngroups = nwarps * gpw;
+  const int gl = lane % G;
+  const int nchunk = ld / 4, nchunkv = sh.ldv / 4;
   const float tol = a.tol;
-  int sweeps = 0, converged = 0;
+  const int trips = (bs + ngroups - 1) / ngroups;
+  const size_t slotf = (size_t)bs * rowp;    // floats of one plane of one block
+  int sweeps = 0, converged = 0, par = 0;
   for (int sw = 0; sw < a.max_sweeps; ++sw) {
     int rotated = 0;
-    for (int r = 0; r < P - 1; ++r) {
-      for (int slot = warp; slot < npairs; slot += nwarps) {
-        int p, q;
-        round_robin_pair(r, slot, P, p, q);
-        if (p >= nv || q >= nv) continue;
-        float2* wp = W + (size_t)p * ld;
-        float2* wq = W + (size_t)q * ld;
-        float al = 0.f, be = 0.f, cr = 0.f, ci = 0.f;
-        for (int e = lane; e < len; e += 32) {
-          const float2 x = wp[e], y = wq[e];
-          al += x.x * x.x + x.y * x.y;
-          be += y.x * y.x + y.y * y.y;
-          cr += x.x * y.x + x.y * y.y;   // Re(x^H y)
-          ci += x.x * y.y - x.y * y.x;   // Im(x^H y)
+    for (int r = 0; r < nb - 1; ++r) {
+      round_robin_pair(r, crank, nb, bx, by);
+      const int vx0 = bx * bs, vy0 = by * bs;
+      const int nlr = r == 0 ? nl - 1 : bs;   // local rounds
+      for (int lr = 0; lr < nlr; ++lr) {
+        for (int k = 0; k < trips; ++k) {
+          const int slot = group + k * ngroups;
+          int p = nl, q = nl;
+          if (slot < bs) {
+            if (r == 0) {
+              round_robin_pair(lr, slot, nl, p, q);
+            } else {
+              p = slot;
+              q = bs + (slot + lr) % bs;
+            }
+          }
+          // a local vector is real if its global index is below nv
+          bool real_pair = p < nl && q < nl;
+          if (real_pair) {
+            const int gp = p < bs ? vx0 + p : vy0 + p - bs;
+            const int gq = q < bs ? vx0 + q : vy0 + q - bs;
+            real_pair = gp < sh.nv && gq < sh.nv;
+          }
+          // every lane of the warp takes part in the shuffles when any group has work
+          if (!__ballot_sync(0xffffffffu, real_pair)) continue;
+          const bool did = jacobi_pair<G, CPL>(Wr, Wi, rowp, real_pair ? nchunk : 0,
+                                               real_pair ? nchunkv : 0, real_pair ? p : 0,
+                                               real_pair ? q : 1, gl, tol);
+          rotated |= (did && real_pair) ? 1 : 0;
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        cr = warp_sum(cr);
-        ci = warp_sum(ci);
-        const float g = hypotf(cr, ci);
-        if (!(g > tol * sqrtf(al) * sqrtf(be))) continue;
-        const float zeta = (be - al) / (2.f * g);
-        float t;
-        if (fabsf(zeta) > 1e18f)
-          t = 0.5f / zeta;
-        else
-          t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-        if (t == 0.f) continue;
-        rotated = 1;
-        // correctly rounded: an approximate reciprocal square root makes every rotation
-        // slightly non-unitary and the vector norms drift over thousands of rotations
-        const float cs = 1.f / sqrtf(1.f + t * t), sn = cs * t;
-        const float er = cr / g, ei = ci / g;       // e^{i phi}
-        const float kr = sn * er, ki = sn * ei;     // sn e^{i phi}
-        for (int e = lane; e < len; e += 32) {
-          const float2 x = wp[e], y = wq[e];
-          // x' = cs x - conj(k) y,   y' = k x + cs y
-          wp[e] = make_float2(cs * x.x - (kr * y.x + ki * y.y), cs * x.y - (kr * y.y - ki * y.x));
-          wq[e] = make_float2(kr * x.x - ki * x.y + cs * y.x, kr * x.y + ki * x.x + cs * y.y);
-        }
+        __syncthreads();
       }
-      __syncthreads();
+      const bool sweep_end = r == nb - 2;
+      int local_any = 0;
+      if (sweep_end) local_any = __syncthreads_or(rotated);
+      if (C > 1) {
+        // trade blocks: write both, barrier, read the next round's pair
+        if (sweep_end && tid == 0) s_flag[sw & 1] = local_any;
+        copy_floats4(xblock(xbuf, sh, par, bx, 0), Wr, slotf);
+        copy_floats4(xblock(xbuf, sh, par, bx, 1), Wi, slotf);
+        copy_floats4(xblock(xbuf, sh, par, by, 0), Wr + slotf, slotf);
+        copy_floats4(xblock(xbuf, sh, par, by, 1), Wi + slotf, slotf);
+        __threadfence();
+        cluster.sync();
+        int nbx, nby;
+        round_robin_pair(sweep_end ? 0 : r + 1, crank, nb, nbx, nby);
+        copy_floats4(Wr, xblock(xbuf, sh, par, nbx, 0), slotf);
+        copy_floats4(Wi, xblock(xbuf, sh, par, nbx, 1), slotf);
+        copy_floats4(Wr + slotf, xblock(xbuf, sh, par, nby, 0), slotf);
+        copy_floats4(Wi + slotf, xblock(xbuf, sh, par, nby, 1), slotf);
+        par ^= 1;
+        if (sweep_end) {
+          int any = 0;
+          for (int c = 0; c < C; ++c) any |= *cluster.map_shared_rank(&s_flag[sw & 1], c);
+          local_any = any;
+        }
+        __syncthreads();
+      }
+      if (sweep_end) {
+        ++sweeps;
+        if (!local_any) converged = 1;
+      }
     }
-    ++sweeps;
-    if (!__syncthreads_or(rotated)) {
-      converged = 1;
-      break;
-    }
+    if (converged) break;
   }
+  // the blocks now held are those of round 0: (bx, by) of circle slot crank
+  round_robin_pair(0, crank, nb, bx, by);
 
-  // ---- singular values: sigma_v = ||w_v||
-  for (int v = warp; v < nv; v += nwarps) {
-    const float2* wv = W + (size_t)v * ld;
+  // ---- singular values of the local vectors: sigma = ||w||
+  for (int v = warp; v < nl; v += nwarps) {
+    const float* wr = Wr + (size_t)v * rowp;
+    const float* wi = Wi + (size_t)v * rowp;
     float acc = 0.f;
-    for (int e = lane; e < len; e += 32) acc += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
-    acc = warp_sum(acc);
+    for (int e = lane; e < len; e += 32) acc += wr[e] * wr[e] + wi[e] * wi[e];
+    acc = group_sum<32>(acc);
     if (lane == 0) sig[v] = sqrtf(acc);
   }
   __syncthreads();
@@ -158,7 +423,9 @@ __global__ void __launch_bounds__(1024) jacobi_svt_kernel(SliceArgs a, SliceShap
   if (tid == 0) {
     int r = 0;
     double nuc = 0.0;
-    for (int v = 0; v < nv; ++v) {
+    for (int v = 0; v < nl; ++v) {
+      const int gv = v < bs ? bx * bs + v : by * bs + v - bs;
+      if (gv >= sh.nv) continue;
       nuc += (double)sig[v];
       if (sig[v] > tau) {
         keep[r++] = v;
@@ -166,13 +433,24 @@ __global__ void __launch_bounds__(1024) jacobi_svt_kernel(SliceArgs a, SliceShap
       }
     }
     s_rank = r;
+    s_nuc = nuc;
+  }
+  if (C > 1) cluster.sync();
+  else __syncthreads();
+  if (crank == 0 && tid == 0) {
+    int rank_all = 0;
+    double nuc_all = 0.0;
+    for (int c = 0; c < C; ++c) {
+      rank_all += C > 1 ? *cluster.map_shared_rank(&s_rank, c) : s_rank;
+      nuc_all += C > 1 ? *cluster.map_shared_rank(&s_nuc, c) : s_nuc;
+    }
     if (a.stat) {
       SliceStat st;
-      st.rank = r;
+      st.rank = rank_all;
       st.sweeps = sweeps;
       st.converged = converged;
       st.pad = 0;
-      st.nuc = nuc;
+      st.nuc = nuc_all;
       a.stat[s] = st;
     }
     if (a.acc) {
@@ -181,107 +459,134 @@ __global__ void __launch_bounds__(1024) jacobi_svt_kernel(SliceArgs a, SliceShap
       atomicMax(&a.acc->max_sweeps, sweeps);
     }
   }
-  __syncthreads();
   const int rank = s_rank;
+  float2* out = C > 1 ? part + (size_t)crank * N12 : Z;
 
   if (rank == 0) {
-    for (int64_t idx = tid; idx < N12; idx += nthr) Z[idx] = make_float2(0.f, 0.f);
-    return;
-  }
-
-  // ---- normalise the kept vectors: u = w / sigma
-  for (int64_t idx = tid; idx < (int64_t)rank * len; idx += nthr) {
-    const int k = (int)(idx / len), e = (int)(idx % len);
-    const int v = keep[k];
-    const float inv = 1.f / sig[v];
-    float2 w = W[(size_t)v * ld + e];
-    W[(size_t)v * ld + e] = make_float2(w.x * inv, w.y * inv);
-  }
-  __syncthreads();
-
-  // ---- rebuild Z = U_r diag(d) U_r^H B, chunk of nc vectors of B at a time
-  for (int c0 = 0; c0 < nv; c0 += nc) {
-    const int ncur = min(nc, nv - c0);
-    // B chunk: Bc[p + len*cc] = B(p, c0+cc)
-    for (int idx = tid; idx < len * ncur; idx += nthr) {
-      int p, cc;
-      size_t gi;
-      if (!sh.rows) {
-        p = idx % len;
-        cc = idx / len;
-        gi = (size_t)p + (size_t)n1 * (c0 + cc);
-      } else {
-        cc = idx % ncur;
-        p = idx / ncur;
-        gi = (size_t)(c0 + cc) + (size_t)n1 * p;
+    for (int64_t idx = tid; idx < N12; idx += nthr) out[idx] = make_float2(0.f, 0.f);
+  } else {
+    if (!sh.vform) {
+      // ---- U form: normalise the kept vectors, u = w / sigma
+      for (int64_t idx = tid; idx < (int64_t)rank * len; idx += nthr) {
+        const int k = (int)(idx / len), e = (int)(idx % len);
+        const int v = keep[k];
+        const float inv = 1.f / sig[v];
+        Wr[(size_t)v * rowp + e] *= inv;
+        Wi[(size_t)v * rowp + e] *= inv;
       }
-      Bc[p + (size_t)len * cc] = A[gi];
+      __syncthreads();
     }
-    __syncthreads();
-    // C(k, cc) = d_k * u_k^H B(:, c0+cc)
-    for (int k = tid; k < rank; k += nthr) {
-      const int v = keep[k];
-      const float2* u = W + (size_t)v * ld;
-      float accr[kNC], acci[kNC];
+    // ---- rebuild the local part of D_tau(B), a chunk of nc columns of B at a time
+    const int nv = sh.nv;
+    for (int c0 = 0; c0 < nv; c0 += nc) {
+      const int ncur = min(nc, nv - c0);
+      if (sh.vform) {
+        // C(k, cc) = d_k conj(v_k(c0 + cc))
+        for (int idx = tid; idx < rank * ncur; idx += nthr) {
+          const int k = idx / ncur, cc = idx % ncur;
+          const int v = keep[k];
+          const float d = dsc[v];
+          const size_t o = (size_t)v * rowp + ld + c0 + cc;
+          Cc[(size_t)k * nc + cc] = make_float2(d * Wr[o], -d * Wi[o]);
+        }
+        __syncthreads();
+      } else {
+        // B chunk: Bc[p + len*cc] = B(p, c0+cc)
+        for (int idx = tid; idx < len * ncur; idx += nthr) {
+          int p, cc;
+          if (!sh.rows) {
+            p = idx % len;
+            cc = idx / len;
+          } else {
+            cc = idx % ncur;
+            p = idx / ncur;
+          }
+          Bc[p + (size_t)len * cc] = A[b_index(sh, n1, p, c0 + cc)];
+        }
+        __syncthreads();
+        // C(k, cc) = d_k u_k^H B(:, c0+cc); thread k starts at a k-dependent entry so the
+        // lanes of a warp hit distinct banks
+        for (int k = tid; k < rank; k += nthr) {
+          const int v = keep[k];
+          const float* ur = Wr + (size_t)v * rowp;
+          const float* ui = Wi + (size_t)v * rowp;
+          float accr[kNC], acci[kNC];
 #pragma unroll
-      for (int cc = 0; cc < kNC; ++cc) accr[cc] = acci[cc] = 0.f;
-      for (int p = 0; p < len; ++p) {
-        const float2 x = u[p];
+          for (int cc = 0; cc < kNC; ++cc) accr[cc] = acci[cc] = 0.f;
+          int p = k % len;
+          for (int it = 0; it < len; ++it) {
+            const float xr = ur[p], xi = ui[p];
 #pragma unroll
-        for (int cc = 0; cc < kNC; ++cc) {
-          if (cc < ncur) {
-            const float2 b = Bc[p + (size_t)len * cc];
-            accr[cc] += x.x * b.x + x.y * b.y;
-            acci[cc] += x.x * b.y - x.y * b.x;
+            for (int cc = 0; cc < kNC; ++cc) {
+              if (cc < ncur) {
+                const float2 b = Bc[p + (size_t)len * cc];
+                accr[cc] += xr * b.x + xi * b.y;
+                acci[cc] += xr * b.y - xi * b.x;
+              }
+            }
+            if (++p == len) p = 0;
+          }
+          const float d = dsc[v];
+#pragma unroll
+          for (int cc = 0; cc < kNC; ++cc)
+            if (cc < ncur) Cc[(size_t)k * nc + cc] = make_float2(d * accr[cc], d * acci[cc]);
+        }
+        __syncthreads();
+      }
+      // Z(p, cc) = sum_k w_k(p) C(k, cc) (U form: w_k = u_k), written into the B chunk
+      for (int p = tid; p < len; p += nthr) {
+        float accr[kNC], acci[kNC];
+#pragma unroll
+        for (int cc = 0; cc < kNC; ++cc) accr[cc] = acci[cc] = 0.f;
+        for (int k = 0; k < rank; ++k) {
+          const int v = keep[k];
+          const float xr = Wr[(size_t)v * rowp + p], xi = Wi[(size_t)v * rowp + p];
+#pragma unroll
+          for (int cc = 0; cc < kNC; ++cc) {
+            if (cc < ncur) {
+              const float2 c = Cc[(size_t)k * nc + cc];
+              accr[cc] += xr * c.x - xi * c.y;
+              acci[cc] += xr * c.y + xi * c.x;
+            }
           }
         }
+#pragma unroll
+        for (int cc = 0; cc < kNC; ++cc)
+          if (cc < ncur) Bc[p + (size_t)len * cc] = make_float2(accr[cc], acci[cc]);
       }
-      const float d = dsc[v];
-#pragma unroll
-      for (int cc = 0; cc < kNC; ++cc)
-        if (cc < ncur) Cc[(size_t)k * nc + cc] = make_float2(d * accr[cc], d * acci[cc]);
-    }
-    __syncthreads();
-    // Z(p, cc) = sum_k u_k(p) C(k, cc), written over the B chunk
-    for (int p = tid; p < len; p += nthr) {
-      float accr[kNC], acci[kNC];
-#pragma unroll
-      for (int cc = 0; cc < kNC; ++cc) accr[cc] = acci[cc] = 0.f;
-      for (int k = 0; k < rank; ++k) {
-        const float2 x = W[(size_t)keep[k] * ld + p];
-#pragma unroll
-        for (int cc = 0; cc < kNC; ++cc) {
-          if (cc < ncur) {
-            const float2 c = Cc[(size_t)k * nc + cc];
-            accr[cc] += x.x * c.x - x.y * c.y;
-            acci[cc] += x.x * c.y + x.y * c.x;
-          }
+      __syncthreads();
+      for (int idx = tid; idx < len * ncur; idx += nthr) {
+        int p, cc;
+        if (!sh.rows) {
+          p = idx % len;
+          cc = idx / len;
+        } else {
+          cc = idx % ncur;
+          p = idx / ncur;
         }
+        out[b_index(sh, n1, p, c0 + cc)] = Bc[p + (size_t)len * cc];
       }
-#pragma unroll
-      for (int cc = 0; cc < kNC; ++cc)
-        if (cc < ncur) Bc[p + (size_t)len * cc] = make_float2(accr[cc], acci[cc]);
+      __syncthreads();
     }
-    __syncthreads();
-    for (int idx = tid; idx < len * ncur; idx += nthr) {
-      int p, cc;
-      size_t gi;
-      if (!sh.rows) {
-        p = idx % len;
-        cc = idx / len;
-        gi = (size_t)p + (size_t)n1 * (c0 + cc);
-      } else {
-        cc = idx % ncur;
-        p = idx / ncur;
-        gi = (size_t)(c0 + cc) + (size_t)n1 * p;
+  }
+  if (C > 1) {
+    // ---- Z = sum of the C partial rebuilds, added in cluster-rank order
+    __threadfence();
+    cluster.sync();
+    const int64_t lo_i = N12 * crank / C, hi_i = N12 * (crank + 1) / C;
+    for (int64_t idx = lo_i + tid; idx < hi_i; idx += nthr) {
+      float2 acc = part[idx];
+      for (int c = 1; c < C; ++c) {
+        const float2 v = part[(size_t)c * N12 + idx];
+        acc.x += v.x;
+        acc.y += v.y;
       }
-      Z[gi] = Bc[p + (size_t)len * cc];
+      Z[idx] = acc;
     }
-    __syncthreads();
   }
 }
 
-bool plan_slice(int n1, int n2, SliceShape& sh, size_t& smem) {
+int max_optin_smem() {
   static int max_optin = -1;
   if (max_optin < 0) {
     int dev = 0;
@@ -290,10 +595,53 @@ bool plan_slice(int n1, int n2, SliceShape& sh, size_t& smem) {
         cudaSuccess)
       max_optin = 227 * 1024;
   }
+  return max_optin;
+}
+
+// Lanes per pair and 4-entry chunks per lane for a vector pitch of ld floats.
+bool pick_group(int ld, int& G, int& cpl) {
+  const int nchunk = ld / 4;
+  const int Gs[2] = {4, 8};
+  for (int gi = 0; gi < 2; ++gi) {
+    if ((nchunk + Gs[gi] - 1) / Gs[gi] <= 2) {
+      G = Gs[gi];
+      cpl = (nchunk + G - 1) / G;
+      return true;
+    }
+  }
+  G = 16;
+  const int need = (nchunk + 15) / 16;
+  const int opts[6] = {1, 2, 3, 4, 6, 8};
+  for (int o : opts)
+    if (need <= o) {
+      cpl = o;
+      return true;
+    }
+  return false;
+}
+
+// A pitch of at least n floats: a multiple of 4 with pitch/4 odd (fewer bank conflicts on
+// strided access).
+int pitch_for(int n) {
+  int p = (n + 3) / 4 * 4;
+  if (((p / 4) & 1) == 0) p += 4;
+  return p;
+}
+
+bool plan_with_ctas(int n1, int n2, int C, int vform, SliceShape& sh, size_t& smem) {
+  const int max_optin = max_optin_smem();
   sh.rows = n1 < n2 ? 1 : 0;
   sh.nv = n1 < n2 ? n1 : n2;
   sh.len = n1 < n2 ? n2 : n1;
-  sh.ld = sh.len | 1;
+  sh.ld = pitch_for(sh.len);
+  sh.vform = vform ? 1 : 0;
+  sh.ldv = sh.vform ? pitch_for(sh.nv) : 0;
+  sh.rowp = sh.ld + sh.ldv;
+  if (!pick_group(sh.ld, sh.G, sh.cpl)) return false;
+  sh.C = C;
+  sh.nb = 2 * C;
+  sh.bs = (sh.nv + sh.nb - 1) / sh.nb;
+  sh.xbuf_floats = C > 1 ? (size_t)2 * sh.nb * 2 * sh.bs * sh.rowp : 0;
   for (int nc = kNC; nc >= 1; nc >>= 1) {
     sh.nc = nc;
     smem = slice_smem_bytes(sh);
@@ -302,30 +650,117 @@ bool plan_slice(int n1, int n2, SliceShape& sh, size_t& smem) {
   return false;
 }
 
+// CTAs per slice: the fewest waves of one CTA per SM, weighted by the work of one CTA
+// (1/C), without blocks thinner than kMinBlock vectors; the smallest C on ties.
+bool plan_slice(int n1, int n2, int nslices, int force, int vform, SliceShape& sh,
+                size_t& smem) {
+  const int nv = n1 < n2 ? n1 : n2;
+  const int cands[4] = {1, 2, 4, 8};
+  double best = 1e300;
+  bool found = false;
+  for (int C : cands) {
+    if (force && C != force) continue;
+    if (!force && C > 1 && nv < 2 * C * kMinBlock) continue;
+    SliceShape t;
+    size_t sm;
+    if (!plan_with_ctas(n1, n2, C, vform, t, sm)) continue;
+    const int waves = (nslices * C + kSMs - 1) / kSMs;
+    const double cost = (double)waves / C;
+    if (cost < best - 1e-12) {
+      best = cost;
+      sh = t;
+      smem = sm;
+      found = true;
+    }
+  }
+  if (!found && !force) {
+    // slices too large for the thin-block rule: take the smallest C that fits
+    for (int C : cands) {
+      SliceShape t;
+      size_t sm;
+      if (plan_with_ctas(n1, n2, C, vform, t, sm)) {
+        sh = t;
+        smem = sm;
+        return true;
+      }
+    }
+  }
+  return found;
+}
+
+size_t scratch_for(const SliceShape& sh, int64_t N12, int nslices) {
+  if (sh.C <= 1) return 0;
+  return (size_t)nslices * (sh.xbuf_floats * sizeof(float) + (size_t)sh.C * N12 * sizeof(float2));
+}
+
+template <int G, int CPL>
+cudaError_t launch_gc(const SliceArgs& a, const SliceShape& sh, size_t smem, int threads,
+                      cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(jacobi_svt_kernel<G, CPL>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.nslices * sh.C), 1, 1);
+  cfg.blockDim = dim3((unsigned)threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)sh.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, jacobi_svt_kernel<G, CPL>, a, sh);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool jacobi_svt_supported(int n1, int n2) {
   SliceShape sh;
   size_t smem;
-  return n1 >= 1 && n2 >= 1 && plan_slice(n1, n2, sh, smem);
+  return n1 >= 1 && n2 >= 1 && plan_slice(n1, n2, 1, 0, 0, sh, smem);
+}
+
+size_t jacobi_svt_scratch_bytes(int n1, int n2, int nslices, int force_ctas, int vform) {
+  SliceShape sh;
+  size_t smem;
+  if (!plan_slice(n1, n2, nslices, force_ctas, vform, sh, smem)) return 0;
+  return scratch_for(sh, (int64_t)n1 * n2, nslices);
+}
+
+int jacobi_svt_ctas_per_slice(int n1, int n2, int nslices, int force_ctas, int vform) {
+  SliceShape sh;
+  size_t smem;
+  if (!plan_slice(n1, n2, nslices, force_ctas, vform, sh, smem)) return 0;
+  return sh.C;
 }
 
 cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st) {
   if (a.nslices <= 0) return cudaSuccess;
   SliceShape sh;
   size_t smem;
-  if (!plan_slice(a.n1, a.n2, sh, smem)) return cudaErrorInvalidValue;
-  const int P = sh.nv + (sh.nv & 1);
-  const int npairs = P / 2;
-  const int passes = (npairs + 31) / 32;
-  int nwarps = (npairs + passes - 1) / passes;
+  if (!plan_slice(a.n1, a.n2, a.nslices, a.force_ctas, a.vform, sh, smem))
+    return cudaErrorInvalidValue;
+  if (sh.C > 1 && (a.scratch == nullptr || a.scratch_bytes < scratch_for(sh, a.N12, a.nslices)))
+    return cudaErrorInvalidValue;
+  const int gpw = 32 / sh.G;
+  const int maxw = max_warps_for(sh.cpl);
+  // enough groups for all pairs of a local round in as few passes as fit, balanced
+  const int passes = (sh.bs + maxw * gpw - 1) / (maxw * gpw);
+  int nwarps = (sh.bs + passes * gpw - 1) / (passes * gpw);
   if (nwarps < kMinWarps) nwarps = kMinWarps;
-  if (nwarps > 32) nwarps = 32;
-  cudaError_t e = cudaFuncSetAttribute(jacobi_svt_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  jacobi_svt_kernel<<<a.nslices, nwarps * 32, smem, st>>>(a, sh);
-  return cudaGetLastError();
+  if (nwarps > maxw) nwarps = maxw;
+  const int threads = nwarps * 32;
+#define TSVD_CASE(G_, C_) \
+  if (sh.G == G_ && sh.cpl == C_) return launch_gc<G_, C_>(a, sh, smem, threads, st);
+  TSVD_CASE(4, 1) TSVD_CASE(4, 2) TSVD_CASE(8, 1) TSVD_CASE(8, 2)
+  TSVD_CASE(16, 1) TSVD_CASE(16, 2) TSVD_CASE(16, 3) TSVD_CASE(16, 4) TSVD_CASE(16, 6)
+  TSVD_CASE(16, 8)
+#undef TSVD_CASE
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace tsvd

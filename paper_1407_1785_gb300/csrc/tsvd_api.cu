@@ -166,6 +166,8 @@ struct Workspace {
   SliceStat* stat = nullptr;
   SweepAccum* acc = nullptr;
   int* bad = nullptr;
+  void* jscratch = nullptr;     // multi-CTA slice SVT scratch
+  size_t jscratch_bytes = 0;
   int ndistinct = 0;
 };
 
@@ -178,7 +180,14 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   const TubeGeom& g = p.g;
   const size_t spec = align_up((size_t)g.nstore * g.N12 * sizeof(float2));
   const size_t real = align_up((size_t)p.N * sizeof(float));
-  size_t off[13], total = 0;
+  c->slices_host.clear();
+  for (int kh = 0; kh < g.hh; ++kh)
+    for (int kf = 0; kf < g.nf; ++kf)
+      if (slice_is_distinct(g, kf, kh)) c->slices_host.push_back(kf + g.nf * kh);
+  w.ndistinct = (int)c->slices_host.size();
+  const size_t jbytes = jacobi_svt_scratch_bytes((int)p.n1, (int)p.n2, w.ndistinct,
+                                                 c->opts.ctas_per_slice, c->opts.accumulate_v);
+  size_t off[14], total = 0;
   auto take = [&](int i, size_t bytes) { off[i] = total; total += align_up(bytes); };
   take(0, spec);
   take(1, spec);
@@ -193,6 +202,7 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   take(10, (size_t)g.nstore * sizeof(SliceStat));
   take(11, sizeof(SweepAccum));
   take(12, sizeof(int));
+  take(13, jbytes);
   if (total > c->ws_cap) {
     if (c->ws) {
       TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -223,6 +233,8 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   w.stat = reinterpret_cast<SliceStat*>(b + off[10]);
   w.acc = reinterpret_cast<SweepAccum*>(b + off[11]);
   w.bad = reinterpret_cast<int*>(b + off[12]);
+  w.jscratch = jbytes ? b + off[13] : nullptr;
+  w.jscratch_bytes = jbytes;
 
   // twiddles (cos, sin)(2 pi m / n) in FP64, exact at the quarter points
   auto table = [](int n, float2* dst) {
@@ -243,11 +255,6 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   c->twid_host.resize((size_t)(g.nh + g.nf));
   table(g.nh, c->twid_host.data());
   table(g.nf, c->twid_host.data() + g.nh);
-  c->slices_host.clear();
-  for (int kh = 0; kh < g.hh; ++kh)
-    for (int kf = 0; kf < g.nf; ++kf)
-      if (slice_is_distinct(g, kf, kh)) c->slices_host.push_back(kf + g.nf * kh);
-  w.ndistinct = (int)c->slices_host.size();
   TSVD_CUDA(c, cudaMemcpyAsync(w.twid, c->twid_host.data(), c->twid_host.size() * sizeof(float2),
                                cudaMemcpyHostToDevice, c->stream));
   TSVD_CUDA(c, cudaMemcpyAsync(w.slices, c->slices_host.data(),
@@ -285,6 +292,10 @@ SliceArgs slice_args(tsvd_ctx* c, const Problem& p, const Workspace& w, float ta
   s.max_sweeps = c->opts.max_sweeps;
   s.stat = w.stat;
   s.acc = w.acc;
+  s.scratch = w.jscratch;
+  s.scratch_bytes = w.jscratch_bytes;
+  s.force_ctas = c->opts.ctas_per_slice;
+  s.vform = c->opts.accumulate_v;
   return s;
 }
 
@@ -305,6 +316,11 @@ tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
   if (o.max_sweeps < 1) return fail(c, TSVD_EINVAL, "max_sweeps must be >= 1");
   if (!(o.jacobi_tol > 0) || !std::isfinite(o.jacobi_tol))
     return fail(c, TSVD_EINVAL, "jacobi_tol must be positive");
+  if (o.ctas_per_slice != 0 && o.ctas_per_slice != 1 && o.ctas_per_slice != 2 &&
+      o.ctas_per_slice != 4 && o.ctas_per_slice != 8)
+    return fail(c, TSVD_EINVAL, "ctas_per_slice must be 0, 1, 2, 4 or 8");
+  if (o.accumulate_v != 0 && o.accumulate_v != 1)
+    return fail(c, TSVD_EINVAL, "accumulate_v must be 0 or 1");
   return TSVD_OK;
 }
 

@@ -91,11 +91,20 @@ struct SliceArgs {
   int max_sweeps;
   SliceStat* stat;        // indexed by slice index (nullable)
   SweepAccum* acc;        // nullable
+  void* scratch;          // global scratch of jacobi_svt_scratch_bytes() (block exchange and
+                          // partial rebuilds of multi-CTA slices); nullable = one CTA per slice
+  size_t scratch_bytes;
+  int force_ctas;         // 0 = choose; else CTAs per slice (1, 2, 4 or 8)
+  int vform;              // 1: accumulate V and rebuild as W diag(d) V^H
 };
 
 // Returns cudaErrorInvalidValue when a slice does not fit the kernel's shared memory.
 cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st);
-// Whether launch_jacobi_svt supports an n1 x n2 slice.
+// Whether launch_jacobi_svt supports an n1 x n2 slice (with scratch available).
 bool jacobi_svt_supported(int n1, int n2);
+// Global scratch the launch of `nslices` n1 x n2 slices needs (0 for one CTA per slice).
+size_t jacobi_svt_scratch_bytes(int n1, int n2, int nslices, int force_ctas, int vform);
+// CTAs per slice the launch would use.
+int jacobi_svt_ctas_per_slice(int n1, int n2, int nslices, int force_ctas, int vform);
 
 }  // namespace tsvd

@@ -120,11 +120,19 @@ extern "C" tsvd_status tsvt_static(const float* Y, float* Z, int order, const in
   if (!tube_pass_supported(g) || !jacobi_svt_supported((int)dims[0], (int)dims[1]))
     return TSVD_EUNSUPPORTED;
 
-  // scratch layout: spectrum A | spectrum B | twiddles (nh + nf) | distinct slice list
+  // scratch layout: spectrum A | spectrum B | twiddles (nh + nf) | distinct slice list |
+  // slice-SVT exchange buffers (multi-CTA slices)
+  int ndistinct = 0;
+  for (int kh = 0; kh < g.hh; ++kh) {
+    const bool selfcol = (kh == 0) || (2 * kh == g.nh);
+    for (int kf = 0; kf < g.nf; ++kf)
+      if (!(selfcol && 2 * kf > g.nf)) ++ndistinct;
+  }
   const size_t spec = align_up((size_t)g.nstore * (size_t)g.N12 * sizeof(float2));
   const size_t tw = align_up((size_t)(g.nh + g.nf) * sizeof(float2));
   const size_t lst = align_up((size_t)g.nstore * sizeof(int));
-  if (2 * spec + tw + lst > kStaticScratchBytes) return TSVD_ENOMEM;
+  const size_t jsc = align_up(jacobi_svt_scratch_bytes((int)dims[0], (int)dims[1], ndistinct, 0, 0));
+  if (2 * spec + tw + lst + jsc > kStaticScratchBytes) return TSVD_ENOMEM;
 
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -185,6 +193,10 @@ extern "C" tsvd_status tsvt_static(const float* Y, float* Z, int order, const in
   s.max_sweeps = o.max_sweeps;
   s.stat = nullptr;
   s.acc = nullptr;
+  s.scratch = jsc ? b + 2 * spec + tw + lst : nullptr;
+  s.scratch_bytes = jsc;
+  s.force_ctas = 0;
+  s.vform = 0;
   if ((st = from_launch(launch_jacobi_svt(s, stream))) != TSVD_OK) return st;
 
   TubeArgs inv{};

@@ -36,7 +36,8 @@ class Opts(ctypes.Structure):
                 ("tnn_scale", ctypes.c_int), ("rho0", ctypes.c_double),
                 ("mu", ctypes.c_double), ("rho_max", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int), ("jacobi_tol", ctypes.c_float),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("ctas_per_slice", ctypes.c_int),
+                ("accumulate_v", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -90,7 +90,7 @@ def gap_threshold(allsv, q):
 
 @pytest.mark.parametrize("shape", [(32, 32, 16), (33, 17, 7), (17, 33, 8), (40, 24, 1),
                                    (5, 64, 2), (1, 9, 5), (9, 1, 4), (64, 48, 13), (3, 130, 6),
-                                   (150, 20, 9)])
+                                   (150, 20, 9), (144, 176, 4), (200, 190, 3)])
 def test_tsvt_parity_3d(gpu_ctx, shape):
     Y = synth.normal(11, 0, int(np.prod(shape))).reshape(shape, order="F")
     sv = slice_singular_values(Y.astype(np.float32))
@@ -124,6 +124,55 @@ def test_tsvt_video_full_size(gpu_ctx):
     Y = (X * om).astype(np.float32)
     for tau in (100.0, 1.0, 1e-3):
         check_tsvt(gpu_ctx, Y, tau)
+
+
+@pytest.mark.parametrize("shape,ctas", [((40, 50, 5), 2), ((40, 50, 5), 8), ((50, 40, 4), 4),
+                                        ((130, 150, 4), 4), ((64, 80, 3), 2),
+                                        ((17, 33, 3, 4), 2), ((260, 270, 3), 8)])
+def test_tsvt_parity_cluster_split(shape, ctas):
+    """One slice spread over a cluster of 2, 4 or 8 CTAs (blocks of vectors traded between
+    CTAs), including ragged blocks padded with zero vectors."""
+    from paper_1407_1785_gb300 import libtsvd
+    torch = _torch()
+    with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
+                         ctas_per_slice=ctas) as ctx:
+        Y = synth.normal(31, 0, int(np.prod(shape))).reshape(shape, order="F")
+        sv = slice_singular_values(Y.astype(np.float32))
+        allsv = np.sort(np.concatenate([s for s in sv.values()]))
+        for q in (0.0, 0.5):
+            check_tsvt(ctx, Y, gap_threshold(allsv, q))
+
+
+@pytest.mark.parametrize("shape,ctas", [((40, 50, 5), 1), ((130, 150, 4), 4),
+                                        ((17, 33, 3, 4), 2), ((144, 176, 6), 2)])
+def test_tsvt_parity_accumulated_v(shape, ctas):
+    """The V-form rebuild (V accumulated during the sweeps)."""
+    from paper_1407_1785_gb300 import libtsvd
+    torch = _torch()
+    with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
+                         ctas_per_slice=ctas, accumulate_v=1) as ctx:
+        Y = synth.normal(41, 0, int(np.prod(shape))).reshape(shape, order="F")
+        sv = slice_singular_values(Y.astype(np.float32))
+        allsv = np.sort(np.concatenate([s for s in sv.values()]))
+        for q in (0.0, 0.5):
+            check_tsvt(ctx, Y, gap_threshold(allsv, q))
+
+
+def test_tsvt_rpca_full_size(gpu_ctx):
+    """240 x 320 x 60 tubal-rank-10 tensor plus 10% sparse corruption: slices larger than one
+    SM's shared memory, spread over CTA clusters."""
+    M, L, S, sup, lam = synth.workload_rpca(seed=1)
+    Y = M.astype(np.float32)
+    check_tsvt(gpu_ctx, Y, 50.0)
+
+
+@pytest.mark.slow
+def test_tsvt_color_video_full_size(gpu_ctx):
+    """288 x 352 x 3 x 60 colour video (2-D DFT over modes 3-4, 93 stored / 91 distinct
+    Fourier slices of 288 x 352)."""
+    X, om = synth.workload_color_video(seed=1)
+    Y = (X * om).astype(np.float32)
+    check_tsvt(gpu_ctx, Y, 20.0)
 
 
 def test_tsvt_deterministic_and_host_path(gpu_ctx):
