@@ -248,6 +248,7 @@ def run_ours(args):
         launches += st["launches"]
         sweeps += st["total_sweeps"]
         nonconv += st["nonconverged"]
+        plan = {"ctas_per_slice": st["slice_ctas"], "lanes_per_pair": st["slice_lanes"]}
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -320,6 +321,7 @@ def run_ours(args):
         "final_rse_db": rse,
         "jacobi_sweeps_per_slice_svd": sweeps / max(slice_launches * hh, 1),
         "jacobi_nonconverged": nonconv,
+        "slice_plan": plan,
         "roofline": roofline,
         "roofline_tube": roofline_tube,
         "cpu_baseline": cpu,

@@ -81,6 +81,13 @@ typedef struct tsvd_opts {
   int accumulate_v;   /* 1: also rotate V during the Jacobi sweeps and rebuild each slice as
                          W diag((s - tau)/s) V^H instead of U diag((s - tau)/s) U^H A;
                          default 0 */
+  int lanes_per_pair; /* lanes that share one vector pair: 4, 8 or 16; 0 (default) = chosen */
+  int autotune;       /* 1 (default): the first slice-SVT launch of each new slice shape in a
+                         context times the valid (ctas_per_slice, lanes_per_pair) plans on the
+                         real input (sweeps capped at 4) and keeps the fastest; choices fixed
+                         by nonzero ctas_per_slice / lanes_per_pair are kept */
+  const char* autotune_cache; /* nullable: text file of tuned plans keyed by GPU name and
+                         slice shape, read at the first tuning and appended to after it */
 } tsvd_opts;
 
 /* Counters of one ADMM solve (host struct). */
@@ -97,6 +104,8 @@ typedef struct tsvd_stats {
   int64_t slice_launches;       /* of which slice-SVT launches */
   double slice_ms;              /* summed device time of the slice-SVT launches (timing=1) */
   double tube_ms;               /* summed device time of the tube-pass launches (timing=1) */
+  int slice_ctas;               /* CTAs per slice of the slice-SVT plan used */
+  int slice_lanes;              /* lanes per vector pair of that plan (0 = planner default) */
 } tsvd_stats;
 
 /* Fill *opts with the defaults listed above. */

@@ -184,19 +184,21 @@ __device__ __forceinline__ bool jacobi_pair(float* __restrict__ Wr, float* __res
   const float ci = group_sum<G>((g1.x + g1.y) - (g2.x + g2.y));
   const float g = sqrtf(cr * cr + ci * ci);
   if (!(g > tol * sqrtf(al) * sqrtf(be))) return false;
-  const float zeta = (be - al) / (2.f * g);
+  const float inv_g = 1.f / g;
+  const float zeta = (be - al) * (0.5f * inv_g);
   float t;
   if (fabsf(zeta) > 1e18f)
     t = 0.5f / zeta;
   else
     t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
   if (t == 0.f) return false;
-  // cs = 1/r, sn = t/r with r = sqrt(1 + t^2), and cs - 1 = -t^2 / (r (1 + r)) to full
-  // relative precision, all correctly rounded: the rotation stays unitary to rounding, so
+  // cs = 1/r, sn = t/r with r = sqrt(1 + t^2), and cs - 1 = -t sn / (1 + r) to full
+  // relative precision, all rounded to nearest: the rotation stays unitary to rounding, so
   // the vector norms do not drift over thousands of rotations
   const float r = sqrtf(1.f + t * t);
-  const float cm = -(t * t) / (r * (1.f + r)), sn = t / r;
-  const float kr = sn * (cr / g), ki = sn * (ci / g);     // k = sn e^{i phi}
+  const float sn = t / r;
+  const float cm = -(t * sn) / (1.f + r);
+  const float kr = sn * (cr * inv_g), ki = sn * (ci * inv_g);     // k = sn e^{i phi}
   const float2 CS = f2(cm, cm), KR = f2(kr, kr), KI = f2(ki, ki), NKR = f2(-kr, -kr),
                NKI = f2(-ki, -ki);
 #pragma unroll
@@ -350,11 +352,22 @@ __global__ void __launch_bounds__(max_warps_for(CPL) * 32)
           const int slot = group + k * ngroups;
           int p = nl, q = nl;
           if (slot < bs) {
+            // the circle method without integer division: lr < nl - 1 and slot < bs
             if (r == 0) {
-              round_robin_pair(lr, slot, nl, p, q);
+              if (slot == 0) {
+                p = nl - 1;
+                q = lr;
+              } else {
+                p = lr + slot;
+                if (p >= nl - 1) p -= nl - 1;
+                q = lr - slot + nl - 1;
+                if (q >= nl - 1) q -= nl - 1;
+              }
             } else {
               p = slot;
-              q = bs + (slot + lr) % bs;
+              q = slot + lr;
+              if (q >= bs) q -= bs;
+              q += bs;
             }
           }
           // a local vector is real if its global index is below nv
@@ -599,25 +612,28 @@ int max_optin_smem() {
 }
 
 // Lanes per pair and 4-entry chunks per lane for a vector pitch of ld floats.
-bool pick_group(int ld, int& G, int& cpl) {
+// `prefer` = 0 picks the narrowest group with at most 2 chunks per lane, else 16 lanes;
+// `prefer` = 4, 8 or 16 asks for that group width (more chunks per lane = more independent
+// work per lane, fewer lanes = fewer shuffle levels and more pairs per warp).
+bool pick_group(int ld, int prefer, int& G, int& cpl) {
   const int nchunk = ld / 4;
-  const int Gs[2] = {4, 8};
-  for (int gi = 0; gi < 2; ++gi) {
-    if ((nchunk + Gs[gi] - 1) / Gs[gi] <= 2) {
-      G = Gs[gi];
-      cpl = (nchunk + G - 1) / G;
-      return true;
-    }
-  }
-  G = 16;
-  const int need = (nchunk + 15) / 16;
   const int opts[6] = {1, 2, 3, 4, 6, 8};
-  for (int o : opts)
-    if (need <= o) {
-      cpl = o;
-      return true;
-    }
-  return false;
+  auto fit = [&](int g) {
+    const int need = (nchunk + g - 1) / g;
+    if (g == 4 && need > 2) return false;
+    for (int o : opts)
+      if (need <= o) {
+        G = g;
+        cpl = o;
+        return true;
+      }
+    return false;
+  };
+  if (prefer) return fit(prefer);
+  const int Gs[2] = {4, 8};
+  for (int gi = 0; gi < 2; ++gi)
+    if ((nchunk + Gs[gi] - 1) / Gs[gi] <= 2) return fit(Gs[gi]);
+  return fit(16);
 }
 
 // A pitch of at least n floats: a multiple of 4 with pitch/4 odd (fewer bank conflicts on
@@ -628,16 +644,16 @@ int pitch_for(int n) {
   return p;
 }
 
-bool plan_with_ctas(int n1, int n2, int C, int vform, SliceShape& sh, size_t& smem) {
+bool plan_with_ctas(int n1, int n2, int C, const SliceKnobs& k, SliceShape& sh, size_t& smem) {
   const int max_optin = max_optin_smem();
   sh.rows = n1 < n2 ? 1 : 0;
   sh.nv = n1 < n2 ? n1 : n2;
   sh.len = n1 < n2 ? n2 : n1;
   sh.ld = pitch_for(sh.len);
-  sh.vform = vform ? 1 : 0;
+  sh.vform = k.vform ? 1 : 0;
   sh.ldv = sh.vform ? pitch_for(sh.nv) : 0;
   sh.rowp = sh.ld + sh.ldv;
-  if (!pick_group(sh.ld, sh.G, sh.cpl)) return false;
+  if (!pick_group(sh.ld, k.lanes, sh.G, sh.cpl)) return false;
   sh.C = C;
   sh.nb = 2 * C;
   sh.bs = (sh.nv + sh.nb - 1) / sh.nb;
@@ -652,9 +668,10 @@ bool plan_with_ctas(int n1, int n2, int C, int vform, SliceShape& sh, size_t& sm
 
 // CTAs per slice: the fewest waves of one CTA per SM, weighted by the work of one CTA
 // (1/C), without blocks thinner than kMinBlock vectors; the smallest C on ties.
-bool plan_slice(int n1, int n2, int nslices, int force, int vform, SliceShape& sh,
+bool plan_slice(int n1, int n2, int nslices, const SliceKnobs& k, SliceShape& sh,
                 size_t& smem) {
   const int nv = n1 < n2 ? n1 : n2;
+  const int force = k.ctas;
   const int cands[4] = {1, 2, 4, 8};
   double best = 1e300;
   bool found = false;
@@ -663,7 +680,7 @@ bool plan_slice(int n1, int n2, int nslices, int force, int vform, SliceShape& s
     if (!force && C > 1 && nv < 2 * C * kMinBlock) continue;
     SliceShape t;
     size_t sm;
-    if (!plan_with_ctas(n1, n2, C, vform, t, sm)) continue;
+    if (!plan_with_ctas(n1, n2, C, k, t, sm)) continue;
     const int waves = (nslices * C + kSMs - 1) / kSMs;
     const double cost = (double)waves / C;
     if (cost < best - 1e-12) {
@@ -678,7 +695,7 @@ bool plan_slice(int n1, int n2, int nslices, int force, int vform, SliceShape& s
     for (int C : cands) {
       SliceShape t;
       size_t sm;
-      if (plan_with_ctas(n1, n2, C, vform, t, sm)) {
+      if (plan_with_ctas(n1, n2, C, k, t, sm)) {
         sh = t;
         smem = sm;
         return true;
@@ -721,20 +738,27 @@ cudaError_t launch_gc(const SliceArgs& a, const SliceShape& sh, size_t smem, int
 bool jacobi_svt_supported(int n1, int n2) {
   SliceShape sh;
   size_t smem;
-  return n1 >= 1 && n2 >= 1 && plan_slice(n1, n2, 1, 0, 0, sh, smem);
+  const SliceKnobs k = {0, 0, 0};
+  return n1 >= 1 && n2 >= 1 && plan_slice(n1, n2, 1, k, sh, smem);
 }
 
-size_t jacobi_svt_scratch_bytes(int n1, int n2, int nslices, int force_ctas, int vform) {
+bool jacobi_svt_plan_ok(int n1, int n2, int nslices, const SliceKnobs& k) {
   SliceShape sh;
   size_t smem;
-  if (!plan_slice(n1, n2, nslices, force_ctas, vform, sh, smem)) return 0;
+  return n1 >= 1 && n2 >= 1 && plan_slice(n1, n2, nslices, k, sh, smem);
+}
+
+size_t jacobi_svt_scratch_bytes(int n1, int n2, int nslices, const SliceKnobs& k) {
+  SliceShape sh;
+  size_t smem;
+  if (!plan_slice(n1, n2, nslices, k, sh, smem)) return 0;
   return scratch_for(sh, (int64_t)n1 * n2, nslices);
 }
 
-int jacobi_svt_ctas_per_slice(int n1, int n2, int nslices, int force_ctas, int vform) {
+int jacobi_svt_ctas_per_slice(int n1, int n2, int nslices, const SliceKnobs& k) {
   SliceShape sh;
   size_t smem;
-  if (!plan_slice(n1, n2, nslices, force_ctas, vform, sh, smem)) return 0;
+  if (!plan_slice(n1, n2, nslices, k, sh, smem)) return 0;
   return sh.C;
 }
 
@@ -742,8 +766,7 @@ cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st) {
   if (a.nslices <= 0) return cudaSuccess;
   SliceShape sh;
   size_t smem;
-  if (!plan_slice(a.n1, a.n2, a.nslices, a.force_ctas, a.vform, sh, smem))
-    return cudaErrorInvalidValue;
+  if (!plan_slice(a.n1, a.n2, a.nslices, a.knobs, sh, smem)) return cudaErrorInvalidValue;
   if (sh.C > 1 && (a.scratch == nullptr || a.scratch_bytes < scratch_for(sh, a.N12, a.nslices)))
     return cudaErrorInvalidValue;
   const int gpw = 32 / sh.G;
@@ -756,7 +779,8 @@ cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st) {
   const int threads = nwarps * 32;
 #define TSVD_CASE(G_, C_) \
   if (sh.G == G_ && sh.cpl == C_) return launch_gc<G_, C_>(a, sh, smem, threads, st);
-  TSVD_CASE(4, 1) TSVD_CASE(4, 2) TSVD_CASE(8, 1) TSVD_CASE(8, 2)
+  TSVD_CASE(4, 1) TSVD_CASE(4, 2) TSVD_CASE(8, 1) TSVD_CASE(8, 2) TSVD_CASE(8, 3)
+  TSVD_CASE(8, 4) TSVD_CASE(8, 6) TSVD_CASE(8, 8)
   TSVD_CASE(16, 1) TSVD_CASE(16, 2) TSVD_CASE(16, 3) TSVD_CASE(16, 4) TSVD_CASE(16, 6)
   TSVD_CASE(16, 8)
 #undef TSVD_CASE

@@ -5,10 +5,13 @@
 #include "tsvd.h"
 #include "tsvd_internal.h"
 
+#include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -31,6 +34,9 @@ struct tsvd_ctx {
   std::vector<cudaEvent_t> events;
   std::vector<int> event_kind;
   size_t events_used = 0;
+  // autotuned slice-SVT plans, keyed by (n1, n2, slices per launch, V form)
+  std::map<std::array<int, 4>, SliceKnobs> tuned;
+  bool cache_loaded = false;
 };
 
 namespace {
@@ -151,6 +157,74 @@ int slice_weight(const TubeGeom& g, int kf, int kh) {
   return (selfcol && selfrow) ? 1 : 2;
 }
 
+std::array<int, 4> plan_key(tsvd_ctx* c, const Problem& p, int nslices) {
+  return {(int)p.n1, (int)p.n2, nslices, c->opts.accumulate_v};
+}
+
+// Slice-SVT plans the autotuner compares (or the single plan fixed by the options).
+std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslices) {
+  const SliceKnobs base = {c->opts.ctas_per_slice, c->opts.lanes_per_pair,
+                           c->opts.accumulate_v};
+  std::vector<SliceKnobs> out;
+  if (c->opts.autotune) {
+    const int ctas[4] = {1, 2, 4, 8};
+    const int lanes[3] = {4, 8, 16};
+    for (int C : ctas) {
+      if (base.ctas && C != base.ctas) continue;
+      for (int L : lanes) {
+        if (base.lanes && L != base.lanes) continue;
+        const SliceKnobs k = {C, L, base.vform};
+        if (jacobi_svt_plan_ok((int)p.n1, (int)p.n2, nslices, k)) out.push_back(k);
+      }
+    }
+  }
+  if (out.empty()) out.push_back(base);
+  return out;
+}
+
+// The plan a slice-SVT launch uses: the tuned one when there is one, else the options.
+SliceKnobs planned_knobs(tsvd_ctx* c, const Problem& p, int nslices) {
+  auto it = c->tuned.find(plan_key(c, p, nslices));
+  if (it != c->tuned.end()) return it->second;
+  return {c->opts.ctas_per_slice, c->opts.lanes_per_pair, c->opts.accumulate_v};
+}
+
+std::string device_name(int dev) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string s = prop.name;
+  std::replace(s.begin(), s.end(), ' ', '_');
+  return s;
+}
+
+// Autotune cache file: one line per plan, "<gpu> <n1> <n2> <slices> <vform> <ctas> <lanes>".
+void load_tune_cache(tsvd_ctx* c) {
+  c->cache_loaded = true;
+  if (!c->opts.autotune_cache) return;
+  FILE* f = std::fopen(c->opts.autotune_cache, "r");
+  if (!f) return;
+  const std::string me = device_name(c->device);
+  char gpu[256];
+  int n1, n2, ns, vf, C, L;
+  while (std::fscanf(f, "%255s %d %d %d %d %d %d", gpu, &n1, &n2, &ns, &vf, &C, &L) == 7) {
+    const SliceKnobs k = {C, L, vf};
+    if (me == gpu && jacobi_svt_plan_ok(n1, n2, ns, k)) c->tuned[{n1, n2, ns, vf}] = k;
+  }
+  std::fclose(f);
+}
+
+void store_tune_cache(tsvd_ctx* c, const std::array<int, 4>& key, const SliceKnobs& k) {
+  if (!c->opts.autotune_cache) return;
+  FILE* f = std::fopen(c->opts.autotune_cache, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %d %d %d %d\n", device_name(c->device).c_str(), key[0], key[1],
+               key[2], key[3], k.ctas, k.lanes);
+  std::fclose(f);
+}
+
 // Device workspace carved from one allocation.
 struct Workspace {
   float2* spec_a = nullptr;
@@ -185,8 +259,10 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
     for (int kf = 0; kf < g.nf; ++kf)
       if (slice_is_distinct(g, kf, kh)) c->slices_host.push_back(kf + g.nf * kh);
   w.ndistinct = (int)c->slices_host.size();
-  const size_t jbytes = jacobi_svt_scratch_bytes((int)p.n1, (int)p.n2, w.ndistinct,
-                                                 c->opts.ctas_per_slice, c->opts.accumulate_v);
+  // scratch for every plan the autotuner may try (or for the one fixed plan)
+  size_t jbytes = 0;
+  for (const SliceKnobs& k : candidate_knobs(c, p, w.ndistinct))
+    jbytes = std::max(jbytes, jacobi_svt_scratch_bytes((int)p.n1, (int)p.n2, w.ndistinct, k));
   size_t off[14], total = 0;
   auto take = [&](int i, size_t bytes) { off[i] = total; total += align_up(bytes); };
   take(0, spec);
@@ -294,9 +370,63 @@ SliceArgs slice_args(tsvd_ctx* c, const Problem& p, const Workspace& w, float ta
   s.acc = w.acc;
   s.scratch = w.jscratch;
   s.scratch_bytes = w.jscratch_bytes;
-  s.force_ctas = c->opts.ctas_per_slice;
-  s.vform = c->opts.accumulate_v;
+  s.knobs = planned_knobs(c, p, w.ndistinct);
   return s;
+}
+
+// Autotuner: before the first slice-SVT launch of a new (shape, slices, form) in this
+// context, time every candidate plan on the current input spectrum (two launches each, the
+// second timed, sweeps capped at 4 so that the comparison is per sweep), keep the fastest.
+// The candidates write the output spectrum, which the real launch then overwrites.
+tsvd_status tune_slices(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau) {
+  if (!c->opts.autotune) return TSVD_OK;
+  if (!c->cache_loaded) load_tune_cache(c);
+  const std::array<int, 4> key = plan_key(c, p, w.ndistinct);
+  if (c->tuned.count(key)) return TSVD_OK;
+  const std::vector<SliceKnobs> cands = candidate_knobs(c, p, w.ndistinct);
+  if (cands.size() == 1) {
+    c->tuned[key] = cands[0];
+    return TSVD_OK;
+  }
+  cudaEvent_t e0, e1;
+  TSVD_CUDA(c, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c, TSVD_ECUDA, "cudaEventCreate failed");
+  }
+  float best = 1e30f;
+  SliceKnobs best_k = cands[0];
+  for (const SliceKnobs& k : cands) {
+    SliceArgs s = slice_args(c, p, w, tau);
+    s.knobs = k;
+    s.max_sweeps = std::min(4, c->opts.max_sweeps);
+    s.stat = nullptr;
+    s.acc = nullptr;
+    cudaError_t e = launch_jacobi_svt(s, c->stream);
+    if (e == cudaSuccess) {
+      ++c->launches;
+      cudaEventRecord(e0, c->stream);
+      e = launch_jacobi_svt(s, c->stream);
+      cudaEventRecord(e1, c->stream);
+    }
+    if (e != cudaSuccess) {   // a plan the device cannot launch (e.g. cluster resources)
+      cudaGetLastError();
+      continue;
+    }
+    ++c->launches;
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+        ms < best) {
+      best = ms;
+      best_k = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TSVD_CUDA(c, cudaGetLastError());
+  c->tuned[key] = best_k;
+  store_tune_cache(c, key, best_k);
+  return TSVD_OK;
 }
 
 double threshold_scale(tsvd_ctx* c, const Problem& p) {
@@ -321,6 +451,10 @@ tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
     return fail(c, TSVD_EINVAL, "ctas_per_slice must be 0, 1, 2, 4 or 8");
   if (o.accumulate_v != 0 && o.accumulate_v != 1)
     return fail(c, TSVD_EINVAL, "accumulate_v must be 0 or 1");
+  if (o.lanes_per_pair != 0 && o.lanes_per_pair != 4 && o.lanes_per_pair != 8 &&
+      o.lanes_per_pair != 16)
+    return fail(c, TSVD_EINVAL, "lanes_per_pair must be 0, 4, 8 or 16");
+  if (o.autotune != 0 && o.autotune != 1) return fail(c, TSVD_EINVAL, "autotune must be 0 or 1");
   return TSVD_OK;
 }
 
@@ -424,6 +558,9 @@ tsvd_status fill_stats(tsvd_ctx* c, const Problem& p, const Workspace& w, int it
   stats->rho_final = rho;
   stats->launches = c->launches;
   stats->slice_launches = c->slice_launches;
+  const SliceKnobs k = planned_knobs(c, p, w.ndistinct);
+  stats->slice_ctas = jacobi_svt_ctas_per_slice((int)p.n1, (int)p.n2, w.ndistinct, k);
+  stats->slice_lanes = k.lanes;
   TSVD_TRY(timed_totals(c, &stats->slice_ms, &stats->tube_ms));
   if (iters <= 0) return TSVD_OK;
   SweepAccum acc;
@@ -455,6 +592,7 @@ void tsvd_default_opts(tsvd_opts* o) {
   o->rho_max = 1e10;
   o->max_sweeps = 40;
   o->jacobi_tol = 1e-6f;
+  o->autotune = 1;
 }
 
 tsvd_status tsvd_create(tsvd_ctx** out, int device, void* cuda_stream, const tsvd_opts* opts) {
@@ -529,6 +667,7 @@ tsvd_status tsvt(tsvd_ctx* c, const float* Y, float* Z, int order, const int64_t
   f.in = y;
   f.spec_out = w.spec_a;
   TSVD_TRY(run_tube(c, f, "tube pass (forward)"));
+  TSVD_TRY(tune_slices(c, p, w, tau));
   SliceArgs s = slice_args(c, p, w, tau);
   TSVD_TRY(run_slice(c, s));
   TubeArgs inv = tube_args(p, w, TUBE_INV);
@@ -603,6 +742,7 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
     TSVD_TRY(run_tube(c, t0, "completion pass"));
     for (int k = 0; k < iters; ++k) {
       const float tau = (float)(scale / rho);
+      if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
       SliceArgs s = slice_args(c, p, w, tau);
       TSVD_TRY(run_slice(c, s));
       const double rho_next = std::fmin(c->opts.mu * rho, c->opts.rho_max);
@@ -682,6 +822,7 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
     TSVD_TRY(run_tube(c, t0, "tube pass (forward)"));
     for (int k = 0; k < iters; ++k) {
       const float tau = (float)(scale / rho);
+      if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
       SliceArgs s = slice_args(c, p, w, tau);
       TSVD_TRY(run_slice(c, s));
       const double rho_next = std::fmin(c->opts.mu * rho, c->opts.rho_max);

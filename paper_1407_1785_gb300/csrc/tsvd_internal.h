@@ -79,6 +79,13 @@ struct SweepAccum {
   int pad;
 };
 
+// Tunable launch choices of the slice SVT (0 = let the planner choose).
+struct SliceKnobs {
+  int ctas;    // CTAs per slice (1, 2, 4 or 8)
+  int lanes;   // lanes per vector pair (4, 8 or 16)
+  int vform;   // 1: accumulate V and rebuild as W diag(d) V^H
+};
+
 struct SliceArgs {
   const float2* ahat;     // input spectrum, nstore slices of n1 x n2
   float2* zhat;           // output spectrum
@@ -94,17 +101,18 @@ struct SliceArgs {
   void* scratch;          // global scratch of jacobi_svt_scratch_bytes() (block exchange and
                           // partial rebuilds of multi-CTA slices); nullable = one CTA per slice
   size_t scratch_bytes;
-  int force_ctas;         // 0 = choose; else CTAs per slice (1, 2, 4 or 8)
-  int vform;              // 1: accumulate V and rebuild as W diag(d) V^H
+  SliceKnobs knobs;
 };
 
 // Returns cudaErrorInvalidValue when a slice does not fit the kernel's shared memory.
 cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st);
 // Whether launch_jacobi_svt supports an n1 x n2 slice (with scratch available).
 bool jacobi_svt_supported(int n1, int n2);
+// Whether the knobs give a valid plan for `nslices` n1 x n2 slices.
+bool jacobi_svt_plan_ok(int n1, int n2, int nslices, const SliceKnobs& k);
 // Global scratch the launch of `nslices` n1 x n2 slices needs (0 for one CTA per slice).
-size_t jacobi_svt_scratch_bytes(int n1, int n2, int nslices, int force_ctas, int vform);
+size_t jacobi_svt_scratch_bytes(int n1, int n2, int nslices, const SliceKnobs& k);
 // CTAs per slice the launch would use.
-int jacobi_svt_ctas_per_slice(int n1, int n2, int nslices, int force_ctas, int vform);
+int jacobi_svt_ctas_per_slice(int n1, int n2, int nslices, const SliceKnobs& k);
 
 }  // namespace tsvd

@@ -37,7 +37,8 @@ class Opts(ctypes.Structure):
                 ("mu", ctypes.c_double), ("rho_max", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int), ("jacobi_tol", ctypes.c_float),
                 ("timing", ctypes.c_int), ("ctas_per_slice", ctypes.c_int),
-                ("accumulate_v", ctypes.c_int)]
+                ("accumulate_v", ctypes.c_int), ("lanes_per_pair", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p)]
 
 
 class Stats(ctypes.Structure):
@@ -46,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("slice_svds", ctypes.c_int64), ("rho_final", ctypes.c_double),
                 ("tnn_last", ctypes.c_double), ("rank_last_max", ctypes.c_int),
                 ("launches", ctypes.c_int64), ("slice_launches", ctypes.c_int64),
-                ("slice_ms", ctypes.c_double), ("tube_ms", ctypes.c_double)]
+                ("slice_ms", ctypes.c_double), ("tube_ms", ctypes.c_double),
+                ("slice_ctas", ctypes.c_int), ("slice_lanes", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

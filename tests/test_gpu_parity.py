@@ -158,6 +158,30 @@ def test_tsvt_parity_accumulated_v(shape, ctas):
             check_tsvt(ctx, Y, gap_threshold(allsv, q))
 
 
+def test_autotune_cache_round_trip(tmp_path):
+    """The first completion on a new slice shape times the candidate plans and appends the
+    winner to the cache file; a second context reads it back instead of re-timing."""
+    from paper_1407_1785_gb300 import libtsvd
+    torch = _torch()
+    cache = str(tmp_path / "tune.txt").encode()
+    X, om = synth.workload_lowrank_completion(seed=5, n1=70, n2=90, n3=8, rank=3, p=0.5)
+    Mobs = (X * om).astype(np.float32)
+    m = dev(Mobs)
+    o = torch.from_numpy(colmajor(om, np.uint8)).cuda()
+    outs, launches = [], []
+    for _ in range(2):
+        with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
+                             autotune=1, autotune_cache=cache) as ctx:
+            x = torch.empty_like(m)
+            st = ctx.tnn_complete(m, o, Mobs.shape, 5, x, stats=True)
+            outs.append(host(x, Mobs.shape))
+            launches.append(st["launches"])
+    lines = open(cache.decode()).read().split()
+    assert len(lines) == 7 and lines[1:5] == ["70", "90", "5", "0"]
+    assert launches[1] < launches[0]
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_tsvt_rpca_full_size(gpu_ctx):
     """240 x 320 x 60 tubal-rank-10 tensor plus 10% sparse corruption: slices larger than one
     SM's shared memory, spread over CTA clusters."""
