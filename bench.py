@@ -248,7 +248,8 @@ def run_ours(args):
         launches += st["launches"]
         sweeps += st["total_sweeps"]
         nonconv += st["nonconverged"]
-        plan = {"ctas_per_slice": st["slice_ctas"], "lanes_per_pair": st["slice_lanes"]}
+        plan = {"ctas_per_slice": st["slice_ctas"], "lanes_per_pair": st["slice_lanes"],
+                "pairs_in_flight": st["slice_pairs_in_flight"]}
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()

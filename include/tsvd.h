@@ -106,6 +106,7 @@ typedef struct tsvd_stats {
   double tube_ms;               /* summed device time of the tube-pass launches (timing=1) */
   int slice_ctas;               /* CTAs per slice of the slice-SVT plan used */
   int slice_lanes;              /* lanes per vector pair of that plan (0 = planner default) */
+  int slice_pairs_in_flight;    /* vector pairs a lane group interleaves (0/1 = one) */
 } tsvd_stats;
 
 /* Fill *opts with the defaults listed above. */

@@ -95,6 +95,7 @@ struct SliceShape {
   int nc;     // rebuild chunk width
   int G;      // lanes per pair
   int cpl;    // 4-entry chunks per lane
+  int np;     // vector pairs a group keeps in flight (1 or 2)
   int vform;  // 1: V form rebuild
   int C;      // CTAs per slice (cluster size)
   int nb;     // vector blocks = 2C
@@ -137,95 +138,143 @@ __device__ __forceinline__ void rotate4(const float2 CS, const float2 KR, const 
   yi = f4(yi0, yi1);
 }
 
-// Rotate local vectors p and q if they are not yet orthogonal.  All G lanes of the group
-// call it with the same (p, q); returns whether a rotation was applied.  nchunk = vector
-// chunks (inner products and rotation), nchunkv = V chunks (rotation only) that follow.
-template <int G, int CPL>
-__device__ __forceinline__ bool jacobi_pair(float* __restrict__ Wr, float* __restrict__ Wi,
-                                            int rowp, int nchunk, int nchunkv, int p, int q,
-                                            int gl, float tol) {
-  float4* xr4 = reinterpret_cast<float4*>(Wr + (size_t)p * rowp);
-  float4* xi4 = reinterpret_cast<float4*>(Wi + (size_t)p * rowp);
-  float4* yr4 = reinterpret_cast<float4*>(Wr + (size_t)q * rowp);
-  float4* yi4 = reinterpret_cast<float4*>(Wi + (size_t)q * rowp);
-  float4 xr[CPL], xi[CPL], yr[CPL], yi[CPL];
-  float2 a0 = f2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0, r0 = a0, r1 = a0, g1 = a0, g2 = a0;
+// Reduce K values over the G lanes of a group, all K shuffles of a level back to back.
+template <int G, int K>
+__device__ __forceinline__ void group_sum_n(float (&v)[K]) {
 #pragma unroll
-  for (int u = 0; u < CPL; ++u) {
-    const int c = gl + G * u;
-    if (c < nchunk) {
-      xr[u] = xr4[c];
-      xi[u] = xi4[c];
-      yr[u] = yr4[c];
-      yi[u] = yi4[c];
-    } else {
-      xr[u] = xi[u] = yr[u] = yi[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    a0 = __ffma2_rn(lo(xr[u]), lo(xr[u]), a0);
-    a1 = __ffma2_rn(hi(xr[u]), hi(xr[u]), a1);
-    a0 = __ffma2_rn(lo(xi[u]), lo(xi[u]), a0);
-    a1 = __ffma2_rn(hi(xi[u]), hi(xi[u]), a1);
-    b0 = __ffma2_rn(lo(yr[u]), lo(yr[u]), b0);
-    b1 = __ffma2_rn(hi(yr[u]), hi(yr[u]), b1);
-    b0 = __ffma2_rn(lo(yi[u]), lo(yi[u]), b0);
-    b1 = __ffma2_rn(hi(yi[u]), hi(yi[u]), b1);
-    r0 = __ffma2_rn(lo(xr[u]), lo(yr[u]), r0);     // Re(x^H y) = xr.yr + xi.yi
-    r1 = __ffma2_rn(hi(xr[u]), hi(yr[u]), r1);
-    r0 = __ffma2_rn(lo(xi[u]), lo(yi[u]), r0);
-    r1 = __ffma2_rn(hi(xi[u]), hi(yi[u]), r1);
-    g1 = __ffma2_rn(lo(xr[u]), lo(yi[u]), g1);     // Im(x^H y) = xr.yi - xi.yr
-    g1 = __ffma2_rn(hi(xr[u]), hi(yi[u]), g1);
-    g2 = __ffma2_rn(lo(xi[u]), lo(yr[u]), g2);
-    g2 = __ffma2_rn(hi(xi[u]), hi(yr[u]), g2);
+  for (int o = G / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   }
-  const float al = group_sum<G>((a0.x + a0.y) + (a1.x + a1.y));
-  const float be = group_sum<G>((b0.x + b0.y) + (b1.x + b1.y));
-  const float cr = group_sum<G>((r0.x + r0.y) + (r1.x + r1.y));
-  const float ci = group_sum<G>((g1.x + g1.y) - (g2.x + g2.y));
-  const float g = sqrtf(cr * cr + ci * ci);
-  if (!(g > tol * sqrtf(al) * sqrtf(be))) return false;
-  const float inv_g = 1.f / g;
-  const float zeta = (be - al) * (0.5f * inv_g);
-  float t;
-  if (fabsf(zeta) > 1e18f)
-    t = 0.5f / zeta;
-  else
-    t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-  if (t == 0.f) return false;
-  // cs = 1/r, sn = t/r with r = sqrt(1 + t^2), and cs - 1 = -t sn / (1 + r) to full
-  // relative precision, all rounded to nearest: the rotation stays unitary to rounding, so
-  // the vector norms do not drift over thousands of rotations
-  const float r = sqrtf(1.f + t * t);
-  const float sn = t / r;
-  const float cm = -(t * sn) / (1.f + r);
-  const float kr = sn * (cr * inv_g), ki = sn * (ci * inv_g);     // k = sn e^{i phi}
-  const float2 CS = f2(cm, cm), KR = f2(kr, kr), KI = f2(ki, ki), NKR = f2(-kr, -kr),
-               NKI = f2(-ki, -ki);
+}
+
+// Rotate NP independent vector pairs (p[i], q[i]) if they are not yet orthogonal; NP = 2
+// interleaves two pairs so that one pair's inner products, shuffles and rotation-parameter
+// chain overlap the other's.  All G lanes of the group call it with the same pairs; pairs
+// with real[i] false are skipped.  nchunk = vector chunks (inner products and rotation),
+// nchunkv = V chunks (rotation only) that follow.  Returns bit 0 set when a rotation was
+// applied and bit 1 set when one of them had |cos| = |x^H y| / (||x|| ||y||) above `big`.
+template <int G, int CPL, int NP>
+__device__ __forceinline__ int jacobi_pairs(float* __restrict__ Wr, float* __restrict__ Wi,
+                                            int rowp, int nchunk, int nchunkv,
+                                            const int (&p)[NP], const int (&q)[NP],
+                                            const bool (&real)[NP], int gl, float tol,
+                                            float big) {
+  float4 xr[NP][CPL], xi[NP][CPL], yr[NP][CPL], yi[NP][CPL];
+  float2 acc[NP][8];
 #pragma unroll
-  for (int u = 0; u < CPL; ++u) {
-    const int c = gl + G * u;
-    if (c < nchunk) {
-      rotate4(CS, KR, KI, NKR, NKI, xr[u], xi[u], yr[u], yi[u]);
-      xr4[c] = xr[u];
-      xi4[c] = xi[u];
-      yr4[c] = yr[u];
-      yi4[c] = yi[u];
+  for (int i = 0; i < NP; ++i) {
+    const int nch = real[i] ? nchunk : 0;
+    const float4* xr4 = reinterpret_cast<const float4*>(Wr + (size_t)p[i] * rowp);
+    const float4* xi4 = reinterpret_cast<const float4*>(Wi + (size_t)p[i] * rowp);
+    const float4* yr4 = reinterpret_cast<const float4*>(Wr + (size_t)q[i] * rowp);
+    const float4* yi4 = reinterpret_cast<const float4*>(Wi + (size_t)q[i] * rowp);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) acc[i][a] = f2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < CPL; ++u) {
+      const int c = gl + G * u;
+      if (c < nch) {
+        xr[i][u] = xr4[c];
+        xi[i][u] = xi4[c];
+        yr[i][u] = yr4[c];
+        yi[i][u] = yi4[c];
+      } else {
+        xr[i][u] = xi[i][u] = yr[i][u] = yi[i][u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
   }
-  for (int c = nchunk + gl; c < nchunk + nchunkv; c += G) {
-    float4 vxr = xr4[c], vxi = xi4[c], vyr = yr4[c], vyi = yi4[c];
-    rotate4(CS, KR, KI, NKR, NKI, vxr, vxi, vyr, vyi);
-    xr4[c] = vxr;
-    xi4[c] = vxi;
-    yr4[c] = vyr;
-    yi4[c] = vyi;
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      float2* A = acc[i];
+      A[0] = __ffma2_rn(lo(xr[i][u]), lo(xr[i][u]), A[0]);   // ||x||^2
+      A[1] = __ffma2_rn(hi(xr[i][u]), hi(xr[i][u]), A[1]);
+      A[0] = __ffma2_rn(lo(xi[i][u]), lo(xi[i][u]), A[0]);
+      A[1] = __ffma2_rn(hi(xi[i][u]), hi(xi[i][u]), A[1]);
+      A[2] = __ffma2_rn(lo(yr[i][u]), lo(yr[i][u]), A[2]);   // ||y||^2
+      A[3] = __ffma2_rn(hi(yr[i][u]), hi(yr[i][u]), A[3]);
+      A[2] = __ffma2_rn(lo(yi[i][u]), lo(yi[i][u]), A[2]);
+      A[3] = __ffma2_rn(hi(yi[i][u]), hi(yi[i][u]), A[3]);
+      A[4] = __ffma2_rn(lo(xr[i][u]), lo(yr[i][u]), A[4]);   // Re(x^H y) = xr.yr + xi.yi
+      A[5] = __ffma2_rn(hi(xr[i][u]), hi(yr[i][u]), A[5]);
+      A[4] = __ffma2_rn(lo(xi[i][u]), lo(yi[i][u]), A[4]);
+      A[5] = __ffma2_rn(hi(xi[i][u]), hi(yi[i][u]), A[5]);
+      A[6] = __ffma2_rn(lo(xr[i][u]), lo(yi[i][u]), A[6]);   // Im(x^H y) = xr.yi - xi.yr
+      A[6] = __ffma2_rn(hi(xr[i][u]), hi(yi[i][u]), A[6]);
+      A[7] = __ffma2_rn(lo(xi[i][u]), lo(yr[i][u]), A[7]);
+      A[7] = __ffma2_rn(hi(xi[i][u]), hi(yr[i][u]), A[7]);
+    }
   }
-  return true;
+  float red[4 * NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const float2* A = acc[i];
+    red[4 * i + 0] = (A[0].x + A[0].y) + (A[1].x + A[1].y);
+    red[4 * i + 1] = (A[2].x + A[2].y) + (A[3].x + A[3].y);
+    red[4 * i + 2] = (A[4].x + A[4].y) + (A[5].x + A[5].y);
+    red[4 * i + 3] = (A[6].x + A[6].y) - (A[7].x + A[7].y);
+  }
+  group_sum_n<G, 4 * NP>(red);
+  int flags = 0;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const float al = red[4 * i + 0], be = red[4 * i + 1];
+    const float cr = red[4 * i + 2], ci = red[4 * i + 3];
+    const float g = sqrtf(cr * cr + ci * ci);
+    const float sab = sqrtf(al) * sqrtf(be);
+    if (!real[i] || !(g > tol * sab)) continue;
+    const float inv_g = 1.f / g;
+    const float zeta = (be - al) * (0.5f * inv_g);
+    float t;
+    if (fabsf(zeta) > 1e18f)
+      t = 0.5f / zeta;
+    else
+      t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+    if (t == 0.f) continue;
+    // cs = 1/r, sn = t/r with r = sqrt(1 + t^2), and cs - 1 = -t sn / (1 + r) to full
+    // relative precision, all rounded to nearest: the rotation stays unitary to rounding,
+    // so the vector norms do not drift over thousands of rotations
+    const float r = sqrtf(1.f + t * t);
+    const float sn = t / r;
+    const float cm = -(t * sn) / (1.f + r);
+    const float kr = sn * (cr * inv_g), ki = sn * (ci * inv_g);     // k = sn e^{i phi}
+    const float2 CM = f2(cm, cm), KR = f2(kr, kr), KI = f2(ki, ki), NKR = f2(-kr, -kr),
+                 NKI = f2(-ki, -ki);
+    float4* xr4 = reinterpret_cast<float4*>(Wr + (size_t)p[i] * rowp);
+    float4* xi4 = reinterpret_cast<float4*>(Wi + (size_t)p[i] * rowp);
+    float4* yr4 = reinterpret_cast<float4*>(Wr + (size_t)q[i] * rowp);
+    float4* yi4 = reinterpret_cast<float4*>(Wi + (size_t)q[i] * rowp);
+#pragma unroll
+    for (int u = 0; u < CPL; ++u) {
+      const int c = gl + G * u;
+      if (c < nchunk) {
+        rotate4(CM, KR, KI, NKR, NKI, xr[i][u], xi[i][u], yr[i][u], yi[i][u]);
+        xr4[c] = xr[i][u];
+        xi4[c] = xi[i][u];
+        yr4[c] = yr[i][u];
+        yi4[c] = yi[i][u];
+      }
+    }
+    for (int c = nchunk + gl; c < nchunk + nchunkv; c += G) {
+      float4 vxr = xr4[c], vxi = xi4[c], vyr = yr4[c], vyi = yi4[c];
+      rotate4(CM, KR, KI, NKR, NKI, vxr, vxi, vyr, vyi);
+      xr4[c] = vxr;
+      xi4[c] = vxi;
+      yr4[c] = vyr;
+      yi4[c] = vyi;
+    }
+    flags |= g > big * sab ? 3 : 1;
+  }
+  return flags;
 }
 
 // Largest CTA for a chunk count: the pair registers (16 floats per chunk) must fit.
-__host__ __device__ constexpr int max_warps_for(int cpl) {
-  return cpl <= 1 ? 32 : cpl == 2 ? 24 : cpl == 3 ? 18 : cpl == 4 ? 16 : cpl <= 6 ? 14 : 12;
+// `chunks` = chunks per lane x pairs in flight.
+__host__ __device__ constexpr int max_warps_for(int chunks) {
+  return chunks <= 2 ? 24 : chunks == 3 ? 18 : chunks == 4 ? 16
+       : chunks <= 8 ? 12 : 8;
 }
 
 // Copy block `blk` of the slice (vectors blk*bs .. blk*bs+bs-1, zero past nv) into local
@@ -278,10 +327,25 @@ __device__ __forceinline__ float* xblock(float* xbuf, const SliceShape& sh, int 
   return xbuf + (((size_t)par * sh.nb + blk) * 2 + plane) * (size_t)sh.bs * sh.rowp;
 }
 
+// Copy n floats (n a multiple of 4) with 128-bit accesses; each thread issues up to 8 loads
+// before its stores so the L2 latency of the block exchange overlaps.
 __device__ void copy_floats4(float* __restrict__ dst, const float* __restrict__ src, size_t n) {
   const float4* s4 = reinterpret_cast<const float4*>(src);
   float4* d4 = reinterpret_cast<float4*>(dst);
-  for (size_t i = threadIdx.x; i < n / 4; i += blockDim.x) d4[i] = s4[i];
+  const size_t n4 = n / 4, step = blockDim.x;
+  for (size_t base = threadIdx.x; base < n4; base += 8 * step) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const size_t i = base + u * step;
+      v[u] = i < n4 ? s4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const size_t i = base + u * step;
+      if (i < n4) d4[i] = v[u];
+    }
+  }
 }
 
 // Global index of entry p of column c of B (the slice in vector orientation).
@@ -289,8 +353,8 @@ __device__ __forceinline__ size_t b_index(const SliceShape& sh, int n1, int p, i
   return sh.rows ? (size_t)c + (size_t)n1 * p : (size_t)p + (size_t)n1 * c;
 }
 
-template <int G, int CPL>
-__global__ void __launch_bounds__(max_warps_for(CPL) * 32)
+template <int G, int CPL, int NP>
+__global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
     jacobi_svt_kernel(SliceArgs a, SliceShape sh) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int len = sh.len, ld = sh.ld, rowp = sh.rowp, nc = sh.nc, bs = sh.bs, nb = sh.nb;
@@ -338,6 +402,10 @@ __global__ void __launch_bounds__(max_warps_for(CPL) * 32)
   const int gl = lane % G;
   const int nchunk = ld / 4, nchunkv = sh.ldv / 4;
   const float tol = a.tol;
+  // Once a sweep's rotations all have |cos| <= big, the later rotations of that sweep move
+  // each pair's cosine by at most ~big^2 per rotation touching it (2 nv of them), so after
+  // the sweep every cosine is below 2 nv big^2 = tol and the checking sweep is skipped.
+  const float big = sqrtf(tol / (2.f * (float)sh.nv));
   const int trips = (bs + ngroups - 1) / ngroups;
   const size_t slotf = (size_t)bs * rowp;    // floats of one plane of one block
   int sweeps = 0, converged = 0, par = 0;
@@ -348,47 +416,56 @@ __global__ void __launch_bounds__(max_warps_for(CPL) * 32)
       const int vx0 = bx * bs, vy0 = by * bs;
       const int nlr = r == 0 ? nl - 1 : bs;   // local rounds
       for (int lr = 0; lr < nlr; ++lr) {
-        for (int k = 0; k < trips; ++k) {
-          const int slot = group + k * ngroups;
-          int p = nl, q = nl;
-          if (slot < bs) {
-            // the circle method without integer division: lr < nl - 1 and slot < bs
-            if (r == 0) {
-              if (slot == 0) {
-                p = nl - 1;
-                q = lr;
+        for (int k0 = 0; k0 < trips; k0 += NP) {
+          int p[NP], q[NP];
+          bool real[NP];
+          bool any_real = false;
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            const int slot = group + (k0 + i) * ngroups;
+            int pp = nl, qq = nl;
+            if (k0 + i < trips && slot < bs) {
+              // the circle method without integer division: lr < nl - 1 and slot < bs
+              if (r == 0) {
+                if (slot == 0) {
+                  pp = nl - 1;
+                  qq = lr;
+                } else {
+                  pp = lr + slot;
+                  if (pp >= nl - 1) pp -= nl - 1;
+                  qq = lr - slot + nl - 1;
+                  if (qq >= nl - 1) qq -= nl - 1;
+                }
               } else {
-                p = lr + slot;
-                if (p >= nl - 1) p -= nl - 1;
-                q = lr - slot + nl - 1;
-                if (q >= nl - 1) q -= nl - 1;
+                pp = slot;
+                qq = slot + lr;
+                if (qq >= bs) qq -= bs;
+                qq += bs;
               }
-            } else {
-              p = slot;
-              q = slot + lr;
-              if (q >= bs) q -= bs;
-              q += bs;
             }
-          }
-          // a local vector is real if its global index is below nv
-          bool real_pair = p < nl && q < nl;
-          if (real_pair) {
-            const int gp = p < bs ? vx0 + p : vy0 + p - bs;
-            const int gq = q < bs ? vx0 + q : vy0 + q - bs;
-            real_pair = gp < sh.nv && gq < sh.nv;
+            // a local vector is real if its global index is below nv
+            bool rp = pp < nl && qq < nl;
+            if (rp) {
+              const int gp = pp < bs ? vx0 + pp : vy0 + pp - bs;
+              const int gq = qq < bs ? vx0 + qq : vy0 + qq - bs;
+              rp = gp < sh.nv && gq < sh.nv;
+            }
+            real[i] = rp;
+            p[i] = rp ? pp : 0;
+            q[i] = rp ? qq : 1;
+            any_real |= rp;
           }
           // every lane of the warp takes part in the shuffles when any group has work
-          if (!__ballot_sync(0xffffffffu, real_pair)) continue;
-          const bool did = jacobi_pair<G, CPL>(Wr, Wi, rowp, real_pair ? nchunk : 0,
-                                               real_pair ? nchunkv : 0, real_pair ? p : 0,
-                                               real_pair ? q : 1, gl, tol);
-          rotated |= (did && real_pair) ? 1 : 0;
+          if (!__ballot_sync(0xffffffffu, any_real)) continue;
+          rotated |= jacobi_pairs<G, CPL, NP>(Wr, Wi, rowp, nchunk, nchunkv, p, q, real, gl,
+                                              tol, big);
         }
         __syncthreads();
       }
       const bool sweep_end = r == nb - 2;
       int local_any = 0;
-      if (sweep_end) local_any = __syncthreads_or(rotated);
+      if (sweep_end)
+        local_any = (__syncthreads_or(rotated & 1) ? 1 : 0) | (__syncthreads_or(rotated & 2) ? 2 : 0);
       if (C > 1) {
         // trade blocks: write both, barrier, read the next round's pair
         if (sweep_end && tid == 0) s_flag[sw & 1] = local_any;
@@ -414,7 +491,8 @@ __global__ void __launch_bounds__(max_warps_for(CPL) * 32)
       }
       if (sweep_end) {
         ++sweeps;
-        if (!local_any) converged = 1;
+        // converged: nothing rotated, or only rotations too small to leave a cosine > tol
+        if (!(local_any & 1) || !(local_any & 2)) converged = 1;
       }
     }
     if (converged) break;
@@ -654,6 +732,9 @@ bool plan_with_ctas(int n1, int n2, int C, const SliceKnobs& k, SliceShape& sh, 
   sh.ldv = sh.vform ? pitch_for(sh.nv) : 0;
   sh.rowp = sh.ld + sh.ldv;
   if (!pick_group(sh.ld, k.lanes, sh.G, sh.cpl)) return false;
+  sh.np = k.ppg == 2 ? 2 : 1;
+  if (k.ppg != 0 && k.ppg != 1 && k.ppg != 2) return false;
+  if (sh.np == 2 && (sh.G == 4 || sh.cpl > 4)) return false;   // register budget
   sh.C = C;
   sh.nb = 2 * C;
   sh.bs = (sh.nv + sh.nb - 1) / sh.nb;
@@ -710,10 +791,10 @@ size_t scratch_for(const SliceShape& sh, int64_t N12, int nslices) {
   return (size_t)nslices * (sh.xbuf_floats * sizeof(float) + (size_t)sh.C * N12 * sizeof(float2));
 }
 
-template <int G, int CPL>
+template <int G, int CPL, int NP>
 cudaError_t launch_gc(const SliceArgs& a, const SliceShape& sh, size_t smem, int threads,
                       cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(jacobi_svt_kernel<G, CPL>,
+  cudaError_t e = cudaFuncSetAttribute(jacobi_svt_kernel<G, CPL, NP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -728,7 +809,7 @@ cudaError_t launch_gc(const SliceArgs& a, const SliceShape& sh, size_t smem, int
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, jacobi_svt_kernel<G, CPL>, a, sh);
+  e = cudaLaunchKernelEx(&cfg, jacobi_svt_kernel<G, CPL, NP>, a, sh);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -738,7 +819,7 @@ cudaError_t launch_gc(const SliceArgs& a, const SliceShape& sh, size_t smem, int
 bool jacobi_svt_supported(int n1, int n2) {
   SliceShape sh;
   size_t smem;
-  const SliceKnobs k = {0, 0, 0};
+  const SliceKnobs k = {0, 0, 0, 0};
   return n1 >= 1 && n2 >= 1 && plan_slice(n1, n2, 1, k, sh, smem);
 }
 
@@ -770,19 +851,23 @@ cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st) {
   if (sh.C > 1 && (a.scratch == nullptr || a.scratch_bytes < scratch_for(sh, a.N12, a.nslices)))
     return cudaErrorInvalidValue;
   const int gpw = 32 / sh.G;
-  const int maxw = max_warps_for(sh.cpl);
+  const int per_warp = gpw * sh.np;           // pairs a warp has in flight
+  const int maxw = max_warps_for(sh.cpl * sh.np);
   // enough groups for all pairs of a local round in as few passes as fit, balanced
-  const int passes = (sh.bs + maxw * gpw - 1) / (maxw * gpw);
-  int nwarps = (sh.bs + passes * gpw - 1) / (passes * gpw);
+  const int passes = (sh.bs + maxw * per_warp - 1) / (maxw * per_warp);
+  int nwarps = (sh.bs + passes * per_warp - 1) / (passes * per_warp);
   if (nwarps < kMinWarps) nwarps = kMinWarps;
   if (nwarps > maxw) nwarps = maxw;
   const int threads = nwarps * 32;
-#define TSVD_CASE(G_, C_) \
-  if (sh.G == G_ && sh.cpl == C_) return launch_gc<G_, C_>(a, sh, smem, threads, st);
-  TSVD_CASE(4, 1) TSVD_CASE(4, 2) TSVD_CASE(8, 1) TSVD_CASE(8, 2) TSVD_CASE(8, 3)
-  TSVD_CASE(8, 4) TSVD_CASE(8, 6) TSVD_CASE(8, 8)
-  TSVD_CASE(16, 1) TSVD_CASE(16, 2) TSVD_CASE(16, 3) TSVD_CASE(16, 4) TSVD_CASE(16, 6)
-  TSVD_CASE(16, 8)
+#define TSVD_CASE(G_, C_, N_) \
+  if (sh.G == G_ && sh.cpl == C_ && sh.np == N_) \
+    return launch_gc<G_, C_, N_>(a, sh, smem, threads, st);
+  TSVD_CASE(4, 1, 1) TSVD_CASE(4, 2, 1) TSVD_CASE(8, 1, 1) TSVD_CASE(8, 2, 1)
+  TSVD_CASE(8, 3, 1) TSVD_CASE(8, 4, 1) TSVD_CASE(8, 6, 1) TSVD_CASE(8, 8, 1)
+  TSVD_CASE(16, 1, 1) TSVD_CASE(16, 2, 1) TSVD_CASE(16, 3, 1) TSVD_CASE(16, 4, 1)
+  TSVD_CASE(16, 6, 1) TSVD_CASE(16, 8, 1)
+  TSVD_CASE(8, 1, 2) TSVD_CASE(8, 2, 2) TSVD_CASE(8, 3, 2) TSVD_CASE(8, 4, 2)
+  TSVD_CASE(16, 1, 2) TSVD_CASE(16, 2, 2) TSVD_CASE(16, 3, 2) TSVD_CASE(16, 4, 2)
 #undef TSVD_CASE
   return cudaErrorInvalidValue;
 }

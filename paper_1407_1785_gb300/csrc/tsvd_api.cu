@@ -163,7 +163,7 @@ std::array<int, 4> plan_key(tsvd_ctx* c, const Problem& p, int nslices) {
 
 // Slice-SVT plans the autotuner compares (or the single plan fixed by the options).
 std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslices) {
-  const SliceKnobs base = {c->opts.ctas_per_slice, c->opts.lanes_per_pair,
+  const SliceKnobs base = {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0,
                            c->opts.accumulate_v};
   std::vector<SliceKnobs> out;
   if (c->opts.autotune) {
@@ -173,8 +173,10 @@ std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslic
       if (base.ctas && C != base.ctas) continue;
       for (int L : lanes) {
         if (base.lanes && L != base.lanes) continue;
-        const SliceKnobs k = {C, L, base.vform};
-        if (jacobi_svt_plan_ok((int)p.n1, (int)p.n2, nslices, k)) out.push_back(k);
+        for (int np = 1; np <= 2; ++np) {
+          const SliceKnobs k = {C, L, np, base.vform};
+          if (jacobi_svt_plan_ok((int)p.n1, (int)p.n2, nslices, k)) out.push_back(k);
+        }
       }
     }
   }
@@ -186,7 +188,7 @@ std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslic
 SliceKnobs planned_knobs(tsvd_ctx* c, const Problem& p, int nslices) {
   auto it = c->tuned.find(plan_key(c, p, nslices));
   if (it != c->tuned.end()) return it->second;
-  return {c->opts.ctas_per_slice, c->opts.lanes_per_pair, c->opts.accumulate_v};
+  return {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, c->opts.accumulate_v};
 }
 
 std::string device_name(int dev) {
@@ -200,7 +202,8 @@ std::string device_name(int dev) {
   return s;
 }
 
-// Autotune cache file: one line per plan, "<gpu> <n1> <n2> <slices> <vform> <ctas> <lanes>".
+// Autotune cache file: one line per plan,
+// "<gpu> <n1> <n2> <slices> <vform> <ctas> <lanes> <pairs in flight>".
 void load_tune_cache(tsvd_ctx* c) {
   c->cache_loaded = true;
   if (!c->opts.autotune_cache) return;
@@ -208,9 +211,10 @@ void load_tune_cache(tsvd_ctx* c) {
   if (!f) return;
   const std::string me = device_name(c->device);
   char gpu[256];
-  int n1, n2, ns, vf, C, L;
-  while (std::fscanf(f, "%255s %d %d %d %d %d %d", gpu, &n1, &n2, &ns, &vf, &C, &L) == 7) {
-    const SliceKnobs k = {C, L, vf};
+  int n1, n2, ns, vf, C, L, np;
+  while (std::fscanf(f, "%255s %d %d %d %d %d %d %d", gpu, &n1, &n2, &ns, &vf, &C, &L, &np) ==
+         8) {
+    const SliceKnobs k = {C, L, np, vf};
     if (me == gpu && jacobi_svt_plan_ok(n1, n2, ns, k)) c->tuned[{n1, n2, ns, vf}] = k;
   }
   std::fclose(f);
@@ -220,8 +224,8 @@ void store_tune_cache(tsvd_ctx* c, const std::array<int, 4>& key, const SliceKno
   if (!c->opts.autotune_cache) return;
   FILE* f = std::fopen(c->opts.autotune_cache, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d %d %d %d\n", device_name(c->device).c_str(), key[0], key[1],
-               key[2], key[3], k.ctas, k.lanes);
+  std::fprintf(f, "%s %d %d %d %d %d %d %d\n", device_name(c->device).c_str(), key[0], key[1],
+               key[2], key[3], k.ctas, k.lanes, k.ppg);
   std::fclose(f);
 }
 
@@ -561,6 +565,7 @@ tsvd_status fill_stats(tsvd_ctx* c, const Problem& p, const Workspace& w, int it
   const SliceKnobs k = planned_knobs(c, p, w.ndistinct);
   stats->slice_ctas = jacobi_svt_ctas_per_slice((int)p.n1, (int)p.n2, w.ndistinct, k);
   stats->slice_lanes = k.lanes;
+  stats->slice_pairs_in_flight = k.ppg;
   TSVD_TRY(timed_totals(c, &stats->slice_ms, &stats->tube_ms));
   if (iters <= 0) return TSVD_OK;
   SweepAccum acc;

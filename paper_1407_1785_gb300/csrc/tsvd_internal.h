@@ -83,6 +83,7 @@ struct SweepAccum {
 struct SliceKnobs {
   int ctas;    // CTAs per slice (1, 2, 4 or 8)
   int lanes;   // lanes per vector pair (4, 8 or 16)
+  int ppg;     // vector pairs each lane group keeps in flight (1 or 2)
   int vform;   // 1: accumulate V and rebuild as W diag(d) V^H
 };
 

@@ -131,7 +131,7 @@ extern "C" tsvd_status tsvt_static(const float* Y, float* Z, int order, const in
   const size_t spec = align_up((size_t)g.nstore * (size_t)g.N12 * sizeof(float2));
   const size_t tw = align_up((size_t)(g.nh + g.nf) * sizeof(float2));
   const size_t lst = align_up((size_t)g.nstore * sizeof(int));
-  const SliceKnobs knobs = {0, 0, 0};
+  const SliceKnobs knobs = {0, 0, 0, 0};
   const size_t jsc = align_up(jacobi_svt_scratch_bytes((int)dims[0], (int)dims[1], ndistinct, knobs));
   if (2 * spec + tw + lst + jsc > kStaticScratchBytes) return TSVD_ENOMEM;
 

@@ -48,7 +48,8 @@ class Stats(ctypes.Structure):
                 ("tnn_last", ctypes.c_double), ("rank_last_max", ctypes.c_int),
                 ("launches", ctypes.c_int64), ("slice_launches", ctypes.c_int64),
                 ("slice_ms", ctypes.c_double), ("tube_ms", ctypes.c_double),
-                ("slice_ctas", ctypes.c_int), ("slice_lanes", ctypes.c_int)]
+                ("slice_ctas", ctypes.c_int), ("slice_lanes", ctypes.c_int),
+                ("slice_pairs_in_flight", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -177,7 +177,7 @@ def test_autotune_cache_round_trip(tmp_path):
             outs.append(host(x, Mobs.shape))
             launches.append(st["launches"])
     lines = open(cache.decode()).read().split()
-    assert len(lines) == 7 and lines[1:5] == ["70", "90", "5", "0"]
+    assert len(lines) == 8 and lines[1:5] == ["70", "90", "5", "0"]
     assert launches[1] < launches[0]
     assert np.array_equal(outs[0], outs[1])
 
