@@ -88,6 +88,10 @@ typedef struct tsvd_opts {
                          by nonzero ctas_per_slice / lanes_per_pair are kept */
   const char* autotune_cache; /* nullable: text file of tuned plans keyed by GPU name and
                          slice shape, read at the first tuning and appended to after it */
+  int use_graphs;     /* 1 (default): tnn_complete / trpca capture their whole launch sequence
+                         (all iterations) into a CUDA graph on a private stream the first time
+                         a given (buffers, shape, iterations, options) combination runs with a
+                         settled plan, and replay it on the context's stream afterwards */
 } tsvd_opts;
 
 /* Counters of one ADMM solve (host struct). */

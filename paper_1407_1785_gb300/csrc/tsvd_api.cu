@@ -37,6 +37,15 @@ struct tsvd_ctx {
   // autotuned slice-SVT plans, keyed by (n1, n2, slices per launch, V form)
   std::map<std::array<int, 4>, SliceKnobs> tuned;
   bool cache_loaded = false;
+  // CUDA graphs of whole solver launch sequences, keyed by everything the launches depend on
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0, slice_launches = 0;
+    size_t events_used = 0;
+  };
+  std::map<std::vector<int64_t>, Graph> graphs;
+  cudaStream_t cap_stream = nullptr;   // private stream used only for capture
+  cudaStream_t cur = nullptr;          // stream the launch helpers enqueue on
 };
 
 namespace {
@@ -60,8 +69,10 @@ tsvd_status fail(tsvd_ctx* c, tsvd_status st, const char* fmt, ...) {
 #define TSVD_CUDA(ctx, expr)                                                              \
   do {                                                                                    \
     cudaError_t e_ = (expr);                                                              \
-    if (e_ != cudaSuccess)                                                                \
+    if (e_ != cudaSuccess) {                                                              \
+      cudaGetLastError(); /* do not leave a non-sticky error for a later launch check */  \
       return fail((ctx), TSVD_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_));             \
+    }                                                                                     \
   } while (0)
 
 // Restores the caller's current device on scope exit.
@@ -289,6 +300,9 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
       cudaFree(c->ws);
       c->ws = nullptr;
       c->ws_cap = 0;
+      // graphs captured on the old workspace must not replay
+      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+      c->graphs.clear();
     }
     void* ptr = nullptr;
     cudaError_t e = cudaMalloc(&ptr, total);
@@ -459,6 +473,8 @@ tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
       o.lanes_per_pair != 16)
     return fail(c, TSVD_EINVAL, "lanes_per_pair must be 0, 4, 8 or 16");
   if (o.autotune != 0 && o.autotune != 1) return fail(c, TSVD_EINVAL, "autotune must be 0 or 1");
+  if (o.use_graphs != 0 && o.use_graphs != 1)
+    return fail(c, TSVD_EINVAL, "use_graphs must be 0 or 1");
   return TSVD_OK;
 }
 
@@ -507,6 +523,7 @@ tsvd_status launch(tsvd_ctx* c, cudaError_t e, const char* what) {
   } while (0)
 
 void begin_call(tsvd_ctx* c) {
+  c->cur = c->stream;
   c->err.clear();
   c->launches = 0;
   c->slice_launches = 0;
@@ -523,21 +540,95 @@ tsvd_status record_event(tsvd_ctx* c, int kind) {
     c->event_kind.push_back(kind);
   }
   c->event_kind[c->events_used] = kind;
-  TSVD_CUDA(c, cudaEventRecord(c->events[c->events_used++], c->stream));
+  // while capturing, an ordinary record only marks a dependency; an external record becomes
+  // an event node of the graph, re-recorded at every replay
+  if (c->cur != c->stream && c->cur == c->cap_stream)
+    TSVD_CUDA(c, cudaEventRecordWithFlags(c->events[c->events_used++], c->cur,
+                                          cudaEventRecordExternal));
+  else
+    TSVD_CUDA(c, cudaEventRecord(c->events[c->events_used++], c->cur));
   return TSVD_OK;
 }
 
+// Launch helpers: they enqueue on c->cur, which is the context's stream or, while a solver's
+// launch sequence is being captured into a graph, the private capture stream.
 tsvd_status run_tube(tsvd_ctx* c, const TubeArgs& a, const char* what) {
   TSVD_TRY(record_event(c, 1));
-  TSVD_TRY(launch(c, launch_tube_pass(a, c->stream), what));
+  TSVD_TRY(launch(c, launch_tube_pass(a, c->cur), what));
   return record_event(c, 1);
 }
 
 tsvd_status run_slice(tsvd_ctx* c, const SliceArgs& a) {
   TSVD_TRY(record_event(c, 0));
-  TSVD_TRY(launch(c, launch_jacobi_svt(a, c->stream), "slice SVT"));
+  TSVD_TRY(launch(c, launch_jacobi_svt(a, c->cur), "slice SVT"));
   ++c->slice_launches;
   return record_event(c, 0);
+}
+
+// Runs `body` (which only enqueues kernels through the helpers above) directly, or -- when
+// graphs are enabled and the launch sequence cannot change (`capturable`: no autotuning or
+// host synchronisation left in it) -- replays the CUDA graph cached under `key`, capturing
+// it on first use.  Key = everything the launches depend on (buffers, shape, iteration
+// count, options, workspace, plan).
+template <class F>
+tsvd_status run_maybe_graph(tsvd_ctx* c, const std::vector<int64_t>& key, bool capturable,
+                            F&& body) {
+  c->cur = c->stream;
+  if (!c->opts.use_graphs || !capturable) return body();
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    if (!c->cap_stream)
+      TSVD_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    if (c->graphs.size() >= 8) {   // keep a few recent graphs only
+      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+      c->graphs.clear();
+    }
+    const int64_t l0 = c->launches, s0 = c->slice_launches;
+    const size_t e0 = c->events_used;
+    TSVD_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    c->cur = c->cap_stream;
+    const tsvd_status st = body();
+    c->cur = c->stream;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (st != TSVD_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ec != cudaSuccess) return fail(c, TSVD_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+    tsvd_ctx::Graph g;
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(c, TSVD_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+    g.launches = c->launches - l0;
+    g.slice_launches = c->slice_launches - s0;
+    g.events_used = c->events_used - e0;
+    it = c->graphs.emplace(key, g).first;
+    c->launches = l0;
+    c->slice_launches = s0;
+    c->events_used = e0;
+  }
+  TSVD_CUDA(c, cudaGraphLaunch(it->second.exec, c->stream));
+  c->launches += it->second.launches;
+  c->slice_launches += it->second.slice_launches;
+  c->events_used += it->second.events_used;
+  return TSVD_OK;
+}
+
+std::vector<int64_t> solver_key(tsvd_ctx* c, int kind, const Problem& p, int iters,
+                                std::initializer_list<const void*> ptrs, const SliceKnobs& k) {
+  std::vector<int64_t> key = {kind, p.order, p.n1, p.n2, p.n3, p.n4, iters,
+                              (int64_t)(intptr_t)c->ws, (int64_t)c->ws_cap, k.ctas, k.lanes,
+                              k.ppg, k.vform, c->opts.tnn_scale, c->opts.sparse_mode,
+                              c->opts.max_sweeps, c->opts.timing};
+  for (const void* q : ptrs) key.push_back((int64_t)(intptr_t)q);
+  double d[4] = {c->opts.rho0, c->opts.mu, c->opts.rho_max, (double)c->opts.jacobi_tol};
+  for (double v : d) {
+    int64_t bits;
+    std::memcpy(&bits, &v, sizeof bits);
+    key.push_back(bits);
+  }
+  return key;
 }
 
 // Sum of the timed pairs per kind (waits for the stream).
@@ -598,6 +689,7 @@ void tsvd_default_opts(tsvd_opts* o) {
   o->max_sweeps = 40;
   o->jacobi_tol = 1e-6f;
   o->autotune = 1;
+  o->use_graphs = 1;
 }
 
 tsvd_status tsvd_create(tsvd_ctx** out, int device, void* cuda_stream, const tsvd_opts* opts) {
@@ -633,6 +725,8 @@ tsvd_status tsvd_destroy(tsvd_ctx* c) {
     cudaFree(c->ws);
   }
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return st;
 }
@@ -736,40 +830,49 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
     TSVD_TRY(launch(c, launch_project_observed(m, om, x, p.N, c->stream), "project"));
     if (z) TSVD_CUDA(c, cudaMemsetAsync(z, 0, bytes, c->stream));
   } else {
-    // iteration 0: X = P_Omega(M), Q = 0, V = X + Q
-    TubeArgs t0 = tube_args(p, w, TUBE_COMPLETE);
-    t0.in = w.yn;
-    t0.state = w.state;
-    t0.spec_out = w.spec_a;
-    t0.first = 1;
-    t0.write_out = iters == 1;
-    t0.out0 = x;
-    TSVD_TRY(run_tube(c, t0, "completion pass"));
-    for (int k = 0; k < iters; ++k) {
-      const float tau = (float)(scale / rho);
-      if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
-      SliceArgs s = slice_args(c, p, w, tau);
-      TSVD_TRY(run_slice(c, s));
-      const double rho_next = std::fmin(c->opts.mu * rho, c->opts.rho_max);
-      if (k + 1 < iters) {
-        TubeArgs t = tube_args(p, w, TUBE_COMPLETE);
-        t.in = w.yn;
-        t.state = w.state;
-        t.spec_in = w.spec_b;
-        t.spec_out = w.spec_a;
-        t.ratio = (float)(rho / rho_next);
-        t.write_out = (k + 2 == iters);
-        t.out0 = x;
-        TSVD_TRY(run_tube(c, t, "completion pass"));
+    const bool tuned = !c->opts.autotune || c->tuned.count(plan_key(c, p, w.ndistinct));
+    const SliceKnobs kn = planned_knobs(c, p, w.ndistinct);
+    const std::vector<int64_t> key = solver_key(c, 1, p, iters, {m, om, x, z}, kn);
+    auto body = [&]() -> tsvd_status {
+      double r = c->opts.rho0;
+      // iteration 0: X = P_Omega(M), Q = 0, V = X + Q
+      TubeArgs t0 = tube_args(p, w, TUBE_COMPLETE);
+      t0.in = w.yn;
+      t0.state = w.state;
+      t0.spec_out = w.spec_a;
+      t0.first = 1;
+      t0.write_out = iters == 1;
+      t0.out0 = x;
+      TSVD_TRY(run_tube(c, t0, "completion pass"));
+      for (int k = 0; k < iters; ++k) {
+        const float tau = (float)(scale / r);
+        if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
+        SliceArgs s = slice_args(c, p, w, tau);
+        TSVD_TRY(run_slice(c, s));
+        const double r_next = std::fmin(c->opts.mu * r, c->opts.rho_max);
+        if (k + 1 < iters) {
+          TubeArgs t = tube_args(p, w, TUBE_COMPLETE);
+          t.in = w.yn;
+          t.state = w.state;
+          t.spec_in = w.spec_b;
+          t.spec_out = w.spec_a;
+          t.ratio = (float)(r / r_next);
+          t.write_out = (k + 2 == iters);
+          t.out0 = x;
+          TSVD_TRY(run_tube(c, t, "completion pass"));
+        }
+        r = r_next;
       }
-      rho = rho_next;
-    }
-    if (z) {
-      TubeArgs inv = tube_args(p, w, TUBE_INV);
-      inv.spec_in = w.spec_b;
-      inv.out0 = z;
-      TSVD_TRY(run_tube(c, inv, "tube pass (inverse)"));
-    }
+      if (z) {
+        TubeArgs inv = tube_args(p, w, TUBE_INV);
+        inv.spec_in = w.spec_b;
+        inv.out0 = z;
+        TSVD_TRY(run_tube(c, inv, "tube pass (inverse)"));
+      }
+      return TSVD_OK;
+    };
+    TSVD_TRY(run_maybe_graph(c, key, tuned, body));
+    for (int k = 0; k < iters; ++k) rho = std::fmin(c->opts.mu * rho, c->opts.rho_max);
   }
   if (kx == 1) TSVD_CUDA(c, cudaMemcpyAsync(X_out, x, bytes, cudaMemcpyDeviceToHost, c->stream));
   if (z && kzz == 1) TSVD_CUDA(c, cudaMemcpyAsync(Z_out, z, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -820,32 +923,44 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
     TSVD_CUDA(c, cudaMemsetAsync(l, 0, bytes, c->stream));
     TSVD_CUDA(c, cudaMemsetAsync(sp, 0, bytes, c->stream));
   } else {
-    // iteration 0: S = W = 0, so the t-SVT input is M itself
-    TubeArgs t0 = tube_args(p, w, TUBE_FWD);
-    t0.in = m;
-    t0.spec_out = w.spec_a;
-    TSVD_TRY(run_tube(c, t0, "tube pass (forward)"));
-    for (int k = 0; k < iters; ++k) {
-      const float tau = (float)(scale / rho);
-      if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
-      SliceArgs s = slice_args(c, p, w, tau);
-      TSVD_TRY(run_slice(c, s));
-      const double rho_next = std::fmin(c->opts.mu * rho, c->opts.rho_max);
-      TubeArgs t = tube_args(p, w, TUBE_RPCA);
-      t.in = m;
-      t.state = w.state;
-      t.spec_in = w.spec_b;
-      t.spec_out = w.spec_a;
-      t.ratio = (float)(rho / rho_next);
-      t.kappa = (float)((double)lambda / rho);
-      t.first = k == 0;
-      t.last = k + 1 == iters;
-      t.out0 = l;
-      t.out1 = sp;
-      t.tube_sparse = c->opts.sparse_mode == TSVD_SPARSE_TUBE;
-      TSVD_TRY(run_tube(c, t, "RPCA pass"));
-      rho = rho_next;
-    }
+    const bool tuned = !c->opts.autotune || c->tuned.count(plan_key(c, p, w.ndistinct));
+    const SliceKnobs kn = planned_knobs(c, p, w.ndistinct);
+    std::vector<int64_t> key = solver_key(c, 2, p, iters, {m, l, sp}, kn);
+    int64_t lbits;
+    std::memcpy(&lbits, &lambda, sizeof lambda);
+    key.push_back(lbits);
+    auto body = [&]() -> tsvd_status {
+      double r = c->opts.rho0;
+      // iteration 0: S = W = 0, so the t-SVT input is M itself
+      TubeArgs t0 = tube_args(p, w, TUBE_FWD);
+      t0.in = m;
+      t0.spec_out = w.spec_a;
+      TSVD_TRY(run_tube(c, t0, "tube pass (forward)"));
+      for (int k = 0; k < iters; ++k) {
+        const float tau = (float)(scale / r);
+        if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
+        SliceArgs s = slice_args(c, p, w, tau);
+        TSVD_TRY(run_slice(c, s));
+        const double r_next = std::fmin(c->opts.mu * r, c->opts.rho_max);
+        TubeArgs t = tube_args(p, w, TUBE_RPCA);
+        t.in = m;
+        t.state = w.state;
+        t.spec_in = w.spec_b;
+        t.spec_out = w.spec_a;
+        t.ratio = (float)(r / r_next);
+        t.kappa = (float)((double)lambda / r);
+        t.first = k == 0;
+        t.last = k + 1 == iters;
+        t.out0 = l;
+        t.out1 = sp;
+        t.tube_sparse = c->opts.sparse_mode == TSVD_SPARSE_TUBE;
+        TSVD_TRY(run_tube(c, t, "RPCA pass"));
+        r = r_next;
+      }
+      return TSVD_OK;
+    };
+    TSVD_TRY(run_maybe_graph(c, key, tuned, body));
+    for (int k = 0; k < iters; ++k) rho = std::fmin(c->opts.mu * rho, c->opts.rho_max);
   }
   if (kl == 1) TSVD_CUDA(c, cudaMemcpyAsync(L_out, l, bytes, cudaMemcpyDeviceToHost, c->stream));
   if (ks == 1) TSVD_CUDA(c, cudaMemcpyAsync(S_out, sp, bytes, cudaMemcpyDeviceToHost, c->stream));

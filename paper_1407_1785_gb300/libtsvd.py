@@ -38,7 +38,8 @@ class Opts(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int), ("jacobi_tol", ctypes.c_float),
                 ("timing", ctypes.c_int), ("ctas_per_slice", ctypes.c_int),
                 ("accumulate_v", ctypes.c_int), ("lanes_per_pair", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p)]
+                ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p),
+                ("use_graphs", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

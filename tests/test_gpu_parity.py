@@ -182,6 +182,33 @@ def test_autotune_cache_round_trip(tmp_path):
     assert np.array_equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("kind", ["complete", "rpca"])
+def test_graph_replay_matches_direct_launches(kind):
+    """Calls 1 (direct, autotunes), 2 (captured into a CUDA graph) and 3 (graph replay) agree
+    bit for bit with a context that never uses graphs; stats survive the replay."""
+    from paper_1407_1785_gb300 import libtsvd
+    torch = _torch()
+    X, om = synth.workload_lowrank_completion(seed=6, n1=40, n2=52, n3=10, rank=3, p=0.5)
+    M = (X * om).astype(np.float32) if kind == "complete" else X.astype(np.float32)
+    m = dev(M)
+    o = torch.from_numpy(colmajor(om, np.uint8)).cuda()
+    outs = []
+    for graphs in (0, 1):
+        with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
+                             use_graphs=graphs, timing=1) as ctx:
+            a, b = torch.empty_like(m), torch.empty_like(m)
+            for call in range(3):
+                if kind == "complete":
+                    st = ctx.tnn_complete(m, o, M.shape, 12, a, b, stats=True)
+                else:
+                    st = ctx.trpca(m, M.shape, 0.05, 12, a, b, stats=True)
+                outs.append((host(a, M.shape), host(b, M.shape)))
+                assert st["slice_launches"] == 12
+                assert st["slice_ms"] > 0 and st["tube_ms"] > 0
+    for x, y in outs[1:]:
+        assert np.array_equal(x, outs[0][0]) and np.array_equal(y, outs[0][1])
+
+
 def test_tsvt_rpca_full_size(gpu_ctx):
     """240 x 320 x 60 tubal-rank-10 tensor plus 10% sparse corruption: slices larger than one
     SM's shared memory, spread over CTA clusters."""
