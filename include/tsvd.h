@@ -164,6 +164,32 @@ tsvd_status tnn_complete(tsvd_ctx* ctx, const float* M_obs, const uint8_t* omega
 tsvd_status trpca(tsvd_ctx* ctx, const float* M, int order, const int64_t* dims, float lambda,
                   int iters, float* L_out, float* S_out, tsvd_stats* stats);
 
+/* One tensor of a batched solve (tsvd_solve_batched). */
+enum { TSVD_PROBLEM_COMPLETE = 1, TSVD_PROBLEM_RPCA = 2 };
+typedef struct tsvd_problem {
+  int kind;             /* TSVD_PROBLEM_COMPLETE or TSVD_PROBLEM_RPCA */
+  int order;            /* 3 or 4 */
+  int64_t dims[4];      /* n1, n2, n3[, n4] */
+  const float* M;       /* completion: observed tensor (read on omega); RPCA: M */
+  const uint8_t* omega; /* completion: uint8 mask; RPCA: unused (NULL) */
+  float lambda;         /* RPCA: sparse weight (> 0); completion: unused */
+  float* out0;          /* completion: X; RPCA: L */
+  float* out1;          /* completion: Z (nullable); RPCA: S */
+} tsvd_problem;
+
+/* Batched solve: runs `iters` ADMM iterations of every problem -- TNN completion (as
+ * tnn_complete) or tensor RPCA (as trpca) -- for `count` tensors of any shapes, with the
+ * context's options (one rho schedule for all).  All pointers must be device memory on the
+ * context's device.  Each tensor's iterations form an independent chain of kernels (its own
+ * slice-SVT plan); the chains of all tensors are issued on parallel stream branches and, with
+ * use_graphs, captured once into one CUDA graph that later calls with the same problems
+ * replay, so the tensors overlap on the GPU.  Plans come from the context's autotune cache
+ * for shapes tuned earlier, else from the planner (no tuning inside a batch).  stats
+ * (nullable, host) sums the counters over the batch.  Errors as tnn_complete / trpca, per
+ * problem; nothing is launched if any problem is invalid. */
+tsvd_status tsvd_solve_batched(tsvd_ctx* ctx, int count, const tsvd_problem* problems, int iters,
+                               tsvd_stats* stats);
+
 /* The paper has no counterpart to this entry point; it exists for callers that cannot
  * allocate device memory.  Some callers cannot call cudaMalloc: a process that has handed the
  * whole device memory budget to its own pool allocator (a later cudaMalloc fails or fragments

@@ -46,6 +46,11 @@ struct tsvd_ctx {
   std::map<std::vector<int64_t>, Graph> graphs;
   cudaStream_t cap_stream = nullptr;   // private stream used only for capture
   cudaStream_t cur = nullptr;          // stream the launch helpers enqueue on
+  bool capturing = false;              // a launch sequence is being captured
+  // batched solves: parallel stream branches and their fork / join events
+  std::vector<cudaStream_t> branches;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -542,7 +547,7 @@ tsvd_status record_event(tsvd_ctx* c, int kind) {
   c->event_kind[c->events_used] = kind;
   // while capturing, an ordinary record only marks a dependency; an external record becomes
   // an event node of the graph, re-recorded at every replay
-  if (c->cur != c->stream && c->cur == c->cap_stream)
+  if (c->capturing)
     TSVD_CUDA(c, cudaEventRecordWithFlags(c->events[c->events_used++], c->cur,
                                           cudaEventRecordExternal));
   else
@@ -587,7 +592,9 @@ tsvd_status run_maybe_graph(tsvd_ctx* c, const std::vector<int64_t>& key, bool c
     const size_t e0 = c->events_used;
     TSVD_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     c->cur = c->cap_stream;
+    c->capturing = true;
     const tsvd_status st = body();
+    c->capturing = false;
     c->cur = c->stream;
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &graph);
@@ -673,6 +680,116 @@ tsvd_status fill_stats(tsvd_ctx* c, const Problem& p, const Workspace& w, int it
   return TSVD_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Batched solves: one workspace region per tensor, one kernel chain per tensor.
+// ---------------------------------------------------------------------------------------------
+struct BatchItem {
+  const tsvd_problem* src = nullptr;
+  Problem p;
+  Workspace w;
+  SliceKnobs kn{};
+  std::vector<float2> twid;
+  std::vector<int> slices;
+};
+
+// Carves the regions of one tensor from `base` (nullptr: only measure); returns its bytes.
+size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base) {
+  const TubeGeom& g = it.p.g;
+  it.slices.clear();
+  for (int kh = 0; kh < g.hh; ++kh)
+    for (int kf = 0; kf < g.nf; ++kf)
+      if (slice_is_distinct(g, kf, kh)) it.slices.push_back(kf + g.nf * kh);
+  it.w.ndistinct = (int)it.slices.size();
+  it.kn = planned_knobs(c, it.p, it.w.ndistinct);
+  const size_t spec = (size_t)g.nstore * g.N12 * sizeof(float2);
+  const size_t real = (size_t)it.p.N * sizeof(float);
+  const bool complete = it.src->kind == TSVD_PROBLEM_COMPLETE;
+  const size_t jbytes = jacobi_svt_scratch_bytes((int)it.p.n1, (int)it.p.n2, it.w.ndistinct, it.kn);
+  size_t total = 0;
+  auto take = [&](size_t bytes) {
+    char* ptr = base ? base + total : nullptr;
+    total += align_up(bytes);
+    return ptr;
+  };
+  it.w.spec_a = reinterpret_cast<float2*>(take(spec));
+  it.w.spec_b = reinterpret_cast<float2*>(take(spec));
+  it.w.state = reinterpret_cast<float*>(take(real));
+  it.w.yn = complete ? reinterpret_cast<float*>(take(real)) : nullptr;
+  it.w.twid = reinterpret_cast<float2*>(take((size_t)(g.nh + g.nf) * sizeof(float2)));
+  it.w.slices = reinterpret_cast<int*>(take((size_t)g.nstore * sizeof(int)));
+  it.w.stat = reinterpret_cast<SliceStat*>(take((size_t)g.nstore * sizeof(SliceStat)));
+  it.w.acc = reinterpret_cast<SweepAccum*>(take(sizeof(SweepAccum)));
+  it.w.jscratch = jbytes ? take(jbytes) : nullptr;
+  it.w.jscratch_bytes = jbytes;
+  return total;
+}
+
+// The whole launch chain of one tensor (all iterations) on c->cur.
+tsvd_status enqueue_item(tsvd_ctx* c, const BatchItem& it, int iters) {
+  const Problem& p = it.p;
+  const Workspace& w = it.w;
+  const tsvd_problem& q = *it.src;
+  const double scale = threshold_scale(c, p);
+  double r = c->opts.rho0;
+  if (q.kind == TSVD_PROBLEM_COMPLETE) {
+    TubeArgs t0 = tube_args(p, w, TUBE_COMPLETE);
+    t0.in = w.yn;
+    t0.state = w.state;
+    t0.spec_out = w.spec_a;
+    t0.first = 1;
+    t0.write_out = iters == 1;
+    t0.out0 = q.out0;
+    TSVD_TRY(run_tube(c, t0, "completion pass"));
+  } else {
+    TubeArgs t0 = tube_args(p, w, TUBE_FWD);
+    t0.in = q.M;
+    t0.spec_out = w.spec_a;
+    TSVD_TRY(run_tube(c, t0, "tube pass (forward)"));
+  }
+  for (int k = 0; k < iters; ++k) {
+    const float tau = (float)(scale / r);
+    SliceArgs s = slice_args(c, p, w, tau);
+    s.knobs = it.kn;
+    TSVD_TRY(run_slice(c, s));
+    const double r_next = std::fmin(c->opts.mu * r, c->opts.rho_max);
+    if (q.kind == TSVD_PROBLEM_COMPLETE) {
+      if (k + 1 < iters) {
+        TubeArgs t = tube_args(p, w, TUBE_COMPLETE);
+        t.in = w.yn;
+        t.state = w.state;
+        t.spec_in = w.spec_b;
+        t.spec_out = w.spec_a;
+        t.ratio = (float)(r / r_next);
+        t.write_out = (k + 2 == iters);
+        t.out0 = q.out0;
+        TSVD_TRY(run_tube(c, t, "completion pass"));
+      }
+    } else {
+      TubeArgs t = tube_args(p, w, TUBE_RPCA);
+      t.in = q.M;
+      t.state = w.state;
+      t.spec_in = w.spec_b;
+      t.spec_out = w.spec_a;
+      t.ratio = (float)(r / r_next);
+      t.kappa = (float)((double)q.lambda / r);
+      t.first = k == 0;
+      t.last = k + 1 == iters;
+      t.out0 = q.out0;
+      t.out1 = q.out1;
+      t.tube_sparse = c->opts.sparse_mode == TSVD_SPARSE_TUBE;
+      TSVD_TRY(run_tube(c, t, "RPCA pass"));
+    }
+    r = r_next;
+  }
+  if (q.kind == TSVD_PROBLEM_COMPLETE && q.out1) {
+    TubeArgs inv = tube_args(p, w, TUBE_INV);
+    inv.spec_in = w.spec_b;
+    inv.out0 = q.out1;
+    TSVD_TRY(run_tube(c, inv, "tube pass (inverse)"));
+  }
+  return TSVD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -727,6 +844,9 @@ tsvd_status tsvd_destroy(tsvd_ctx* c) {
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (cudaStream_t s : c->branches) cudaStreamDestroy(s);
+  for (cudaEvent_t e : c->joins) cudaEventDestroy(e);
+  if (c->fork) cudaEventDestroy(c->fork);
   delete c;
   return st;
 }
@@ -966,6 +1086,203 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
   if (ks == 1) TSVD_CUDA(c, cudaMemcpyAsync(S_out, sp, bytes, cudaMemcpyDeviceToHost, c->stream));
   if (kl == 1 || ks == 1) TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
   TSVD_TRY(fill_stats(c, p, w, iters, rho, stats));
+  TSVD_CUDA(c, cudaGetLastError());
+  return TSVD_OK;
+}
+
+tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, int iters,
+                               tsvd_stats* stats) {
+  if (!c) return TSVD_EINVAL;
+  begin_call(c);
+  if (count < 0 || (count > 0 && !problems)) return fail(c, TSVD_EINVAL, "bad problem list");
+  if (iters < 0) return fail(c, TSVD_EINVAL, "iters must be >= 0");
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
+  std::vector<BatchItem> items((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    const tsvd_problem& q = problems[i];
+    BatchItem& it = items[(size_t)i];
+    it.src = &q;
+    if (q.kind != TSVD_PROBLEM_COMPLETE && q.kind != TSVD_PROBLEM_RPCA)
+      return fail(c, TSVD_EINVAL, "problem %d: bad kind %d", i, q.kind);
+    tsvd_status st = make_problem(c, q.order, q.dims, it.p);
+    if (st != TSVD_OK) return fail(c, st, "problem %d: %s", i, c->err.c_str());
+    const bool complete = q.kind == TSVD_PROBLEM_COMPLETE;
+    if (!q.M || !q.out0 || (complete && !q.omega) || (!complete && !q.out1))
+      return fail(c, TSVD_EINVAL, "problem %d: missing buffer", i);
+    if (!complete && (!(q.lambda > 0.f) || !std::isfinite(q.lambda)))
+      return fail(c, TSVD_EINVAL, "problem %d: lambda must be finite and > 0", i);
+    const void* ptrs[4] = {q.M, complete ? (const void*)q.omega : nullptr, q.out0, q.out1};
+    for (const void* ptr : ptrs)
+      if (ptr && pointer_kind(ptr, c->device) != 0)
+        return fail(c, TSVD_EINVAL, "problem %d: batched tensors must be device memory", i);
+  }
+  if (count == 0) {
+    if (stats) std::memset(stats, 0, sizeof *stats);
+    return TSVD_OK;
+  }
+  // one allocation for every tensor's regions plus the batch's non-finite counters
+  size_t total = 0;
+  std::vector<size_t> offs((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    offs[(size_t)i] = total;
+    total += carve_item(c, items[(size_t)i], nullptr);
+  }
+  const size_t bad_off = total;
+  total += align_up((size_t)count * sizeof(int));
+  if (total > c->ws_cap) {
+    if (c->ws) {
+      TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+      cudaFree(c->ws);
+      c->ws = nullptr;
+      c->ws_cap = 0;
+      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+      c->graphs.clear();
+    }
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, TSVD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", total, cudaGetErrorString(e));
+    }
+    c->ws = static_cast<char*>(ptr);
+    c->ws_cap = total;
+  }
+  int* bad = reinterpret_cast<int*>(c->ws + bad_off);
+  TSVD_CUDA(c, cudaMemsetAsync(bad, 0, (size_t)count * sizeof(int), c->stream));
+  for (int i = 0; i < count; ++i) {
+    BatchItem& it = items[(size_t)i];
+    carve_item(c, it, c->ws + offs[(size_t)i]);
+    const TubeGeom& g = it.p.g;
+    it.twid.resize((size_t)(g.nh + g.nf));
+    for (int pass = 0; pass < 2; ++pass) {   // same FP64 tables as the single-tensor calls
+      const int n = pass ? g.nf : g.nh;
+      float2* dst = it.twid.data() + (pass ? g.nh : 0);
+      for (int m = 0; m < n; ++m) {
+        double cr, sr;
+        if (m == 0) { cr = 1; sr = 0; }
+        else if (2 * m == n) { cr = -1; sr = 0; }
+        else if (4 * m == n) { cr = 0; sr = 1; }
+        else if (4 * m == 3 * n) { cr = 0; sr = -1; }
+        else {
+          const double a = 2.0 * M_PI * (double)m / (double)n;
+          cr = std::cos(a);
+          sr = std::sin(a);
+        }
+        dst[m] = make_float2((float)cr, (float)sr);
+      }
+    }
+    TSVD_CUDA(c, cudaMemcpyAsync(it.w.twid, it.twid.data(), it.twid.size() * sizeof(float2),
+                                 cudaMemcpyHostToDevice, c->stream));
+    TSVD_CUDA(c, cudaMemcpyAsync(it.w.slices, it.slices.data(), it.slices.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, c->stream));
+    TSVD_CUDA(c, cudaMemsetAsync(it.w.acc, 0, sizeof(SweepAccum), c->stream));
+    TSVD_CUDA(c, cudaMemsetAsync(it.w.stat, 0, (size_t)g.nstore * sizeof(SliceStat), c->stream));
+    const tsvd_problem& q = *it.src;
+    if (q.kind == TSVD_PROBLEM_COMPLETE)
+      TSVD_TRY(launch(c, launch_encode_observed(q.M, q.omega, it.w.yn, it.p.N, bad + i, c->stream),
+                      "encode observed"));
+    else
+      TSVD_TRY(launch(c, launch_count_nonfinite(q.M, it.p.N, bad + i, c->stream), "check input"));
+  }
+  std::vector<int> bad_h((size_t)count);
+  TSVD_CUDA(c, cudaMemcpyAsync(bad_h.data(), bad, (size_t)count * sizeof(int),
+                               cudaMemcpyDeviceToHost, c->stream));
+  TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < count; ++i)
+    if (bad_h[(size_t)i]) return fail(c, TSVD_EINVAL, "problem %d: %d entries are not finite", i, bad_h[(size_t)i]);
+
+  double rho = c->opts.rho0;
+  for (int k = 0; k < iters; ++k) rho = std::fmin(c->opts.mu * rho, c->opts.rho_max);
+  if (iters == 0) {
+    for (const BatchItem& it : items) {
+      const tsvd_problem& q = *it.src;
+      const size_t bytes = (size_t)it.p.N * sizeof(float);
+      if (q.kind == TSVD_PROBLEM_COMPLETE) {
+        TSVD_TRY(launch(c, launch_project_observed(q.M, q.omega, q.out0, it.p.N, c->stream), "project"));
+        if (q.out1) TSVD_CUDA(c, cudaMemsetAsync(q.out1, 0, bytes, c->stream));
+      } else {
+        TSVD_CUDA(c, cudaMemsetAsync(q.out0, 0, bytes, c->stream));
+        TSVD_CUDA(c, cudaMemsetAsync(q.out1, 0, bytes, c->stream));
+      }
+    }
+  } else {
+    // stream branches: tensor i runs on branch i mod B, all branches fork from and join the
+    // issuing stream, so the tensors' chains overlap on the GPU
+    const int nbr = std::min(count, 16);
+    while ((int)c->branches.size() < nbr) {
+      cudaStream_t s;
+      cudaEvent_t e;
+      TSVD_CUDA(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      TSVD_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      c->branches.push_back(s);
+      c->joins.push_back(e);
+    }
+    if (!c->fork) TSVD_CUDA(c, cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    std::vector<int64_t> key = {3, count, iters, (int64_t)(intptr_t)c->ws, (int64_t)c->ws_cap,
+                                c->opts.tnn_scale, c->opts.sparse_mode, c->opts.max_sweeps,
+                                c->opts.timing};
+    double d[4] = {c->opts.rho0, c->opts.mu, c->opts.rho_max, (double)c->opts.jacobi_tol};
+    for (double v : d) {
+      int64_t bits;
+      std::memcpy(&bits, &v, sizeof bits);
+      key.push_back(bits);
+    }
+    for (const BatchItem& it : items) {
+      const tsvd_problem& q = *it.src;
+      int64_t lbits = 0;
+      std::memcpy(&lbits, &q.lambda, sizeof q.lambda);
+      const int64_t vals[] = {q.kind, q.order, q.dims[0], q.dims[1], q.dims[2],
+                              q.order == 4 ? q.dims[3] : 1, (int64_t)(intptr_t)q.M,
+                              (int64_t)(intptr_t)q.omega, (int64_t)(intptr_t)q.out0,
+                              (int64_t)(intptr_t)q.out1, lbits, it.kn.ctas, it.kn.lanes,
+                              it.kn.ppg, it.kn.vform};
+      key.insert(key.end(), std::begin(vals), std::end(vals));
+    }
+    auto body = [&]() -> tsvd_status {
+      cudaStream_t base = c->cur;
+      TSVD_CUDA(c, cudaEventRecord(c->fork, base));
+      for (int b = 0; b < nbr; ++b) TSVD_CUDA(c, cudaStreamWaitEvent(c->branches[(size_t)b], c->fork, 0));
+      for (int i = 0; i < count; ++i) {
+        c->cur = c->branches[(size_t)(i % nbr)];
+        const tsvd_status st = enqueue_item(c, items[(size_t)i], iters);
+        if (st != TSVD_OK) {
+          c->cur = base;
+          return st;
+        }
+      }
+      for (int b = 0; b < nbr; ++b) {
+        TSVD_CUDA(c, cudaEventRecord(c->joins[(size_t)b], c->branches[(size_t)b]));
+        TSVD_CUDA(c, cudaStreamWaitEvent(base, c->joins[(size_t)b], 0));
+      }
+      c->cur = base;
+      return TSVD_OK;
+    };
+    TSVD_TRY(run_maybe_graph(c, key, true, body));
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof *stats);
+    stats->iters = iters;
+    stats->rho_final = rho;
+    stats->launches = c->launches;
+    stats->slice_launches = c->slice_launches;
+    TSVD_TRY(timed_totals(c, &stats->slice_ms, &stats->tube_ms));
+    if (iters > 0) {
+      for (const BatchItem& it : items) {
+        SweepAccum acc;
+        TSVD_CUDA(c, cudaMemcpyAsync(&acc, it.w.acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+        int rmax = 0;
+        double tnn = 0;
+        TSVD_TRY(read_slice_stats(c, it.p, it.w, nullptr, &tnn, &rmax, nullptr));
+        stats->max_sweeps_used = std::max(stats->max_sweeps_used, acc.max_sweeps);
+        stats->total_sweeps += (int64_t)acc.total_sweeps;
+        stats->nonconverged += (int64_t)acc.nonconverged;
+        stats->slice_svds += (int64_t)iters * it.w.ndistinct;
+        stats->tnn_last += tnn;
+        stats->rank_last_max = std::max(stats->rank_last_max, rmax);
+      }
+    }
+  }
   TSVD_CUDA(c, cudaGetLastError());
   return TSVD_OK;
 }

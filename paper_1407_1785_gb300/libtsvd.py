@@ -28,7 +28,15 @@ SCALE_AVG, SCALE_SUM = 0, 1
 
 # Every symbol include/tsvd.h declares.
 EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_last_error",
-                    "tsvt", "tnn_complete", "trpca", "tsvt_static")
+                    "tsvt", "tnn_complete", "trpca", "tsvd_solve_batched", "tsvt_static")
+PROBLEM_COMPLETE, PROBLEM_RPCA = 1, 2
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("order", ctypes.c_int),
+                ("dims", ctypes.c_int64 * 4), ("M", ctypes.c_void_p),
+                ("omega", ctypes.c_void_p), ("lam", ctypes.c_float),
+                ("out0", ctypes.c_void_p), ("out1", ctypes.c_void_p)]
 
 
 class Opts(ctypes.Structure):
@@ -99,6 +107,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.trpca.restype = ctypes.c_int
     L.tsvt_static.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_float, P]
     L.tsvt_static.restype = ctypes.c_int
+    L.tsvd_solve_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
+                                     ctypes.POINTER(Stats)]
+    L.tsvd_solve_batched.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -206,6 +217,26 @@ class Context:
         st = self._L.trpca(self._h, _ptr(M), len(dims), _dims(dims), float(lam), int(iters),
                            _ptr(L_out), _ptr(S_out), ctypes.byref(s) if stats else None)
         self._check("trpca", st)
+        return s.as_dict() if stats else None
+
+    def solve_batched(self, problems, iters: int, stats: bool = False):
+        """problems: sequence of dicts with keys kind ('complete' | 'rpca'), dims, M,
+        omega (completion), lam (RPCA), out0, out1 (device buffers)."""
+        arr = (Problem * len(problems))()
+        for i, q in enumerate(problems):
+            d = list(q["dims"]) + [1] * (4 - len(q["dims"]))
+            arr[i].kind = PROBLEM_COMPLETE if q["kind"] == "complete" else PROBLEM_RPCA
+            arr[i].order = len(q["dims"])
+            arr[i].dims = (ctypes.c_int64 * 4)(*[int(x) for x in d])
+            arr[i].M = _ptr(q["M"])
+            arr[i].omega = _ptr(q.get("omega"))
+            arr[i].lam = float(q.get("lam", 0.0))
+            arr[i].out0 = _ptr(q["out0"])
+            arr[i].out1 = _ptr(q.get("out1"))
+        s = Stats()
+        st = self._L.tsvd_solve_batched(self._h, len(problems), arr, int(iters),
+                                        ctypes.byref(s) if stats else None)
+        self._check("tsvd_solve_batched", st)
         return s.as_dict() if stats else None
 
     # raw status variants (for error-path tests)

@@ -209,6 +209,60 @@ def test_graph_replay_matches_direct_launches(kind):
         assert np.array_equal(x, outs[0][0]) and np.array_equal(y, outs[0][1])
 
 
+def test_batched_uneven_problems_match_oracle():
+    """A batch of uneven tensors (completion and RPCA, 3-way and 4-way) in one call: every
+    tensor matches the oracle's solve; a second call replays the captured batch graph and
+    gives the same bits."""
+    from paper_1407_1785_gb300 import libtsvd
+    torch = _torch()
+    specs = [("complete", (30, 41, 8), 3, 0.4), ("rpca", (52, 36, 6), 2, 0.1),
+             ("complete", (64, 20, 11), 4, 0.5), ("rpca", (20, 70, 9), 2, 0.08),
+             ("complete", (18, 22, 3, 6), 0, 0.5), ("rpca", (96, 80, 5), 3, 0.12)]
+    iters = 25
+    probs, refs, keep = [], [], []
+    for i, (kind, shape, rank, frac) in enumerate(specs):
+        if len(shape) == 3:
+            L0 = synth.lowrank_tensor(shape[0], shape[1], shape[2], rank, seed=50 + i)
+        else:
+            L0 = np.empty(shape)
+            for ch in range(shape[2]):
+                L0[:, :, ch, :] = synth.translating_texture(shape[0], shape[1], shape[3],
+                                                            seed=50 + i, channel=ch)
+        if kind == "complete":
+            om = synth.sampling_mask(shape, frac, seed=50 + i)
+            M = (L0 * om).astype(np.float32)
+            Xo, Zo = oracle.tnn_complete(M.astype(np.float64), om, iters)
+            refs.append((Xo, Zo))
+            q = dict(kind=kind, dims=shape, M=dev(M),
+                     omega=torch.from_numpy(colmajor(om, np.uint8)).cuda())
+        else:
+            S0, _ = synth.sparse_corruption(shape, frac, seed=50 + i)
+            M = (L0 + S0).astype(np.float32)
+            lam = 1.0 / math.sqrt(max(shape[0], shape[1]) * shape[2])
+            Lo, So = oracle.trpca(M.astype(np.float64), lam, iters)
+            refs.append((Lo, So))
+            q = dict(kind=kind, dims=shape, M=dev(M), lam=lam)
+        q["out0"] = torch.empty_like(q["M"])
+        q["out1"] = torch.empty_like(q["M"])
+        probs.append(q)
+        keep.append(M)
+    with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream) as ctx:
+        first = None
+        for call in range(2):
+            st = ctx.solve_batched(probs, iters, stats=True)
+            got = [(host(q["out0"], q["dims"]), host(q["out1"], q["dims"])) for q in probs]
+            if first is None:
+                first = got
+            else:
+                for (a, b), (c, d) in zip(got, first):
+                    assert np.array_equal(a, c) and np.array_equal(b, d)
+            assert st["slice_launches"] == iters * len(specs)
+            assert st["nonconverged"] == 0
+    for (a, b), (ra, rb), M in zip(first, refs, keep):
+        assert relerr(a, ra, floor=1e-6) <= ADMM_TOL
+        assert relerr(b, rb, floor=1e-3 * np.linalg.norm(M)) <= ADMM_TOL
+
+
 def test_tsvt_rpca_full_size(gpu_ctx):
     """240 x 320 x 60 tubal-rank-10 tensor plus 10% sparse corruption: slices larger than one
     SM's shared memory, spread over CTA clusters."""
