@@ -41,8 +41,8 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of one jacobi_svt_kernel launch from an ncu capture of this workload, valid
 # only for the kernel source it was taken on (see profiles/).
 TRAFFIC = {"source": "paper_1407_1785_gb300/csrc/slice_svt.cu",
-           "sha256": "60f8cb147ac5c40e053a33a2d8e64b75d0f6bb119e5502f64376351a57a9b430",
-           "bytes_per_launch": 10396672 + 0}
+           "sha256": "8f46dfad975484d40755d0d1dd1c1444b478ba1a6e75877ecee5e31e4378f61b",
+           "bytes_per_launch": 10575360 + 15321344}
 
 
 def parse_args():
