@@ -50,10 +50,20 @@ typedef enum tsvd_status {
   TSVD_EUNSUPPORTED = 6
 } tsvd_status;
 
-/* Precision of the slice SVDs.  Only TSVD_PRECISION_FP32 (one-sided Jacobi in FP32) is
- * implemented; the other values are rejected with TSVD_EUNSUPPORTED. */
+/* Arithmetic of the slice SVTs.
+ *   FP32       the plain form: one-sided Jacobi SVD of every Fourier slice in FP32.
+ *   TF32, BF16, 3XTF32, RAND_FP32
+ *              the mixed form: a rank-adaptive randomized subspace-iteration SVT.  Per slice
+ *              A: Y = A P (P warm-started from the previous call's right singular vectors),
+ *              Q = CholeskyQR2(Y), D = D_tau(Q^H A) by one-sided Jacobi on the k x n matrix,
+ *              Z = Q D.  The three products with A and Z run as 3M complex products on the
+ *              tensor cores with TF32 operands, BF16 operands or split TF32 operands
+ *              (hi*hi + hi*lo + lo*hi: FP32-level accuracy), all with FP32 accumulation;
+ *              RAND_FP32 runs them in FP32 on the CUDA cores.  The result equals
+ *              D_tau(Q Q^H A); it is the t-SVT when the sketch width k covers every singular
+ *              value above tau (k adapts to the ranks seen, see rsvt_* options). */
 enum { TSVD_PRECISION_FP32 = 0, TSVD_PRECISION_TF32 = 1, TSVD_PRECISION_BF16 = 2,
-       TSVD_PRECISION_3XTF32 = 3 };
+       TSVD_PRECISION_3XTF32 = 3, TSVD_PRECISION_RAND_FP32 = 4 };
 
 /* Sparse penalty of tensor RPCA: entrywise l1 (soft threshold at lambda/rho) or the
  * tube-wise l_{1,1,2} norm of Sec. 5 (eq. sparse2; for order 4 the group is S(i,j,:,:)). */
@@ -91,7 +101,17 @@ typedef struct tsvd_opts {
   int use_graphs;     /* 1 (default): tnn_complete / trpca capture their whole launch sequence
                          (all iterations) into a CUDA graph on a private stream the first time
                          a given (buffers, shape, iterations, options) combination runs with a
-                         settled plan, and replay it on the context's stream afterwards */
+                         settled plan, and replay it on the context's stream afterwards
+                         (the mixed precisions choose the sketch width on the host during a
+                         solve and are not captured) */
+  int rsvt_oversample; /* mixed form: sketch width = (singular values above the threshold and
+                         the products' noise floor) + this margin, rounded up to 8; the
+                         width only grows during a solve; default 10 */
+  int rsvt_kmax;      /* mixed form: largest sketch width (<= 128 and <= min(n1, n2));
+                         0 (default) = min(128, n1, n2) */
+  int rsvt_power;     /* mixed form, tsvt() only: extra power steps from a random start
+                         (ADMM solves start each iteration from the previous basis);
+                         default 2 */
 } tsvd_opts;
 
 /* Counters of one ADMM solve (host struct). */
@@ -111,6 +131,11 @@ typedef struct tsvd_stats {
   int slice_ctas;               /* CTAs per slice of the slice-SVT plan used */
   int slice_lanes;              /* lanes per vector pair of that plan (0 = planner default) */
   int slice_pairs_in_flight;    /* vector pairs a lane group interleaves (0/1 = one) */
+  int rsvt_k_last;              /* mixed form: sketch width of the last slice SVT */
+  int64_t rsvt_saturated;       /* mixed form: slice SVTs whose whole sketch lay above the
+                                   threshold (the result may miss directions) */
+  int64_t rsvt_drops;           /* mixed form: sketch columns dropped as dependent by the
+                                   CholeskyQR factorisations (refilled at random) */
 } tsvd_stats;
 
 /* Fill *opts with the defaults listed above. */

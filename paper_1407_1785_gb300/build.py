@@ -19,7 +19,8 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libtsvd.so")
 
-SOURCES = ["tsvd_api.cu", "tube_pass.cu", "slice_svt.cu", "tsvd_noalloc.cu"]
+SOURCES = ["tsvd_api.cu", "tube_pass.cu", "slice_svt.cu", "tsvd_noalloc.cu", "rsvt.cu",
+           "tc_gemm.cu"]
 HEADERS = ["tsvd_internal.h"]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]

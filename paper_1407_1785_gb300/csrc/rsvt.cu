@@ -1,0 +1,443 @@
+// rsvt.cu -- randomized, rank-adaptive singular value thresholding of the Fourier slices:
+// the mixed-precision form of the per-slice step D_tau of the Lemma in Sec. 4.1 (used by the
+// completion Z-step, eq. shrink / shrink2, and the RPCA L-step, eq. low_rank).
+//
+// Per slice, the working matrix Aw (mw x nw complex) is the slice or its transpose, whichever
+// has fewer columns (D_tau(A^T) = D_tau(A)^T).  With a sketch width k and a right basis
+// P (nw x k) carried from the previous call:
+//   Y  = Aw P                              sketch                              (GEMM)
+//   Q  = orth(Y)                           CholeskyQR2 (cholqr_factor_kernel)
+//   Bt = Aw^T conj(Q)  = (Q^H Aw)^T        projection onto range(Q), nw x k    (GEMM)
+//   Dt = D_tau(Bt)                         one-sided Jacobi SVT of the small matrix
+//   Zw = Q Dt^T        = Q D_tau(Q^H Aw)   rebuild                             (GEMM)
+//   P' = conj(W), W = Bt J the converged Jacobi vectors = the right singular vectors of
+//        Q^H Aw scaled by sigma: the next call starts from the Ritz basis (one step of
+//        subspace iteration per call), so Y' = Aw P' has nearly orthogonal columns.
+// Because Q has orthonormal columns, Q D_tau(Q^H Aw) = D_tau(Q Q^H Aw): the result is the exact
+// thresholding of the projection of Aw onto the sketched subspace, and it equals D_tau(Aw)
+// when that subspace holds every singular direction above tau.
+//
+// Rank adaptivity.  After each call the kernel rsvt_refill_kernel counts, per slice, the
+// singular values above max(tau, floor * sigma_max) (floor is the product precision's noise
+// level) and records the maximum over slices; the caller picks the next k as that count plus
+// an oversampling margin.  Columns of P that carry no direction (dropped by the Cholesky
+// factorisation, or beyond the previous k) are refilled with counter-based random vectors.
+//
+// Orthonormalisation (CholeskyQR2).  G = Y^H Y (FP32), scaled to unit diagonal,
+// Gs = D^-1 G D^-1 = R^H R, Q = Y D^-1 R^-1, done twice.  The column scaling makes the FP32
+// rounding of G relative to each column's norm, so graded sketches (columns of norm sigma^2)
+// factor accurately.  The Schur complement is updated in FP32 and the pivots in FP64.  A pivot
+// below chol_tol marks a column that depends on the previous ones: it is dropped (its column of
+// Q is zero) instead of failing the factorisation.
+//
+// Products.  The three slice products (sketch, projection, rebuild) run on the engine the
+// caller selects: FP32 CUDA cores here, or the tensor-core engines of tc_gemm.cu.  The Gram
+// matrices and the k x k triangular applications always run in FP32 on CUDA cores.
+#include "tsvd_internal.h"
+
+#include <algorithm>
+
+namespace tsvd {
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16;
+
+__device__ __forceinline__ float2 cload(const float2* p, int64_t o, int conj) {
+  float2 v = p[o];
+  if (conj) v.y = -v.y;
+  return v;
+}
+
+// C = op(A) op(B), batched, generic strides (see CGemm in tsvd_internal.h).  64 x 64 tile per
+// CTA, 4 x 4 complex outputs per thread; operand tiles staged through shared memory with
+// threads running along whichever index is contiguous in global memory.
+__global__ void __launch_bounds__(256) cgemm_fp32_kernel(CGemm g) {
+  __shared__ float2 As[TK][TM + 1];
+  __shared__ float2 Bs[TK][TN + 1];
+  const int bz = blockIdx.z;
+  const float2* A = g.a.p + (int64_t)(g.a.idx ? g.a.idx[bz] : bz) * g.a.bs;
+  const float2* B = g.b.p + (int64_t)(g.b.idx ? g.b.idx[bz] : bz) * g.b.bs;
+  float2* C = const_cast<float2*>(g.c.p) + (int64_t)(g.c.idx ? g.c.idx[bz] : bz) * g.c.bs;
+  const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const bool a_rows = g.a.s0 == 1;
+  const bool b_ctr = g.b.s0 == 1;
+  float accr[4][4], acci[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) accr[r][c] = acci[r][c] = 0.f;
+  for (int l0 = 0; l0 < g.K; l0 += TK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u;
+      int ii, ll;
+      if (a_rows) {
+        ii = e % TM;
+        ll = e / TM;
+      } else {
+        ll = e % TK;
+        ii = e / TK;
+      }
+      int i = i0 + ii, l = l0 + ll;
+      As[ll][ii] = (i < g.M && l < g.K) ? cload(A, i * g.a.s0 + l * g.a.s1, g.a.conj)
+                                         : make_float2(0.f, 0.f);
+      int jj;
+      if (b_ctr) {
+        ll = e % TK;
+        jj = e / TK;
+      } else {
+        jj = e % TN;
+        ll = e / TN;
+      }
+      const int j = j0 + jj;
+      l = l0 + ll;
+      Bs[ll][jj] = (j < g.N && l < g.K) ? cload(B, l * g.b.s0 + j * g.b.s1, g.b.conj)
+                                         : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int l = 0; l < TK; ++l) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[l][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[l][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          accr[r][c] = fmaf(a[r].x, b[c].x, fmaf(-a[r].y, b[c].y, accr[r][c]));
+          acci[r][c] = fmaf(a[r].x, b[c].y, fmaf(a[r].y, b[c].x, acci[r][c]));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty + 16 * r;
+    if (i >= g.M) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx + 16 * c;
+      if (j < g.N) C[i * g.c.s0 + j * g.c.s1] = make_float2(accr[r][c], acci[r][c]);
+    }
+  }
+}
+
+// One CTA per slice: column-scaled Cholesky factorisation Gs = R^H R of the k x k Gram G
+// (col-major, ld ldg) with dropped pivots, then T = D^-1 R^-1 (zero columns for dropped
+// pivots), written over the same layout.  Shared memory: S (k x (k+1) complex: R in the upper
+// triangle, then (R^-1)^T in the strict lower triangle), pivots and scales in FP64.
+__global__ void __launch_bounds__(256) cholqr_factor_kernel(const float2* G, float2* T,
+                                                            const int* slices, int k, int ldg,
+                                                            int64_t gs, float tol,
+                                                            RsvtStat* rstat) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = slices[blockIdx.x];
+  const int ldS = k + 1;
+  float2* S = reinterpret_cast<float2*>(smem_raw);
+  double* dd = reinterpret_cast<double*>(S + (size_t)k * ldS);
+  double* dsc = dd + k;
+  float2* xd = reinterpret_cast<float2*>(dsc + k);
+  int* okc = reinterpret_cast<int*>(xd + k);
+  __shared__ double s_dmax;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const float2* Gp = G + (size_t)s * gs;
+  float2* Tp = T + (size_t)s * gs;
+
+  for (int i = tid; i < k; i += nthr) {
+    const double g = (double)Gp[i + (size_t)i * ldg].x;
+    dsc[i] = g > 0.0 ? sqrt(g) : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < k; ++i) m = fmax(m, dsc[i]);
+    s_dmax = m;
+  }
+  __syncthreads();
+  const double dmin = 1e-30 * s_dmax;
+  for (int i = tid; i < k; i += nthr) {
+    const bool zero = !(dsc[i] > dmin) || s_dmax == 0.0;
+    dd[i] = zero ? 0.0 : 1.0;
+    if (zero) dsc[i] = 1.0;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < k * k; idx += nthr) {
+    const int r = idx % k, c = idx / k;
+    if (r > c) continue;
+    float2 v = Gp[r + (size_t)c * ldg];
+    const float inv = (float)(1.0 / (dsc[r] * dsc[c]));
+    v.x *= inv;
+    v.y *= inv;
+    if (dd[r] == 0.0 || dd[c] == 0.0) v = make_float2(0.f, 0.f);
+    S[(size_t)r * ldS + c] = v;
+  }
+  __syncthreads();
+
+  for (int j = 0; j < k; ++j) {
+    const double pj = dd[j];
+    const bool okj = pj > (double)tol;
+    const float rjj = okj ? (float)sqrt(pj) : 1.f;
+    const float irjj = 1.f / rjj;
+    for (int l = j + 1 + tid; l < k; l += nthr) {
+      const float2 v = S[(size_t)j * ldS + l];
+      S[(size_t)j * ldS + l] = okj ? make_float2(v.x * irjj, v.y * irjj) : make_float2(0.f, 0.f);
+    }
+    if (tid == 0) {
+      S[(size_t)j * ldS + j] = make_float2(rjj, 0.f);
+      okc[j] = okj ? 1 : 0;
+    }
+    __syncthreads();
+    if (okj) {
+      const int nt = k - j - 1;
+      // S(l, l2) -= conj(R(j, l)) R(j, l2) on the upper triangle of the trailing block
+      for (int idx = tid; idx < nt * nt; idx += nthr) {
+        const int l = j + 1 + idx / nt, l2 = j + 1 + idx % nt;
+        if (l2 < l) continue;
+        const float2 a = S[(size_t)j * ldS + l], b = S[(size_t)j * ldS + l2];
+        float2 v = S[(size_t)l * ldS + l2];
+        v.x -= a.x * b.x + a.y * b.y;
+        v.y -= a.x * b.y - a.y * b.x;
+        S[(size_t)l * ldS + l2] = v;
+      }
+      for (int l = j + 1 + tid; l < k; l += nthr) {
+        const float2 a = S[(size_t)j * ldS + l];
+        dd[l] -= (double)a.x * a.x + (double)a.y * a.y;
+      }
+    }
+    __syncthreads();
+  }
+
+  // X = R^-1 column by column (one thread per column): X(i, c) for i < c kept at S(c, i)
+  for (int c = tid; c < k; c += nthr) {
+    const float xcc = 1.f / S[(size_t)c * ldS + c].x;
+    xd[c] = make_float2(xcc, 0.f);
+    for (int i = c - 1; i >= 0; --i) {
+      // sum_{l = i+1..c} R(i, l) X(l, c)
+      const float2 ric = S[(size_t)i * ldS + c];
+      float sr = ric.x * xcc, si = ric.y * xcc;
+      for (int l = i + 1; l < c; ++l) {
+        const float2 r = S[(size_t)i * ldS + l];
+        const float2 x = S[(size_t)c * ldS + l];
+        sr += r.x * x.x - r.y * x.y;
+        si += r.x * x.y + r.y * x.x;
+      }
+      const float inv = -1.f / S[(size_t)i * ldS + i].x;
+      S[(size_t)c * ldS + i] = make_float2(sr * inv, si * inv);
+    }
+  }
+  __syncthreads();
+  // T(i, c) = X(i, c) / d_i, zero below the diagonal and in dropped columns
+  for (int idx = tid; idx < k * k; idx += nthr) {
+    const int i = idx % k, c = idx / k;
+    float2 v = make_float2(0.f, 0.f);
+    if (okc[c] && i <= c) {
+      v = i == c ? xd[c] : S[(size_t)c * ldS + i];
+      const float inv = (float)(1.0 / dsc[i]);
+      v.x *= inv;
+      v.y *= inv;
+    }
+    Tp[i + (size_t)c * ldg] = v;
+  }
+  if (rstat && tid == 0) {
+    int nd = 0;
+    for (int c = 0; c < k; ++c) nd += okc[c] ? 0 : 1;
+    if (nd) atomicAdd(&rstat->drops, nd);
+  }
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Uniform in [-1, 1) from a counter (SplitMix64 finaliser of key + counter * golden gamma).
+__device__ __forceinline__ float urand(unsigned long long key, unsigned long long ctr) {
+  const unsigned long long h = mix64(key + (ctr + 1ull) * 0x9e3779b97f4a7c15ull);
+  return (float)((double)(h >> 11) * (1.0 / 4503599627370496.0) - 1.0);
+}
+
+// One CTA per slice.  Counts the singular values above max(tau, floor * sigma_max) among the
+// k of this call (max over slices into rstat), then refills with random vectors the columns
+// c < kfill of P that carry no direction: c >= k, or sigma_c <= 1e-6 sigma_max.
+__global__ void __launch_bounds__(256) rsvt_refill_kernel(float2* P, const float* sig,
+                                                          const int* slices,
+                                                          const unsigned char* isreal, int nw,
+                                                          int kmax, int k, int kfill, float tau,
+                                                          float floor_rel,
+                                                          unsigned long long seed, int iter,
+                                                          RsvtStat* rstat) {
+  const int s = slices[blockIdx.x];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  __shared__ float s_max;
+  const float* sg = sig + (size_t)s * kmax;
+  if (tid == 0) {
+    float m = 0.f;
+    for (int v = 0; v < k; ++v) m = fmaxf(m, sg[v]);
+    const float thr = fmaxf(tau, floor_rel * m);
+    int cnt = 0;
+    for (int v = 0; v < k; ++v) cnt += sg[v] > thr ? 1 : 0;
+    s_max = m;
+    if (rstat && k > 0) {
+      atomicMax(&rstat->rank_max, cnt);
+      if (cnt >= k) atomicAdd(&rstat->saturated, 1);
+    }
+  }
+  __syncthreads();
+  const float smax = s_max;
+  const bool real = isreal && isreal[s];
+  const unsigned long long key =
+      mix64(seed ^ ((unsigned long long)(unsigned)iter << 32) ^ (unsigned long long)s);
+  float2* Ps = P + (size_t)s * nw * kmax;
+  for (int c = 0; c < kfill; ++c) {
+    const bool need = c >= k || !(sg[c] > 1e-6f * smax);
+    if (!need) continue;
+    for (int e = tid; e < nw; e += nthr) {
+      const unsigned long long ctr = 2ull * ((unsigned long long)c * nw + e);
+      Ps[(size_t)e + (size_t)nw * c] =
+          make_float2(urand(key, ctr), real ? 0.f : urand(key, ctr + 1ull));
+    }
+  }
+}
+
+size_t cholqr_smem(int k) {
+  return (size_t)k * (k + 1) * sizeof(float2) + 2 * (size_t)k * sizeof(double) +
+         (size_t)k * sizeof(float2) + (size_t)k * sizeof(int);
+}
+
+cudaError_t gemm_fp32(const CGemm& g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  dim3 grid((g.M + TM - 1) / TM, (g.N + TN - 1) / TN, g.batch);
+  cgemm_fp32_kernel<<<grid, 256, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+CMat mat(const float2* p, const int* idx, int64_t bs, int64_t s0, int64_t s1, int conj = 0) {
+  CMat m;
+  m.p = p;
+  m.idx = idx;
+  m.bs = bs;
+  m.s0 = s0;
+  m.s1 = s1;
+  m.conj = conj;
+  return m;
+}
+
+CGemm gemm(int M, int N, int K, int batch, const CMat& a, const CMat& b, const CMat& c) {
+  CGemm g;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.batch = batch;
+  g.a = a;
+  g.b = b;
+  g.c = c;
+  return g;
+}
+
+}  // namespace
+
+cudaError_t launch_cgemm(const CGemm& g, int engine, cudaStream_t st) {
+  if (engine == RSVT_GEMM_FP32) return gemm_fp32(g, st);
+  return launch_cgemm_tc(g, engine, st);
+}
+
+int rsvt_max_k() { return 128; }
+
+size_t rsvt_jacobi_scratch_bytes(int nw, int kmax, int nslices) {
+  size_t b = 0;
+  SliceKnobs auto_k = {0, 0, 0, 0};
+  for (int k = 1; k <= kmax; ++k)
+    if (jacobi_svt_supported(nw, k)) b = std::max(b, jacobi_svt_scratch_bytes(nw, k, nslices, auto_k));
+  return b;
+}
+
+cudaError_t launch_rsvt_refill(const RsvtArgs& a, int k, int kfill, cudaStream_t st) {
+  if (a.nslices <= 0) return cudaSuccess;
+  rsvt_refill_kernel<<<a.nslices, 256, 0, st>>>(a.P, a.sig, a.slices, a.isreal, a.nw, a.kmax, k,
+                                                kfill, a.tau, a.floor_rel, a.seed, a.iter,
+                                                a.rstat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
+  if (a.nslices <= 0) return cudaSuccess;
+  const int k = a.k, kmax = a.kmax, mw = a.mw, nw = a.nw, ns = a.nslices;
+  if (k < 1 || k > kmax || kmax > rsvt_max_k() || k > nw) return cudaErrorInvalidValue;
+  cudaError_t e;
+  const int64_t ys = (int64_t)mw * kmax, ps = (int64_t)nw * kmax, gs = (int64_t)kmax * kmax;
+  const int64_t bs = (int64_t)nw * k;
+  const int* idx = a.slices;
+  // the working matrix Aw(i, j) = A(i, j) or A(j, i): strides (wr, wc) in the spectrum
+  const CMat Aw = mat(a.ahat, idx, a.N12, a.wr, a.wc);
+  const CMat AwT = mat(a.ahat, idx, a.N12, a.wc, a.wr);
+  const size_t csm = cholqr_smem(k);
+  static bool attr_set = false;
+  if (!attr_set) {
+    e = cudaFuncSetAttribute(cholqr_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cholqr_smem(rsvt_max_k()));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  for (int pw = 0; pw <= a.power; ++pw) {
+    // Y = Aw P   (power steps: P = conj(Bt) of the previous projection)
+    const CMat Pm = pw == 0 ? mat(a.P, idx, ps, 1, nw) : mat(a.Bt, idx, bs, 1, nw, 1);
+    e = launch_cgemm(gemm(mw, k, nw, ns, Aw, Pm, mat(a.Y, idx, ys, 1, mw)), a.engine, st);
+    if (e != cudaSuccess) return e;
+    // CholeskyQR2: Y -> Q -> Y
+    for (int pass = 0; pass < 2; ++pass) {
+      float2* src = pass == 0 ? a.Y : a.Q;
+      float2* dst = pass == 0 ? a.Q : a.Y;
+      e = gemm_fp32(gemm(k, k, mw, ns, mat(src, idx, ys, mw, 1, 1), mat(src, idx, ys, 1, mw),
+                         mat(a.G, idx, gs, 1, kmax)),
+                    st);
+      if (e != cudaSuccess) return e;
+      cholqr_factor_kernel<<<ns, 256, csm, st>>>(a.G, a.T, idx, k, kmax, gs, a.chol_tol,
+                                                 a.rstat);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      e = gemm_fp32(gemm(mw, k, k, ns, mat(src, idx, ys, 1, mw), mat(a.T, idx, gs, 1, kmax),
+                         mat(dst, idx, ys, 1, mw)),
+                    st);
+      if (e != cudaSuccess) return e;
+    }
+    // Bt = Aw^T conj(Q)
+    e = launch_cgemm(gemm(nw, k, mw, ns, AwT, mat(a.Y, idx, ys, 1, mw, 1), mat(a.Bt, idx, bs, 1, nw)),
+                     a.engine, st);
+    if (e != cudaSuccess) return e;
+  }
+  // Dt = D_tau(Bt), converged vectors -> P (conjugated), singular values -> sig
+  SliceArgs j;
+  j.ahat = a.Bt;
+  j.zhat = a.Dt;
+  j.slices = idx;
+  j.nslices = ns;
+  j.n1 = nw;
+  j.n2 = k;
+  j.N12 = bs;
+  j.tau = a.tau;
+  j.tol = a.tol;
+  j.max_sweeps = a.max_sweeps;
+  j.stat = a.stat;
+  j.acc = a.acc;
+  j.scratch = a.jscratch;
+  j.scratch_bytes = a.jscratch_bytes;
+  j.knobs = {0, 0, 0, 0};
+  j.wout = a.P;
+  j.wout_stride = ps;
+  j.wout_conj = 1;
+  j.sigout = a.sig;
+  j.sig_stride = kmax;
+  e = launch_jacobi_svt(j, st);
+  if (e != cudaSuccess) return e;
+  // Zw = Q Dt^T, written into the output spectrum with the orientation of Aw
+  e = launch_cgemm(gemm(mw, nw, k, ns, mat(a.Y, idx, ys, 1, mw), mat(a.Dt, idx, bs, nw, 1),
+                        mat(a.zhat, idx, a.N12, a.wr, a.wc)),
+                   a.engine, st);
+  if (e != cudaSuccess) return e;
+  return launch_rsvt_refill(a, k, a.kfill, st);
+}
+
+}  // namespace tsvd

@@ -510,6 +510,20 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
     if (lane == 0) sig[v] = sqrtf(acc);
   }
   __syncthreads();
+  if (a.wout) {
+    // the converged vectors (and their norms) for callers that continue from them
+    const float si = a.wout_conj ? -1.f : 1.f;
+    float2* wo = a.wout + (size_t)s * a.wout_stride;
+    for (int v = warp; v < nl; v += nwarps) {
+      const int gv = v < bs ? bx * bs + v : by * bs + v - bs;
+      if (gv >= sh.nv) continue;
+      const float* wr = Wr + (size_t)v * rowp;
+      const float* wi = Wi + (size_t)v * rowp;
+      for (int e = lane; e < len; e += 32)
+        wo[(size_t)e + (size_t)n1 * gv] = make_float2(wr[e], si * wi[e]);
+      if (lane == 0 && a.sigout) a.sigout[(size_t)s * a.sig_stride + gv] = sig[v];
+    }
+  }
   const float tau = a.tau;
   if (tid == 0) {
     int r = 0;
@@ -850,6 +864,7 @@ cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st) {
   if (!plan_slice(a.n1, a.n2, a.nslices, a.knobs, sh, smem)) return cudaErrorInvalidValue;
   if (sh.C > 1 && (a.scratch == nullptr || a.scratch_bytes < scratch_for(sh, a.N12, a.nslices)))
     return cudaErrorInvalidValue;
+  if (a.wout && (sh.rows || a.wout_stride < (int64_t)a.n1 * a.n2)) return cudaErrorInvalidValue;
   const int gpw = 32 / sh.G;
   const int per_warp = gpw * sh.np;           // pairs a warp has in flight
   const int maxw = max_warps_for(sh.cpl * sh.np);

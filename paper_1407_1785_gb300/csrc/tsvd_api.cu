@@ -26,6 +26,7 @@ struct tsvd_ctx {
   size_t ws_cap = 0;
   std::vector<float2> twid_host;   // kept alive while copies may be in flight
   std::vector<int> slices_host;
+  std::vector<unsigned char> isreal_host;
   std::vector<SliceStat> stat_host;
   // launch accounting of the current call
   int64_t launches = 0;
@@ -51,6 +52,13 @@ struct tsvd_ctx {
   std::vector<cudaStream_t> branches;
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
+  // mixed form: per-iteration sketch statistics copied to pinned host memory (a ring read
+  // two iterations late, so the host never waits for the iteration it just enqueued)
+  static constexpr int kRing = 4;
+  RsvtStat* rs_host = nullptr;
+  cudaEvent_t rs_ev[kRing] = {};
+  int rs_k_last = 0;
+  int64_t rs_saturated = 0, rs_drops = 0;
 };
 
 namespace {
@@ -105,6 +113,9 @@ int pointer_kind(const void* p, int dev) {
   return 1;
 }
 
+// The mixed form: randomized slice SVT (every precision but plain FP32 Jacobi).
+bool mixed_precision(const tsvd_ctx* c) { return c->opts.precision != TSVD_PRECISION_FP32; }
+
 // Problem geometry shared by every entry point.
 struct Problem {
   int order = 0;
@@ -141,6 +152,13 @@ tsvd_status make_problem(tsvd_ctx* c, int order, const int64_t* dims, Problem& p
   if (!tube_pass_supported(p.g))
     return fail(c, TSVD_EUNSUPPORTED, "tube of %lld entries exceeds the tube-pass limit",
                 (long long)p.nslices);
+  if (mixed_precision(c)) {
+    // the randomized SVT only runs Jacobi on the projected nw x k matrices
+    const int nw = (int)std::min(p.n1, p.n2);
+    if (!jacobi_svt_supported(nw, std::min(nw, rsvt_max_k())))
+      return fail(c, TSVD_EUNSUPPORTED, "slices with min(n1, n2) = %d are not supported", nw);
+    return TSVD_OK;
+  }
   if (!jacobi_svt_supported((int)p.n1, (int)p.n2))
     return fail(c, TSVD_EUNSUPPORTED,
                 "a %lld x %lld complex slice does not fit one SM's shared memory",
@@ -263,12 +281,51 @@ struct Workspace {
   void* jscratch = nullptr;     // multi-CTA slice SVT scratch
   size_t jscratch_bytes = 0;
   int ndistinct = 0;
+  // mixed form (randomized slice SVT): working matrix Aw = the slice (n1 >= n2) or its
+  // transpose, mw x nw with nw <= mw, and its buffers (see RsvtArgs)
+  bool rsvt = false;
+  int mw = 0, nw = 0, kmax = 0;
+  int64_t wr = 0, wc = 0;
+  float2 *rP = nullptr, *rY = nullptr, *rQ = nullptr, *rBt = nullptr, *rDt = nullptr,
+         *rG = nullptr, *rT = nullptr;
+  float* rsig = nullptr;
+  unsigned char* risreal = nullptr;
+  RsvtStat* rstat = nullptr;     // tsvd_ctx::kRing slots
+  void* rjs = nullptr;
+  size_t rjs_bytes = 0;
 };
 
 struct WsRequest {
   bool state = false, yn = false, stage_in = false, stage_om = false, stage_out0 = false,
        stage_out1 = false;
+  bool rsvt = false;
 };
+
+int rsvt_engine(const tsvd_ctx* c) {
+  switch (c->opts.precision) {
+    case TSVD_PRECISION_TF32: return RSVT_GEMM_TF32;
+    case TSVD_PRECISION_BF16: return RSVT_GEMM_BF16;
+    case TSVD_PRECISION_3XTF32: return RSVT_GEMM_3XTF32;
+    default: return RSVT_GEMM_FP32;
+  }
+}
+
+// Noise floor of the slice products relative to sigma_max: singular values below it are
+// rounding noise of the products and do not count toward the rank the sketch must cover.
+float rsvt_floor(const tsvd_ctx* c) {
+  switch (rsvt_engine(c)) {
+    case RSVT_GEMM_TF32: return 2e-3f;
+    case RSVT_GEMM_BF16: return 1.6e-2f;
+    default: return 3e-6f;
+  }
+}
+
+// A stored slice is real when it is its own conjugate partner.
+bool slice_is_real(const TubeGeom& g, int kf, int kh) {
+  const bool fh = kh == 0 || 2 * kh == g.nh;
+  const bool ff = kf == 0 || 2 * kf == g.nf;
+  return fh && ff;
+}
 
 tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq, Workspace& w) {
   const TubeGeom& g = p.g;
@@ -281,9 +338,26 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   w.ndistinct = (int)c->slices_host.size();
   // scratch for every plan the autotuner may try (or for the one fixed plan)
   size_t jbytes = 0;
-  for (const SliceKnobs& k : candidate_knobs(c, p, w.ndistinct))
-    jbytes = std::max(jbytes, jacobi_svt_scratch_bytes((int)p.n1, (int)p.n2, w.ndistinct, k));
-  size_t off[14], total = 0;
+  if (!rq.rsvt)
+    for (const SliceKnobs& k : candidate_knobs(c, p, w.ndistinct))
+      jbytes = std::max(jbytes, jacobi_svt_scratch_bytes((int)p.n1, (int)p.n2, w.ndistinct, k));
+  // mixed form: orientation and sketch buffers
+  w.rsvt = rq.rsvt;
+  if (rq.rsvt) {
+    const bool tr = p.n1 < p.n2;
+    w.mw = (int)(tr ? p.n2 : p.n1);
+    w.nw = (int)(tr ? p.n1 : p.n2);
+    w.wr = tr ? p.n1 : 1;
+    w.wc = tr ? 1 : p.n1;
+    w.kmax = std::min(w.nw, rsvt_max_k());
+    if (c->opts.rsvt_kmax > 0) w.kmax = std::min(w.kmax, c->opts.rsvt_kmax);
+  }
+  const size_t ns = (size_t)g.nstore, km = (size_t)w.kmax;
+  const size_t rs_nw = rq.rsvt ? ns * w.nw * km * sizeof(float2) : 0;
+  const size_t rs_mw = rq.rsvt ? ns * w.mw * km * sizeof(float2) : 0;
+  const size_t rs_kk = rq.rsvt ? ns * km * km * sizeof(float2) : 0;
+  const size_t rjs = rq.rsvt ? rsvt_jacobi_scratch_bytes(w.nw, w.kmax, w.ndistinct) : 0;
+  size_t off[26], total = 0;
   auto take = [&](int i, size_t bytes) { off[i] = total; total += align_up(bytes); };
   take(0, spec);
   take(1, spec);
@@ -299,6 +373,17 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   take(11, sizeof(SweepAccum));
   take(12, sizeof(int));
   take(13, jbytes);
+  take(14, rs_nw);   // P
+  take(15, rs_mw);   // Y
+  take(16, rs_mw);   // Q
+  take(17, rs_nw);   // Bt
+  take(18, rs_nw);   // Dt
+  take(19, rs_kk);   // G
+  take(20, rs_kk);   // T
+  take(21, rq.rsvt ? ns * km * sizeof(float) : 0);                  // sig
+  take(22, rq.rsvt ? ns : 0);                                       // isreal
+  take(23, rq.rsvt ? tsvd_ctx::kRing * sizeof(RsvtStat) : 0);       // per-iteration stats
+  take(24, rjs);
   if (total > c->ws_cap) {
     if (c->ws) {
       TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -334,6 +419,27 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   w.bad = reinterpret_cast<int*>(b + off[12]);
   w.jscratch = jbytes ? b + off[13] : nullptr;
   w.jscratch_bytes = jbytes;
+  if (rq.rsvt) {
+    w.rP = reinterpret_cast<float2*>(b + off[14]);
+    w.rY = reinterpret_cast<float2*>(b + off[15]);
+    w.rQ = reinterpret_cast<float2*>(b + off[16]);
+    w.rBt = reinterpret_cast<float2*>(b + off[17]);
+    w.rDt = reinterpret_cast<float2*>(b + off[18]);
+    w.rG = reinterpret_cast<float2*>(b + off[19]);
+    w.rT = reinterpret_cast<float2*>(b + off[20]);
+    w.rsig = reinterpret_cast<float*>(b + off[21]);
+    w.risreal = reinterpret_cast<unsigned char*>(b + off[22]);
+    w.rstat = reinterpret_cast<RsvtStat*>(b + off[23]);
+    w.rjs = rjs ? b + off[24] : nullptr;
+    w.rjs_bytes = rjs;
+    c->isreal_host.assign(ns, 0);
+    for (int kh = 0; kh < g.hh; ++kh)
+      for (int kf = 0; kf < g.nf; ++kf)
+        c->isreal_host[(size_t)(kf + g.nf * kh)] = slice_is_real(g, kf, kh) ? 1 : 0;
+    TSVD_CUDA(c, cudaMemcpyAsync(w.risreal, c->isreal_host.data(), ns, cudaMemcpyHostToDevice,
+                                 c->stream));
+    TSVD_CUDA(c, cudaMemsetAsync(w.rstat, 0, tsvd_ctx::kRing * sizeof(RsvtStat), c->stream));
+  }
 
   // twiddles (cos, sin)(2 pi m / n) in FP64, exact at the quarter points
   auto table = [](int n, float2* dst) {
@@ -457,8 +563,12 @@ double threshold_scale(tsvd_ctx* c, const Problem& p) {
 }
 
 tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
-  if (o.precision != TSVD_PRECISION_FP32)
-    return fail(c, TSVD_EUNSUPPORTED, "precision %d is not implemented (FP32 only)", o.precision);
+  if (o.precision < TSVD_PRECISION_FP32 || o.precision > TSVD_PRECISION_RAND_FP32)
+    return fail(c, TSVD_EINVAL, "bad precision %d", o.precision);
+  if (o.rsvt_oversample < 0 || o.rsvt_oversample > 64)
+    return fail(c, TSVD_EINVAL, "rsvt_oversample must be in [0, 64]");
+  if (o.rsvt_kmax < 0) return fail(c, TSVD_EINVAL, "rsvt_kmax must be >= 0");
+  if (o.rsvt_power < 0 || o.rsvt_power > 8) return fail(c, TSVD_EINVAL, "rsvt_power must be in [0, 8]");
   if (o.sparse_mode != TSVD_SPARSE_ENTRY && o.sparse_mode != TSVD_SPARSE_TUBE)
     return fail(c, TSVD_EINVAL, "bad sparse_mode %d", o.sparse_mode);
   if (o.tnn_scale != TSVD_SCALE_AVG && o.tnn_scale != TSVD_SCALE_SUM)
@@ -570,6 +680,146 @@ tsvd_status run_slice(tsvd_ctx* c, const SliceArgs& a) {
   return record_event(c, 0);
 }
 
+// ---- mixed form: randomized slice SVT
+RsvtArgs rsvt_args(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau, int k,
+                   int iter) {
+  RsvtArgs a{};
+  a.ahat = w.spec_a;
+  a.zhat = w.spec_b;
+  a.slices = w.slices;
+  a.nslices = w.ndistinct;
+  a.mw = w.mw;
+  a.nw = w.nw;
+  a.wr = w.wr;
+  a.wc = w.wc;
+  a.N12 = p.g.N12;
+  a.k = k;
+  a.kmax = w.kmax;
+  a.kfill = w.kmax;
+  a.power = 0;
+  a.tau = tau;
+  a.floor_rel = rsvt_floor(c);
+  a.chol_tol = 1e-5f;
+  a.tol = c->opts.jacobi_tol;
+  a.max_sweeps = c->opts.max_sweeps;
+  a.seed = 0x7473766473656564ull;
+  a.iter = iter;
+  a.engine = rsvt_engine(c);
+  a.stat = w.stat;
+  a.acc = w.acc;
+  a.rstat = w.rstat + (iter % tsvd_ctx::kRing);
+  a.P = w.rP;
+  a.Y = w.rY;
+  a.Q = w.rQ;
+  a.Bt = w.rBt;
+  a.Dt = w.rDt;
+  a.G = w.rG;
+  a.T = w.rT;
+  a.sig = w.rsig;
+  a.isreal = w.risreal;
+  a.jscratch = w.rjs;
+  a.jscratch_bytes = w.rjs_bytes;
+  return a;
+}
+
+// Kernels one launch_rsvt call enqueues.
+int rsvt_kernels(const RsvtArgs& a) { return 8 * (a.power + 1) + 3; }
+
+// Smallest sketch width: the oversampling margin over rank 8, rounded up to 8.
+int rsvt_k0(const tsvd_ctx* c, const Workspace& w) {
+  const int k = (8 + c->opts.rsvt_oversample + 7) / 8 * 8;
+  return std::max(1, std::min(k, w.kmax));
+}
+
+int rsvt_k_for(const tsvd_ctx* c, const Workspace& w, int rank) {
+  const int k = (rank + c->opts.rsvt_oversample + 7) / 8 * 8;
+  return std::max(1, std::min(k, w.kmax));
+}
+
+tsvd_status rsvt_host_ring(tsvd_ctx* c) {
+  if (c->rs_host) return TSVD_OK;
+  void* h = nullptr;
+  TSVD_CUDA(c, cudaMallocHost(&h, tsvd_ctx::kRing * sizeof(RsvtStat)));
+  c->rs_host = static_cast<RsvtStat*>(h);
+  std::memset(c->rs_host, 0, tsvd_ctx::kRing * sizeof(RsvtStat));
+  for (int i = 0; i < tsvd_ctx::kRing; ++i)
+    TSVD_CUDA(c, cudaEventCreateWithFlags(&c->rs_ev[i], cudaEventDisableTiming));
+  return TSVD_OK;
+}
+
+// Starts a randomized-SVT sequence: random P (all columns), counters reset.
+tsvd_status rsvt_begin(tsvd_ctx* c, const Problem& p, const Workspace& w) {
+  TSVD_TRY(rsvt_host_ring(c));
+  c->rs_k_last = 0;
+  c->rs_saturated = c->rs_drops = 0;
+  RsvtArgs a = rsvt_args(c, p, w, 0.f, 0, 0);
+  a.rstat = nullptr;
+  TSVD_TRY(launch(c, launch_rsvt_refill(a, 0, w.kmax, c->cur), "sketch initialisation"));
+  return TSVD_OK;
+}
+
+// One randomized slice SVT (iteration `iter` of a sequence) with sketch width k; its
+// statistics land in ring slot iter % kRing of the host copy, signalled by rs_ev.
+tsvd_status rsvt_step(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau, int k,
+                      int iter, int power) {
+  RsvtArgs a = rsvt_args(c, p, w, tau, k, iter);
+  a.power = power;
+  const int slot = iter % tsvd_ctx::kRing;
+  TSVD_CUDA(c, cudaMemsetAsync(a.rstat, 0, sizeof(RsvtStat), c->cur));
+  TSVD_TRY(record_event(c, 0));
+  TSVD_TRY(launch(c, launch_rsvt(a, c->cur), "randomized slice SVT"));
+  c->launches += rsvt_kernels(a) - 1;
+  ++c->slice_launches;
+  TSVD_TRY(record_event(c, 0));
+  TSVD_CUDA(c, cudaMemcpyAsync(c->rs_host + slot, a.rstat, sizeof(RsvtStat),
+                               cudaMemcpyDeviceToHost, c->cur));
+  TSVD_CUDA(c, cudaEventRecord(c->rs_ev[slot], c->cur));
+  c->rs_k_last = k;
+  return TSVD_OK;
+}
+
+// Waits for the statistics of iteration `iter` and folds them into the call's counters.
+tsvd_status rsvt_collect(tsvd_ctx* c, int iter, RsvtStat* out) {
+  const int slot = iter % tsvd_ctx::kRing;
+  TSVD_CUDA(c, cudaEventSynchronize(c->rs_ev[slot]));
+  const RsvtStat s = c->rs_host[slot];
+  c->rs_saturated += s.saturated;
+  c->rs_drops += s.drops;
+  if (out) *out = s;
+  return TSVD_OK;
+}
+
+// The sketch widths of an ADMM loop: iteration t uses the width chosen from the ranks seen in
+// iteration t - 2 (never smaller than the previous width).
+struct RsvtLoop {
+  tsvd_ctx* c;
+  const Problem& p;
+  const Workspace& w;
+  int k = 0;
+  int done = 0;   // iterations whose statistics were collected
+  int issued = 0;
+  RsvtLoop(tsvd_ctx* c_, const Problem& p_, const Workspace& w_) : c(c_), p(p_), w(w_) {}
+  tsvd_status begin() {
+    k = rsvt_k0(c, w);
+    return rsvt_begin(c, p, w);
+  }
+  tsvd_status step(float tau) {
+    while (done + 2 <= issued) {
+      RsvtStat s;
+      TSVD_TRY(rsvt_collect(c, done, &s));
+      k = std::max(k, rsvt_k_for(c, w, s.rank_max));
+      ++done;
+    }
+    TSVD_TRY(rsvt_step(c, p, w, tau, k, issued, 0));
+    ++issued;
+    return TSVD_OK;
+  }
+  tsvd_status finish() {
+    while (done < issued) TSVD_TRY(rsvt_collect(c, done++, nullptr));
+    return TSVD_OK;
+  }
+};
+
 // Runs `body` (which only enqueues kernels through the helpers above) directly, or -- when
 // graphs are enabled and the launch sequence cannot change (`capturable`: no autotuning or
 // host synchronisation left in it) -- replays the CUDA graph cached under `key`, capturing
@@ -660,10 +910,19 @@ tsvd_status fill_stats(tsvd_ctx* c, const Problem& p, const Workspace& w, int it
   stats->rho_final = rho;
   stats->launches = c->launches;
   stats->slice_launches = c->slice_launches;
-  const SliceKnobs k = planned_knobs(c, p, w.ndistinct);
-  stats->slice_ctas = jacobi_svt_ctas_per_slice((int)p.n1, (int)p.n2, w.ndistinct, k);
-  stats->slice_lanes = k.lanes;
-  stats->slice_pairs_in_flight = k.ppg;
+  if (w.rsvt) {
+    const SliceKnobs ak = {0, 0, 0, 0};
+    stats->slice_ctas =
+        c->rs_k_last ? jacobi_svt_ctas_per_slice(w.nw, c->rs_k_last, w.ndistinct, ak) : 0;
+    stats->rsvt_k_last = c->rs_k_last;
+    stats->rsvt_saturated = c->rs_saturated;
+    stats->rsvt_drops = c->rs_drops;
+  } else {
+    const SliceKnobs k = planned_knobs(c, p, w.ndistinct);
+    stats->slice_ctas = jacobi_svt_ctas_per_slice((int)p.n1, (int)p.n2, w.ndistinct, k);
+    stats->slice_lanes = k.lanes;
+    stats->slice_pairs_in_flight = k.ppg;
+  }
   TSVD_TRY(timed_totals(c, &stats->slice_ms, &stats->tube_ms));
   if (iters <= 0) return TSVD_OK;
   SweepAccum acc;
@@ -807,6 +1066,9 @@ void tsvd_default_opts(tsvd_opts* o) {
   o->jacobi_tol = 1e-6f;
   o->autotune = 1;
   o->use_graphs = 1;
+  o->rsvt_oversample = 10;
+  o->rsvt_kmax = 0;
+  o->rsvt_power = 2;
 }
 
 tsvd_status tsvd_create(tsvd_ctx** out, int device, void* cuda_stream, const tsvd_opts* opts) {
@@ -847,6 +1109,9 @@ tsvd_status tsvd_destroy(tsvd_ctx* c) {
   for (cudaStream_t s : c->branches) cudaStreamDestroy(s);
   for (cudaEvent_t e : c->joins) cudaEventDestroy(e);
   if (c->fork) cudaEventDestroy(c->fork);
+  for (cudaEvent_t e : c->rs_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->rs_host) cudaFreeHost(c->rs_host);
   delete c;
   return st;
 }
@@ -871,6 +1136,7 @@ tsvd_status tsvt(tsvd_ctx* c, const float* Y, float* Z, int order, const int64_t
   WsRequest rq;
   rq.stage_in = ky == 1;
   rq.stage_out0 = kz == 1;
+  rq.rsvt = mixed_precision(c);
   Workspace w;
   TSVD_TRY(prepare_workspace(c, p, rq, w));
   const size_t bytes = (size_t)p.N * sizeof(float);
@@ -886,9 +1152,23 @@ tsvd_status tsvt(tsvd_ctx* c, const float* Y, float* Z, int order, const int64_t
   f.in = y;
   f.spec_out = w.spec_a;
   TSVD_TRY(run_tube(c, f, "tube pass (forward)"));
-  TSVD_TRY(tune_slices(c, p, w, tau));
-  SliceArgs s = slice_args(c, p, w, tau);
-  TSVD_TRY(run_slice(c, s));
+  if (w.rsvt) {
+    // random start with power steps; the sketch doubles while the ranks fill it
+    TSVD_TRY(rsvt_begin(c, p, w));
+    int k = rsvt_k0(c, w);
+    for (int attempt = 0;; ++attempt) {
+      TSVD_TRY(rsvt_step(c, p, w, tau, k, attempt, c->opts.rsvt_power));
+      RsvtStat st;
+      TSVD_TRY(rsvt_collect(c, attempt, &st));
+      const int need = rsvt_k_for(c, w, st.rank_max);
+      if (need <= k || k >= w.kmax) break;
+      k = std::min(w.kmax, std::max(need, 2 * k));
+    }
+  } else {
+    TSVD_TRY(tune_slices(c, p, w, tau));
+    SliceArgs s = slice_args(c, p, w, tau);
+    TSVD_TRY(run_slice(c, s));
+  }
   TubeArgs inv = tube_args(p, w, TUBE_INV);
   inv.spec_in = w.spec_b;
   inv.out0 = z;
@@ -922,6 +1202,7 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
   rq.stage_om = ko == 1;
   rq.stage_out0 = kx == 1;
   rq.stage_out1 = Z_out && kzz == 1;
+  rq.rsvt = mixed_precision(c);
   Workspace w;
   TSVD_TRY(prepare_workspace(c, p, rq, w));
   const size_t bytes = (size_t)p.N * sizeof(float);
@@ -955,6 +1236,8 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
     const std::vector<int64_t> key = solver_key(c, 1, p, iters, {m, om, x, z}, kn);
     auto body = [&]() -> tsvd_status {
       double r = c->opts.rho0;
+      RsvtLoop rl(c, p, w);
+      if (w.rsvt) TSVD_TRY(rl.begin());
       // iteration 0: X = P_Omega(M), Q = 0, V = X + Q
       TubeArgs t0 = tube_args(p, w, TUBE_COMPLETE);
       t0.in = w.yn;
@@ -966,9 +1249,13 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
       TSVD_TRY(run_tube(c, t0, "completion pass"));
       for (int k = 0; k < iters; ++k) {
         const float tau = (float)(scale / r);
-        if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
-        SliceArgs s = slice_args(c, p, w, tau);
-        TSVD_TRY(run_slice(c, s));
+        if (w.rsvt) {
+          TSVD_TRY(rl.step(tau));
+        } else {
+          if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
+          SliceArgs s = slice_args(c, p, w, tau);
+          TSVD_TRY(run_slice(c, s));
+        }
         const double r_next = std::fmin(c->opts.mu * r, c->opts.rho_max);
         if (k + 1 < iters) {
           TubeArgs t = tube_args(p, w, TUBE_COMPLETE);
@@ -989,9 +1276,10 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
         inv.out0 = z;
         TSVD_TRY(run_tube(c, inv, "tube pass (inverse)"));
       }
+      if (w.rsvt) TSVD_TRY(rl.finish());
       return TSVD_OK;
     };
-    TSVD_TRY(run_maybe_graph(c, key, tuned, body));
+    TSVD_TRY(run_maybe_graph(c, key, tuned && !w.rsvt, body));
     for (int k = 0; k < iters; ++k) rho = std::fmin(c->opts.mu * rho, c->opts.rho_max);
   }
   if (kx == 1) TSVD_CUDA(c, cudaMemcpyAsync(X_out, x, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -1021,6 +1309,7 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
   rq.stage_in = km == 1;
   rq.stage_out0 = kl == 1;
   rq.stage_out1 = ks == 1;
+  rq.rsvt = mixed_precision(c);
   Workspace w;
   TSVD_TRY(prepare_workspace(c, p, rq, w));
   const size_t bytes = (size_t)p.N * sizeof(float);
@@ -1051,6 +1340,8 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
     key.push_back(lbits);
     auto body = [&]() -> tsvd_status {
       double r = c->opts.rho0;
+      RsvtLoop rl(c, p, w);
+      if (w.rsvt) TSVD_TRY(rl.begin());
       // iteration 0: S = W = 0, so the t-SVT input is M itself
       TubeArgs t0 = tube_args(p, w, TUBE_FWD);
       t0.in = m;
@@ -1058,9 +1349,13 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
       TSVD_TRY(run_tube(c, t0, "tube pass (forward)"));
       for (int k = 0; k < iters; ++k) {
         const float tau = (float)(scale / r);
-        if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
-        SliceArgs s = slice_args(c, p, w, tau);
-        TSVD_TRY(run_slice(c, s));
+        if (w.rsvt) {
+          TSVD_TRY(rl.step(tau));
+        } else {
+          if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
+          SliceArgs s = slice_args(c, p, w, tau);
+          TSVD_TRY(run_slice(c, s));
+        }
         const double r_next = std::fmin(c->opts.mu * r, c->opts.rho_max);
         TubeArgs t = tube_args(p, w, TUBE_RPCA);
         t.in = m;
@@ -1077,9 +1372,10 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
         TSVD_TRY(run_tube(c, t, "RPCA pass"));
         r = r_next;
       }
+      if (w.rsvt) TSVD_TRY(rl.finish());
       return TSVD_OK;
     };
-    TSVD_TRY(run_maybe_graph(c, key, tuned, body));
+    TSVD_TRY(run_maybe_graph(c, key, tuned && !w.rsvt, body));
     for (int k = 0; k < iters; ++k) rho = std::fmin(c->opts.mu * rho, c->opts.rho_max);
   }
   if (kl == 1) TSVD_CUDA(c, cudaMemcpyAsync(L_out, l, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -1096,6 +1392,8 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
   begin_call(c);
   if (count < 0 || (count > 0 && !problems)) return fail(c, TSVD_EINVAL, "bad problem list");
   if (iters < 0) return fail(c, TSVD_EINVAL, "iters must be >= 0");
+  if (mixed_precision(c))
+    return fail(c, TSVD_EUNSUPPORTED, "batched solves run the plain FP32 form only");
   DeviceGuard dg(c->device);
   if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
   std::vector<BatchItem> items((size_t)count);

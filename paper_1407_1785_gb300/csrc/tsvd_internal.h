@@ -103,6 +103,15 @@ struct SliceArgs {
                           // partial rebuilds of multi-CTA slices); nullable = one CTA per slice
   size_t scratch_bytes;
   SliceKnobs knobs;
+  // Optional outputs of the converged vectors W = B V = U diag(sigma) (only when the vectors
+  // are the columns, n1 >= n2): entry e of vector v of slice s (the index the slice list
+  // gives) is written, conjugated when wout_conj, to wout[s * wout_stride + e + n1 * v], and
+  // sigma_v to sigout[s * sig_stride + v].
+  float2* wout = nullptr;
+  int64_t wout_stride = 0;
+  int wout_conj = 0;
+  float* sigout = nullptr;
+  int64_t sig_stride = 0;
 };
 
 // Returns cudaErrorInvalidValue when a slice does not fit the kernel's shared memory.
@@ -115,5 +124,72 @@ bool jacobi_svt_plan_ok(int n1, int n2, int nslices, const SliceKnobs& k);
 size_t jacobi_svt_scratch_bytes(int n1, int n2, int nslices, const SliceKnobs& k);
 // CTAs per slice the launch would use.
 int jacobi_svt_ctas_per_slice(int n1, int n2, int nslices, const SliceKnobs& k);
+
+// ---- batched complex GEMM with generic strides (rsvt.cu, tc_gemm.cu)
+// One operand or the result: entry (i0, i1) of batch entry b at
+// p[(idx ? idx[b] : b) * bs + i0 * s0 + i1 * s1], conjugated when conj.
+struct CMat {
+  const float2* p;
+  const int* idx;
+  int64_t bs;
+  int64_t s0, s1;
+  int conj;
+};
+// C(i, j) = sum_l A(i, l) B(l, j) for i < M, j < N, l < K, for every batch entry.
+struct CGemm {
+  int M, N, K, batch;
+  CMat a, b, c;
+};
+// Arithmetic of the slice products: FP32 on CUDA cores, or 3M complex products on the tensor
+// cores with TF32, BF16 or split (3xTF32) operands and FP32 accumulation.
+enum RsvtEngine : int { RSVT_GEMM_FP32 = 0, RSVT_GEMM_TF32 = 1, RSVT_GEMM_BF16 = 2,
+                        RSVT_GEMM_3XTF32 = 3 };
+cudaError_t launch_cgemm(const CGemm& g, int engine, cudaStream_t st);
+cudaError_t launch_cgemm_tc(const CGemm& g, int engine, cudaStream_t st);
+
+// ---- randomized, rank-adaptive slice SVT (rsvt.cu)
+struct RsvtStat {
+  int rank_max;    // max over slices of the singular values above max(tau, floor sigma_max)
+  int saturated;   // slices whose whole sketch lay above that level
+  int drops;       // columns dropped by the Cholesky factorisations
+  int pad;
+};
+
+struct RsvtArgs {
+  const float2* ahat;     // input spectrum (slices at slices[s] * N12)
+  float2* zhat;           // output spectrum
+  const int* slices;      // stored slice indices to process
+  int nslices;
+  int mw, nw;             // working matrix Aw: mw x nw (nw <= mw)
+  int64_t wr, wc;         // Aw(i, j) at i * wr + j * wc inside a slice
+  int64_t N12;
+  int k, kmax;            // sketch width of this call; allocated width
+  int kfill;              // columns of P to refill after the call (<= kmax)
+  int power;              // extra power steps (0 in warm-started ADMM loops)
+  float tau;
+  float floor_rel;        // noise floor of the products, relative to sigma_max
+  float chol_tol;         // dropped-pivot tolerance of CholeskyQR
+  float tol;              // Jacobi rotation tolerance
+  int max_sweeps;
+  unsigned long long seed;
+  int iter;               // counter of the random refills
+  int engine;             // RsvtEngine
+  SliceStat* stat;        // per stored slice (nullable)
+  SweepAccum* acc;        // nullable
+  RsvtStat* rstat;        // nullable
+  // per stored slice: P nw x kmax, Y and Q mw x kmax, Bt and Dt nw x kmax, G and T kmax x kmax,
+  // sig kmax; isreal: 1 for slices whose matrix is real (self-conjugate)
+  float2 *P, *Y, *Q, *Bt, *Dt, *G, *T;
+  float* sig;
+  const unsigned char* isreal;
+  void* jscratch;
+  size_t jscratch_bytes;
+};
+
+int rsvt_max_k();
+size_t rsvt_jacobi_scratch_bytes(int nw, int kmax, int nslices);
+cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st);
+// Refill columns c < kfill of P that carry no direction (all of them when k = 0).
+cudaError_t launch_rsvt_refill(const RsvtArgs& a, int k, int kfill, cudaStream_t st);
 
 }  // namespace tsvd

@@ -23,6 +23,7 @@ TSVD_ETIMEOUT, TSVD_EUNSUPPORTED = 5, 6
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT",
                 6: "EUNSUPPORTED"}
 PRECISION_FP32, PRECISION_TF32, PRECISION_BF16, PRECISION_3XTF32 = 0, 1, 2, 3
+PRECISION_RAND_FP32 = 4
 SPARSE_ENTRY, SPARSE_TUBE = 0, 1
 SCALE_AVG, SCALE_SUM = 0, 1
 
@@ -47,7 +48,8 @@ class Opts(ctypes.Structure):
                 ("timing", ctypes.c_int), ("ctas_per_slice", ctypes.c_int),
                 ("accumulate_v", ctypes.c_int), ("lanes_per_pair", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p),
-                ("use_graphs", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("rsvt_oversample", ctypes.c_int),
+                ("rsvt_kmax", ctypes.c_int), ("rsvt_power", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -58,7 +60,8 @@ class Stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("slice_launches", ctypes.c_int64),
                 ("slice_ms", ctypes.c_double), ("tube_ms", ctypes.c_double),
                 ("slice_ctas", ctypes.c_int), ("slice_lanes", ctypes.c_int),
-                ("slice_pairs_in_flight", ctypes.c_int)]
+                ("slice_pairs_in_flight", ctypes.c_int), ("rsvt_k_last", ctypes.c_int),
+                ("rsvt_saturated", ctypes.c_int64), ("rsvt_drops", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

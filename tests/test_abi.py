@@ -49,6 +49,7 @@ def test_default_opts():
     assert o.rho_max == pytest.approx(1e10)
     assert o.max_sweeps == 40
     assert o.jacobi_tol == pytest.approx(1e-6)
+    assert (o.rsvt_oversample, o.rsvt_kmax, o.rsvt_power) == (10, 0, 2)
 
 
 def test_null_arguments_are_rejected_without_touching_a_device():
@@ -68,9 +69,12 @@ def test_bad_options_rejected():
     o.mu = 0.5
     h = ctypes.c_void_p()
     assert L.tsvd_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == libtsvd.TSVD_EINVAL
-    o = libtsvd.default_opts()
-    o.precision = libtsvd.PRECISION_BF16
-    assert L.tsvd_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == libtsvd.TSVD_EUNSUPPORTED
+    for field, bad in (("precision", 5), ("precision", -1), ("rsvt_oversample", -1),
+                       ("rsvt_oversample", 65), ("rsvt_kmax", -3), ("rsvt_power", 9)):
+        o = libtsvd.default_opts()
+        setattr(o, field, bad)
+        assert L.tsvd_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == libtsvd.TSVD_EINVAL
+    assert not h.value
 
 
 def test_create_without_gpu_reports_cuda_error():
