@@ -778,6 +778,15 @@ tsvd_status rsvt_step(tsvd_ctx* c, const Problem& p, const Workspace& w, float t
   return TSVD_OK;
 }
 
+// Tensor-core products whose bounded waits expired make the call fail with ETIMEOUT.
+tsvd_status rsvt_check_timeouts(tsvd_ctx* c) {
+  if (rsvt_engine(c) == RSVT_GEMM_FP32) return TSVD_OK;
+  int n = 0;
+  TSVD_CUDA(c, tc_gemm_take_timeouts(&n, c->stream));
+  if (n) return fail(c, TSVD_ETIMEOUT, "%d tensor-core product launches timed out", n);
+  return TSVD_OK;
+}
+
 // Waits for the statistics of iteration `iter` and folds them into the call's counters.
 tsvd_status rsvt_collect(tsvd_ctx* c, int iter, RsvtStat* out) {
   const int slot = iter % tsvd_ctx::kRing;
@@ -816,7 +825,7 @@ struct RsvtLoop {
   }
   tsvd_status finish() {
     while (done < issued) TSVD_TRY(rsvt_collect(c, done++, nullptr));
-    return TSVD_OK;
+    return rsvt_check_timeouts(c);
   }
 };
 
@@ -1164,6 +1173,7 @@ tsvd_status tsvt(tsvd_ctx* c, const float* Y, float* Z, int order, const int64_t
       if (need <= k || k >= w.kmax) break;
       k = std::min(w.kmax, std::max(need, 2 * k));
     }
+    TSVD_TRY(rsvt_check_timeouts(c));
   } else {
     TSVD_TRY(tune_slices(c, p, w, tau));
     SliceArgs s = slice_args(c, p, w, tau);

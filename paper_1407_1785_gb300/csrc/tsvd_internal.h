@@ -146,6 +146,9 @@ enum RsvtEngine : int { RSVT_GEMM_FP32 = 0, RSVT_GEMM_TF32 = 1, RSVT_GEMM_BF16 =
                         RSVT_GEMM_3XTF32 = 3 };
 cudaError_t launch_cgemm(const CGemm& g, int engine, cudaStream_t st);
 cudaError_t launch_cgemm_tc(const CGemm& g, int engine, cudaStream_t st);
+// Number of tensor-core product launches whose bounded waits expired since the last call
+// (reset to 0); waits for `st`.
+cudaError_t tc_gemm_take_timeouts(int* count, cudaStream_t st);
 
 // ---- randomized, rank-adaptive slice SVT (rsvt.cu)
 struct RsvtStat {

@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 # (name, precision value, per-call tolerance, equal-error slack of the recovery error)
 FORMS = [("rand_fp32", 4, 1e-4, 0.01), ("3xtf32", 3, 1e-4, 0.01), ("tf32", 1, 1e-3, 0.01),
          ("bf16", 2, 1e-2, 0.05)]
-IMPLEMENTED = {"rand_fp32"}
+IMPLEMENTED = {"rand_fp32", "3xtf32", "tf32", "bf16"}
 
 
 def _forms():
