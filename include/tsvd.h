@@ -215,6 +215,25 @@ typedef struct tsvd_problem {
 tsvd_status tsvd_solve_batched(tsvd_ctx* ctx, int count, const tsvd_problem* problems, int iters,
                                tsvd_stats* stats);
 
+/* Operand forms of tsvd_cgemm: as stored, transposed, conjugate-transposed. */
+enum { TSVD_OP_N = 0, TSVD_OP_T = 1, TSVD_OP_C = 2 };
+
+/* Batched complex product of Fourier slices, C_b = op(A_b) op(B_b) for b < batch: the
+ * slice-wise product by which the t-product is computed in the Fourier domain (Sec. 2.1),
+ * and the engine of the mixed form's slice products.  Complex single precision, interleaved
+ * (re, im), column-major: entry (i, j) of a matrix with leading dimension ld at float offset
+ * 2 (i + j ld); matrix b of A starts stride_a complex entries after matrix b - 1 (likewise
+ * for B and C).  op(A) is m x k, op(B) is k x n, C is m x n (lda, ldb, ldc >= the stored
+ * row counts).  Arithmetic follows the context's precision: FP32 and RAND_FP32 on CUDA cores
+ * in FP32; TF32, BF16 and 3XTF32 as 3M products on the tensor cores (see
+ * TSVD_PRECISION_*).  A, B and C are device pointers on the context's device (C must not
+ * overlap A or B); asynchronous on the context's stream.  Errors: EINVAL (bad sizes, strides
+ * or pointers). */
+tsvd_status tsvd_cgemm(tsvd_ctx* ctx, int transa, int transb, int m, int n, int k,
+                       const float* A, int64_t lda, int64_t stride_a, const float* B,
+                       int64_t ldb, int64_t stride_b, float* C, int64_t ldc, int64_t stride_c,
+                       int batch);
+
 /* The paper has no counterpart to this entry point; it exists for callers that cannot
  * allocate device memory.  Some callers cannot call cudaMalloc: a process that has handed the
  * whole device memory budget to its own pool allocator (a later cudaMalloc fails or fragments

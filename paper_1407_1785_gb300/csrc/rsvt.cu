@@ -126,9 +126,13 @@ __global__ void __launch_bounds__(256) cgemm_fp32_kernel(CGemm g) {
 }
 
 // One CTA per slice: column-scaled Cholesky factorisation Gs = R^H R of the k x k Gram G
-// (col-major, ld ldg) with dropped pivots, then T = D^-1 R^-1 (zero columns for dropped
-// pivots), written over the same layout.  Shared memory: S (k x (k+1) complex: R in the upper
-// triangle, then (R^-1)^T in the strict lower triangle), pivots and scales in FP64.
+// (col-major, ld ldg) with dropped pivots, and T = D^-1 R^-1 (zero columns for dropped
+// pivots), written over the same layout.  R^-1 is built in the same k steps as R, as the
+// coefficients of Gram-Schmidt on the scaled columns: at step j column x_j of R^-1 is final
+// once scaled by 1 / R_jj, and every later column subtracts R_jl x_j.  Shared memory: S
+// (k x (k+1) complex) holds R in the upper triangle and (R^-1)^T in the strict lower one; the
+// diagonal of R^-1, the pivots and the column scales sit in separate arrays (pivots in FP64).
+// Threads form a 16 x 16 grid over the trailing block.
 __global__ void __launch_bounds__(256) cholqr_factor_kernel(const float2* G, float2* T,
                                                             const int* slices, int k, int ldg,
                                                             int64_t gs, float tol,
@@ -143,6 +147,7 @@ __global__ void __launch_bounds__(256) cholqr_factor_kernel(const float2* G, flo
   int* okc = reinterpret_cast<int*>(xd + k);
   __shared__ double s_dmax;
   const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tx = tid & 15, ty = tid >> 4;
   const float2* Gp = G + (size_t)s * gs;
   float2* Tp = T + (size_t)s * gs;
 
@@ -162,85 +167,80 @@ __global__ void __launch_bounds__(256) cholqr_factor_kernel(const float2* G, flo
     const bool zero = !(dsc[i] > dmin) || s_dmax == 0.0;
     dd[i] = zero ? 0.0 : 1.0;
     if (zero) dsc[i] = 1.0;
+    xd[i] = make_float2(1.f, 0.f);
   }
   __syncthreads();
-  for (int idx = tid; idx < k * k; idx += nthr) {
-    const int r = idx % k, c = idx / k;
-    if (r > c) continue;
-    float2 v = Gp[r + (size_t)c * ldg];
-    const float inv = (float)(1.0 / (dsc[r] * dsc[c]));
-    v.x *= inv;
-    v.y *= inv;
-    if (dd[r] == 0.0 || dd[c] == 0.0) v = make_float2(0.f, 0.f);
-    S[(size_t)r * ldS + c] = v;
-  }
+  // scaled Gram in the upper triangle, zero (R^-1)^T in the strict lower triangle
+  for (int r = ty; r < k; r += 16)
+    for (int c = tx; c < k; c += 16) {
+      float2 v = make_float2(0.f, 0.f);
+      if (r <= c && dd[r] != 0.0 && dd[c] != 0.0) {
+        v = Gp[r + (size_t)c * ldg];
+        const float inv = (float)(1.0 / (dsc[r] * dsc[c]));
+        v.x *= inv;
+        v.y *= inv;
+      }
+      S[(size_t)r * ldS + c] = v;
+    }
   __syncthreads();
 
   for (int j = 0; j < k; ++j) {
     const double pj = dd[j];
     const bool okj = pj > (double)tol;
     const float rjj = okj ? (float)sqrt(pj) : 1.f;
-    const float irjj = 1.f / rjj;
+    const float irjj = okj ? 1.f / rjj : 0.f;
+    // row j of R; x_j scaled by 1 / R_jj (zeroed when the column is dropped)
     for (int l = j + 1 + tid; l < k; l += nthr) {
       const float2 v = S[(size_t)j * ldS + l];
-      S[(size_t)j * ldS + l] = okj ? make_float2(v.x * irjj, v.y * irjj) : make_float2(0.f, 0.f);
+      S[(size_t)j * ldS + l] = make_float2(v.x * irjj, v.y * irjj);
+    }
+    for (int i = tid; i < j; i += nthr) {
+      const float2 v = S[(size_t)j * ldS + i];
+      S[(size_t)j * ldS + i] = make_float2(v.x * irjj, v.y * irjj);
     }
     if (tid == 0) {
       S[(size_t)j * ldS + j] = make_float2(rjj, 0.f);
+      const float2 v = xd[j];
+      xd[j] = make_float2(v.x * irjj, v.y * irjj);
       okc[j] = okj ? 1 : 0;
     }
     __syncthreads();
     if (okj) {
-      const int nt = k - j - 1;
-      // S(l, l2) -= conj(R(j, l)) R(j, l2) on the upper triangle of the trailing block
-      for (int idx = tid; idx < nt * nt; idx += nthr) {
-        const int l = j + 1 + idx / nt, l2 = j + 1 + idx % nt;
-        if (l2 < l) continue;
-        const float2 a = S[(size_t)j * ldS + l], b = S[(size_t)j * ldS + l2];
-        float2 v = S[(size_t)l * ldS + l2];
-        v.x -= a.x * b.x + a.y * b.y;
-        v.y -= a.x * b.y - a.y * b.x;
-        S[(size_t)l * ldS + l2] = v;
-      }
-      for (int l = j + 1 + tid; l < k; l += nthr) {
+      // trailing Schur complement (upper triangle) and its FP64 pivots
+      for (int l = j + 1 + ty; l < k; l += 16) {
         const float2 a = S[(size_t)j * ldS + l];
-        dd[l] -= (double)a.x * a.x + (double)a.y * a.y;
+        for (int l2 = l + tx; l2 < k; l2 += 16) {
+          const float2 b = S[(size_t)j * ldS + l2];
+          float2 v = S[(size_t)l * ldS + l2];
+          v.x -= a.x * b.x + a.y * b.y;
+          v.y -= a.x * b.y - a.y * b.x;
+          S[(size_t)l * ldS + l2] = v;
+        }
+        if (tx == 0) dd[l] -= (double)a.x * a.x + (double)a.y * a.y;
+        // x_l -= R_jl x_j on entries i <= j (X(i, l) kept at S(l, i), X(j, j) in xd)
+        for (int i = tx; i <= j; i += 16) {
+          const float2 xj = i == j ? xd[j] : S[(size_t)j * ldS + i];
+          float2 v = S[(size_t)l * ldS + i];
+          v.x -= a.x * xj.x - a.y * xj.y;
+          v.y -= a.x * xj.y + a.y * xj.x;
+          S[(size_t)l * ldS + i] = v;
+        }
       }
     }
     __syncthreads();
   }
-
-  // X = R^-1 column by column (one thread per column): X(i, c) for i < c kept at S(c, i)
-  for (int c = tid; c < k; c += nthr) {
-    const float xcc = 1.f / S[(size_t)c * ldS + c].x;
-    xd[c] = make_float2(xcc, 0.f);
-    for (int i = c - 1; i >= 0; --i) {
-      // sum_{l = i+1..c} R(i, l) X(l, c)
-      const float2 ric = S[(size_t)i * ldS + c];
-      float sr = ric.x * xcc, si = ric.y * xcc;
-      for (int l = i + 1; l < c; ++l) {
-        const float2 r = S[(size_t)i * ldS + l];
-        const float2 x = S[(size_t)c * ldS + l];
-        sr += r.x * x.x - r.y * x.y;
-        si += r.x * x.y + r.y * x.x;
-      }
-      const float inv = -1.f / S[(size_t)i * ldS + i].x;
-      S[(size_t)c * ldS + i] = make_float2(sr * inv, si * inv);
-    }
-  }
-  __syncthreads();
   // T(i, c) = X(i, c) / d_i, zero below the diagonal and in dropped columns
-  for (int idx = tid; idx < k * k; idx += nthr) {
-    const int i = idx % k, c = idx / k;
-    float2 v = make_float2(0.f, 0.f);
-    if (okc[c] && i <= c) {
-      v = i == c ? xd[c] : S[(size_t)c * ldS + i];
-      const float inv = (float)(1.0 / dsc[i]);
-      v.x *= inv;
-      v.y *= inv;
+  for (int c = ty; c < k; c += 16)
+    for (int i = tx; i < k; i += 16) {
+      float2 v = make_float2(0.f, 0.f);
+      if (okc[c] && i <= c) {
+        v = i == c ? xd[c] : S[(size_t)c * ldS + i];
+        const float inv = (float)(1.0 / dsc[i]);
+        v.x *= inv;
+        v.y *= inv;
+      }
+      Tp[i + (size_t)c * ldg] = v;
     }
-    Tp[i + (size_t)c * ldg] = v;
-  }
   if (rstat && tid == 0) {
     int nd = 0;
     for (int c = 0; c < k; ++c) nd += okc[c] ? 0 : 1;
@@ -347,11 +347,11 @@ cudaError_t launch_cgemm(const CGemm& g, int engine, cudaStream_t st) {
 
 int rsvt_max_k() { return 128; }
 
-size_t rsvt_jacobi_scratch_bytes(int nw, int kmax, int nslices) {
+size_t rsvt_jacobi_scratch_bytes(int nw, int kmax, int nslices, const SliceKnobs& kn) {
   size_t b = 0;
-  SliceKnobs auto_k = {0, 0, 0, 0};
   for (int k = 1; k <= kmax; ++k)
-    if (jacobi_svt_supported(nw, k)) b = std::max(b, jacobi_svt_scratch_bytes(nw, k, nslices, auto_k));
+    if (jacobi_svt_plan_ok(nw, k, nslices, kn))
+      b = std::max(b, jacobi_svt_scratch_bytes(nw, k, nslices, kn));
   return b;
 }
 
@@ -424,7 +424,7 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
   j.acc = a.acc;
   j.scratch = a.jscratch;
   j.scratch_bytes = a.jscratch_bytes;
-  j.knobs = {0, 0, 0, 0};
+  j.knobs = a.jknobs;
   j.wout = a.P;
   j.wout_stride = ps;
   j.wout_conj = 1;

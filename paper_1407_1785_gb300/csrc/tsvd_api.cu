@@ -320,6 +320,11 @@ float rsvt_floor(const tsvd_ctx* c) {
   }
 }
 
+// Plan of the mixed form's small Jacobi SVTs: the context's fixed choices, else the planner's.
+SliceKnobs rsvt_knobs(const tsvd_ctx* c) {
+  return {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, 0};
+}
+
 // A stored slice is real when it is its own conjugate partner.
 bool slice_is_real(const TubeGeom& g, int kf, int kh) {
   const bool fh = kh == 0 || 2 * kh == g.nh;
@@ -356,7 +361,7 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   const size_t rs_nw = rq.rsvt ? ns * w.nw * km * sizeof(float2) : 0;
   const size_t rs_mw = rq.rsvt ? ns * w.mw * km * sizeof(float2) : 0;
   const size_t rs_kk = rq.rsvt ? ns * km * km * sizeof(float2) : 0;
-  const size_t rjs = rq.rsvt ? rsvt_jacobi_scratch_bytes(w.nw, w.kmax, w.ndistinct) : 0;
+  const size_t rjs = rq.rsvt ? rsvt_jacobi_scratch_bytes(w.nw, w.kmax, w.ndistinct, rsvt_knobs(c)) : 0;
   size_t off[26], total = 0;
   auto take = [&](int i, size_t bytes) { off[i] = total; total += align_up(bytes); };
   take(0, spec);
@@ -719,6 +724,7 @@ RsvtArgs rsvt_args(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau,
   a.isreal = w.risreal;
   a.jscratch = w.rjs;
   a.jscratch_bytes = w.rjs_bytes;
+  a.jknobs = rsvt_knobs(c);
   return a;
 }
 
@@ -920,9 +926,8 @@ tsvd_status fill_stats(tsvd_ctx* c, const Problem& p, const Workspace& w, int it
   stats->launches = c->launches;
   stats->slice_launches = c->slice_launches;
   if (w.rsvt) {
-    const SliceKnobs ak = {0, 0, 0, 0};
     stats->slice_ctas =
-        c->rs_k_last ? jacobi_svt_ctas_per_slice(w.nw, c->rs_k_last, w.ndistinct, ak) : 0;
+        c->rs_k_last ? jacobi_svt_ctas_per_slice(w.nw, c->rs_k_last, w.ndistinct, rsvt_knobs(c)) : 0;
     stats->rsvt_k_last = c->rs_k_last;
     stats->rsvt_saturated = c->rs_saturated;
     stats->rsvt_drops = c->rs_drops;
@@ -1592,6 +1597,61 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
     }
   }
   TSVD_CUDA(c, cudaGetLastError());
+  return TSVD_OK;
+}
+
+tsvd_status tsvd_cgemm(tsvd_ctx* c, int transa, int transb, int m, int n, int k,
+                       const float* A, int64_t lda, int64_t stride_a, const float* B,
+                       int64_t ldb, int64_t stride_b, float* C, int64_t ldc, int64_t stride_c,
+                       int batch) {
+  if (!c) return TSVD_EINVAL;
+  begin_call(c);
+  auto op_ok = [](int t) { return t == TSVD_OP_N || t == TSVD_OP_T || t == TSVD_OP_C; };
+  if (!op_ok(transa) || !op_ok(transb)) return fail(c, TSVD_EINVAL, "bad operand form");
+  if (m < 0 || n < 0 || k < 0 || batch < 0) return fail(c, TSVD_EINVAL, "negative size");
+  if (m == 0 || n == 0 || batch == 0) return TSVD_OK;
+  if (!A || !B || !C) return fail(c, TSVD_EINVAL, "A, B and C must not be NULL");
+  const int64_t ra = transa == TSVD_OP_N ? m : k, rb = transb == TSVD_OP_N ? k : n;
+  if (lda < std::max<int64_t>(1, ra) || ldb < std::max<int64_t>(1, rb) ||
+      ldc < std::max<int64_t>(1, m))
+    return fail(c, TSVD_EINVAL, "leading dimension too small");
+  if (batch > 1 && (stride_a < 0 || stride_b < 0 || stride_c < ldc * n))
+    return fail(c, TSVD_EINVAL, "bad batch stride");
+  if (batch > 65535) return fail(c, TSVD_EINVAL, "batch must be <= 65535");
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
+  if (pointer_kind(A, c->device) != 0 || pointer_kind(B, c->device) != 0 ||
+      pointer_kind(C, c->device) != 0)
+    return fail(c, TSVD_EINVAL, "A, B and C must be device memory of the context's device");
+  CGemm g;
+  g.M = m;
+  g.N = n;
+  g.K = k;
+  g.batch = batch;
+  // op(A)(i, l)
+  g.a.p = reinterpret_cast<const float2*>(A);
+  g.a.idx = nullptr;
+  g.a.bs = stride_a;
+  g.a.s0 = transa == TSVD_OP_N ? 1 : lda;
+  g.a.s1 = transa == TSVD_OP_N ? lda : 1;
+  g.a.conj = transa == TSVD_OP_C;
+  // op(B)(l, j)
+  g.b.p = reinterpret_cast<const float2*>(B);
+  g.b.idx = nullptr;
+  g.b.bs = stride_b;
+  g.b.s0 = transb == TSVD_OP_N ? 1 : ldb;
+  g.b.s1 = transb == TSVD_OP_N ? ldb : 1;
+  g.b.conj = transb == TSVD_OP_C;
+  g.c.p = reinterpret_cast<const float2*>(C);
+  g.c.idx = nullptr;
+  g.c.bs = stride_c;
+  g.c.s0 = 1;
+  g.c.s1 = ldc;
+  g.c.conj = 0;
+  const int engine = c->opts.precision == TSVD_PRECISION_FP32 ? RSVT_GEMM_FP32 : rsvt_engine(c);
+  TSVD_TRY(record_event(c, 0));
+  TSVD_TRY(launch(c, launch_cgemm(g, engine, c->stream), "complex product"));
+  TSVD_TRY(record_event(c, 0));
   return TSVD_OK;
 }
 

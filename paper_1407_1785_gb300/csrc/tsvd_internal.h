@@ -187,10 +187,11 @@ struct RsvtArgs {
   const unsigned char* isreal;
   void* jscratch;
   size_t jscratch_bytes;
+  SliceKnobs jknobs;      // plan of the small Jacobi SVTs (0 = planner's choice)
 };
 
 int rsvt_max_k();
-size_t rsvt_jacobi_scratch_bytes(int nw, int kmax, int nslices);
+size_t rsvt_jacobi_scratch_bytes(int nw, int kmax, int nslices, const SliceKnobs& kn);
 cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st);
 // Refill columns c < kfill of P that carry no direction (all of them when k = 0).
 cudaError_t launch_rsvt_refill(const RsvtArgs& a, int k, int kfill, cudaStream_t st);

@@ -29,7 +29,9 @@ SCALE_AVG, SCALE_SUM = 0, 1
 
 # Every symbol include/tsvd.h declares.
 EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_last_error",
-                    "tsvt", "tnn_complete", "trpca", "tsvd_solve_batched", "tsvt_static")
+                    "tsvt", "tnn_complete", "trpca", "tsvd_solve_batched", "tsvt_static",
+                    "tsvd_cgemm")
+OP_N, OP_T, OP_C = 0, 1, 2
 PROBLEM_COMPLETE, PROBLEM_RPCA = 1, 2
 
 
@@ -113,6 +115,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tsvd_solve_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
                                      ctypes.POINTER(Stats)]
     L.tsvd_solve_batched.restype = ctypes.c_int
+    i64 = ctypes.c_int64
+    L.tsvd_cgemm.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                             ctypes.c_int, P, i64, i64, P, i64, i64, P, i64, i64, ctypes.c_int]
+    L.tsvd_cgemm.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -241,6 +247,14 @@ class Context:
                                         ctypes.byref(s) if stats else None)
         self._check("tsvd_solve_batched", st)
         return s.as_dict() if stats else None
+
+    def cgemm(self, transa, transb, m, n, k, A, lda, stride_a, B, ldb, stride_b, C, ldc,
+              stride_c, batch):
+        """C_b = op(A_b) op(B_b) on complex64 column-major device buffers (see tsvd_cgemm)."""
+        st = self._L.tsvd_cgemm(self._h, int(transa), int(transb), int(m), int(n), int(k),
+                                _ptr(A), int(lda), int(stride_a), _ptr(B), int(ldb),
+                                int(stride_b), _ptr(C), int(ldc), int(stride_c), int(batch))
+        self._check("tsvd_cgemm", st)
 
     # raw status variants (for error-path tests)
     def raw_tnn_complete(self, M_obs, omega, order, dims, iters, X_out, Z_out=None) -> int:
