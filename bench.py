@@ -1,12 +1,29 @@
 #!/usr/bin/env python
-"""ADMM throughput of t-SVT TNN completion on the 144 x 176 x 100 video workload.
+"""ADMM throughput of t-SVT tensor completion / tensor RPCA on one GB300.
 
-One step = one complete TNN completion solve (150 ADMM iterations: tube pass + batched
-Jacobi t-SVT per iteration) of a seeded synthetic grayscale video (a smooth texture under
-linear camera motion plus N(0, 0.01^2) noise, 20% of entries observed), with the inputs
-already resident on the GPU.  `value` is ADMM iterations per second over the whole job.
+One step = one complete ADMM solve of a seeded synthetic workload with its inputs already
+resident on the GPU; `value` is ADMM iterations per second over the whole job (for the
+batched workload an iteration advances all 64 tensors).  Workloads (`--workload`):
+
+  video    grayscale video completion 144x176x100 (translating texture + N(0, 0.01^2)
+           noise), 20% of entries observed, 150 iterations            [default]
+  rpca     tensor RPCA, L = tubal-rank-10 t-product of N(0,1) factors 240x320x60,
+           10% entrywise corruption U[-5, 5], lambda = 1/sqrt(320*60), 200 iterations
+  color    colour video completion 288x352x3x60 (per-channel textures), 15% observed,
+           150 iterations, FFT along modes 3 and 4
+  lowrank  tubal-rank-3 32x32x16, 50% observed, 100 iterations
+  batch    64 tensors of uneven shapes (n1, n2 in [48, 256], n3 in [8, 64]), half completion
+           and half RPCA, 100 iterations, one batched call
+
+`--precision` picks the slice SVT of the headline line: fp32 (plain one-sided Jacobi) or a
+mixed form (tf32, bf16, 3xtf32: tensor-core products; rand_fp32: CUDA-core products).  For
+the plain headline on a single-tensor workload, `--mixed` (default 3xtf32) also times that
+mixed form on the same workload and steps and reports it, with its final recovery error and
+whether it meets the equal-error rule (e_mixed <= e_plain + 0.01 e_plain + 1e-5: no worse
+than the plain form's recovery error beyond 1%), under the key "mixed".
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                        [--workload NAME] [--precision P] [--mixed P|none]
 For N > 1 run under torchrun (one rank per GPU); every rank solves its own replica (weak
 scaling, no collective on the data path) and the slowest rank's time counts.
 """
@@ -31,15 +48,31 @@ if ROOT not in sys.path:
 import numpy as np
 
 METRIC = "t-SVT ADMM iters/s & HBM/TC roofline %, mixed/batched vs plain FP32 at equal err"
-N1, N2, N3, P_OBS, ITERS = 144, 176, 100, 0.2, 150
-WORKLOAD = (f"grayscale video completion {N1}x{N2}x{N3}, {int(P_OBS * 100)}% observed, "
-            f"{ITERS} ADMM iterations per step, plain FP32 one-sided Jacobi t-SVT")
 FLUSH_BYTES = 256 << 20      # > 129 MB L2
 SMS = 152
 FP32_LANES_PER_SM = 128
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates
+PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "3xtf32": 3, "rand_fp32": 4}
+# executed tensor-core flops per algorithmic flop of a complex product (3M: 6 of 8; 3XTF32
+# issues three products per real product)
+EXECUTED_PER_ALG = {"tf32": 0.75, "bf16": 0.75, "3xtf32": 2.25, "rand_fp32": 0.0}
 
-# DRAM traffic of one jacobi_svt_kernel launch from an ncu capture of this workload, valid
-# only for the kernel source it was taken on (see profiles/).
+WORKLOADS = {
+    "video": dict(kind="complete", iters=150, cpu_iters=10,
+                  desc="grayscale video completion 144x176x100, 20% observed"),
+    "rpca": dict(kind="rpca", iters=200, cpu_iters=2,
+                 desc="tensor RPCA 240x320x60, tubal rank 10, 10% entrywise corruption"),
+    "color": dict(kind="complete", iters=150, cpu_iters=1,
+                  desc="colour video completion 288x352x3x60, 15% observed"),
+    "lowrank": dict(kind="complete", iters=100, cpu_iters=100,
+                    desc="low-tubal-rank completion 32x32x16, rank 3, 50% observed"),
+    "batch": dict(kind="batch", iters=100, cpu_iters=10,
+                  desc="64 uneven tensors (n1, n2 in [48, 256], n3 in [8, 64]), half "
+                       "completion / half RPCA, one batched call"),
+}
+
+# DRAM traffic of one jacobi_svt_kernel launch from an ncu capture of the video workload,
+# valid only for the kernel source it was taken on (see profiles/).
 TRAFFIC = {"source": "paper_1407_1785_gb300/csrc/slice_svt.cu",
            "sha256": "8f46dfad975484d40755d0d1dd1c1444b478ba1a6e75877ecee5e31e4378f61b",
            "bytes_per_launch": 10575360 + 15321344}
@@ -51,9 +84,13 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--iters", type=int, default=ITERS)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="video")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32")
+    ap.add_argument("--mixed", choices=sorted(PRECISIONS) + ["none"], default="3xtf32")
+    ap.add_argument("--iters", type=int, default=0, help="ADMM iterations per step (0 = the "
+                    "workload's count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-iters", type=int, default=10)
+    ap.add_argument("--cpu-sample-iters", type=int, default=0)
     return ap.parse_args()
 
 
@@ -126,71 +163,273 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def jacobi_alg_flops_per_launch(n1, n2, nslices):
+def file_sha256(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def half_slices(dims):
+    """Distinct Fourier slices the t-SVT computes (conjugate symmetry of the last mode)."""
+    if len(dims) == 3:
+        return dims[2] // 2 + 1
+    n3, n4 = dims[2], dims[3]
+    hh = n4 // 2 + 1
+    self_cols = 1 + (1 if n4 % 2 == 0 else 0)
+    return n3 * hh - self_cols * ((n3 - 1) // 2)
+
+
+def jacobi_gvl_flops(n1, n2, nslices):
     """Golub-Van Loan operation count of a complex SVD returning Sigma and V of an m x n
     matrix (m >= n): 4 (4 m n^2 + 8 n^3) real flops, per distinct Fourier slice."""
     m, n = max(n1, n2), min(n1, n2)
     return 4.0 * (4.0 * m * n * n + 8.0 * n ** 3) * nslices
 
 
-def tube_alg_bytes_per_launch(N, nslices, n12):
-    """Completion tube pass: read Zhat (complex half spectrum), V, Y; write V, Vhat."""
-    sc = 8.0 * n12 * nslices
+def tube_bytes(dims):
+    """Tube pass per iteration: read the complex half spectrum, write the next one, and read /
+    write the real state tensors (completion: read Yn and V, write V; RPCA: read M and W,
+    write W)."""
+    N = int(np.prod(dims))
+    n12 = dims[0] * dims[1]
+    stored = (dims[2] if len(dims) == 4 else 1) * (dims[-1] // 2 + 1)
+    sc = 8.0 * n12 * stored
     return 2 * sc + 3 * 4.0 * N
 
 
-def file_sha256(path):
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+# ------------------------------------------------------------------------------- workloads
+
+def build_workload(name, seed):
+    """Host inputs of one workload: dict with kind, dims, M, omega / lam, truth; for the batch
+    a list of such dicts under "items"."""
+    from paper_1407_1785_gb300 import synth
+    if name in ("video", "color", "lowrank"):
+        gen = {"video": synth.workload_video_completion, "color": synth.workload_color_video,
+               "lowrank": synth.workload_lowrank_completion}[name]
+        X, om = gen(seed=seed)
+        return dict(kind="complete", dims=X.shape, M=(X * om).astype(np.float32), omega=om,
+                    truth=X)
+    if name == "rpca":
+        M, L0, S0, sup, lam = synth.workload_rpca(seed=seed)
+        return dict(kind="rpca", dims=M.shape, M=M.astype(np.float32), lam=lam, truth=L0)
+    if name == "batch":
+        items = []
+        for b, sp in enumerate(synth.workload_batch_shapes(seed=seed)):
+            s = seed * 1000 + b
+            L = synth.lowrank_tensor(sp["n1"], sp["n2"], sp["n3"], sp["rank"], seed=s)
+            if sp["kind"] == "complete":
+                om = synth.sampling_mask(L.shape, sp["p"], seed=s)
+                items.append(dict(kind="complete", dims=L.shape,
+                                  M=(L * om).astype(np.float32), omega=om, truth=L))
+            else:
+                S, _ = synth.sparse_corruption(L.shape, sp["frac"], seed=s)
+                lam = 1.0 / math.sqrt(max(sp["n1"], sp["n2"]) * sp["n3"])
+                items.append(dict(kind="rpca", dims=L.shape, M=(L + S).astype(np.float32),
+                                  lam=lam, truth=L))
+        return dict(kind="batch", items=items)
+    raise ValueError(name)
 
 
-def cpu_baseline(Mobs64, om, iters_sample):
+def to_device(wl):
+    import torch
+    from paper_1407_1785_gb300 import synth
+
+    def one(it):
+        d = dict(it)
+        d["m"] = torch.from_numpy(synth.to_colmajor(it["M"])).cuda()
+        if it["kind"] == "complete":
+            d["o"] = torch.from_numpy(synth.to_colmajor(it["omega"], np.uint8)).cuda()
+        d["out0"] = torch.empty_like(d["m"])
+        d["out1"] = torch.empty_like(d["m"])
+        return d
+    if wl["kind"] == "batch":
+        return dict(kind="batch", items=[one(it) for it in wl["items"]])
+    return one(wl)
+
+
+def solver(ctx, dw, iters):
+    """A callable running one full solve through the C ABI (device buffers); returns stats."""
+    if dw["kind"] == "complete":
+        return lambda: ctx.tnn_complete(dw["m"], dw["o"], dw["dims"], iters, dw["out0"],
+                                        stats=True)
+    if dw["kind"] == "rpca":
+        return lambda: ctx.trpca(dw["m"], dw["dims"], dw["lam"], iters, dw["out0"], dw["out1"],
+                                 stats=True)
+    probs = []
+    for it in dw["items"]:
+        q = dict(kind=it["kind"], dims=it["dims"], M=it["m"], out0=it["out0"], out1=it["out1"])
+        if it["kind"] == "complete":
+            q["omega"] = it["o"]
+        else:
+            q["lam"] = it["lam"]
+        probs.append(q)
+    return lambda: ctx.solve_batched(probs, iters, stats=True)
+
+
+def recovery_errors(dw):
+    """Relative Frobenius recovery error of each tensor against its ground truth."""
+    from paper_1407_1785_gb300 import synth
+    items = dw["items"] if dw["kind"] == "batch" else [dw]
+    out = []
+    for it in items:
+        R = synth.from_colmajor(it["out0"].cpu().numpy(), it["dims"])
+        out.append(float(np.linalg.norm(R - it["truth"]) / np.linalg.norm(it["truth"])))
+    return out
+
+
+def n_voxels(wl):
+    items = wl["items"] if wl["kind"] == "batch" else [wl]
+    return sum(int(np.prod(it["dims"])) for it in items)
+
+
+# ------------------------------------------------------------------------------- oracle timing
+
+def oracle_sample(wl, iters_sample):
+    """Times the FP64 oracle on a bounded sample of the workload; returns (iters/s of the whole
+    workload, seconds, description of the sample)."""
     import oracle
     oracle.build()
+    items = wl["items"] if wl["kind"] == "batch" else [wl]
+    take = items[:4] if wl["kind"] == "batch" else items
     t0 = time.perf_counter()
-    oracle.tnn_complete(Mobs64, om, iters_sample)
+    for it in take:
+        M = it["M"].astype(np.float64)
+        if it["kind"] == "complete":
+            oracle.tnn_complete(M, it["omega"], iters_sample)
+        else:
+            oracle.trpca(M, it["lam"], iters_sample)
     dt = time.perf_counter() - t0
-    return {"value": iters_sample / dt, "unit": "iters/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"first {iters_sample} of the {ITERS} ADMM iterations of the same "
-                      f"{N1}x{N2}x{N3} completion (FP64 C oracle, OpenMP over slices)",
-            "seconds": dt}
+    frac = sum(int(np.prod(it["dims"])) for it in take) / n_voxels(wl)
+    what = (f"first {iters_sample} ADMM iterations of the same workload" if wl["kind"] != "batch"
+            else f"first {iters_sample} ADMM iterations of the first {len(take)} of the 64 "
+                 f"tensors, scaled by their share of the voxels ({frac:.3f})")
+    return iters_sample * frac / dt, dt, what + " (FP64 C oracle, OpenMP over slices)"
 
 
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return 0
-    from paper_1407_1785_gb300 import synth
     import oracle
-    oracle.build()
-    X, om = synth.workload_video_completion(seed=1)
-    Mobs = (X * om).astype(np.float32).astype(np.float64)
-    sample = 2                                   # ADMM iterations per bounded step
+    wl = build_workload(args.workload, 1)
+    spec = WORKLOADS[args.workload]
+    sample = args.cpu_sample_iters or max(1, min(spec["cpu_iters"], 2))
     for _ in range(args.warmup):
-        oracle.tnn_complete(Mobs, om, sample)
-    t0 = time.perf_counter()
+        oracle_sample(wl, sample)
+    tot, what = 0.0, ""
+    vals = []
     for _ in range(args.steps):
-        oracle.tnn_complete(Mobs, om, sample)
-    dt = time.perf_counter() - t0
-    value = sample * args.steps / dt
+        v, dt, what = oracle_sample(wl, sample)
+        tot += dt
+        vals.append(v)
+    value = len(vals) / sum(1.0 / v for v in vals)      # whole-run rate
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": dt * 1000.0 / args.steps, "higher_is_better": True,
+        "ms_per_step": tot * 1000.0 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n1": N1, "n2": N2, "n3": N3, "observed": P_OBS,
-                   "admm_iters_per_step": sample, "seed": 1},
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "admm_iters_per_step": sample,
+                   "seed": 1},
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": "iters/s", "cores": oracle.num_threads(),
-                         "kind": "oracle",
-                         "sample": f"{sample} ADMM iterations per step of the same "
-                                   f"{N1}x{N2}x{N3} completion (FP64 C oracle)"},
+                         "kind": "oracle", "sample": what},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------------------- GPU runs
+
+def timed_solves(solve, steps, flush, stream, barrier):
+    """K timed solves (L2 flushed before each); returns (ms of the whole region, stats list)."""
+    import torch
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    ev0.record(stream)
+    for _ in range(steps):
+        flush.zero_()
+        stats.append(solve())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return ev0.elapsed_time(ev1), stats
+
+
+def sum_stats(stats, key):
+    return sum(s[key] for s in stats)
+
+
+def alu_peak(peaks):
+    return SMS * FP32_LANES_PER_SM * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+
+
+def mixed_rooflines(stats, prec_name, peaks):
+    g_gf, g_ms = sum_stats(stats, "rsvt_gemm_gflop"), sum_stats(stats, "rsvt_gemm_ms")
+    s_gf, s_ms = sum_stats(stats, "rsvt_svd_gflop"), sum_stats(stats, "rsvt_svd_ms")
+    peak = alu_peak(peaks)
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) * TF32_PER_BF16
+    svd_tf = s_gf / max(s_ms, 1e-9)      # GFLOP / ms = TFLOP/s
+    gemm_tf = g_gf / max(g_ms, 1e-9)
+    roof_svd = {"bound": "alu", "kernel": "jacobi_svt_kernel (n x k projections)",
+                "achieved": svd_tf, "peak": peak, "unit": "TFLOP/s", "frac": svd_tf / peak,
+                "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x max SM clock",
+                "alg": "Golub-Van Loan 4 (4 n k^2 + 8 k^3) per n x k projection",
+                "ms": s_ms}
+    if prec_name == "rand_fp32":
+        roof_gemm = {"bound": "alu", "kernel": "cgemm_fp32_kernel", "achieved": gemm_tf,
+                     "peak": peak, "unit": "TFLOP/s", "frac": gemm_tf / peak, "traffic": None,
+                     "peak_source": "derived FP32 CUDA-core peak",
+                     "alg": "8 m n k per complex product", "ms": g_ms}
+    else:
+        roof_gemm = {"bound": "tensor", "kernel": f"cgemm_tc_kernel ({prec_name})",
+                     "achieved": gemm_tf, "peak": tf32_peak, "unit": "TFLOP/s",
+                     "frac": gemm_tf / tf32_peak, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 1.1/2.25",
+                     "alg": "8 m n k per complex product; executed tensor flops per algorithmic "
+                            f"flop {EXECUTED_PER_ALG.get(prec_name, 0)}",
+                     "ms": g_ms}
+    return roof_svd, roof_gemm
+
+
+def mixed_form(args, dw, iters, prec_name, e_plain, stream, flush, barrier, peaks, t_plain_ms):
+    """Times the mixed form on the same workload; returns the "mixed" object."""
+    from paper_1407_1785_gb300 import libtsvd
+    ctx = libtsvd.Context(device=stream.device.index, stream=stream.cuda_stream, timing=1,
+                          precision=PRECISIONS[prec_name])
+    solve = solver(ctx, dw, iters)
+    for _ in range(max(args.warmup, 1)):
+        solve()
+    t_ms, stats = timed_solves(solve, args.steps, flush, stream, barrier)
+    ctx.close()
+    e = recovery_errors(dw)[0]
+    n_it = iters * args.steps
+    parts = {"small_svd": sum_stats(stats, "rsvt_svd_ms"),
+             "slice_products": sum_stats(stats, "rsvt_gemm_ms"),
+             "cholqr2": sum_stats(stats, "rsvt_orth_ms"),
+             "tube_pass": sum_stats(stats, "tube_ms")}
+    parts["other"] = max(t_ms - sum(parts.values()), 0.0)
+    roof_svd, roof_gemm = mixed_rooflines(stats, prec_name, peaks)
+    dominant = max(("small_svd", "slice_products", "cholqr2", "tube_pass"), key=parts.get)
+    return {
+        "precision": prec_name, "value": iters * args.steps / (t_ms / 1000.0),
+        "unit": "iters/s", "ms_per_step": t_ms / args.steps,
+        "speedup_vs_plain": t_plain_ms / t_ms,
+        "final_rse_db": 20 * math.log10(e), "plain_rse_db": 20 * math.log10(e_plain),
+        # equal error: not worse than the plain form's recovery error beyond 1% (+1e-5)
+        "equal_error": e <= e_plain + 0.01 * e_plain + 1e-5,
+        "sketch_width_last": stats[-1]["rsvt_k_last"],
+        "saturated_slice_svts": stats[-1]["rsvt_saturated"],
+        "ms_per_iter": {k: v / n_it for k, v in parts.items()},
+        "dominant": dominant,
+        "roofline_small_svd": roof_svd,
+        "roofline_slice_products": roof_gemm,
+        "gpu_launches": sum_stats(stats, "launches"),
+    }
 
 
 def run_ours(args):
@@ -207,122 +446,143 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    iters = args.iters
-    X, om = synth.workload_video_completion(seed=1 + rank)
-    Mobs = (X * om).astype(np.float32)
-    dims = Mobs.shape
-    N = Mobs.size
+    spec = WORKLOADS[args.workload]
+    iters = args.iters or spec["iters"]
+    wl = build_workload(args.workload, 1 + rank)
+    batch = wl["kind"] == "batch"
+    items = wl["items"] if batch else [wl]
+    N = n_voxels(wl)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(Mobs.astype(np.float64), om, args.cpu_sample_iters)
+        import oracle
+        v, dt, what = oracle_sample(wl, args.cpu_sample_iters or spec["cpu_iters"])
+        cpu = {"value": v, "unit": "iters/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": what, "seconds": dt}
 
     stream = torch.cuda.current_stream()
-    m = torch.from_numpy(synth.to_colmajor(Mobs)).cuda()
-    o = torch.from_numpy(synth.to_colmajor(om, np.uint8)).cuda()
-    x = torch.empty_like(m)
+    dw = to_device(wl)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    ctx = libtsvd.Context(device=local, stream=stream.cuda_stream, timing=1)
-
+    prec = args.precision
+    ctx = libtsvd.Context(device=local, stream=stream.cuda_stream, timing=1,
+                          precision=PRECISIONS[prec])
+    solve = solver(ctx, dw, iters)
     for _ in range(max(args.warmup, 0)):
-        ctx.tnn_complete(m, o, dims, iters, x)
+        solve()
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
     sampler.start()
-    barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    slice_ms = tube_ms = 0.0
-    slice_launches = launches = 0
-    sweeps = 0
-    nonconv = 0
-    ev0.record(stream)
-    for _ in range(args.steps):
-        flush.zero_()
-        st = ctx.tnn_complete(m, o, dims, iters, x, stats=True)
-        slice_ms += st["slice_ms"]
-        tube_ms += st["tube_ms"]
-        slice_launches += st["slice_launches"]
-        launches += st["launches"]
-        sweeps += st["total_sweeps"]
-        nonconv += st["nonconverged"]
-        plan = {"ctas_per_slice": st["slice_ctas"], "lanes_per_pair": st["slice_lanes"],
-                "pairs_in_flight": st["slice_pairs_in_flight"]}
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    t_ms, stats = timed_solves(solve, args.steps, flush, stream, barrier)
     clocks = sampler.stop()
-    t_ms = ev0.elapsed_time(ev1)
     if world > 1:
         tt = torch.tensor([t_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
     value = world * iters * args.steps / (t_ms / 1000.0)
+    errs = recovery_errors(dw)
+    slice_ms, tube_ms = sum_stats(stats, "slice_ms"), sum_stats(stats, "tube_ms")
+    slice_launches, launches = sum_stats(stats, "slice_launches"), sum_stats(stats, "launches")
 
-    Xg = synth.from_colmajor(x.cpu().numpy(), dims)
-    rse = 20 * math.log10(np.linalg.norm(Xg - X) / np.linalg.norm(X))
+    # end to end through the public API from pinned host buffers, copies inside the region
+    ctx_e2e = None
+    if batch:
+        hin = [(torch.from_numpy(synth.to_colmajor(it["M"])).pin_memory(),
+                torch.from_numpy(synth.to_colmajor(it["omega"], np.uint8)).pin_memory()
+                if it["kind"] == "complete" else None) for it in items]
+        hout = [torch.empty(it["m"].numel(), dtype=torch.float32).pin_memory()
+                for it in dw["items"]]
 
-    # end to end through the public API with host buffers (pinned), copies inside
-    mh = torch.from_numpy(synth.to_colmajor(Mobs)).pin_memory()
-    oh = torch.from_numpy(synth.to_colmajor(om, np.uint8)).pin_memory()
-    xh = torch.empty(N, dtype=torch.float32).pin_memory()
-    ctx_e2e = libtsvd.Context(device=local, stream=stream.cuda_stream)
-    ctx_e2e.tnn_complete(mh, oh, dims, iters, xh)          # warm-up (workspace)
+        def e2e_step():
+            for (mh, oh), it in zip(hin, dw["items"]):
+                it["m"].copy_(mh, non_blocking=True)
+                if oh is not None:
+                    it["o"].copy_(oh, non_blocking=True)
+            solve()
+            for xh, it in zip(hout, dw["items"]):
+                xh.copy_(it["out0"], non_blocking=True)
+            torch.cuda.synchronize()
+        h2d = sum(mh.numel() * 4 + (oh.numel() if oh is not None else 0) for mh, oh in hin)
+        d2h = sum(xh.numel() * 4 for xh in hout)
+    else:
+        mh = torch.from_numpy(synth.to_colmajor(wl["M"])).pin_memory()
+        xh = torch.empty(N, dtype=torch.float32).pin_memory()
+        ctx_e2e = libtsvd.Context(device=local, stream=stream.cuda_stream,
+                                  precision=PRECISIONS[prec])
+        dims = wl["dims"]
+        if wl["kind"] == "complete":
+            oh = torch.from_numpy(synth.to_colmajor(wl["omega"], np.uint8)).pin_memory()
+
+            def e2e_step():
+                ctx_e2e.tnn_complete(mh, oh, dims, iters, xh)   # returns after the D2H copy
+            h2d, d2h = mh.numel() * 4 + oh.numel(), xh.numel() * 4
+        else:
+            sh = torch.empty(N, dtype=torch.float32).pin_memory()
+
+            def e2e_step():
+                ctx_e2e.trpca(mh, dims, wl["lam"], iters, xh, sh)
+            h2d, d2h = mh.numel() * 4, 2 * xh.numel() * 4
+    e2e_step()                                             # warm-up (workspace)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ctx_e2e.tnn_complete(mh, oh, dims, iters, xh)      # returns after the D2H copy
+        e2e_step()
     e2e_s = time.perf_counter() - t0
     if world > 1:
         tt = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
     e2e = {"value": world * iters * args.steps / e2e_s, "unit": "iters/s",
-           "h2d_bytes_per_step": int(mh.numel() * 4 + oh.numel()),
-           "d2h_bytes_per_step": int(xh.numel() * 4)}
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     peaks = measured_peaks()
-    hh = N3 // 2 + 1
-    flops = jacobi_alg_flops_per_launch(N1, N2, hh)
-    slice_avg_s = (slice_ms / max(slice_launches, 1)) / 1000.0
-    achieved = flops / slice_avg_s / 1e12
-    peak_alu = SMS * FP32_LANES_PER_SM * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
-    traffic = None
-    if TRAFFIC["sha256"] and TRAFFIC["bytes_per_launch"]:
-        if file_sha256(os.path.join(ROOT, TRAFFIC["source"])) == TRAFFIC["sha256"]:
-            traffic = TRAFFIC["bytes_per_launch"]
-    roofline = {"bound": "alu", "kernel": "jacobi_svt_kernel", "achieved": achieved,
-                "peak": peak_alu, "unit": "TFLOP/s", "frac": achieved / peak_alu,
-                "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x max SM clock",
-                "alg_flops_per_launch": flops, "avg_launch_ms": slice_avg_s * 1e3,
-                "share_of_step": slice_ms / t_ms}
-    tube_launches = max(launches - slice_launches - args.steps, 1)
-    tube_avg_s = (tube_ms / tube_launches) / 1000.0
-    tbytes = tube_alg_bytes_per_launch(N, hh, N1 * N2)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    roofline_tube = {"bound": "hbm", "kernel": "tube_pass_kernel", "achieved": tbytes / tube_avg_s / 1e9,
-                     "peak": hbm_peak, "unit": "GB/s",
-                     "frac": tbytes / tube_avg_s / 1e9 / hbm_peak,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback",
-                     "alg_bytes_per_launch": tbytes, "avg_launch_ms": tube_avg_s * 1e3}
+    n_it = iters * args.steps
+    if prec == "fp32":
+        # algorithmic flops of one iteration (all tensors), per-iteration slice time
+        flops = sum(jacobi_gvl_flops(it["dims"][0], it["dims"][1], half_slices(it["dims"]))
+                    for it in items)
+        achieved = flops / (slice_ms / 1000.0 / n_it) / 1e12
+        traffic = None
+        if (args.workload == "video" and
+                file_sha256(os.path.join(ROOT, TRAFFIC["source"])) == TRAFFIC["sha256"]):
+            traffic = TRAFFIC["bytes_per_launch"]
+        roofline = {"bound": "alu", "kernel": "jacobi_svt_kernel", "achieved": achieved,
+                    "peak": alu_peak(peaks), "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak(peaks), "traffic": traffic,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x max SM clock",
+                    "alg_flops_per_iteration": flops,
+                    "avg_launch_ms": slice_ms / max(slice_launches, 1),
+                    "share_of_step": slice_ms / t_ms}
+    else:
+        roof_svd, roof_gemm = mixed_rooflines(stats, prec, peaks)
+        roofline = roof_svd if roof_svd["ms"] >= roof_gemm["ms"] else roof_gemm
+    t_bytes = sum(tube_bytes(it["dims"]) for it in items)
+    roofline_tube = None
+    if tube_ms > 0:
+        gbs = t_bytes * n_it / (tube_ms / 1000.0) / 1e9
+        roofline_tube = {"bound": "hbm", "kernel": "tube_pass_kernel", "achieved": gbs,
+                         "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                         "peak_source": ("MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks
+                                         else "fallback"),
+                         "alg_bytes_per_iteration": t_bytes, "ms_per_iteration": tube_ms / n_it}
 
+    mixed = None
+    if not batch and prec == "fp32" and args.mixed not in ("none", "fp32"):
+        mixed = mixed_form(args, dw, iters, args.mixed, errs[0], stream, flush, barrier, peaks,
+                           t_ms)
+
+    e_db = [20 * math.log10(max(e, 1e-300)) for e in errs]
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n1": N1, "n2": N2, "n3": N3, "observed": P_OBS,
-                   "admm_iters_per_step": iters, "seed": 1,
-                   "l2": "flushed between steps (256 MiB write); per-step working set ~62 MB",
+        "config": {"workload": spec["desc"], "admm_iters_per_step": iters, "seed": 1,
+                   "precision": prec, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "voxels_per_s": value * N1 * N2 * N3,
-        "final_rse_db": rse,
-        "jacobi_sweeps_per_slice_svd": sweeps / max(slice_launches * hh, 1),
-        "jacobi_nonconverged": nonconv,
-        "slice_plan": plan,
+        "voxels_per_s": value * N,
+        "final_rse_db": e_db[0] if not batch else statistics.mean(e_db),
         "roofline": roofline,
         "roofline_tube": roofline_tube,
         "cpu_baseline": cpu,
@@ -330,8 +590,26 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if batch:
+        line["final_rse_db_max"] = max(e_db)
+    if prec == "fp32":
+        line["jacobi_sweeps_per_slice_svd"] = (sum_stats(stats, "total_sweeps") /
+                                               max(sum_stats(stats, "slice_svds"), 1))
+        line["jacobi_nonconverged"] = sum_stats(stats, "nonconverged")
+        line["slice_plan"] = {"ctas_per_slice": stats[-1]["slice_ctas"],
+                              "lanes_per_pair": stats[-1]["slice_lanes"],
+                              "pairs_in_flight": stats[-1]["slice_pairs_in_flight"]}
+    else:
+        line["sketch_width_last"] = stats[-1]["rsvt_k_last"]
+        line["ms_per_iter"] = {"small_svd": sum_stats(stats, "rsvt_svd_ms") / n_it,
+                               "slice_products": sum_stats(stats, "rsvt_gemm_ms") / n_it,
+                               "cholqr2": sum_stats(stats, "rsvt_orth_ms") / n_it,
+                               "tube_pass": tube_ms / n_it}
+    if mixed is not None:
+        line["mixed"] = mixed
     ctx.close()
-    ctx_e2e.close()
+    if ctx_e2e is not None:
+        ctx_e2e.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -136,6 +136,14 @@ typedef struct tsvd_stats {
                                    threshold (the result may miss directions) */
   int64_t rsvt_drops;           /* mixed form: sketch columns dropped as dependent by the
                                    CholeskyQR factorisations (refilled at random) */
+  double rsvt_gemm_ms;          /* mixed form, timing=1: device time of the three slice
+                                   products (sketch, projection, rebuild) */
+  double rsvt_orth_ms;          /* ... of the CholeskyQR2 orthonormalisations */
+  double rsvt_svd_ms;           /* ... of the small Jacobi SVTs */
+  double rsvt_gemm_gflop;       /* algorithmic GFLOP of those products: 8 m n k per complex
+                                   m x k times k x n product */
+  double rsvt_svd_gflop;        /* Golub-Van Loan count of the small SVDs: 4 (4 n k^2 + 8 k^3)
+                                   per n x k matrix */
 } tsvd_stats;
 
 /* Fill *opts with the defaults listed above. */

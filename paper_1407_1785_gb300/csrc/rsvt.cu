@@ -132,8 +132,10 @@ __global__ void __launch_bounds__(256) cgemm_fp32_kernel(CGemm g) {
 // once scaled by 1 / R_jj, and every later column subtracts R_jl x_j.  Shared memory: S
 // (k x (k+1) complex) holds R in the upper triangle and (R^-1)^T in the strict lower one; the
 // diagonal of R^-1, the pivots and the column scales sit in separate arrays (pivots in FP64).
-// Threads form a 16 x 16 grid over the trailing block.
-__global__ void __launch_bounds__(256) cholqr_factor_kernel(const float2* G, float2* T,
+// Threads form a 32 x 32 grid over the trailing block.  A Gram that is already the identity
+// to FP32 resolution (every scaled off-diagonal entry below 1e-6, the usual case of the second
+// pass) skips the factorisation: R = I, T = D^-1.
+__global__ void __launch_bounds__(1024) cholqr_factor_kernel(const float2* G, float2* T,
                                                             const int* slices, int k, int ldg,
                                                             int64_t gs, float tol,
                                                             RsvtStat* rstat) {
@@ -144,10 +146,11 @@ __global__ void __launch_bounds__(256) cholqr_factor_kernel(const float2* G, flo
   double* dd = reinterpret_cast<double*>(S + (size_t)k * ldS);
   double* dsc = dd + k;
   float2* xd = reinterpret_cast<float2*>(dsc + k);
-  int* okc = reinterpret_cast<int*>(xd + k);
+  float* isc = reinterpret_cast<float*>(xd + k);
+  int* okc = reinterpret_cast<int*>(isc + k);
   __shared__ double s_dmax;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int tx = tid & 31, ty = tid >> 5;
   const float2* Gp = G + (size_t)s * gs;
   float2* Tp = T + (size_t)s * gs;
 
@@ -167,27 +170,45 @@ __global__ void __launch_bounds__(256) cholqr_factor_kernel(const float2* G, flo
     const bool zero = !(dsc[i] > dmin) || s_dmax == 0.0;
     dd[i] = zero ? 0.0 : 1.0;
     if (zero) dsc[i] = 1.0;
+    isc[i] = (float)(1.0 / dsc[i]);
     xd[i] = make_float2(1.f, 0.f);
   }
   __syncthreads();
   // scaled Gram in the upper triangle, zero (R^-1)^T in the strict lower triangle
-  for (int r = ty; r < k; r += 16)
-    for (int c = tx; c < k; c += 16) {
+  for (int r = ty; r < k; r += 32)
+    for (int c = tx; c < k; c += 32) {
       float2 v = make_float2(0.f, 0.f);
       if (r <= c && dd[r] != 0.0 && dd[c] != 0.0) {
         v = Gp[r + (size_t)c * ldg];
-        const float inv = (float)(1.0 / (dsc[r] * dsc[c]));
+        const float inv = isc[r] * isc[c];
         v.x *= inv;
         v.y *= inv;
       }
       S[(size_t)r * ldS + c] = v;
     }
   __syncthreads();
+  {
+    int far = 0;
+    for (int r = ty; r < k; r += 32)
+      for (int c = r + 1 + tx; c < k; c += 32) {
+        const float2 v = S[(size_t)r * ldS + c];
+        far |= fabsf(v.x) + fabsf(v.y) > 1e-6f;
+      }
+    for (int r = tid; r < k; r += nthr) far |= dd[r] == 0.0;
+    if (__syncthreads_or(far) == 0) {
+      // R = I: T = D^-1
+      for (int c = ty; c < k; c += 32)
+        for (int i = tx; i < k; i += 32)
+          Tp[i + (size_t)c * ldg] = i == c ? make_float2(isc[i], 0.f) : make_float2(0.f, 0.f);
+      return;
+    }
+  }
 
   for (int j = 0; j < k; ++j) {
+    // the pivot is accumulated in FP64 (cancellation); its square root needs only FP32
     const double pj = dd[j];
     const bool okj = pj > (double)tol;
-    const float rjj = okj ? (float)sqrt(pj) : 1.f;
+    const float rjj = okj ? sqrtf((float)pj) : 1.f;
     const float irjj = okj ? 1.f / rjj : 0.f;
     // row j of R; x_j scaled by 1 / R_jj (zeroed when the column is dropped)
     for (int l = j + 1 + tid; l < k; l += nthr) {
@@ -207,9 +228,9 @@ __global__ void __launch_bounds__(256) cholqr_factor_kernel(const float2* G, flo
     __syncthreads();
     if (okj) {
       // trailing Schur complement (upper triangle) and its FP64 pivots
-      for (int l = j + 1 + ty; l < k; l += 16) {
+      for (int l = j + 1 + ty; l < k; l += 32) {
         const float2 a = S[(size_t)j * ldS + l];
-        for (int l2 = l + tx; l2 < k; l2 += 16) {
+        for (int l2 = l + tx; l2 < k; l2 += 32) {
           const float2 b = S[(size_t)j * ldS + l2];
           float2 v = S[(size_t)l * ldS + l2];
           v.x -= a.x * b.x + a.y * b.y;
@@ -218,7 +239,7 @@ __global__ void __launch_bounds__(256) cholqr_factor_kernel(const float2* G, flo
         }
         if (tx == 0) dd[l] -= (double)a.x * a.x + (double)a.y * a.y;
         // x_l -= R_jl x_j on entries i <= j (X(i, l) kept at S(l, i), X(j, j) in xd)
-        for (int i = tx; i <= j; i += 16) {
+        for (int i = tx; i <= j; i += 32) {
           const float2 xj = i == j ? xd[j] : S[(size_t)j * ldS + i];
           float2 v = S[(size_t)l * ldS + i];
           v.x -= a.x * xj.x - a.y * xj.y;
@@ -230,14 +251,13 @@ __global__ void __launch_bounds__(256) cholqr_factor_kernel(const float2* G, flo
     __syncthreads();
   }
   // T(i, c) = X(i, c) / d_i, zero below the diagonal and in dropped columns
-  for (int c = ty; c < k; c += 16)
-    for (int i = tx; i < k; i += 16) {
+  for (int c = ty; c < k; c += 32)
+    for (int i = tx; i < k; i += 32) {
       float2 v = make_float2(0.f, 0.f);
       if (okc[c] && i <= c) {
         v = i == c ? xd[c] : S[(size_t)c * ldS + i];
-        const float inv = (float)(1.0 / dsc[i]);
-        v.x *= inv;
-        v.y *= inv;
+        v.x *= isc[i];
+        v.y *= isc[i];
       }
       Tp[i + (size_t)c * ldg] = v;
     }
@@ -257,7 +277,7 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
 // Uniform in [-1, 1) from a counter (SplitMix64 finaliser of key + counter * golden gamma).
 __device__ __forceinline__ float urand(unsigned long long key, unsigned long long ctr) {
   const unsigned long long h = mix64(key + (ctr + 1ull) * 0x9e3779b97f4a7c15ull);
-  return (float)((double)(h >> 11) * (1.0 / 4503599627370496.0) - 1.0);
+  return (float)(unsigned)(h >> 40) * (1.0f / 8388608.0f) - 1.0f;   // 24 bits, FP32
 }
 
 // One CTA per slice.  Counts the singular values above max(tau, floor * sigma_max) among the
@@ -305,7 +325,7 @@ __global__ void __launch_bounds__(256) rsvt_refill_kernel(float2* P, const float
 
 size_t cholqr_smem(int k) {
   return (size_t)k * (k + 1) * sizeof(float2) + 2 * (size_t)k * sizeof(double) +
-         (size_t)k * sizeof(float2) + (size_t)k * sizeof(int);
+         (size_t)k * sizeof(float2) + (size_t)k * sizeof(float) + (size_t)k * sizeof(int);
 }
 
 cudaError_t gemm_fp32(const CGemm& g, cudaStream_t st) {
@@ -382,11 +402,17 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  // stage boundaries for the caller's timing (power-step-free calls only)
+  auto mark = [&](int i) -> cudaError_t {
+    return (a.stage_ev && a.power == 0) ? cudaEventRecord(a.stage_ev[i], st) : cudaSuccess;
+  };
+  if ((e = mark(0)) != cudaSuccess) return e;
   for (int pw = 0; pw <= a.power; ++pw) {
     // Y = Aw P   (power steps: P = conj(Bt) of the previous projection)
     const CMat Pm = pw == 0 ? mat(a.P, idx, ps, 1, nw) : mat(a.Bt, idx, bs, 1, nw, 1);
     e = launch_cgemm(gemm(mw, k, nw, ns, Aw, Pm, mat(a.Y, idx, ys, 1, mw)), a.engine, st);
     if (e != cudaSuccess) return e;
+    if ((e = mark(1)) != cudaSuccess) return e;
     // CholeskyQR2: Y -> Q -> Y
     for (int pass = 0; pass < 2; ++pass) {
       float2* src = pass == 0 ? a.Y : a.Q;
@@ -395,7 +421,7 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
                          mat(a.G, idx, gs, 1, kmax)),
                     st);
       if (e != cudaSuccess) return e;
-      cholqr_factor_kernel<<<ns, 256, csm, st>>>(a.G, a.T, idx, k, kmax, gs, a.chol_tol,
+      cholqr_factor_kernel<<<ns, 1024, csm, st>>>(a.G, a.T, idx, k, kmax, gs, a.chol_tol,
                                                  a.rstat);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       e = gemm_fp32(gemm(mw, k, k, ns, mat(src, idx, ys, 1, mw), mat(a.T, idx, gs, 1, kmax),
@@ -403,10 +429,12 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
                     st);
       if (e != cudaSuccess) return e;
     }
+    if ((e = mark(2)) != cudaSuccess) return e;
     // Bt = Aw^T conj(Q)
     e = launch_cgemm(gemm(nw, k, mw, ns, AwT, mat(a.Y, idx, ys, 1, mw, 1), mat(a.Bt, idx, bs, 1, nw)),
                      a.engine, st);
     if (e != cudaSuccess) return e;
+    if ((e = mark(3)) != cudaSuccess) return e;
   }
   // Dt = D_tau(Bt), converged vectors -> P (conjugated), singular values -> sig
   SliceArgs j;
@@ -432,12 +460,15 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
   j.sig_stride = kmax;
   e = launch_jacobi_svt(j, st);
   if (e != cudaSuccess) return e;
+  if ((e = mark(4)) != cudaSuccess) return e;
   // Zw = Q Dt^T, written into the output spectrum with the orientation of Aw
   e = launch_cgemm(gemm(mw, nw, k, ns, mat(a.Y, idx, ys, 1, mw), mat(a.Dt, idx, bs, nw, 1),
                         mat(a.zhat, idx, a.N12, a.wr, a.wc)),
                    a.engine, st);
   if (e != cudaSuccess) return e;
-  return launch_rsvt_refill(a, k, a.kfill, st);
+  if ((e = mark(5)) != cudaSuccess) return e;
+  if ((e = launch_rsvt_refill(a, k, a.kfill, st)) != cudaSuccess) return e;
+  return mark(6);
 }
 
 }  // namespace tsvd

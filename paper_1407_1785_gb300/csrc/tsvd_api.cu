@@ -59,6 +59,10 @@ struct tsvd_ctx {
   cudaEvent_t rs_ev[kRing] = {};
   int rs_k_last = 0;
   int64_t rs_saturated = 0, rs_drops = 0;
+  double rs_gemm_gflop = 0, rs_svd_gflop = 0;
+  // opts.timing: stage events of every randomized SVT of the current call
+  std::vector<std::array<cudaEvent_t, 7>> rs_stage;
+  size_t rs_stage_used = 0;
 };
 
 namespace {
@@ -758,6 +762,8 @@ tsvd_status rsvt_begin(tsvd_ctx* c, const Problem& p, const Workspace& w) {
   TSVD_TRY(rsvt_host_ring(c));
   c->rs_k_last = 0;
   c->rs_saturated = c->rs_drops = 0;
+  c->rs_gemm_gflop = c->rs_svd_gflop = 0;
+  c->rs_stage_used = 0;
   RsvtArgs a = rsvt_args(c, p, w, 0.f, 0, 0);
   a.rstat = nullptr;
   TSVD_TRY(launch(c, launch_rsvt_refill(a, 0, w.kmax, c->cur), "sketch initialisation"));
@@ -771,6 +777,18 @@ tsvd_status rsvt_step(tsvd_ctx* c, const Problem& p, const Workspace& w, float t
   RsvtArgs a = rsvt_args(c, p, w, tau, k, iter);
   a.power = power;
   const int slot = iter % tsvd_ctx::kRing;
+  if (c->opts.timing && power == 0) {
+    if (c->rs_stage_used == c->rs_stage.size()) {
+      std::array<cudaEvent_t, 7> evs{};
+      for (cudaEvent_t& ev : evs) TSVD_CUDA(c, cudaEventCreate(&ev));
+      c->rs_stage.push_back(evs);
+    }
+    a.stage_ev = c->rs_stage[c->rs_stage_used++].data();
+  }
+  // algorithmic work: three complex products and the GvL count of the small SVDs
+  const double mw = w.mw, nw = w.nw, kk = k, ns = w.ndistinct;
+  c->rs_gemm_gflop += (power + 1) * ns * 3.0 * 8.0 * mw * nw * kk * 1e-9;
+  c->rs_svd_gflop += ns * 4.0 * (4.0 * nw * kk * kk + 8.0 * kk * kk * kk) * 1e-9;
   TSVD_CUDA(c, cudaMemsetAsync(a.rstat, 0, sizeof(RsvtStat), c->cur));
   TSVD_TRY(record_event(c, 0));
   TSVD_TRY(launch(c, launch_rsvt(a, c->cur), "randomized slice SVT"));
@@ -931,6 +949,19 @@ tsvd_status fill_stats(tsvd_ctx* c, const Problem& p, const Workspace& w, int it
     stats->rsvt_k_last = c->rs_k_last;
     stats->rsvt_saturated = c->rs_saturated;
     stats->rsvt_drops = c->rs_drops;
+    stats->rsvt_gemm_gflop = c->rs_gemm_gflop;
+    stats->rsvt_svd_gflop = c->rs_svd_gflop;
+    if (c->opts.timing && c->rs_stage_used) {
+      TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+      for (size_t i = 0; i < c->rs_stage_used; ++i) {
+        const auto& ev = c->rs_stage[i];
+        float t[6];
+        for (int j = 0; j < 6; ++j) TSVD_CUDA(c, cudaEventElapsedTime(&t[j], ev[j], ev[j + 1]));
+        stats->rsvt_gemm_ms += t[0] + t[2] + t[4];
+        stats->rsvt_orth_ms += t[1];
+        stats->rsvt_svd_ms += t[3];
+      }
+    }
   } else {
     const SliceKnobs k = planned_knobs(c, p, w.ndistinct);
     stats->slice_ctas = jacobi_svt_ctas_per_slice((int)p.n1, (int)p.n2, w.ndistinct, k);
@@ -1125,6 +1156,8 @@ tsvd_status tsvd_destroy(tsvd_ctx* c) {
   if (c->fork) cudaEventDestroy(c->fork);
   for (cudaEvent_t e : c->rs_ev)
     if (e) cudaEventDestroy(e);
+  for (auto& evs : c->rs_stage)
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
   if (c->rs_host) cudaFreeHost(c->rs_host);
   delete c;
   return st;

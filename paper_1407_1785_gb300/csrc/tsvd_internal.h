@@ -188,6 +188,10 @@ struct RsvtArgs {
   void* jscratch;
   size_t jscratch_bytes;
   SliceKnobs jknobs;      // plan of the small Jacobi SVTs (0 = planner's choice)
+  // nullable: 7 events recorded at the stage boundaries of a call without power steps:
+  // [0] sketch product [1] CholeskyQR2 [2] projection product [3] small SVT [4] rebuild
+  // product [5] refill [6]
+  cudaEvent_t* stage_ev = nullptr;
 };
 
 int rsvt_max_k();

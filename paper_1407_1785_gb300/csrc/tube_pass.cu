@@ -266,6 +266,326 @@ __global__ void __launch_bounds__(TB) tube_pass_kernel(TubeArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Tile form (used whenever the shape fits): one CTA of 256 threads per tile of TT = 32
+// consecutive tubes.  Global accesses are rows of 32 consecutive tubes (128 B real, 256 B
+// complex).  The tile lives in shared memory as
+//   zt[jf*nh + jh][t]          the real tube entries,
+//   yt[jf*2hh + 2kh + c][t]    the half spectrum as (re, im) rows, c = 0, 1,
+// and the half-mode DFTs of the tile are two small real matrix products against one shared
+// matrix Fr[jh][2kh + c] = (cos, -sin)(2 pi kh jh / nh):
+//   forward  (R2C)   yt = Fr^T zt   per jf block (M = 2hh rows, K = nh);
+//   inverse  (C2R)   zt = Fr  (w . yt) per jf block (M = nh rows, K = 2hh), where the weights
+//                    w_kh = c_kh / (nf nh) (c = 1 at kh = 0 and nh/2, else 2) are applied when
+//                    the spectrum is loaded.
+// 256 threads = 8 groups of 4 tubes x 32 row groups; a thread accumulates RM rows x 4 tubes.
+// The full-mode DFT of the 4-way case (length nf <= 8) runs in registers per (kh, tube).
+// The fused ADMM steps are those of the thread-per-tube form above, on the tile in shared
+// memory.
+constexpr int TT = 32;
+constexpr int TILE_THREADS = 256;
+constexpr int NF_MAX = 8;
+
+struct TileSmem {
+  float* fr;     // [nh][ldq]
+  float* zt;     // [nf*nh][TT]
+  float* yt;     // [nf*2hh][TT]
+  float* nrm;    // [TT] tube norms (RPCA tube mode)
+  int ldq;
+};
+
+__host__ __device__ inline int tile_ldq(const TubeGeom& g) { return (2 * g.hh) | 1; }
+
+// Floats of the Fr matrix, rounded up to 4 so that the tiles after it stay 16-byte aligned.
+__host__ __device__ inline size_t tile_fr_floats(const TubeGeom& g) {
+  return ((size_t)g.nh * tile_ldq(g) + 3) / 4 * 4;
+}
+
+__host__ __device__ inline size_t tile_smem_bytes(const TubeGeom& g) {
+  return (tile_fr_floats(g) + (size_t)g.nf * g.nh * TT + (size_t)g.nf * 2 * g.hh * TT + TT) *
+         sizeof(float);
+}
+
+// out[r][t] = sum_k A(r, k) B[k][t] for r < M, the 32 tubes of the tile; A(r, k) at
+// a[r * sra + k * ska], B rows of TT floats, out rows of TT floats.
+template <int RM>
+__device__ __forceinline__ void tile_product(const float* __restrict__ a, int sra, int ska,
+                                             const float* __restrict__ b, float* __restrict__ out,
+                                             int M, int K) {
+  const int tg = threadIdx.x & 7, rg = threadIdx.x >> 3;
+  float acc[RM][4];
+#pragma unroll
+  for (int i = 0; i < RM; ++i)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+  for (int k = 0; k < K; ++k) {
+    const float4 bv = *reinterpret_cast<const float4*>(b + (size_t)k * TT + 4 * tg);
+#pragma unroll
+    for (int i = 0; i < RM; ++i) {
+      const int r = rg + 32 * i;
+      const float av = r < M ? a[(size_t)r * sra + (size_t)k * ska] : 0.f;
+      acc[i][0] = fmaf(av, bv.x, acc[i][0]);
+      acc[i][1] = fmaf(av, bv.y, acc[i][1]);
+      acc[i][2] = fmaf(av, bv.z, acc[i][2]);
+      acc[i][3] = fmaf(av, bv.w, acc[i][3]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    const int r = rg + 32 * i;
+    if (r < M)
+      *reinterpret_cast<float4*>(out + (size_t)r * TT + 4 * tg) =
+          make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  }
+}
+
+// Full-mode DFT of length nf of every (kh, tube) column of the spectrum tile, in place:
+// sign +1 (inverse, no scaling) or -1 (forward).
+__device__ void tile_full_dft(const TileSmem& s, const TubeGeom& g, const float2* __restrict__ twf,
+                              float sign) {
+  const int nf = g.nf, hh = g.hh;
+  for (int idx = threadIdx.x; idx < hh * TT; idx += TILE_THREADS) {
+    const int kh = idx / TT, t = idx % TT;
+    float2 x[NF_MAX], y[NF_MAX];
+    for (int f = 0; f < nf; ++f) {
+      const size_t row = (size_t)f * 2 * hh + 2 * kh;
+      x[f] = make_float2(s.yt[row * TT + t], s.yt[(row + 1) * TT + t]);
+    }
+    for (int o = 0; o < nf; ++o) {
+      float ar = 0.f, ai = 0.f;
+      int m = 0;
+      for (int f = 0; f < nf; ++f) {
+        const float2 w = twf[m];
+        const float ws = sign * w.y;
+        ar += x[f].x * w.x - x[f].y * ws;
+        ai += x[f].x * ws + x[f].y * w.x;
+        m += o;
+        if (m >= nf) m -= nf;
+      }
+      y[o] = make_float2(ar, ai);
+    }
+    for (int f = 0; f < nf; ++f) {
+      const size_t row = (size_t)f * 2 * hh + 2 * kh;
+      s.yt[row * TT + t] = y[f].x;
+      s.yt[(row + 1) * TT + t] = y[f].y;
+    }
+  }
+}
+
+// Spectrum tile (loaded, weighted) -> real tile.
+template <int RM>
+__device__ void tile_inverse(const TileSmem& s, const TubeGeom& g, const float2* twf) {
+  if (g.nf > 1) {
+    tile_full_dft(s, g, twf, 1.f);
+    __syncthreads();
+  }
+  for (int f = 0; f < g.nf; ++f)
+    tile_product<RM>(s.fr, s.ldq, 1, s.yt + (size_t)f * 2 * g.hh * TT,
+                     s.zt + (size_t)f * g.nh * TT, g.nh, 2 * g.hh);
+  __syncthreads();
+}
+
+// Real tile -> spectrum tile.
+template <int RM>
+__device__ void tile_forward(const TileSmem& s, const TubeGeom& g, const float2* twf) {
+  for (int f = 0; f < g.nf; ++f)
+    tile_product<RM>(s.fr, 1, s.ldq, s.zt + (size_t)f * g.nh * TT,
+                     s.yt + (size_t)f * 2 * g.hh * TT, 2 * g.hh, g.nh);
+  __syncthreads();
+  if (g.nf > 1) {
+    tile_full_dft(s, g, twf, -1.f);
+    __syncthreads();
+  }
+}
+
+// Loads the stored spectrum of the tile (conjugate partners on the self-conjugate columns)
+// and applies the C2R weights c_kh / (nf nh).
+__device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
+                                   const float2* __restrict__ spec, int64_t t0) {
+  const int nf = g.nf, nh = g.nh, hh = g.hh;
+  const float inv = 1.f / (float)(nf * nh);
+  for (int idx = threadIdx.x; idx < nf * hh * TT; idx += TILE_THREADS) {
+    const int q = idx / TT, t = idx % TT;
+    const int kf = q % nf, kh = q / nf;
+    const bool selfcol = (kh == 0) || (2 * kh == nh);
+    float2 v = make_float2(0.f, 0.f);
+    if (t0 + t < g.N12) {
+      if (selfcol && 2 * kf > nf) {
+        v = spec[(size_t)((nf - kf) + nf * kh) * g.N12 + t0 + t];
+        v.y = -v.y;
+      } else {
+        v = spec[(size_t)q * g.N12 + t0 + t];
+      }
+    }
+    const float w = (selfcol ? 1.f : 2.f) * inv;
+    const size_t row = (size_t)kf * 2 * hh + 2 * kh;
+    s.yt[row * TT + t] = v.x * w;
+    s.yt[(row + 1) * TT + t] = v.y * w;
+  }
+}
+
+__device__ void tile_store_spectrum(const TileSmem& s, const TubeGeom& g, float2* __restrict__ spec,
+                                    int64_t t0) {
+  const int nf = g.nf, hh = g.hh;
+  for (int idx = threadIdx.x; idx < nf * hh * TT; idx += TILE_THREADS) {
+    const int q = idx / TT, t = idx % TT;
+    if (t0 + t >= g.N12) continue;
+    const int kf = q % nf, kh = q / nf;
+    const size_t row = (size_t)kf * 2 * hh + 2 * kh;
+    spec[(size_t)q * g.N12 + t0 + t] = make_float2(s.yt[row * TT + t], s.yt[(row + 1) * TT + t]);
+  }
+}
+
+template <int RM>
+__global__ void __launch_bounds__(TILE_THREADS) tube_tile_kernel(TubeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TubeGeom g = a.g;
+  TileSmem s;
+  s.ldq = tile_ldq(g);
+  s.fr = reinterpret_cast<float*>(smem_raw);
+  s.zt = s.fr + tile_fr_floats(g);
+  s.yt = s.zt + (size_t)g.nf * g.nh * TT;
+  s.nrm = s.yt + (size_t)g.nf * 2 * g.hh * TT;
+  const int tid = threadIdx.x;
+  const int nh = g.nh, hh = g.hh, nreal = g.nf * g.nh;
+  const int64_t N12 = g.N12;
+  const int64_t t0 = (int64_t)blockIdx.x * TT;
+  // Fr[jh][2kh + c] from the twiddle table (exact at the quarter points)
+  for (int idx = tid; idx < nh * hh; idx += TILE_THREADS) {
+    const int jh = idx / hh, kh = idx % hh;
+    const float2 w = a.twid_h[(int)(((int64_t)jh * kh) % nh)];
+    s.fr[(size_t)jh * s.ldq + 2 * kh] = w.x;
+    s.fr[(size_t)jh * s.ldq + 2 * kh + 1] = -w.y;
+  }
+  const bool need_inv = a.mode == TUBE_INV || a.mode == TUBE_RPCA ||
+                        (a.mode == TUBE_COMPLETE && !a.first);
+  if (need_inv) tile_load_spectrum(s, g, a.spec_in, t0);
+  __syncthreads();
+  if (need_inv) tile_inverse<RM>(s, g, a.twid_f);
+
+  // element (j, t) of the tile; t = tid % TT is fixed per thread (TILE_THREADS % TT == 0).
+  // Tube offset j = jf + nf*jh of the tensor (mode 3 fastest) is tile row jf*nh + jh.
+  const int t = tid % TT;
+  const int nf = g.nf;
+  auto zrow = [&](int j) -> size_t { return ((size_t)(j % nf) * nh + j / nf) * TT + t; };
+  const bool live = t0 + t < N12;
+  switch (a.mode) {
+    case TUBE_FWD:
+      for (int j = tid / TT; j < nreal; j += TILE_THREADS / TT)
+        s.zt[zrow(j)] = live ? a.in[t0 + t + N12 * j] : 0.f;
+      break;
+    case TUBE_INV:
+      for (int j = tid / TT; j < nreal; j += TILE_THREADS / TT)
+        if (live) a.out0[t0 + t + N12 * j] = s.zt[zrow(j)];
+      break;
+    case TUBE_COMPLETE:
+      for (int j = tid / TT; j < nreal; j += TILE_THREADS / TT) {
+        float vn = 0.f;
+        if (live) {
+          const int64_t e = t0 + t + N12 * j;
+          float z = 0.f, q = 0.f;
+          if (!a.first) {
+            z = s.zt[zrow(j)];
+            q = (a.state[e] - z) * a.ratio;
+          }
+          const float y = a.in[e];
+          const float x = (y != y) ? z - q : y;   // NaN marks an unobserved entry
+          vn = x + q;
+          a.state[e] = vn;
+          if (a.write_out) a.out0[e] = x;
+        }
+        s.zt[zrow(j)] = vn;
+      }
+      break;
+    case TUBE_RPCA: {
+      const float kappa = a.kappa;
+      float f = 0.f;
+      if (a.tube_sparse) {
+        // eq. sparse2: one shrink factor per tube; D kept in the tile
+        float part = 0.f;
+        for (int j = tid / TT; j < nreal; j += TILE_THREADS / TT) {
+          float d = 0.f;
+          if (live) {
+            const int64_t e = t0 + t + N12 * j;
+            const float l = s.zt[zrow(j)];
+            if (a.last) a.out0[e] = l;
+            const float w = a.first ? 0.f : a.state[e];
+            d = a.in[e] - w - l;
+          }
+          s.zt[zrow(j)] = d;
+          part += d * d;
+        }
+        if (tid < TT) s.nrm[tid] = 0.f;
+        __syncthreads();
+        atomicAdd(&s.nrm[t], part);
+        __syncthreads();
+        const float nrm = sqrtf(s.nrm[t]);
+        f = nrm > 0.f ? fmaxf(1.f - kappa / nrm, 0.f) : 0.f;
+      }
+      for (int j = tid / TT; j < nreal; j += TILE_THREADS / TT) {
+        float vnext = 0.f;
+        if (live) {
+          const int64_t e = t0 + t + N12 * j;
+          const float m = a.in[e];
+          float d;
+          if (a.tube_sparse) {
+            d = s.zt[zrow(j)];
+          } else {
+            const float l = s.zt[zrow(j)];
+            if (a.last) a.out0[e] = l;
+            const float w = a.first ? 0.f : a.state[e];
+            d = m - w - l;
+          }
+          float sv;
+          if (a.tube_sparse) {
+            sv = f * d;
+          } else {
+            const float r = fabsf(d) - kappa;
+            sv = r > 0.f ? (d > 0.f ? r : -r) : 0.f;
+          }
+          if (a.last) {
+            a.out1[e] = sv;
+          } else {
+            const float wn = (sv - d) * a.ratio;
+            a.state[e] = wn;
+            vnext = m - sv - wn;
+          }
+        }
+        s.zt[zrow(j)] = vnext;
+      }
+      break;
+    }
+    default:
+      break;
+  }
+  const bool need_fwd = a.mode == TUBE_FWD || a.mode == TUBE_COMPLETE ||
+                        (a.mode == TUBE_RPCA && !a.last);
+  if (!need_fwd) return;
+  __syncthreads();
+  tile_forward<RM>(s, g, a.twid_f);
+  tile_store_spectrum(s, g, a.spec_out, t0);
+}
+
+// The tile form handles nf <= NF_MAX, 2 hh <= 256 (RM <= 8) and a tile that fits in shared
+// memory.
+int tile_rm(const TubeGeom& g) {
+  const int m = 2 * g.hh > g.nh ? 2 * g.hh : g.nh;
+  if (g.nf > NF_MAX || m > 256 || tile_smem_bytes(g) > 200 * 1024) return 0;
+  return m <= 128 ? 4 : 8;
+}
+
+template <int RM>
+cudaError_t launch_tile(const TubeArgs& a, cudaStream_t st) {
+  const size_t smem = tile_smem_bytes(a.g);
+  cudaError_t e = cudaFuncSetAttribute(tube_tile_kernel<RM>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t grid = (a.g.N12 + TT - 1) / TT;
+  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
+  tube_tile_kernel<RM><<<(unsigned)grid, TILE_THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 size_t tube_smem_bytes(const TubeGeom& g, int tb) {
   return (size_t)(g.nh + g.nf) * sizeof(float2) + (size_t)g.nf * g.hh * tb * sizeof(float2) +
          (size_t)g.nf * tb * sizeof(float2) + (size_t)g.nf * g.nh * tb * sizeof(float);
@@ -323,11 +643,14 @@ unsigned elementwise_grid(int64_t N) {
 }  // namespace
 
 bool tube_pass_supported(const TubeGeom& g) {
-  return tube_smem_bytes(g, 32) <= 220 * 1024;
+  return tile_rm(g) > 0 || tube_smem_bytes(g, 32) <= 220 * 1024;
 }
 
 cudaError_t launch_tube_pass(const TubeArgs& a, cudaStream_t st) {
   if (a.g.N12 <= 0) return cudaSuccess;
+  const int rm = tile_rm(a.g);
+  if (rm == 4) return launch_tile<4>(a, st);
+  if (rm == 8) return launch_tile<8>(a, st);
   size_t smem = tube_smem_bytes(a.g, 128);
   if (smem <= 110 * 1024) return launch_tb<128>(a, smem, st);
   smem = tube_smem_bytes(a.g, 64);

@@ -63,7 +63,10 @@ class Stats(ctypes.Structure):
                 ("slice_ms", ctypes.c_double), ("tube_ms", ctypes.c_double),
                 ("slice_ctas", ctypes.c_int), ("slice_lanes", ctypes.c_int),
                 ("slice_pairs_in_flight", ctypes.c_int), ("rsvt_k_last", ctypes.c_int),
-                ("rsvt_saturated", ctypes.c_int64), ("rsvt_drops", ctypes.c_int64)]
+                ("rsvt_saturated", ctypes.c_int64), ("rsvt_drops", ctypes.c_int64),
+                ("rsvt_gemm_ms", ctypes.c_double), ("rsvt_orth_ms", ctypes.c_double),
+                ("rsvt_svd_ms", ctypes.c_double), ("rsvt_gemm_gflop", ctypes.c_double),
+                ("rsvt_svd_gflop", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
