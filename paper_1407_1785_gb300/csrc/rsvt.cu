@@ -32,7 +32,9 @@
 //
 // Products.  The three slice products (sketch, projection, rebuild) run on the engine the
 // caller selects: FP32 CUDA cores here, or the tensor-core engines of tc_gemm.cu.  The Gram
-// matrices and the k x k triangular applications always run in FP32 on CUDA cores.
+// matrices and the k x k triangular applications of CholeskyQR2 need FP32-level accuracy:
+// they run as split-TF32 tensor-core products when the caller's engine uses tensor cores,
+// else in FP32 on CUDA cores.
 #include "tsvd_internal.h"
 
 #include <algorithm>
@@ -204,12 +206,23 @@ __global__ void __launch_bounds__(1024) cholqr_factor_kernel(const float2* G, fl
     }
   }
 
+  __shared__ float s_rjj, s_irjj;
+  __shared__ int s_ok;
   for (int j = 0; j < k; ++j) {
-    // the pivot is accumulated in FP64 (cancellation); its square root needs only FP32
-    const double pj = dd[j];
-    const bool okj = pj > (double)tol;
-    const float rjj = okj ? sqrtf((float)pj) : 1.f;
-    const float irjj = okj ? 1.f / rjj : 0.f;
+    // the pivot is accumulated in FP64 (cancellation); one thread turns it into R_jj in FP32
+    // (FP64 instructions issued by every thread would dominate the kernel on this GPU)
+    if (tid == 0) {
+      const double pj = dd[j];
+      const bool ok = pj > (double)tol;
+      const float r = ok ? sqrtf((float)pj) : 1.f;
+      s_ok = ok ? 1 : 0;
+      s_rjj = r;
+      s_irjj = ok ? 1.f / r : 0.f;
+    }
+    __syncthreads();
+    const bool okj = s_ok != 0;
+    const float rjj = s_rjj;
+    const float irjj = s_irjj;
     // row j of R; x_j scaled by 1 / R_jj (zeroed when the column is dropped)
     for (int l = j + 1 + tid; l < k; l += nthr) {
       const float2 v = S[(size_t)j * ldS + l];
@@ -403,6 +416,9 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
     attr_set = true;
   }
   // stage boundaries for the caller's timing (power-step-free calls only)
+  // the Gram matrices and triangular applications need FP32-level accuracy (orthogonality):
+  // split-TF32 tensor-core products with the tensor-core engines, FP32 CUDA cores otherwise
+  const int orth_engine = a.engine == RSVT_GEMM_FP32 ? RSVT_GEMM_FP32 : RSVT_GEMM_3XTF32;
   auto mark = [&](int i) -> cudaError_t {
     return (a.stage_ev && a.power == 0) ? cudaEventRecord(a.stage_ev[i], st) : cudaSuccess;
   };
@@ -417,16 +433,16 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
     for (int pass = 0; pass < 2; ++pass) {
       float2* src = pass == 0 ? a.Y : a.Q;
       float2* dst = pass == 0 ? a.Q : a.Y;
-      e = gemm_fp32(gemm(k, k, mw, ns, mat(src, idx, ys, mw, 1, 1), mat(src, idx, ys, 1, mw),
-                         mat(a.G, idx, gs, 1, kmax)),
-                    st);
+      e = launch_cgemm(gemm(k, k, mw, ns, mat(src, idx, ys, mw, 1, 1), mat(src, idx, ys, 1, mw),
+                            mat(a.G, idx, gs, 1, kmax)),
+                       orth_engine, st);
       if (e != cudaSuccess) return e;
       cholqr_factor_kernel<<<ns, 1024, csm, st>>>(a.G, a.T, idx, k, kmax, gs, a.chol_tol,
                                                  a.rstat);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      e = gemm_fp32(gemm(mw, k, k, ns, mat(src, idx, ys, 1, mw), mat(a.T, idx, gs, 1, kmax),
-                         mat(dst, idx, ys, 1, mw)),
-                    st);
+      e = launch_cgemm(gemm(mw, k, k, ns, mat(src, idx, ys, 1, mw), mat(a.T, idx, gs, 1, kmax),
+                            mat(dst, idx, ys, 1, mw)),
+                       orth_engine, st);
       if (e != cudaSuccess) return e;
     }
     if ((e = mark(2)) != cudaSuccess) return e;
