@@ -26,7 +26,8 @@
 // Orthonormalisation (CholeskyQR2).  G = Y^H Y (FP32), scaled to unit diagonal,
 // Gs = D^-1 G D^-1 = R^H R, Q = Y D^-1 R^-1, done twice.  The column scaling makes the FP32
 // rounding of G relative to each column's norm, so graded sketches (columns of norm sigma^2)
-// factor accurately.  The Schur complement is updated in FP32 and the pivots in FP64.  A pivot
+// factor accurately.  The Schur complement is updated in FP32 and the pivots in double-single
+// arithmetic (FP32 pairs).  A pivot
 // below chol_tol marks a column that depends on the previous ones: it is dropped (its column of
 // Q is zero) instead of failing the factorisation.
 //
@@ -127,13 +128,34 @@ __global__ void __launch_bounds__(256) cgemm_fp32_kernel(CGemm g) {
   }
 }
 
+// (hi, lo) -= ax^2 + ay^2 in double-single arithmetic: the squares are split exactly with
+// FMA, the sums are two-sums (the _rn intrinsics keep the compiler from contracting them).
+__device__ __forceinline__ void ds_sub_norm2(float& hi, float& lo, float ax, float ay) {
+  const float p = __fmul_rn(ax, ax), pe = fmaf(ax, ax, -p);
+  const float q = __fmul_rn(ay, ay), qe = fmaf(ay, ay, -q);
+  const float s = __fadd_rn(p, q);
+  const float bq = __fsub_rn(s, p);
+  const float se = __fadd_rn(__fadd_rn(__fsub_rn(p, __fsub_rn(s, bq)), __fsub_rn(q, bq)),
+                             __fadd_rn(pe, qe));
+  const float t = __fsub_rn(hi, s);
+  const float bt = __fsub_rn(t, hi);
+  const float te = __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(t, bt)), __fsub_rn(-s, bt)),
+                             __fsub_rn(lo, se));
+  const float nh = __fadd_rn(t, te);
+  lo = __fsub_rn(te, __fsub_rn(nh, t));
+  hi = nh;
+}
+
 // One CTA per slice: column-scaled Cholesky factorisation Gs = R^H R of the k x k Gram G
 // (col-major, ld ldg) with dropped pivots, and T = D^-1 R^-1 (zero columns for dropped
 // pivots), written over the same layout.  R^-1 is built in the same k steps as R, as the
 // coefficients of Gram-Schmidt on the scaled columns: at step j column x_j of R^-1 is final
 // once scaled by 1 / R_jj, and every later column subtracts R_jl x_j.  Shared memory: S
 // (k x (k+1) complex) holds R in the upper triangle and (R^-1)^T in the strict lower one; the
-// diagonal of R^-1, the pivots and the column scales sit in separate arrays (pivots in FP64).
+// diagonal of R^-1, the pivots and the column scales sit in separate arrays.  The pivots are
+// accumulated in double-single arithmetic (an FP32 pair updated with exact products and
+// two-sums): about twice FP32's precision against the cancellation in 1 - sum |R_ij|^2,
+// without FP64 instructions, which run at a small fraction of the FP32 rate on this GPU.
 // Threads form a 32 x 32 grid over the trailing block.  A Gram that is already the identity
 // to FP32 resolution (every scaled off-diagonal entry below 1e-6, the usual case of the second
 // pass) skips the factorisation: R = I, T = D^-1.
@@ -145,8 +167,9 @@ __global__ void __launch_bounds__(1024) cholqr_factor_kernel(const float2* G, fl
   const int s = slices[blockIdx.x];
   const int ldS = k + 1;
   float2* S = reinterpret_cast<float2*>(smem_raw);
-  double* dd = reinterpret_cast<double*>(S + (size_t)k * ldS);
-  double* dsc = dd + k;
+  float* ddh = reinterpret_cast<float*>(S + (size_t)k * ldS);   // pivots: hi + lo
+  float* ddl = ddh + k;
+  double* dsc = reinterpret_cast<double*>(ddl + k);
   float2* xd = reinterpret_cast<float2*>(dsc + k);
   float* isc = reinterpret_cast<float*>(xd + k);
   int* okc = reinterpret_cast<int*>(isc + k);
@@ -170,7 +193,8 @@ __global__ void __launch_bounds__(1024) cholqr_factor_kernel(const float2* G, fl
   const double dmin = 1e-30 * s_dmax;
   for (int i = tid; i < k; i += nthr) {
     const bool zero = !(dsc[i] > dmin) || s_dmax == 0.0;
-    dd[i] = zero ? 0.0 : 1.0;
+    ddh[i] = zero ? 0.f : 1.f;
+    ddl[i] = 0.f;
     if (zero) dsc[i] = 1.0;
     isc[i] = (float)(1.0 / dsc[i]);
     xd[i] = make_float2(1.f, 0.f);
@@ -180,7 +204,7 @@ __global__ void __launch_bounds__(1024) cholqr_factor_kernel(const float2* G, fl
   for (int r = ty; r < k; r += 32)
     for (int c = tx; c < k; c += 32) {
       float2 v = make_float2(0.f, 0.f);
-      if (r <= c && dd[r] != 0.0 && dd[c] != 0.0) {
+      if (r <= c && ddh[r] != 0.f && ddh[c] != 0.f) {
         v = Gp[r + (size_t)c * ldg];
         const float inv = isc[r] * isc[c];
         v.x *= inv;
@@ -196,7 +220,7 @@ __global__ void __launch_bounds__(1024) cholqr_factor_kernel(const float2* G, fl
         const float2 v = S[(size_t)r * ldS + c];
         far |= fabsf(v.x) + fabsf(v.y) > 1e-6f;
       }
-    for (int r = tid; r < k; r += nthr) far |= dd[r] == 0.0;
+    for (int r = tid; r < k; r += nthr) far |= ddh[r] == 0.f;
     if (__syncthreads_or(far) == 0) {
       // R = I: T = D^-1
       for (int c = ty; c < k; c += 32)
@@ -209,12 +233,12 @@ __global__ void __launch_bounds__(1024) cholqr_factor_kernel(const float2* G, fl
   __shared__ float s_rjj, s_irjj;
   __shared__ int s_ok;
   for (int j = 0; j < k; ++j) {
-    // the pivot is accumulated in FP64 (cancellation); one thread turns it into R_jj in FP32
-    // (FP64 instructions issued by every thread would dominate the kernel on this GPU)
+    // the pivot 1 - sum |R_ij|^2 cancels; it is accumulated in double-single arithmetic and
+    // one thread turns it into R_jj
     if (tid == 0) {
-      const double pj = dd[j];
-      const bool ok = pj > (double)tol;
-      const float r = ok ? sqrtf((float)pj) : 1.f;
+      const float pj = ddh[j] + ddl[j];
+      const bool ok = pj > tol;
+      const float r = ok ? sqrtf(pj) : 1.f;
       s_ok = ok ? 1 : 0;
       s_rjj = r;
       s_irjj = ok ? 1.f / r : 0.f;
@@ -250,7 +274,7 @@ __global__ void __launch_bounds__(1024) cholqr_factor_kernel(const float2* G, fl
           v.y -= a.x * b.y - a.y * b.x;
           S[(size_t)l * ldS + l2] = v;
         }
-        if (tx == 0) dd[l] -= (double)a.x * a.x + (double)a.y * a.y;
+        if (tx == 0) ds_sub_norm2(ddh[l], ddl[l], a.x, a.y);
         // x_l -= R_jl x_j on entries i <= j (X(i, l) kept at S(l, i), X(j, j) in xd)
         for (int i = tx; i <= j; i += 32) {
           const float2 xj = i == j ? xd[j] : S[(size_t)j * ldS + i];
