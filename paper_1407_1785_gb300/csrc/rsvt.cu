@@ -8,11 +8,13 @@
 //   Y  = Aw P                              sketch                              (GEMM)
 //   Q  = orth(Y)                           CholeskyQR2 (cholqr_factor_kernel)
 //   Bt = Aw^T conj(Q)  = (Q^H Aw)^T        projection onto range(Q), nw x k    (GEMM)
-//   Dt = D_tau(Bt)                         one-sided Jacobi SVT of the small matrix
+//   Dt = D_tau(Bt)                         SVT of the small matrix: two-sided Jacobi on its
+//                                          k x k Gram (k <= 112), else one-sided Jacobi
 //   Zw = Q Dt^T        = Q D_tau(Q^H Aw)   rebuild                             (GEMM)
-//   P' = conj(W), W = Bt J the converged Jacobi vectors = the right singular vectors of
-//        Q^H Aw scaled by sigma: the next call starts from the Ritz basis (one step of
-//        subspace iteration per call), so Y' = Aw P' has nearly orthogonal columns.
+//   P' = conj(Bt J), J the accumulated Jacobi rotations: the right singular vectors of Q^H Aw
+//        scaled by sigma: the next call starts from the Ritz basis (one step of subspace
+//        iteration per call), so Y' = Aw P' has nearly orthogonal columns and the small
+//        Jacobi converges in a few sweeps.
 // Because Q has orthonormal columns, Q D_tau(Q^H Aw) = D_tau(Q Q^H Aw): the result is the exact
 // thresholding of the projection of Aw onto the sketched subspace, and it equals D_tau(Aw)
 // when that subspace holds every singular direction above tau.
@@ -305,6 +307,180 @@ __global__ void __launch_bounds__(1024) cholqr_factor_kernel(const float2* G, fl
   }
 }
 
+// Circle-method pair (p, q) of slot `slot` in round r over P (even) players.
+__device__ __forceinline__ void circle_pair(int r, int slot, int P, int& p, int& q) {
+  if (slot == 0) {
+    p = P - 1;
+    q = r;
+  } else {
+    p = r + slot;
+    if (p >= P - 1) p -= P - 1;
+    q = r - slot + P - 1;
+    if (q >= P - 1) q -= P - 1;
+  }
+}
+
+// One CTA per slice: the SVD of the projected nw x k matrix Bt through its k x k Gram
+// H = Bt^H Bt (col-major, ld ldh, in G), by cyclic two-sided Jacobi: H <- J^H H J over all
+// pairs of a circle-method round at once, J accumulated into W.  The pair rotation is the one
+// of the one-sided form (same parameters from a = H_pp, b = H_qq, c = H_pq, the same
+// cos - 1 form), so this computes what one-sided Jacobi on the columns of Bt computes, with
+// the inner products read from H instead of recomputed.  At convergence the eigenvalues are
+// sigma^2 and Bt = (Bt W Sigma^-1) Sigma W^H.  Writes W (into T), Wf = W diag(f) with
+// f = (sigma - tau)_+ / sigma (into G), sigma (sig) and the slice statistics.  Shared memory:
+// H and W as k x (k + 1) complex matrices, the round's rotations.
+__global__ void __launch_bounds__(1024) eig_svt_kernel(float2* G, float2* T, float* sig,
+                                                       const int* slices, int k, int ldg,
+                                                       int64_t gs, int64_t sig_stride,
+                                                       float tau, float tol, int max_sweeps,
+                                                       SliceStat* stat, SweepAccum* acc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = slices[blockIdx.x];
+  const int ldh = k + 1;
+  float2* H = reinterpret_cast<float2*>(smem_raw);
+  float2* W = H + (size_t)k * ldh;
+  float4* rot = reinterpret_cast<float4*>(W + (size_t)k * ldh);   // (cm, kr, ki, on)
+  int2* prs = reinterpret_cast<int2*>(rot + (k + 1) / 2);
+  __shared__ int s_flags;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+  float2* Gp = G + (size_t)s * gs;
+  float2* Tp = T + (size_t)s * gs;
+  for (int c = warp; c < k; c += nwarps)
+    for (int m = lane; m < k; m += 32) {
+      H[m + (size_t)c * ldh] = Gp[m + (size_t)c * ldg];
+      W[m + (size_t)c * ldh] = make_float2(m == c ? 1.f : 0.f, 0.f);
+    }
+  const int kp = k + (k & 1);
+  const int npair = kp / 2;
+  const float big = sqrtf(tol / (2.f * (float)k));
+  int sweeps = 0, converged = 0;
+  __syncthreads();
+  for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
+    if (tid == 0) s_flags = 0;
+    __syncthreads();
+    for (int r = 0; r < kp - 1; ++r) {
+      // rotation parameters, one thread per pair
+      if (tid < npair) {
+        int p, q;
+        circle_pair(r, tid, kp, p, q);
+        float4 ro = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p < k && q < k) {
+          const float al = H[p + (size_t)p * ldh].x, be = H[q + (size_t)q * ldh].x;
+          const float2 c = H[p + (size_t)q * ldh];   // H_pq = col_p^H col_q
+          const float g = sqrtf(c.x * c.x + c.y * c.y);
+          const float sab = sqrtf(fmaxf(al, 0.f)) * sqrtf(fmaxf(be, 0.f));
+          if (g > tol * sab) {
+            const float inv_g = 1.f / g;
+            const float zeta = (be - al) * (0.5f * inv_g);
+            float t;
+            if (fabsf(zeta) > 1e18f)
+              t = 0.5f / zeta;
+            else
+              t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+            if (t != 0.f) {
+              const float rr = sqrtf(1.f + t * t);
+              const float sn = t / rr;
+              const float cm = -(t * sn) / (1.f + rr);
+              ro = make_float4(cm, sn * (c.x * inv_g), sn * (c.y * inv_g), 1.f);
+              atomicOr(&s_flags, g > big * sab ? 3 : 1);
+            }
+          }
+        }
+        rot[tid] = ro;
+        prs[tid] = make_int2(p, q);
+      }
+      __syncthreads();
+      // columns: [x, y] <- [x + cm x - conj(kk) y, y + cm y + kk x] on H and W; a warp per
+      // pair, a lane per row
+      for (int i = warp; i < npair; i += nwarps) {
+        const float4 ro = rot[i];
+        if (ro.w == 0.f) continue;
+        const int2 pq = prs[i];
+        const float cm = ro.x, kr = ro.y, ki = ro.z;
+        for (int m = lane; m < k; m += 32) {
+#pragma unroll
+          for (int mat = 0; mat < 2; ++mat) {
+            float2* X = mat == 0 ? H : W;
+            float2& x = X[m + (size_t)pq.x * ldh];
+            float2& y = X[m + (size_t)pq.y * ldh];
+            const float2 xv = x, yv = y;
+            // conj(kk) y = (kr yr + ki yi, kr yi - ki yr);  kk x = (kr xr - ki xi, kr xi + ki xr)
+            x = make_float2(xv.x + cm * xv.x - (kr * yv.x + ki * yv.y),
+                            xv.y + cm * xv.y - (kr * yv.y - ki * yv.x));
+            y = make_float2(yv.x + cm * yv.x + (kr * xv.x - ki * xv.y),
+                            yv.y + cm * yv.y + (kr * xv.y + ki * xv.x));
+          }
+        }
+      }
+      __syncthreads();
+      // rows: row_p <- row_p + cm row_p - kk row_q, row_q <- row_q + cm row_q + conj(kk) row_p
+      for (int i = warp; i < npair; i += nwarps) {
+        const float4 ro = rot[i];
+        if (ro.w == 0.f) continue;
+        const int2 pq = prs[i];
+        const float cm = ro.x, kr = ro.y, ki = ro.z;
+        for (int m = lane; m < k; m += 32) {
+          float2& x = H[pq.x + (size_t)m * ldh];
+          float2& y = H[pq.y + (size_t)m * ldh];
+          const float2 xv = x, yv = y;
+          x = make_float2(xv.x + cm * xv.x - (kr * yv.x - ki * yv.y),
+                          xv.y + cm * xv.y - (kr * yv.y + ki * yv.x));
+          y = make_float2(yv.x + cm * yv.x + (kr * xv.x + ki * xv.y),
+                          yv.y + cm * yv.y + (kr * xv.y - ki * xv.x));
+        }
+      }
+      __syncthreads();
+    }
+    const int fl = s_flags;
+    ++sweeps;
+    // converged: nothing rotated, or only rotations too small to leave a cosine above tol
+    if (!(fl & 1) || !(fl & 2)) converged = 1;
+    __syncthreads();
+  }
+  // sigma_v = sqrt(lambda_v); W and W diag(f) out
+  __shared__ int s_rank;
+  __shared__ double s_nuc;
+  if (tid == 0) {
+    int rank = 0;
+    double nuc = 0.0;
+    for (int v = 0; v < k; ++v) {
+      const float sv = sqrtf(fmaxf(H[v + (size_t)v * ldh].x, 0.f));
+      sig[(size_t)s * sig_stride + v] = sv;
+      nuc += (double)sv;
+      rank += sv > tau ? 1 : 0;
+    }
+    s_rank = rank;
+    s_nuc = nuc;
+  }
+  for (int v = warp; v < k; v += nwarps) {
+    const float sv = sqrtf(fmaxf(H[v + (size_t)v * ldh].x, 0.f));
+    const float f = sv > tau ? (sv - tau) / sv : 0.f;
+    for (int m = lane; m < k; m += 32) {
+      const float2 w = W[m + (size_t)v * ldh];
+      Tp[m + (size_t)v * ldg] = w;
+      Gp[m + (size_t)v * ldg] = make_float2(w.x * f, w.y * f);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (stat) {
+      SliceStat st;
+      st.rank = s_rank;
+      st.sweeps = sweeps;
+      st.converged = converged;
+      st.pad = 0;
+      st.nuc = s_nuc;
+      stat[s] = st;
+    }
+    if (acc) {
+      atomicAdd(&acc->total_sweeps, (unsigned long long)sweeps);
+      if (!converged) atomicAdd(&acc->nonconverged, 1ull);
+      atomicMax(&acc->max_sweeps, sweeps);
+    }
+  }
+}
+
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
@@ -360,6 +536,13 @@ __global__ void __launch_bounds__(256) rsvt_refill_kernel(float2* P, const float
   }
 }
 
+// Largest sketch width whose Gram and eigenvectors fit one CTA's shared memory.
+constexpr int eig_max_k() { return 112; }
+
+size_t eig_smem(int k) {
+  return 2 * (size_t)k * (k + 1) * sizeof(float2) + (size_t)((k + 1) / 2) * (sizeof(float4) + sizeof(int2));
+}
+
 size_t cholqr_smem(int k) {
   return (size_t)k * (k + 1) * sizeof(float2) + 2 * (size_t)k * sizeof(double) +
          (size_t)k * sizeof(float2) + (size_t)k * sizeof(float) + (size_t)k * sizeof(int);
@@ -403,6 +586,7 @@ cudaError_t launch_cgemm(const CGemm& g, int engine, cudaStream_t st) {
 }
 
 int rsvt_max_k() { return 128; }
+int rsvt_eig_max_k() { return eig_max_k(); }
 
 size_t rsvt_jacobi_scratch_bytes(int nw, int kmax, int nslices, const SliceKnobs& kn) {
   size_t b = 0;
@@ -436,6 +620,9 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
   if (!attr_set) {
     e = cudaFuncSetAttribute(cholqr_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cholqr_smem(rsvt_max_k()));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(eig_svt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)eig_smem(eig_max_k()));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -475,6 +662,33 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
                      a.engine, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(3)) != cudaSuccess) return e;
+  }
+  if (k <= eig_max_k()) {
+    // Dt = D_tau(Bt) through the k x k Gram: H = Bt^H Bt, two-sided Jacobi -> W, W diag(f),
+    // sigma; P = conj(Bt W); Dt = Bt W diag(f) W^H = conj(P) (W diag(f))^H
+    e = launch_cgemm(gemm(k, k, nw, ns, mat(a.Bt, idx, bs, nw, 1, 1), mat(a.Bt, idx, bs, 1, nw),
+                          mat(a.G, idx, gs, 1, kmax)),
+                     orth_engine, st);
+    if (e != cudaSuccess) return e;
+    eig_svt_kernel<<<ns, 1024, eig_smem(k), st>>>(a.G, a.T, a.sig, idx, k, kmax, gs, kmax, a.tau,
+                                                  a.tol, a.max_sweeps, a.stat, a.acc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_cgemm(gemm(nw, k, k, ns, mat(a.Bt, idx, bs, 1, nw, 1), mat(a.T, idx, gs, 1, kmax, 1),
+                          mat(a.P, idx, ps, 1, nw)),
+                     orth_engine, st);
+    if (e != cudaSuccess) return e;
+    e = launch_cgemm(gemm(nw, k, k, ns, mat(a.P, idx, ps, 1, nw, 1), mat(a.G, idx, gs, kmax, 1, 1),
+                          mat(a.Dt, idx, bs, 1, nw)),
+                     orth_engine, st);
+    if (e != cudaSuccess) return e;
+    if ((e = mark(4)) != cudaSuccess) return e;
+    e = launch_cgemm(gemm(mw, nw, k, ns, mat(a.Y, idx, ys, 1, mw), mat(a.Dt, idx, bs, nw, 1),
+                          mat(a.zhat, idx, a.N12, a.wr, a.wc)),
+                     a.engine, st);
+    if (e != cudaSuccess) return e;
+    if ((e = mark(5)) != cudaSuccess) return e;
+    if ((e = launch_rsvt_refill(a, k, a.kfill, st)) != cudaSuccess) return e;
+    return mark(6);
   }
   // Dt = D_tau(Bt), converged vectors -> P (conjugated), singular values -> sig
   SliceArgs j;

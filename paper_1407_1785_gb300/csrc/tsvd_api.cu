@@ -733,7 +733,9 @@ RsvtArgs rsvt_args(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau,
 }
 
 // Kernels one launch_rsvt call enqueues.
-int rsvt_kernels(const RsvtArgs& a) { return 8 * (a.power + 1) + 3; }
+int rsvt_kernels(const RsvtArgs& a) {
+  return 8 * (a.power + 1) + 3 + (a.k <= rsvt_eig_max_k() ? 3 : 0);
+}
 
 // Smallest sketch width: the oversampling margin over rank 8, rounded up to 8.
 int rsvt_k0(const tsvd_ctx* c, const Workspace& w) {
@@ -945,7 +947,10 @@ tsvd_status fill_stats(tsvd_ctx* c, const Problem& p, const Workspace& w, int it
   stats->slice_launches = c->slice_launches;
   if (w.rsvt) {
     stats->slice_ctas =
-        c->rs_k_last ? jacobi_svt_ctas_per_slice(w.nw, c->rs_k_last, w.ndistinct, rsvt_knobs(c)) : 0;
+        c->rs_k_last == 0 ? 0
+        : c->rs_k_last <= rsvt_eig_max_k()
+            ? 1
+            : jacobi_svt_ctas_per_slice(w.nw, c->rs_k_last, w.ndistinct, rsvt_knobs(c));
     stats->rsvt_k_last = c->rs_k_last;
     stats->rsvt_saturated = c->rs_saturated;
     stats->rsvt_drops = c->rs_drops;

@@ -195,6 +195,8 @@ struct RsvtArgs {
 };
 
 int rsvt_max_k();
+// Widest sketch whose small SVD runs as the two-sided Jacobi of its Gram (wider: one-sided).
+int rsvt_eig_max_k();
 size_t rsvt_jacobi_scratch_bytes(int nw, int kmax, int nslices, const SliceKnobs& kn);
 cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st);
 // Refill columns c < kfill of P that carry no direction (all of them when k = 0).
