@@ -74,8 +74,8 @@ WORKLOADS = {
 # DRAM traffic of one jacobi_svt_kernel launch from an ncu capture of the video workload,
 # valid only for the kernel source it was taken on (see profiles/).
 TRAFFIC = {"source": "paper_1407_1785_gb300/csrc/slice_svt.cu",
-           "sha256": "8f46dfad975484d40755d0d1dd1c1444b478ba1a6e75877ecee5e31e4378f61b",
-           "bytes_per_launch": 10575360 + 15321344}
+           "sha256": "e449d168b481a3e36ecfebaa58f9c4490e4ccd52dcc061aa5b2029c017a02c1d",
+           "bytes_per_launch": 10556928 + 15997440}
 
 
 def parse_args():
