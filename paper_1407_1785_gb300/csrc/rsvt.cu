@@ -59,6 +59,13 @@ __device__ __forceinline__ float2 cload(const float2* p, int64_t o, int conj) {
 __global__ void __launch_bounds__(256) cgemm_fp32_kernel(CGemm g) {
   __shared__ float2 As[TK][TM + 1];
   __shared__ float2 Bs[TK][TN + 1];
+  if (g.kdev) {
+    const int kk = *g.kdev;
+    if (g.dynM) g.M = kk;
+    if (g.dynN) g.N = kk;
+    if (g.dynK) g.K = kk;
+  }
+  if ((int)blockIdx.x * TM >= g.M || (int)blockIdx.y * TN >= g.N) return;
   const int bz = blockIdx.z;
   const float2* A = g.a.p + (int64_t)(g.a.idx ? g.a.idx[bz] : bz) * g.a.bs;
   const float2* B = g.b.p + (int64_t)(g.b.idx ? g.b.idx[bz] : bz) * g.b.bs;
@@ -164,8 +171,9 @@ __device__ __forceinline__ void ds_sub_norm2(float& hi, float& lo, float ax, flo
 __global__ void __launch_bounds__(1024) cholqr_factor_kernel(const float2* G, float2* T,
                                                             const int* slices, int k, int ldg,
                                                             int64_t gs, float tol,
-                                                            RsvtStat* rstat) {
+                                                            RsvtStat* rstat, const int* kdev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (kdev) k = *kdev;
   const int s = slices[blockIdx.x];
   const int ldS = k + 1;
   float2* S = reinterpret_cast<float2*>(smem_raw);
@@ -333,8 +341,10 @@ __global__ void __launch_bounds__(1024) eig_svt_kernel(float2* G, float2* T, flo
                                                        const int* slices, int k, int ldg,
                                                        int64_t gs, int64_t sig_stride,
                                                        float tau, float tol, int max_sweeps,
-                                                       SliceStat* stat, SweepAccum* acc) {
+                                                       SliceStat* stat, SweepAccum* acc,
+                                                       const int* kdev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (kdev) k = *kdev;
   const int s = slices[blockIdx.x];
   const int ldh = k + 1;
   float2* H = reinterpret_cast<float2*>(smem_raw);
@@ -502,7 +512,8 @@ __global__ void __launch_bounds__(256) rsvt_refill_kernel(float2* P, const float
                                                           int kmax, int k, int kfill, float tau,
                                                           float floor_rel,
                                                           unsigned long long seed, int iter,
-                                                          RsvtStat* rstat) {
+                                                          RsvtStat* rstat, const int* kdev) {
+  if (kdev) k = *kdev;
   const int s = slices[blockIdx.x];
   const int tid = threadIdx.x, nthr = blockDim.x;
   __shared__ float s_max;
@@ -534,6 +545,26 @@ __global__ void __launch_bounds__(256) rsvt_refill_kernel(float2* P, const float
           make_float2(urand(key, ctr), real ? 0.f : urand(key, ctr + 1ull));
     }
   }
+}
+
+// Device-chosen width: after a call, the next width is the rank seen (max over slices) plus
+// the oversampling margin, rounded up to 8, never below the current width, at most kmax; the
+// rank maximum restarts for the next call.
+__global__ void rsvt_next_k_kernel(RsvtStat* st, int oversample, int kmax) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int kn = (st->rank_max + oversample + 7) / 8 * 8;
+  kn = kn > st->k ? kn : st->k;
+  kn = kn < kmax ? kn : kmax;
+  st->k = kn > 1 ? kn : 1;
+  st->rank_max = 0;
+}
+
+__global__ void rsvt_state_init_kernel(RsvtStat* st, int k0) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  st->rank_max = 0;
+  st->saturated = 0;
+  st->drops = 0;
+  st->k = k0;
 }
 
 // Largest sketch width whose Gram and eigenvectors fit one CTA's shared memory.
@@ -596,11 +627,17 @@ size_t rsvt_jacobi_scratch_bytes(int nw, int kmax, int nslices, const SliceKnobs
   return b;
 }
 
+cudaError_t launch_rsvt_state_init(RsvtStat* st_dev, int k0, cudaStream_t st) {
+  rsvt_state_init_kernel<<<1, 32, 0, st>>>(st_dev, k0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rsvt_refill(const RsvtArgs& a, int k, int kfill, cudaStream_t st) {
   if (a.nslices <= 0) return cudaSuccess;
+  // k = 0 (initialisation) refills every column whatever the device width says
   rsvt_refill_kernel<<<a.nslices, 256, 0, st>>>(a.P, a.sig, a.slices, a.isreal, a.nw, a.kmax, k,
                                                 kfill, a.tau, a.floor_rel, a.seed, a.iter,
-                                                a.rstat);
+                                                a.rstat, k > 0 ? a.kdev : nullptr);
   return cudaGetLastError();
 }
 
@@ -608,6 +645,8 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
   if (a.nslices <= 0) return cudaSuccess;
   const int k = a.k, kmax = a.kmax, mw = a.mw, nw = a.nw, ns = a.nslices;
   if (k < 1 || k > kmax || kmax > rsvt_max_k() || k > nw) return cudaErrorInvalidValue;
+  // with a device-chosen width (k = its bound) only the Gram path of the small SVD applies
+  if (a.kdev && (k > eig_max_k() || !a.rstat)) return cudaErrorInvalidValue;
   cudaError_t e;
   const int64_t ys = (int64_t)mw * kmax, ps = (int64_t)nw * kmax, gs = (int64_t)kmax * kmax;
   const int64_t bs = (int64_t)nw * k;
@@ -630,6 +669,16 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
   // the Gram matrices and triangular applications need FP32-level accuracy (orthogonality):
   // split-TF32 tensor-core products with the tensor-core engines, FP32 CUDA cores otherwise
   const int orth_engine = a.engine == RSVT_GEMM_FP32 ? RSVT_GEMM_FP32 : RSVT_GEMM_3XTF32;
+  // products whose flagged dimensions equal the width read it from the device in that mode
+  auto dyn = [&](CGemm g, int dm, int dn, int dk) {
+    if (a.kdev) {
+      g.kdev = a.kdev;
+      g.dynM = dm;
+      g.dynN = dn;
+      g.dynK = dk;
+    }
+    return g;
+  };
   auto mark = [&](int i) -> cudaError_t {
     return (a.stage_ev && a.power == 0) ? cudaEventRecord(a.stage_ev[i], st) : cudaSuccess;
   };
@@ -637,57 +686,70 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
   for (int pw = 0; pw <= a.power; ++pw) {
     // Y = Aw P   (power steps: P = conj(Bt) of the previous projection)
     const CMat Pm = pw == 0 ? mat(a.P, idx, ps, 1, nw) : mat(a.Bt, idx, bs, 1, nw, 1);
-    e = launch_cgemm(gemm(mw, k, nw, ns, Aw, Pm, mat(a.Y, idx, ys, 1, mw)), a.engine, st);
+    e = launch_cgemm(dyn(gemm(mw, k, nw, ns, Aw, Pm, mat(a.Y, idx, ys, 1, mw)), 0, 1, 0),
+                     a.engine, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(1)) != cudaSuccess) return e;
     // CholeskyQR2: Y -> Q -> Y
     for (int pass = 0; pass < 2; ++pass) {
       float2* src = pass == 0 ? a.Y : a.Q;
       float2* dst = pass == 0 ? a.Q : a.Y;
-      e = launch_cgemm(gemm(k, k, mw, ns, mat(src, idx, ys, mw, 1, 1), mat(src, idx, ys, 1, mw),
-                            mat(a.G, idx, gs, 1, kmax)),
+      e = launch_cgemm(dyn(gemm(k, k, mw, ns, mat(src, idx, ys, mw, 1, 1),
+                                mat(src, idx, ys, 1, mw), mat(a.G, idx, gs, 1, kmax)),
+                           1, 1, 0),
                        orth_engine, st);
       if (e != cudaSuccess) return e;
       cholqr_factor_kernel<<<ns, 1024, csm, st>>>(a.G, a.T, idx, k, kmax, gs, a.chol_tol,
-                                                 a.rstat);
+                                                 a.rstat, a.kdev);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      e = launch_cgemm(gemm(mw, k, k, ns, mat(src, idx, ys, 1, mw), mat(a.T, idx, gs, 1, kmax),
-                            mat(dst, idx, ys, 1, mw)),
+      e = launch_cgemm(dyn(gemm(mw, k, k, ns, mat(src, idx, ys, 1, mw),
+                                mat(a.T, idx, gs, 1, kmax), mat(dst, idx, ys, 1, mw)),
+                           0, 1, 1),
                        orth_engine, st);
       if (e != cudaSuccess) return e;
     }
     if ((e = mark(2)) != cudaSuccess) return e;
     // Bt = Aw^T conj(Q)
-    e = launch_cgemm(gemm(nw, k, mw, ns, AwT, mat(a.Y, idx, ys, 1, mw, 1), mat(a.Bt, idx, bs, 1, nw)),
-                     a.engine, st);
+    e = launch_cgemm(
+        dyn(gemm(nw, k, mw, ns, AwT, mat(a.Y, idx, ys, 1, mw, 1), mat(a.Bt, idx, bs, 1, nw)), 0,
+            1, 0),
+        a.engine, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(3)) != cudaSuccess) return e;
   }
   if (k <= eig_max_k()) {
     // Dt = D_tau(Bt) through the k x k Gram: H = Bt^H Bt, two-sided Jacobi -> W, W diag(f),
     // sigma; P = conj(Bt W); Dt = Bt W diag(f) W^H = conj(P) (W diag(f))^H
-    e = launch_cgemm(gemm(k, k, nw, ns, mat(a.Bt, idx, bs, nw, 1, 1), mat(a.Bt, idx, bs, 1, nw),
-                          mat(a.G, idx, gs, 1, kmax)),
+    e = launch_cgemm(dyn(gemm(k, k, nw, ns, mat(a.Bt, idx, bs, nw, 1, 1),
+                              mat(a.Bt, idx, bs, 1, nw), mat(a.G, idx, gs, 1, kmax)),
+                         1, 1, 0),
                      orth_engine, st);
     if (e != cudaSuccess) return e;
     eig_svt_kernel<<<ns, 1024, eig_smem(k), st>>>(a.G, a.T, a.sig, idx, k, kmax, gs, kmax, a.tau,
-                                                  a.tol, a.max_sweeps, a.stat, a.acc);
+                                                  a.tol, a.max_sweeps, a.stat, a.acc, a.kdev);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = launch_cgemm(gemm(nw, k, k, ns, mat(a.Bt, idx, bs, 1, nw, 1), mat(a.T, idx, gs, 1, kmax, 1),
-                          mat(a.P, idx, ps, 1, nw)),
+    e = launch_cgemm(dyn(gemm(nw, k, k, ns, mat(a.Bt, idx, bs, 1, nw, 1),
+                              mat(a.T, idx, gs, 1, kmax, 1), mat(a.P, idx, ps, 1, nw)),
+                         0, 1, 1),
                      orth_engine, st);
     if (e != cudaSuccess) return e;
-    e = launch_cgemm(gemm(nw, k, k, ns, mat(a.P, idx, ps, 1, nw, 1), mat(a.G, idx, gs, kmax, 1, 1),
-                          mat(a.Dt, idx, bs, 1, nw)),
+    e = launch_cgemm(dyn(gemm(nw, k, k, ns, mat(a.P, idx, ps, 1, nw, 1),
+                              mat(a.G, idx, gs, kmax, 1, 1), mat(a.Dt, idx, bs, 1, nw)),
+                         0, 1, 1),
                      orth_engine, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(4)) != cudaSuccess) return e;
-    e = launch_cgemm(gemm(mw, nw, k, ns, mat(a.Y, idx, ys, 1, mw), mat(a.Dt, idx, bs, nw, 1),
-                          mat(a.zhat, idx, a.N12, a.wr, a.wc)),
+    e = launch_cgemm(dyn(gemm(mw, nw, k, ns, mat(a.Y, idx, ys, 1, mw), mat(a.Dt, idx, bs, nw, 1),
+                              mat(a.zhat, idx, a.N12, a.wr, a.wc)),
+                         0, 0, 1),
                      a.engine, st);
     if (e != cudaSuccess) return e;
     if ((e = mark(5)) != cudaSuccess) return e;
     if ((e = launch_rsvt_refill(a, k, a.kfill, st)) != cudaSuccess) return e;
+    if (a.kdev) {
+      rsvt_next_k_kernel<<<1, 32, 0, st>>>(a.rstat, a.oversample, kmax < k ? kmax : k);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     return mark(6);
   }
   // Dt = D_tau(Bt), converged vectors -> P (conjugated), singular values -> sig

@@ -227,6 +227,14 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(CGemm g) {
   using C = Cfg<ENG>;
   using L = Layout<ENG>;
   extern __shared__ __align__(1024) unsigned char smem[];
+  if (g.kdev) {
+    const int kk = *g.kdev;
+    if (g.dynM) g.M = kk;
+    if (g.dynN) g.N = kk;
+    if (g.dynK) g.K = kk;
+  }
+  // tiles past a device-chosen extent have nothing to do (before any barrier or allocation)
+  if ((int)blockIdx.x * BM >= g.M || (int)blockIdx.y * BN >= g.N) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int bz = blockIdx.z;
   const float2* A = g.a.p + (int64_t)(g.a.idx ? g.a.idx[bz] : bz) * g.a.bs;

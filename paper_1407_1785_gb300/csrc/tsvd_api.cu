@@ -999,6 +999,7 @@ struct BatchItem {
   SliceKnobs kn{};
   std::vector<float2> twid;
   std::vector<int> slices;
+  std::vector<unsigned char> isreal;   // mixed form
 };
 
 // Carves the regions of one tensor from `base` (nullptr: only measure); returns its bytes.
@@ -1013,7 +1014,9 @@ size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base) {
   const size_t spec = (size_t)g.nstore * g.N12 * sizeof(float2);
   const size_t real = (size_t)it.p.N * sizeof(float);
   const bool complete = it.src->kind == TSVD_PROBLEM_COMPLETE;
-  const size_t jbytes = jacobi_svt_scratch_bytes((int)it.p.n1, (int)it.p.n2, it.w.ndistinct, it.kn);
+  const bool mixed = mixed_precision(c);
+  const size_t jbytes =
+      mixed ? 0 : jacobi_svt_scratch_bytes((int)it.p.n1, (int)it.p.n2, it.w.ndistinct, it.kn);
   size_t total = 0;
   auto take = [&](size_t bytes) {
     char* ptr = base ? base + total : nullptr;
@@ -1030,6 +1033,34 @@ size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base) {
   it.w.acc = reinterpret_cast<SweepAccum*>(take(sizeof(SweepAccum)));
   it.w.jscratch = jbytes ? take(jbytes) : nullptr;
   it.w.jscratch_bytes = jbytes;
+  it.w.rsvt = mixed;
+  if (mixed) {
+    // mixed form with the device-chosen width (graph-capturable): widths up to the Gram path's
+    const bool tr = it.p.n1 < it.p.n2;
+    it.w.mw = (int)(tr ? it.p.n2 : it.p.n1);
+    it.w.nw = (int)(tr ? it.p.n1 : it.p.n2);
+    it.w.wr = tr ? it.p.n1 : 1;
+    it.w.wc = tr ? 1 : it.p.n1;
+    it.w.kmax = std::min(it.w.nw, rsvt_eig_max_k());
+    if (c->opts.rsvt_kmax > 0) it.w.kmax = std::min(it.w.kmax, c->opts.rsvt_kmax);
+    const size_t ns = (size_t)g.nstore, km = (size_t)it.w.kmax;
+    it.w.rP = reinterpret_cast<float2*>(take(ns * it.w.nw * km * sizeof(float2)));
+    it.w.rY = reinterpret_cast<float2*>(take(ns * it.w.mw * km * sizeof(float2)));
+    it.w.rQ = reinterpret_cast<float2*>(take(ns * it.w.mw * km * sizeof(float2)));
+    it.w.rBt = reinterpret_cast<float2*>(take(ns * it.w.nw * km * sizeof(float2)));
+    it.w.rDt = reinterpret_cast<float2*>(take(ns * it.w.nw * km * sizeof(float2)));
+    it.w.rG = reinterpret_cast<float2*>(take(ns * km * km * sizeof(float2)));
+    it.w.rT = reinterpret_cast<float2*>(take(ns * km * km * sizeof(float2)));
+    it.w.rsig = reinterpret_cast<float*>(take(ns * km * sizeof(float)));
+    it.w.risreal = reinterpret_cast<unsigned char*>(take(ns));
+    it.w.rstat = reinterpret_cast<RsvtStat*>(take(sizeof(RsvtStat)));
+    it.w.rjs = nullptr;
+    it.w.rjs_bytes = 0;
+    it.isreal.assign(ns, 0);
+    for (int kh = 0; kh < g.hh; ++kh)
+      for (int kf = 0; kf < g.nf; ++kf)
+        it.isreal[(size_t)(kf + g.nf * kh)] = slice_is_real(g, kf, kh) ? 1 : 0;
+  }
   return total;
 }
 
@@ -1055,11 +1086,30 @@ tsvd_status enqueue_item(tsvd_ctx* c, const BatchItem& it, int iters) {
     t0.spec_out = w.spec_a;
     TSVD_TRY(run_tube(c, t0, "tube pass (forward)"));
   }
+  if (w.rsvt) {
+    // device-chosen sketch width: counters and width reset, random start basis
+    TSVD_TRY(launch(c, launch_rsvt_state_init(w.rstat, rsvt_k0(c, w), c->cur), "sketch state"));
+    RsvtArgs a0 = rsvt_args(c, p, w, 0.f, 0, 0);
+    a0.rstat = nullptr;
+    TSVD_TRY(launch(c, launch_rsvt_refill(a0, 0, w.kmax, c->cur), "sketch initialisation"));
+  }
   for (int k = 0; k < iters; ++k) {
     const float tau = (float)(scale / r);
-    SliceArgs s = slice_args(c, p, w, tau);
-    s.knobs = it.kn;
-    TSVD_TRY(run_slice(c, s));
+    if (w.rsvt) {
+      RsvtArgs a = rsvt_args(c, p, w, tau, w.kmax, k);
+      a.rstat = w.rstat;
+      a.kdev = &w.rstat->k;
+      a.oversample = c->opts.rsvt_oversample;
+      TSVD_TRY(record_event(c, 0));
+      TSVD_TRY(launch(c, launch_rsvt(a, c->cur), "randomized slice SVT"));
+      c->launches += rsvt_kernels(a);   // + the width update
+      ++c->slice_launches;
+      TSVD_TRY(record_event(c, 0));
+    } else {
+      SliceArgs s = slice_args(c, p, w, tau);
+      s.knobs = it.kn;
+      TSVD_TRY(run_slice(c, s));
+    }
     const double r_next = std::fmin(c->opts.mu * r, c->opts.rho_max);
     if (q.kind == TSVD_PROBLEM_COMPLETE) {
       if (k + 1 < iters) {
@@ -1445,8 +1495,6 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
   begin_call(c);
   if (count < 0 || (count > 0 && !problems)) return fail(c, TSVD_EINVAL, "bad problem list");
   if (iters < 0) return fail(c, TSVD_EINVAL, "iters must be >= 0");
-  if (mixed_precision(c))
-    return fail(c, TSVD_EUNSUPPORTED, "batched solves run the plain FP32 form only");
   DeviceGuard dg(c->device);
   if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
   std::vector<BatchItem> items((size_t)count);
@@ -1529,6 +1577,9 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
                                  cudaMemcpyHostToDevice, c->stream));
     TSVD_CUDA(c, cudaMemsetAsync(it.w.acc, 0, sizeof(SweepAccum), c->stream));
     TSVD_CUDA(c, cudaMemsetAsync(it.w.stat, 0, (size_t)g.nstore * sizeof(SliceStat), c->stream));
+    if (it.w.rsvt)
+      TSVD_CUDA(c, cudaMemcpyAsync(it.w.risreal, it.isreal.data(), it.isreal.size(),
+                                   cudaMemcpyHostToDevice, c->stream));
     const tsvd_problem& q = *it.src;
     if (q.kind == TSVD_PROBLEM_COMPLETE)
       TSVD_TRY(launch(c, launch_encode_observed(q.M, q.omega, it.w.yn, it.p.N, bad + i, c->stream),
@@ -1572,7 +1623,8 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
     if (!c->fork) TSVD_CUDA(c, cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     std::vector<int64_t> key = {3, count, iters, (int64_t)(intptr_t)c->ws, (int64_t)c->ws_cap,
                                 c->opts.tnn_scale, c->opts.sparse_mode, c->opts.max_sweeps,
-                                c->opts.timing};
+                                c->opts.timing, c->opts.precision, c->opts.rsvt_oversample,
+                                c->opts.rsvt_kmax};
     double d[4] = {c->opts.rho0, c->opts.mu, c->opts.rho_max, (double)c->opts.jacobi_tol};
     for (double v : d) {
       int64_t bits;
@@ -1631,6 +1683,15 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
         stats->slice_svds += (int64_t)iters * it.w.ndistinct;
         stats->tnn_last += tnn;
         stats->rank_last_max = std::max(stats->rank_last_max, rmax);
+        if (it.w.rsvt) {
+          RsvtStat rs;
+          TSVD_CUDA(c, cudaMemcpyAsync(&rs, it.w.rstat, sizeof rs, cudaMemcpyDeviceToHost,
+                                       c->stream));
+          TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+          stats->rsvt_k_last = std::max(stats->rsvt_k_last, rs.k);
+          stats->rsvt_saturated += rs.saturated;
+          stats->rsvt_drops += rs.drops;
+        }
       }
     }
   }

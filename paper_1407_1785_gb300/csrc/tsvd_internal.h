@@ -135,10 +135,14 @@ struct CMat {
   int64_t s0, s1;
   int conj;
 };
-// C(i, j) = sum_l A(i, l) B(l, j) for i < M, j < N, l < K, for every batch entry.
+// C(i, j) = sum_l A(i, l) B(l, j) for i < M, j < N, l < K, for every batch entry.  With kdev
+// set, the dimensions flagged dyn* are read from *kdev on the device (at most the value given,
+// which sizes the grid).
 struct CGemm {
   int M, N, K, batch;
   CMat a, b, c;
+  const int* kdev = nullptr;
+  int dynM = 0, dynN = 0, dynK = 0;
 };
 // Arithmetic of the slice products: FP32 on CUDA cores, or 3M complex products on the tensor
 // cores with TF32, BF16 or split (3xTF32) operands and FP32 accumulation.
@@ -155,7 +159,7 @@ struct RsvtStat {
   int rank_max;    // max over slices of the singular values above max(tau, floor sigma_max)
   int saturated;   // slices whose whole sketch lay above that level
   int drops;       // columns dropped by the Cholesky factorisations
-  int pad;
+  int k;           // device-chosen sketch width (RsvtArgs::kdev mode)
 };
 
 struct RsvtArgs {
@@ -188,6 +192,12 @@ struct RsvtArgs {
   void* jscratch;
   size_t jscratch_bytes;
   SliceKnobs jknobs;      // plan of the small Jacobi SVTs (0 = planner's choice)
+  // Device-chosen width: when set (= &rstat->k), the kernels read the width from it, k above
+  // is its upper bound (grids, shared memory, strides), the small SVD always takes the Gram
+  // path (k <= rsvt_eig_max_k()), and the call ends with rsvt_next_k_kernel picking the next
+  // width from the ranks it saw: no host decision, so the sequence can be captured.
+  const int* kdev = nullptr;
+  int oversample = 10;
   // nullable: 7 events recorded at the stage boundaries of a call without power steps:
   // [0] sketch product [1] CholeskyQR2 [2] projection product [3] small SVT [4] rebuild
   // product [5] refill [6]
@@ -201,5 +211,7 @@ size_t rsvt_jacobi_scratch_bytes(int nw, int kmax, int nslices, const SliceKnobs
 cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st);
 // Refill columns c < kfill of P that carry no direction (all of them when k = 0).
 cudaError_t launch_rsvt_refill(const RsvtArgs& a, int k, int kfill, cudaStream_t st);
+// Device-chosen width mode: counters zero, width k0.
+cudaError_t launch_rsvt_state_init(RsvtStat* st_dev, int k0, cudaStream_t st);
 
 }  // namespace tsvd
