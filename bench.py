@@ -24,8 +24,10 @@ than the plain form's recovery error beyond 1%), under the key "mixed".
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                         [--workload NAME] [--precision P] [--mixed P|none]
-For N > 1 run under torchrun (one rank per GPU); every rank solves its own replica (weak
-scaling, no collective on the data path) and the slowest rank's time counts.
+For N > 1 run under torchrun (one rank per GPU); every rank solves its own replica of a
+single-tensor workload, and the 64 tensors of the batch are split over the ranks by cost
+(longest processing time first): weak scaling, no collective on the data path; the slowest
+rank's time counts.
 """
 from __future__ import annotations
 
@@ -99,6 +101,38 @@ def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x: float) -> float:
+    """The maximum of a per-rank scalar over all ranks (the rank itself when not distributed);
+    works with the gloo (CPU) and NCCL (GPU) backends."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def tensor_cost(dims):
+    """Estimated slice-SVD work of one ADMM iteration of a tensor: m n^2 per distinct Fourier
+    slice (n = min(n1, n2))."""
+    m, n = max(dims[0], dims[1]), min(dims[0], dims[1])
+    return float(m) * n * n * half_slices(dims)
+
+
+def lpt_shard(costs, world):
+    """Longest-processing-time split of independent tensors over `world` ranks: tensors in
+    decreasing cost, each to the least loaded rank.  Returns one sorted index list per rank."""
+    loads = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda j: (-costs[j], j)):
+        r = min(range(world), key=lambda q: (loads[q], q))
+        parts[r].append(i)
+        loads[r] += costs[i]
+    return [sorted(p) for p in parts]
 
 
 def measured_peaks():
@@ -448,8 +482,14 @@ def run_ours(args):
 
     spec = WORKLOADS[args.workload]
     iters = args.iters or spec["iters"]
-    wl = build_workload(args.workload, 1 + rank)
-    batch = wl["kind"] == "batch"
+    batch = spec["kind"] == "batch"
+    # single tensors: every rank solves its own replica (seed 1 + rank); the batch: one batch,
+    # its tensors split over the ranks (no collective on the data path)
+    wl = build_workload(args.workload, 1 if batch else 1 + rank)
+    n_per_iter = n_voxels(wl)      # voxels of one iteration: one replica, or the whole batch
+    if batch and world > 1:
+        mine = lpt_shard([tensor_cost(it["dims"]) for it in wl["items"]], world)[rank]
+        wl = dict(kind="batch", items=[wl["items"][i] for i in mine])
     items = wl["items"] if batch else [wl]
     N = n_voxels(wl)
 
@@ -475,11 +515,10 @@ def run_ours(args):
     sampler.start()
     t_ms, stats = timed_solves(solve, args.steps, flush, stream, barrier)
     clocks = sampler.stop()
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * iters * args.steps / (t_ms / 1000.0)
+    t_ms = max_over_ranks(t_ms)
+    # replicas: the ranks' iterations add up; the sharded batch: one batch iteration spans them
+    units = 1 if batch else world
+    value = units * iters * args.steps / (t_ms / 1000.0)
     errs = recovery_errors(dw)
     slice_ms, tube_ms = sum_stats(stats, "slice_ms"), sum_stats(stats, "tube_ms")
     slice_launches, launches = sum_stats(stats, "slice_launches"), sum_stats(stats, "launches")
@@ -527,12 +566,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": world * iters * args.steps / e2e_s, "unit": "iters/s",
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": units * iters * args.steps / e2e_s, "unit": "iters/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     peaks = measured_peaks()
@@ -585,7 +620,7 @@ def run_ours(args):
         "config": {"workload": spec["desc"], "admm_iters_per_step": iters, "seed": 1,
                    "precision": prec, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "voxels_per_s": value * N,
+        "voxels_per_s": value * n_per_iter,
         "final_rse_db": e_db[0] if not batch else statistics.mean(e_db),
         "roofline": roofline,
         "roofline_tube": roofline_tube,
