@@ -75,6 +75,9 @@ enum { TSVD_SPARSE_ENTRY = 0, TSVD_SPARSE_TUBE = 1 };
  * of the TNN exactly as defined in Thm 2.4.1 (sum over all Fourier slices). */
 enum { TSVD_SCALE_AVG = 0, TSVD_SCALE_SUM = 1 };
 
+/* Warm start of the plain-form slice SVDs inside ADMM solves (tsvd_opts.warm_start). */
+enum { TSVD_WARM_OFF = 0, TSVD_WARM_ON = 1, TSVD_WARM_AUTO = 2 };
+
 typedef struct tsvd_opts {
   int precision;      /* TSVD_PRECISION_*; default FP32 */
   int sparse_mode;    /* TSVD_SPARSE_*; default ENTRY */
@@ -112,6 +115,16 @@ typedef struct tsvd_opts {
   int rsvt_power;     /* mixed form, tsvt() only: extra power steps from a random start
                          (ADMM solves start each iteration from the previous basis);
                          default 2 */
+  int warm_start;     /* plain form, tnn_complete / trpca: TSVD_WARM_ON starts each slice's
+                         Jacobi SVD from the previous iteration's right singular vectors V
+                         (the slice is pre-rotated to B V and the rotations accumulate into V,
+                         the V form), with a cold start every 16 iterations; the rebuild
+                         still projects B itself (U form), so the result is the same SVT,
+                         reached in fewer sweeps.  TSVD_WARM_OFF: every SVD starts from B.
+                         TSVD_WARM_AUTO (default): on for tnn_complete, off for trpca, whose
+                         sparse residual changes the small singular vectors at every
+                         iteration, so a warm start saves fewer sweeps than the V form's
+                         extra rotations cost. */
 } tsvd_opts;
 
 /* Counters of one ADMM solve (host struct). */

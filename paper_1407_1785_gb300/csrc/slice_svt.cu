@@ -18,7 +18,10 @@
 //            u_i = w_i / sigma_i, re-reading the original slice B from global memory (L2);
 //   V form (opt-in):   the rotations are also applied to V (stored after each vector, V = I
 //            at the start) and D_tau(B) = sum_{sigma_i > tau} ((sigma_i - tau)/sigma_i) w_i v_i^H.
-// The V form costs one more rotation of an nv-vector per pair and halves the rebuild.
+// The V form costs one more rotation of an nv-vector per pair and halves the rebuild, but
+// W and V collect independent rounding over the rotations, so W v^H drifts from B v v^H by
+// about eps sqrt(rotations) |B|; the U form projects the original B and does not.  With V
+// accumulated for a warm start (vin / vout), the rebuild can still be the U form (brb).
 //
 // Rounding.  Each rotation is applied as x + (cs - 1) x - conj(k) y with cs - 1 computed to
 // full relative precision: in FP32, cs rounds to exactly 1 for small angles while sn = t
@@ -33,8 +36,10 @@
 // Inside a CTA the pairs of a local round are disjoint and run concurrently, G lanes per
 // pair (32/G pairs per warp), with the inner products reduced by shuffles inside the group.
 // Between block rounds the CTAs trade blocks through a double-buffered global buffer (one
-// cluster barrier per exchange).  Each CTA then rebuilds the part of D_tau(B) spanned by its
-// own kept vectors; the C partial slices are summed in a fixed order (deterministic).
+// cluster barrier per exchange).  For the rebuild the CTAs pool their kept vectors in the
+// exchange buffer (in cluster-rank order) and each CTA writes D_tau(B) for 1/C of the
+// columns from all of them: every entry is summed in a fixed order (deterministic) and no
+// CTA writes a partial slice.
 //
 // Shared memory holds a CTA's 2 bs vectors in planar form: a real plane and an imaginary
 // plane, rows of pitch rowp floats (the vector's ld entries, then in the V form its ldv V
@@ -280,7 +285,8 @@ __host__ __device__ constexpr int max_warps_for(int chunks) {
 // Copy block `blk` of the slice (vectors blk*bs .. blk*bs+bs-1, zero past nv) into local
 // slot `slot`; in the V form the V entries of vector g start as the unit vector e_g.
 __device__ void load_block_from_slice(float* Wr, float* Wi, const float2* __restrict__ A,
-                                      const SliceShape& sh, int n1, int blk, int slot) {
+                                      const SliceShape& sh, int n1, int blk, int slot,
+                                      const float2* __restrict__ Vin) {
   const int bs = sh.bs, len = sh.len, rowp = sh.rowp;
   const int v0 = blk * bs;
   const int nvalid = max(0, min(bs, sh.nv - v0));
@@ -300,8 +306,17 @@ __device__ void load_block_from_slice(float* Wr, float* Wi, const float2* __rest
     i0[(size_t)k * rowp + p] = 0.f;
   }
   __syncthreads();
-  if (sh.vform)
+  if (sh.vform && Vin) {
+    // warm start: V entries of vector g are column g of the given V (nv x nv, col-major)
+    for (int idx = tid; idx < nvalid * sh.nv; idx += nthr) {
+      const int k = idx / sh.nv, i = idx % sh.nv;
+      const float2 v = Vin[(size_t)i + (size_t)sh.nv * (v0 + k)];
+      r0[(size_t)k * rowp + sh.ld + i] = v.x;
+      i0[(size_t)k * rowp + sh.ld + i] = v.y;
+    }
+  } else if (sh.vform) {
     for (int k = tid; k < nvalid; k += nthr) r0[(size_t)k * rowp + sh.ld + v0 + k] = 1.f;
+  }
   if (!sh.rows) {
     // vector v = column v0 + k: entries A[p + n1 (v0 + k)], contiguous in p
     for (int idx = tid; idx < nvalid * len; idx += nthr) {
@@ -378,21 +393,22 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
   const int n1 = a.n1;
   const int64_t N12 = a.N12;
   const float2* __restrict__ A = a.ahat + (size_t)s * N12;
+  // the slice the U-form rebuild reads, and which rebuild runs
+  const float2* __restrict__ Ab = a.brb ? a.brb + (size_t)s * N12 : A;
+  const bool uform = !sh.vform || a.brb != nullptr;
   float2* __restrict__ Z = a.zhat + (size_t)s * N12;
   char* scr = static_cast<char*>(a.scratch);
   const size_t xbytes = sh.xbuf_floats * sizeof(float);
-  const size_t pbytes = (size_t)C * N12 * sizeof(float2);
-  float* xbuf = C > 1 ? reinterpret_cast<float*>(scr + (size_t)so * (xbytes + pbytes)) : nullptr;
-  float2* part = C > 1 ? reinterpret_cast<float2*>(scr + (size_t)so * (xbytes + pbytes) + xbytes)
-                       : nullptr;
+  float* xbuf = C > 1 ? reinterpret_cast<float*>(scr + (size_t)so * xbytes) : nullptr;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
 
   // ---- initial blocks: slot 0 / slot 1 hold the blocks of circle slot `crank`, round 0
   int bx, by;
   round_robin_pair(0, crank, nb, bx, by);
-  load_block_from_slice(Wr, Wi, A, sh, n1, bx, 0);
-  load_block_from_slice(Wr, Wi, A, sh, n1, by, 1);
+  const float2* Vin = a.vin ? a.vin + (size_t)s * a.vstride : nullptr;
+  load_block_from_slice(Wr, Wi, A, sh, n1, bx, 0, Vin);
+  load_block_from_slice(Wr, Wi, A, sh, n1, by, 1, Vin);
   __syncthreads();
 
   // ---- Jacobi sweeps
@@ -510,6 +526,18 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
     if (lane == 0) sig[v] = sqrtf(acc);
   }
   __syncthreads();
+  if (a.vout && sh.vform) {
+    // the accumulated right rotations V (columns of the local vectors), for a warm start
+    float2* vo = a.vout + (size_t)s * a.vstride;
+    for (int v = warp; v < nl; v += nwarps) {
+      const int gv = v < bs ? bx * bs + v : by * bs + v - bs;
+      if (gv >= sh.nv) continue;
+      const float* vr = Wr + (size_t)v * rowp + ld;
+      const float* vi = Wi + (size_t)v * rowp + ld;
+      for (int i = lane; i < sh.nv; i += 32)
+        vo[(size_t)i + (size_t)sh.nv * gv] = make_float2(vr[i], vi[i]);
+    }
+  }
   if (a.wout) {
     // the converged vectors (and their norms) for callers that continue from them
     const float si = a.wout_conj ? -1.f : 1.f;
@@ -564,28 +592,82 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
       atomicMax(&a.acc->max_sweeps, sweeps);
     }
   }
-  const int rank = s_rank;
-  float2* out = C > 1 ? part + (size_t)crank * N12 : Z;
-
-  if (rank == 0) {
-    for (int64_t idx = tid; idx < N12; idx += nthr) out[idx] = make_float2(0.f, 0.f);
-  } else {
-    if (!sh.vform) {
-      // ---- U form: normalise the kept vectors, u = w / sigma
-      for (int64_t idx = tid; idx < (int64_t)rank * len; idx += nthr) {
-        const int k = (int)(idx / len), e = (int)(idx % len);
-        const int v = keep[k];
-        const float inv = 1.f / sig[v];
-        Wr[(size_t)v * rowp + e] *= inv;
-        Wi[(size_t)v * rowp + e] *= inv;
+  // ---- rebuild.  One CTA: its kept vectors, all columns.  A cluster: every CTA exports its
+  // kept vectors (U form: u = w / sigma; V form: w with its V entries) and shrink factors to
+  // the exchange buffer, idle after the sweeps, in cluster-rank order; then each CTA
+  // rebuilds the columns [col0, col1) of D_tau(B) from all kept vectors, imported nl at a
+  // time, so no CTA writes a partial slice.
+  const int rank_loc = s_rank;
+  int off = 0, rank_all = rank_loc;
+  if (C > 1) {
+    rank_all = 0;
+    for (int c = 0; c < C; ++c) {
+      const int rc = *cluster.map_shared_rank(&s_rank, c);
+      if (c < crank) off += rc;
+      rank_all += rc;
+    }
+  }
+  if (uform) {
+    // ---- U form: normalise the kept vectors, u = w / sigma
+    for (int64_t idx = tid; idx < (int64_t)rank_loc * len; idx += nthr) {
+      const int k = (int)(idx / len), e = (int)(idx % len);
+      const int v = keep[k];
+      const float inv = 1.f / sig[v];
+      Wr[(size_t)v * rowp + e] *= inv;
+      Wi[(size_t)v * rowp + e] *= inv;
+    }
+    __syncthreads();
+  }
+  const int nv = sh.nv;
+  const int col0 = C > 1 ? (int)((int64_t)nv * crank / C) : 0;
+  const int col1 = C > 1 ? (int)((int64_t)nv * (crank + 1) / C) : nv;
+  // exported rows: [kept index][plane][rowp] floats, then the shrink factors
+  const int xw = uform ? ld : rowp;          // floats of a row the rebuild reads
+  float* xd = xbuf ? xbuf + (size_t)2 * nv * rowp : nullptr;
+  if (C > 1) {
+    for (int k = warp; k < rank_loc; k += nwarps) {
+      const int v = keep[k];
+      float* dr = xbuf + (size_t)2 * (off + k) * rowp;
+      for (int e = lane * 4; e < xw; e += 128) {
+        *reinterpret_cast<float4*>(dr + e) = *reinterpret_cast<const float4*>(Wr + (size_t)v * rowp + e);
+        *reinterpret_cast<float4*>(dr + rowp + e) =
+            *reinterpret_cast<const float4*>(Wi + (size_t)v * rowp + e);
+      }
+      if (lane == 0) xd[off + k] = dsc[v];
+    }
+    __threadfence();
+    cluster.sync();
+  }
+  if (rank_all == 0) {
+    for (int64_t idx = tid; idx < (int64_t)len * (col1 - col0); idx += nthr) {
+      const int p = (int)(idx % len), col = col0 + (int)(idx / len);
+      Z[b_index(sh, n1, p, col)] = make_float2(0.f, 0.f);
+    }
+  }
+  for (int g0 = 0; g0 < rank_all; g0 += nl) {
+    const int rank = C > 1 ? min(nl, rank_all - g0) : rank_loc;
+    if (C > 1) {
+      // import kept vectors g0 .. g0 + rank - 1 into local slots 0 .. rank - 1
+      __syncthreads();
+      for (int k = warp; k < rank; k += nwarps) {
+        const float* sr = xbuf + (size_t)2 * (g0 + k) * rowp;
+        for (int e = lane * 4; e < xw; e += 128) {
+          *reinterpret_cast<float4*>(Wr + (size_t)k * rowp + e) = *reinterpret_cast<const float4*>(sr + e);
+          *reinterpret_cast<float4*>(Wi + (size_t)k * rowp + e) =
+              *reinterpret_cast<const float4*>(sr + rowp + e);
+        }
+        if (lane == 0) {
+          keep[k] = k;
+          dsc[k] = xd[g0 + k];
+        }
       }
       __syncthreads();
     }
-    // ---- rebuild the local part of D_tau(B), a chunk of nc columns of B at a time
-    const int nv = sh.nv;
-    for (int c0 = 0; c0 < nv; c0 += nc) {
-      const int ncur = min(nc, nv - c0);
-      if (sh.vform) {
+    const bool first = g0 == 0;
+    // ---- D_tau(B) columns [col0, col1), a chunk of nc columns at a time
+    for (int c0 = col0; c0 < col1; c0 += nc) {
+      const int ncur = min(nc, col1 - c0);
+      if (!uform) {
         // C(k, cc) = d_k conj(v_k(c0 + cc))
         for (int idx = tid; idx < rank * ncur; idx += nthr) {
           const int k = idx / ncur, cc = idx % ncur;
@@ -606,20 +688,19 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
             cc = idx % ncur;
             p = idx / ncur;
           }
-          Bc[p + (size_t)len * cc] = A[b_index(sh, n1, p, c0 + cc)];
+          Bc[p + (size_t)len * cc] = Ab[b_index(sh, n1, p, c0 + cc)];
         }
         __syncthreads();
-        // C(k, cc) = d_k u_k^H B(:, c0+cc); thread k starts at a k-dependent entry so the
-        // lanes of a warp hit distinct banks
-        for (int k = tid; k < rank; k += nthr) {
+        // C(k, cc) = d_k u_k^H B(:, c0+cc): one warp per kept vector, its lanes striding
+        // over the entries (consecutive banks), then a butterfly sum over the warp
+        for (int k = warp; k < rank; k += nwarps) {
           const int v = keep[k];
           const float* ur = Wr + (size_t)v * rowp;
           const float* ui = Wi + (size_t)v * rowp;
           float accr[kNC], acci[kNC];
 #pragma unroll
           for (int cc = 0; cc < kNC; ++cc) accr[cc] = acci[cc] = 0.f;
-          int p = k % len;
-          for (int it = 0; it < len; ++it) {
+          for (int p = lane; p < len; p += 32) {
             const float xr = ur[p], xi = ui[p];
 #pragma unroll
             for (int cc = 0; cc < kNC; ++cc) {
@@ -629,12 +710,23 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
                 acci[cc] += xr * b.y - xi * b.x;
               }
             }
-            if (++p == len) p = 0;
+          }
+#pragma unroll
+          for (int cc = 0; cc < kNC; ++cc) {
+            accr[cc] = group_sum<32>(accr[cc]);
+            acci[cc] = group_sum<32>(acci[cc]);
           }
           const float d = dsc[v];
+          if (lane < ncur) {
+            float cr = 0.f, ci = 0.f;
 #pragma unroll
-          for (int cc = 0; cc < kNC; ++cc)
-            if (cc < ncur) Cc[(size_t)k * nc + cc] = make_float2(d * accr[cc], d * acci[cc]);
+            for (int cc = 0; cc < kNC; ++cc)
+              if (cc == lane) {
+                cr = accr[cc];
+                ci = acci[cc];
+              }
+            Cc[(size_t)k * nc + lane] = make_float2(d * cr, d * ci);
+          }
         }
         __syncthreads();
       }
@@ -660,6 +752,8 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
           if (cc < ncur) Bc[p + (size_t)len * cc] = make_float2(accr[cc], acci[cc]);
       }
       __syncthreads();
+      // later groups add to the columns the first wrote (this CTA owns them; the
+      // __syncthreads between groups orders the accesses)
       for (int idx = tid; idx < len * ncur; idx += nthr) {
         int p, cc;
         if (!sh.rows) {
@@ -669,24 +763,16 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
           cc = idx % ncur;
           p = idx / ncur;
         }
-        out[b_index(sh, n1, p, c0 + cc)] = Bc[p + (size_t)len * cc];
+        const size_t o = b_index(sh, n1, p, c0 + cc);
+        float2 zv = Bc[p + (size_t)len * cc];
+        if (!first) {
+          const float2 prev = Z[o];
+          zv.x += prev.x;
+          zv.y += prev.y;
+        }
+        Z[o] = zv;
       }
       __syncthreads();
-    }
-  }
-  if (C > 1) {
-    // ---- Z = sum of the C partial rebuilds, added in cluster-rank order
-    __threadfence();
-    cluster.sync();
-    const int64_t lo_i = N12 * crank / C, hi_i = N12 * (crank + 1) / C;
-    for (int64_t idx = lo_i + tid; idx < hi_i; idx += nthr) {
-      float2 acc = part[idx];
-      for (int c = 1; c < C; ++c) {
-        const float2 v = part[(size_t)c * N12 + idx];
-        acc.x += v.x;
-        acc.y += v.y;
-      }
-      Z[idx] = acc;
     }
   }
 }
@@ -801,8 +887,9 @@ bool plan_slice(int n1, int n2, int nslices, const SliceKnobs& k, SliceShape& sh
 }
 
 size_t scratch_for(const SliceShape& sh, int64_t N12, int nslices) {
+  (void)N12;
   if (sh.C <= 1) return 0;
-  return (size_t)nslices * (sh.xbuf_floats * sizeof(float) + (size_t)sh.C * N12 * sizeof(float2));
+  return (size_t)nslices * sh.xbuf_floats * sizeof(float);
 }
 
 template <int G, int CPL, int NP>
@@ -865,6 +952,8 @@ cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st) {
   if (sh.C > 1 && (a.scratch == nullptr || a.scratch_bytes < scratch_for(sh, a.N12, a.nslices)))
     return cudaErrorInvalidValue;
   if (a.wout && (sh.rows || a.wout_stride < (int64_t)a.n1 * a.n2)) return cudaErrorInvalidValue;
+  if ((a.vin || a.vout) && (!sh.vform || a.vstride < (int64_t)sh.nv * sh.nv))
+    return cudaErrorInvalidValue;
   const int gpw = 32 / sh.G;
   const int per_warp = gpw * sh.np;           // pairs a warp has in flight
   const int maxw = max_warps_for(sh.cpl * sh.np);

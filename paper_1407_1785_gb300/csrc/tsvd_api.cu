@@ -52,6 +52,8 @@ struct tsvd_ctx {
   std::vector<cudaStream_t> branches;
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
+  // plain form: the current solve runs the V form (warm start), for the plan lookups
+  bool vform_now = false;
   // mixed form: per-iteration sketch statistics copied to pinned host memory (a ring read
   // two iterations late, so the host never waits for the iteration it just enqueued)
   static constexpr int kRing = 4;
@@ -195,14 +197,15 @@ int slice_weight(const TubeGeom& g, int kf, int kh) {
   return (selfcol && selfrow) ? 1 : 2;
 }
 
+int vform_of(const tsvd_ctx* c) { return (c->opts.accumulate_v || c->vform_now) ? 1 : 0; }
+
 std::array<int, 4> plan_key(tsvd_ctx* c, const Problem& p, int nslices) {
-  return {(int)p.n1, (int)p.n2, nslices, c->opts.accumulate_v};
+  return {(int)p.n1, (int)p.n2, nslices, vform_of(c)};
 }
 
 // Slice-SVT plans the autotuner compares (or the single plan fixed by the options).
 std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslices) {
-  const SliceKnobs base = {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0,
-                           c->opts.accumulate_v};
+  const SliceKnobs base = {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, vform_of(c)};
   std::vector<SliceKnobs> out;
   if (c->opts.autotune) {
     const int ctas[4] = {1, 2, 4, 8};
@@ -226,7 +229,7 @@ std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslic
 SliceKnobs planned_knobs(tsvd_ctx* c, const Problem& p, int nslices) {
   auto it = c->tuned.find(plan_key(c, p, nslices));
   if (it != c->tuned.end()) return it->second;
-  return {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, c->opts.accumulate_v};
+  return {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, vform_of(c)};
 }
 
 std::string device_name(int dev) {
@@ -297,12 +300,18 @@ struct Workspace {
   RsvtStat* rstat = nullptr;     // tsvd_ctx::kRing slots
   void* rjs = nullptr;
   size_t rjs_bytes = 0;
+  // plain form, warm start: pre-rotated slices and the accumulated right rotations
+  bool warm = false;
+  int nv = 0;                    // min(n1, n2)
+  float2* abar = nullptr;        // nstore slices like the spectrum
+  float2* vwarm = nullptr;       // nstore x nv x nv
 };
 
 struct WsRequest {
   bool state = false, yn = false, stage_in = false, stage_om = false, stage_out0 = false,
        stage_out1 = false;
   bool rsvt = false;
+  bool warm = false;
 };
 
 int rsvt_engine(const tsvd_ctx* c) {
@@ -366,7 +375,9 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   const size_t rs_mw = rq.rsvt ? ns * w.mw * km * sizeof(float2) : 0;
   const size_t rs_kk = rq.rsvt ? ns * km * km * sizeof(float2) : 0;
   const size_t rjs = rq.rsvt ? rsvt_jacobi_scratch_bytes(w.nw, w.kmax, w.ndistinct, rsvt_knobs(c)) : 0;
-  size_t off[26], total = 0;
+  const size_t warm_v = rq.warm ? ns * (size_t)std::min(p.n1, p.n2) * std::min(p.n1, p.n2) *
+                                       sizeof(float2) : 0;
+  size_t off[28], total = 0;
   auto take = [&](int i, size_t bytes) { off[i] = total; total += align_up(bytes); };
   take(0, spec);
   take(1, spec);
@@ -393,6 +404,8 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   take(22, rq.rsvt ? ns : 0);                                       // isreal
   take(23, rq.rsvt ? tsvd_ctx::kRing * sizeof(RsvtStat) : 0);       // per-iteration stats
   take(24, rjs);
+  take(25, rq.warm ? spec : 0);
+  take(26, warm_v);
   if (total > c->ws_cap) {
     if (c->ws) {
       TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -428,6 +441,10 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   w.bad = reinterpret_cast<int*>(b + off[12]);
   w.jscratch = jbytes ? b + off[13] : nullptr;
   w.jscratch_bytes = jbytes;
+  w.warm = rq.warm;
+  w.nv = (int)std::min(p.n1, p.n2);
+  w.abar = rq.warm ? reinterpret_cast<float2*>(b + off[25]) : nullptr;
+  w.vwarm = rq.warm ? reinterpret_cast<float2*>(b + off[26]) : nullptr;
   if (rq.rsvt) {
     w.rP = reinterpret_cast<float2*>(b + off[14]);
     w.rY = reinterpret_cast<float2*>(b + off[15]);
@@ -578,6 +595,9 @@ tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
     return fail(c, TSVD_EINVAL, "rsvt_oversample must be in [0, 64]");
   if (o.rsvt_kmax < 0) return fail(c, TSVD_EINVAL, "rsvt_kmax must be >= 0");
   if (o.rsvt_power < 0 || o.rsvt_power > 8) return fail(c, TSVD_EINVAL, "rsvt_power must be in [0, 8]");
+  if (o.warm_start != TSVD_WARM_OFF && o.warm_start != TSVD_WARM_ON &&
+      o.warm_start != TSVD_WARM_AUTO)
+    return fail(c, TSVD_EINVAL, "warm_start must be TSVD_WARM_OFF, _ON or _AUTO");
   if (o.sparse_mode != TSVD_SPARSE_ENTRY && o.sparse_mode != TSVD_SPARSE_TUBE)
     return fail(c, TSVD_EINVAL, "bad sparse_mode %d", o.sparse_mode);
   if (o.tnn_scale != TSVD_SCALE_AVG && o.tnn_scale != TSVD_SCALE_SUM)
@@ -648,6 +668,7 @@ tsvd_status launch(tsvd_ctx* c, cudaError_t e, const char* what) {
 
 void begin_call(tsvd_ctx* c) {
   c->cur = c->stream;
+  c->vform_now = false;
   c->err.clear();
   c->launches = 0;
   c->slice_launches = 0;
@@ -687,6 +708,50 @@ tsvd_status run_slice(tsvd_ctx* c, const SliceArgs& a) {
   TSVD_TRY(launch(c, launch_jacobi_svt(a, c->cur), "slice SVT"));
   ++c->slice_launches;
   return record_event(c, 0);
+}
+
+// ---- plain form with warm start
+constexpr int kColdEvery = 16;   // iterations between cold starts of the warm-started Jacobi
+
+// Whether the V form (needed by the warm start) has a plan for this slice shape.
+bool warm_plan_exists(tsvd_ctx* c, const Problem& p) {
+  const SliceKnobs k = {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, 1};
+  return jacobi_svt_plan_ok((int)p.n1, (int)p.n2, p.g.nstore, k);
+}
+
+// Plain slice SVT of ADMM iteration `it`.  With the warm start every slice keeps its
+// accumulated right rotations V: a warm iteration pre-rotates the slice to B V (vectors as
+// columns) or V^T B (vectors as rows) with an FP32 product and starts the Jacobi rotations
+// from V; every kColdEvery-th iteration starts from B and V = I (bounding the drift of V).
+// The rebuild reads B itself (U form), so neither the FP32 pre-rotation nor a V that is
+// unitary only to rounding reaches D_tau(B); they only change how many sweeps converge.
+tsvd_status plain_slice_step(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau, int it) {
+  SliceArgs s = slice_args(c, p, w, tau);
+  if (w.warm) {
+    const int nv = w.nv, n1 = (int)p.n1, n2 = (int)p.n2;
+    s.vout = w.vwarm;
+    s.vstride = (int64_t)nv * nv;
+    s.brb = w.spec_a;   // U-form rebuild from B: V only seeds the next iteration
+    if (it % kColdEvery != 0) {
+      CGemm g{};
+      g.batch = w.ndistinct;
+      g.M = n1;
+      g.N = n2;
+      const bool rows = n1 < n2;   // the Jacobi vectors are the rows of the slice
+      g.K = rows ? n1 : n2;
+      // A(i, l): the slice (columns) or V^T (rows); B(l, j): V (columns) or the slice (rows)
+      const CMat slice_m = {w.spec_a, w.slices, p.g.N12, 1, (int64_t)n1, 0};
+      const CMat v_m = {w.vwarm, w.slices, (int64_t)nv * nv, 1, (int64_t)nv, 0};
+      const CMat vt_m = {w.vwarm, w.slices, (int64_t)nv * nv, (int64_t)nv, 1, 0};
+      g.a = rows ? vt_m : slice_m;
+      g.b = rows ? slice_m : v_m;
+      g.c = {w.abar, w.slices, p.g.N12, 1, (int64_t)n1, 0};
+      TSVD_TRY(launch(c, launch_cgemm(g, RSVT_GEMM_FP32, c->cur), "warm-start rotation"));
+      s.ahat = w.abar;
+      s.vin = w.vwarm;
+    }
+  }
+  return run_slice(c, s);
 }
 
 // ---- mixed form: randomized slice SVT
@@ -912,7 +977,7 @@ std::vector<int64_t> solver_key(tsvd_ctx* c, int kind, const Problem& p, int ite
   std::vector<int64_t> key = {kind, p.order, p.n1, p.n2, p.n3, p.n4, iters,
                               (int64_t)(intptr_t)c->ws, (int64_t)c->ws_cap, k.ctas, k.lanes,
                               k.ppg, k.vform, c->opts.tnn_scale, c->opts.sparse_mode,
-                              c->opts.max_sweeps, c->opts.timing};
+                              c->opts.max_sweeps, c->opts.timing, c->vform_now ? 1 : 0};
   for (const void* q : ptrs) key.push_back((int64_t)(intptr_t)q);
   double d[4] = {c->opts.rho0, c->opts.mu, c->opts.rho_max, (double)c->opts.jacobi_tol};
   for (double v : d) {
@@ -1169,6 +1234,7 @@ void tsvd_default_opts(tsvd_opts* o) {
   o->rsvt_oversample = 10;
   o->rsvt_kmax = 0;
   o->rsvt_power = 2;
+  o->warm_start = TSVD_WARM_AUTO;
 }
 
 tsvd_status tsvd_create(tsvd_ctx** out, int device, void* cuda_stream, const tsvd_opts* opts) {
@@ -1306,6 +1372,10 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
   rq.stage_out0 = kx == 1;
   rq.stage_out1 = Z_out && kzz == 1;
   rq.rsvt = mixed_precision(c);
+  rq.warm = !rq.rsvt && c->opts.warm_start != TSVD_WARM_OFF && iters >= 2 &&
+            warm_plan_exists(c, p);
+  // the plans (and the scratch sized for them) are those of the V form when warm
+  c->vform_now = rq.warm;
   Workspace w;
   TSVD_TRY(prepare_workspace(c, p, rq, w));
   const size_t bytes = (size_t)p.N * sizeof(float);
@@ -1356,8 +1426,7 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
           TSVD_TRY(rl.step(tau));
         } else {
           if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
-          SliceArgs s = slice_args(c, p, w, tau);
-          TSVD_TRY(run_slice(c, s));
+          TSVD_TRY(plain_slice_step(c, p, w, tau, k));
         }
         const double r_next = std::fmin(c->opts.mu * r, c->opts.rho_max);
         if (k + 1 < iters) {
@@ -1413,6 +1482,10 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
   rq.stage_out0 = kl == 1;
   rq.stage_out1 = ks == 1;
   rq.rsvt = mixed_precision(c);
+  rq.warm = !rq.rsvt && c->opts.warm_start == TSVD_WARM_ON && iters >= 2 &&
+            warm_plan_exists(c, p);
+  // the plans (and the scratch sized for them) are those of the V form when warm
+  c->vform_now = rq.warm;
   Workspace w;
   TSVD_TRY(prepare_workspace(c, p, rq, w));
   const size_t bytes = (size_t)p.N * sizeof(float);
@@ -1456,8 +1529,7 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
           TSVD_TRY(rl.step(tau));
         } else {
           if (k == 0) TSVD_TRY(tune_slices(c, p, w, tau));
-          SliceArgs s = slice_args(c, p, w, tau);
-          TSVD_TRY(run_slice(c, s));
+          TSVD_TRY(plain_slice_step(c, p, w, tau, k));
         }
         const double r_next = std::fmin(c->opts.mu * r, c->opts.rho_max);
         TubeArgs t = tube_args(p, w, TUBE_RPCA);

@@ -112,6 +112,18 @@ struct SliceArgs {
   int wout_conj = 0;
   float* sigout = nullptr;
   int64_t sig_stride = 0;
+  // V form only (nullable): the accumulated rotations start from vin instead of the identity
+  // and end in vout (may equal vin); slice s at v*[s * vstride], nv x nv complex, column-major
+  // (column g belongs to vector g).  With vin = V0 the input slice must be B V0 (columns
+  // orientation) or V0^T B (rows orientation): the SVT is then D_tau(B) exactly.
+  const float2* vin = nullptr;
+  float2* vout = nullptr;
+  int64_t vstride = 0;
+  // Nullable: the original slices B (same layout as ahat).  When set, the rebuild is the
+  // U form over these slices even while V is accumulated, so a pre-rotated input (vin) or a
+  // V that is only unitary to rounding does not enter D_tau(B): the kept u_i span range(W)
+  // and u_i^H B is taken from B itself.
+  const float2* brb = nullptr;
 };
 
 // Returns cudaErrorInvalidValue when a slice does not fit the kernel's shared memory.

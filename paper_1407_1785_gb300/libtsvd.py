@@ -32,6 +32,7 @@ EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_la
                     "tsvt", "tnn_complete", "trpca", "tsvd_solve_batched", "tsvt_static",
                     "tsvd_cgemm")
 OP_N, OP_T, OP_C = 0, 1, 2
+WARM_OFF, WARM_ON, WARM_AUTO = 0, 1, 2
 PROBLEM_COMPLETE, PROBLEM_RPCA = 1, 2
 
 
@@ -51,7 +52,8 @@ class Opts(ctypes.Structure):
                 ("accumulate_v", ctypes.c_int), ("lanes_per_pair", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p),
                 ("use_graphs", ctypes.c_int), ("rsvt_oversample", ctypes.c_int),
-                ("rsvt_kmax", ctypes.c_int), ("rsvt_power", ctypes.c_int)]
+                ("rsvt_kmax", ctypes.c_int), ("rsvt_power", ctypes.c_int),
+                ("warm_start", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

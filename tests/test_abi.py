@@ -50,6 +50,7 @@ def test_default_opts():
     assert o.max_sweeps == 40
     assert o.jacobi_tol == pytest.approx(1e-6)
     assert (o.rsvt_oversample, o.rsvt_kmax, o.rsvt_power) == (10, 0, 2)
+    assert o.warm_start == libtsvd.WARM_AUTO
 
 
 def test_null_arguments_are_rejected_without_touching_a_device():
@@ -70,7 +71,8 @@ def test_bad_options_rejected():
     h = ctypes.c_void_p()
     assert L.tsvd_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == libtsvd.TSVD_EINVAL
     for field, bad in (("precision", 5), ("precision", -1), ("rsvt_oversample", -1),
-                       ("rsvt_oversample", 65), ("rsvt_kmax", -3), ("rsvt_power", 9)):
+                       ("rsvt_oversample", 65), ("rsvt_kmax", -3), ("rsvt_power", 9),
+                       ("warm_start", 3), ("warm_start", -1)):
         o = libtsvd.default_opts()
         setattr(o, field, bad)
         assert L.tsvd_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == libtsvd.TSVD_EINVAL

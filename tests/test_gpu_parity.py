@@ -144,7 +144,8 @@ def test_tsvt_parity_cluster_split(shape, ctas):
 
 
 @pytest.mark.parametrize("shape,ctas", [((40, 50, 5), 1), ((130, 150, 4), 4),
-                                        ((17, 33, 3, 4), 2), ((144, 176, 6), 2)])
+                                        ((17, 33, 3, 4), 2), ((144, 176, 6), 2),
+                                        ((260, 270, 3), 8)])
 def test_tsvt_parity_accumulated_v(shape, ctas):
     """The V-form rebuild (V accumulated during the sweeps)."""
     from paper_1407_1785_gb300 import libtsvd
@@ -177,7 +178,8 @@ def test_autotune_cache_round_trip(tmp_path):
             outs.append(host(x, Mobs.shape))
             launches.append(st["launches"])
     lines = open(cache.decode()).read().split()
-    assert len(lines) == 8 and lines[1:5] == ["70", "90", "5", "0"]
+    # key: n1, n2, distinct slices, V form (on: the warm-started ADMM solve tunes that plan)
+    assert len(lines) == 8 and lines[1:5] == ["70", "90", "5", "1"]
     assert launches[1] < launches[0]
     assert np.array_equal(outs[0], outs[1])
 
@@ -430,6 +432,46 @@ def test_rpca_4d_parity(gpu_ctx):
     Lo, So = oracle.trpca(M.astype(np.float64), lam, 30)
     Lg, Sg, _ = gpu_rpca(gpu_ctx, M, lam, 30)
     assert relerr(Lg, Lo) <= ADMM_TOL
+
+
+@pytest.mark.parametrize("shape,ctas", [((40, 30, 9), 0), ((30, 44, 8), 0), ((70, 60, 6), 4),
+                                        ((60, 72, 5), 8)])
+@pytest.mark.parametrize("kind", ["complete", "rpca"])
+def test_warm_start_matches_oracle_and_cold(shape, ctas, kind):
+    """Warm-started slice SVDs (pre-rotation to B V or V^T B, cold restarts every 16
+    iterations, U-form rebuild from B, one CTA or a cluster per slice) reach the oracle's
+    iterates like the cold solve."""
+    from paper_1407_1785_gb300 import libtsvd
+    torch = _torch()
+    n1, n2, n3 = shape
+    if kind == "complete":
+        X, om = synth.workload_lowrank_completion(seed=6, n1=n1, n2=n2, n3=n3, rank=3, p=0.4)
+        M = (X * om).astype(np.float32)
+        Ro, _ = oracle.tnn_complete(M.astype(np.float64), om, 40)
+    else:
+        X = synth.lowrank_tensor(n1, n2, n3, 2, seed=6)
+        S0, _ = synth.sparse_corruption(X.shape, 0.1, seed=6)
+        M = (X + S0).astype(np.float32)
+        lam = 1.0 / math.sqrt(max(n1, n2) * n3)
+        Ro, _ = oracle.trpca(M.astype(np.float64), lam, 40)
+    out = {}
+    for warm in (libtsvd.WARM_OFF, libtsvd.WARM_ON):
+        ctx = libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
+                              warm_start=warm, ctas_per_slice=ctas)
+        try:
+            if kind == "complete":
+                R, _, st = gpu_complete(ctx, M, om, 40, stats=True)
+            else:
+                R, _, st = gpu_rpca(ctx, M, lam, 40, stats=True)
+        finally:
+            ctx.close()
+        out[warm] = (R, st)
+        assert relerr(R, Ro) <= ADMM_TOL, (warm, relerr(R, Ro))
+        assert st["nonconverged"] == 0
+    (Rc, sc), (Rw, sw) = out[libtsvd.WARM_OFF], out[libtsvd.WARM_ON]
+    e_c, e_w = relerr(Rc, X), relerr(Rw, X)
+    assert e_w <= 1.01 * e_c + 1e-5, (e_w, e_c)
+    assert sw["total_sweeps"] < sc["total_sweeps"]
 
 
 # ------------------------------------------------------------------------ error paths
