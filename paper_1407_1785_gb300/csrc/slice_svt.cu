@@ -10,7 +10,7 @@
 //     c = |c| e^{i phi},  zeta = (b - a) / (2|c|),  t = sign(zeta) / (|zeta| + sqrt(1+zeta^2)),
 //     cs = 1/sqrt(1+t^2), sn = cs t,
 //     x <- cs x - sn e^{-i phi} y,   y <- sn e^{i phi} x + cs y.
-// A pair is rotated while |c| > tol sqrt(a b); sweeps stop when a whole sweep rotates
+// A pair is rotated while |c|^2 > tol^2 a b; sweeps stop when a whole sweep rotates
 // nothing (or at max_sweeps).  The converged vectors are W = B V = U diag(sigma).
 //
 // Rebuild.  Two forms:
@@ -156,57 +156,78 @@ __device__ __forceinline__ void group_sum_n(float (&v)[K]) {
 // Rotate NP independent vector pairs (p[i], q[i]) if they are not yet orthogonal; NP = 2
 // interleaves two pairs so that one pair's inner products, shuffles and rotation-parameter
 // chain overlap the other's.  All G lanes of the group call it with the same pairs; pairs
-// with real[i] false are skipped.  nchunk = vector chunks (inner products and rotation),
-// nchunkv = V chunks (rotation only) that follow.  Returns bit 0 set when a rotation was
-// applied and bit 1 set when one of them had |cos| = |x^H y| / (||x|| ||y||) above `big`.
+// with real[i] false are skipped.  A row holds exactly G * CPL vector chunks (zero padded
+// past the vector, so no lane needs a bounds test) and then nchunkv V chunks, a multiple of
+// G.  Returns bit 0 set when a rotation was applied and bit 1 set when one of them had
+// |cos|^2 = |x^H y|^2 / (||x||^2 ||y||^2) above big2.
+//
+// Rotation parameters: the exact rotation of the pair's 2x2 Gram matrix needs t, and a
+// unitary update needs cs^2 + sn^2 = 1.  t only steers convergence, so it is computed with
+// the approximate reciprocal square root and division; cs and sn come from r = sqrt(1 + t^2)
+// as sn = t / r and cs - 1 = -t sn / (1 + r), an identity that holds for any r, so a relative
+// error d in r (or in 1/|x^H y| for the phase) changes cs^2 + sn^2 by only ~1.5 t^2 d: nothing
+// for the small rotations that make up all but the first sweep.
 template <int G, int CPL, int NP>
 __device__ __forceinline__ int jacobi_pairs(float* __restrict__ Wr, float* __restrict__ Wi,
-                                            int rowp, int nchunk, int nchunkv,
-                                            const int (&p)[NP], const int (&q)[NP],
-                                            const bool (&real)[NP], int gl, float tol,
-                                            float big) {
+                                            int rowp, int nchunkv, const int (&p)[NP],
+                                            const int (&q)[NP], const bool (&real)[NP],
+                                            int gl, float tol2, float big2) {
   float4 xr[NP][CPL], xi[NP][CPL], yr[NP][CPL], yi[NP][CPL];
   float2 acc[NP][8];
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
-    const int nch = real[i] ? nchunk : 0;
-    const float4* xr4 = reinterpret_cast<const float4*>(Wr + (size_t)p[i] * rowp);
-    const float4* xi4 = reinterpret_cast<const float4*>(Wi + (size_t)p[i] * rowp);
-    const float4* yr4 = reinterpret_cast<const float4*>(Wr + (size_t)q[i] * rowp);
-    const float4* yi4 = reinterpret_cast<const float4*>(Wi + (size_t)q[i] * rowp);
-#pragma unroll
-    for (int a = 0; a < 8; ++a) acc[i][a] = f2(0.f, 0.f);
+    const float4* xr4 = reinterpret_cast<const float4*>(Wr + p[i] * rowp);
+    const float4* xi4 = reinterpret_cast<const float4*>(Wi + p[i] * rowp);
+    const float4* yr4 = reinterpret_cast<const float4*>(Wr + q[i] * rowp);
+    const float4* yi4 = reinterpret_cast<const float4*>(Wi + q[i] * rowp);
 #pragma unroll
     for (int u = 0; u < CPL; ++u) {
       const int c = gl + G * u;
-      if (c < nch) {
-        xr[i][u] = xr4[c];
-        xi[i][u] = xi4[c];
-        yr[i][u] = yr4[c];
-        yi[i][u] = yi4[c];
-      } else {
-        xr[i][u] = xi[i][u] = yr[i][u] = yi[i][u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
+      xr[i][u] = xr4[c];
+      xi[i][u] = xi4[c];
+      yr[i][u] = yr4[c];
+      yi[i][u] = yi4[c];
     }
   }
 #pragma unroll
-  for (int u = 0; u < CPL; ++u) {
+  for (int i = 0; i < NP; ++i) {
+    float2* A = acc[i];
+    // first chunk initialises the sums
+    A[0] = __fmul2_rn(lo(xr[i][0]), lo(xr[i][0]));   // ||x||^2
+    A[1] = __fmul2_rn(hi(xr[i][0]), hi(xr[i][0]));
+    A[2] = __fmul2_rn(lo(yr[i][0]), lo(yr[i][0]));   // ||y||^2
+    A[3] = __fmul2_rn(hi(yr[i][0]), hi(yr[i][0]));
+    A[4] = __fmul2_rn(lo(xr[i][0]), lo(yr[i][0]));   // Re(x^H y) = xr.yr + xi.yi
+    A[5] = __fmul2_rn(hi(xr[i][0]), hi(yr[i][0]));
+    A[6] = __fmul2_rn(lo(xr[i][0]), lo(yi[i][0]));   // Im(x^H y) = xr.yi - xi.yr
+    A[7] = __fmul2_rn(lo(xi[i][0]), lo(yr[i][0]));
+    A[0] = __ffma2_rn(lo(xi[i][0]), lo(xi[i][0]), A[0]);
+    A[1] = __ffma2_rn(hi(xi[i][0]), hi(xi[i][0]), A[1]);
+    A[2] = __ffma2_rn(lo(yi[i][0]), lo(yi[i][0]), A[2]);
+    A[3] = __ffma2_rn(hi(yi[i][0]), hi(yi[i][0]), A[3]);
+    A[4] = __ffma2_rn(lo(xi[i][0]), lo(yi[i][0]), A[4]);
+    A[5] = __ffma2_rn(hi(xi[i][0]), hi(yi[i][0]), A[5]);
+    A[6] = __ffma2_rn(hi(xr[i][0]), hi(yi[i][0]), A[6]);
+    A[7] = __ffma2_rn(hi(xi[i][0]), hi(yr[i][0]), A[7]);
+  }
+#pragma unroll
+  for (int u = 1; u < CPL; ++u) {
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       float2* A = acc[i];
-      A[0] = __ffma2_rn(lo(xr[i][u]), lo(xr[i][u]), A[0]);   // ||x||^2
+      A[0] = __ffma2_rn(lo(xr[i][u]), lo(xr[i][u]), A[0]);
       A[1] = __ffma2_rn(hi(xr[i][u]), hi(xr[i][u]), A[1]);
       A[0] = __ffma2_rn(lo(xi[i][u]), lo(xi[i][u]), A[0]);
       A[1] = __ffma2_rn(hi(xi[i][u]), hi(xi[i][u]), A[1]);
-      A[2] = __ffma2_rn(lo(yr[i][u]), lo(yr[i][u]), A[2]);   // ||y||^2
+      A[2] = __ffma2_rn(lo(yr[i][u]), lo(yr[i][u]), A[2]);
       A[3] = __ffma2_rn(hi(yr[i][u]), hi(yr[i][u]), A[3]);
       A[2] = __ffma2_rn(lo(yi[i][u]), lo(yi[i][u]), A[2]);
       A[3] = __ffma2_rn(hi(yi[i][u]), hi(yi[i][u]), A[3]);
-      A[4] = __ffma2_rn(lo(xr[i][u]), lo(yr[i][u]), A[4]);   // Re(x^H y) = xr.yr + xi.yi
+      A[4] = __ffma2_rn(lo(xr[i][u]), lo(yr[i][u]), A[4]);
       A[5] = __ffma2_rn(hi(xr[i][u]), hi(yr[i][u]), A[5]);
       A[4] = __ffma2_rn(lo(xi[i][u]), lo(yi[i][u]), A[4]);
       A[5] = __ffma2_rn(hi(xi[i][u]), hi(yi[i][u]), A[5]);
-      A[6] = __ffma2_rn(lo(xr[i][u]), lo(yi[i][u]), A[6]);   // Im(x^H y) = xr.yi - xi.yr
+      A[6] = __ffma2_rn(lo(xr[i][u]), lo(yi[i][u]), A[6]);
       A[6] = __ffma2_rn(hi(xr[i][u]), hi(yi[i][u]), A[6]);
       A[7] = __ffma2_rn(lo(xi[i][u]), lo(yr[i][u]), A[7]);
       A[7] = __ffma2_rn(hi(xi[i][u]), hi(yr[i][u]), A[7]);
@@ -222,47 +243,48 @@ __device__ __forceinline__ int jacobi_pairs(float* __restrict__ Wr, float* __res
     red[4 * i + 3] = (A[6].x + A[6].y) - (A[7].x + A[7].y);
   }
   group_sum_n<G, 4 * NP>(red);
+  const int ncv = nchunkv / G;
   int flags = 0;
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
     const float al = red[4 * i + 0], be = red[4 * i + 1];
     const float cr = red[4 * i + 2], ci = red[4 * i + 3];
-    const float g = sqrtf(cr * cr + ci * ci);
-    const float sab = sqrtf(al) * sqrtf(be);
-    if (!real[i] || !(g > tol * sab)) continue;
-    const float inv_g = 1.f / g;
+    const float c2 = cr * cr + ci * ci;
+    const float ab = al * be;
+    if (!real[i] || !(c2 > tol2 * ab)) continue;
+    // ~ 1 / |x^H y| (the exact form below the normal range, where the approximation is not
+    // defined: only vectors of norm ~1e-14 get there)
+    const float inv_g = c2 >= 1e-30f ? rsqrtf(c2) : 1.f / sqrtf(c2);
     const float zeta = (be - al) * (0.5f * inv_g);
-    float t;
-    if (fabsf(zeta) > 1e18f)
-      t = 0.5f / zeta;
-    else
-      t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+    const float az = fabsf(zeta);
+    const float z1 = fmaf(zeta, zeta, 1.f);                         // inf past |zeta| ~ 1e19
+    const float t0 = __fdividef(1.f, az + z1 * rsqrtf(z1));
+    float t = az > 1e18f ? __fdividef(0.5f, az) : t0;
+    t = zeta >= 0.f ? t : -t;
     if (t == 0.f) continue;
-    // cs = 1/r, sn = t/r with r = sqrt(1 + t^2), and cs - 1 = -t sn / (1 + r) to full
-    // relative precision, all rounded to nearest: the rotation stays unitary to rounding,
-    // so the vector norms do not drift over thousands of rotations
-    const float r = sqrtf(1.f + t * t);
-    const float sn = t / r;
-    const float cm = -(t * sn) / (1.f + r);
+    const float q1 = fmaf(t, t, 1.f);
+    const float rs = rsqrtf(q1);                                    // ~ 1 / r
+    const float r = q1 * rs;
+    const float sn = t * rs;
+    const float cm = __fdividef(-(t * sn), 1.f + r);
     const float kr = sn * (cr * inv_g), ki = sn * (ci * inv_g);     // k = sn e^{i phi}
     const float2 CM = f2(cm, cm), KR = f2(kr, kr), KI = f2(ki, ki), NKR = f2(-kr, -kr),
                  NKI = f2(-ki, -ki);
-    float4* xr4 = reinterpret_cast<float4*>(Wr + (size_t)p[i] * rowp);
-    float4* xi4 = reinterpret_cast<float4*>(Wi + (size_t)p[i] * rowp);
-    float4* yr4 = reinterpret_cast<float4*>(Wr + (size_t)q[i] * rowp);
-    float4* yi4 = reinterpret_cast<float4*>(Wi + (size_t)q[i] * rowp);
+    float4* xr4 = reinterpret_cast<float4*>(Wr + p[i] * rowp);
+    float4* xi4 = reinterpret_cast<float4*>(Wi + p[i] * rowp);
+    float4* yr4 = reinterpret_cast<float4*>(Wr + q[i] * rowp);
+    float4* yi4 = reinterpret_cast<float4*>(Wi + q[i] * rowp);
 #pragma unroll
     for (int u = 0; u < CPL; ++u) {
       const int c = gl + G * u;
-      if (c < nchunk) {
-        rotate4(CM, KR, KI, NKR, NKI, xr[i][u], xi[i][u], yr[i][u], yi[i][u]);
-        xr4[c] = xr[i][u];
-        xi4[c] = xi[i][u];
-        yr4[c] = yr[i][u];
-        yi4[c] = yi[i][u];
-      }
+      rotate4(CM, KR, KI, NKR, NKI, xr[i][u], xi[i][u], yr[i][u], yi[i][u]);
+      xr4[c] = xr[i][u];
+      xi4[c] = xi[i][u];
+      yr4[c] = yr[i][u];
+      yi4[c] = yi[i][u];
     }
-    for (int c = nchunk + gl; c < nchunk + nchunkv; c += G) {
+    for (int u = 0; u < ncv; ++u) {
+      const int c = G * CPL + gl + G * u;
       float4 vxr = xr4[c], vxi = xi4[c], vyr = yr4[c], vyi = yi4[c];
       rotate4(CM, KR, KI, NKR, NKI, vxr, vxi, vyr, vyi);
       xr4[c] = vxr;
@@ -270,7 +292,7 @@ __device__ __forceinline__ int jacobi_pairs(float* __restrict__ Wr, float* __res
       yr4[c] = vyr;
       yi4[c] = vyi;
     }
-    flags |= g > big * sab ? 3 : 1;
+    flags |= c2 > big2 * ab ? 3 : 1;
   }
   return flags;
 }
@@ -416,12 +438,12 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
   const int group = warp * gpw + lane / G;   // group index in the CTA
   const int ngroups = nwarps * gpw;
   const int gl = lane % G;
-  const int nchunk = ld / 4, nchunkv = sh.ldv / 4;
-  const float tol = a.tol;
+  const int nchunkv = sh.ldv / 4;
+  const float tol2 = a.tol * a.tol;
   // Once a sweep's rotations all have |cos| <= big, the later rotations of that sweep move
   // each pair's cosine by at most ~big^2 per rotation touching it (2 nv of them), so after
   // the sweep every cosine is below 2 nv big^2 = tol and the checking sweep is skipped.
-  const float big = sqrtf(tol / (2.f * (float)sh.nv));
+  const float big2 = a.tol / (2.f * (float)sh.nv);
   const int trips = (bs + ngroups - 1) / ngroups;
   const size_t slotf = (size_t)bs * rowp;    // floats of one plane of one block
   int sweeps = 0, converged = 0, par = 0;
@@ -473,8 +495,8 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
           }
           // every lane of the warp takes part in the shuffles when any group has work
           if (!__ballot_sync(0xffffffffu, any_real)) continue;
-          rotated |= jacobi_pairs<G, CPL, NP>(Wr, Wi, rowp, nchunk, nchunkv, p, q, real, gl,
-                                              tol, big);
+          rotated |= jacobi_pairs<G, CPL, NP>(Wr, Wi, rowp, nchunkv, p, q, real, gl, tol2,
+                                              big2);
         }
         __syncthreads();
       }
@@ -829,9 +851,13 @@ bool plan_with_ctas(int n1, int n2, int C, const SliceKnobs& k, SliceShape& sh, 
   sh.len = n1 < n2 ? n2 : n1;
   sh.ld = pitch_for(sh.len);
   sh.vform = k.vform ? 1 : 0;
-  sh.ldv = sh.vform ? pitch_for(sh.nv) : 0;
-  sh.rowp = sh.ld + sh.ldv;
   if (!pick_group(sh.ld, k.lanes, sh.G, sh.cpl)) return false;
+  // rows padded so that the vector part is exactly G * cpl chunks and the V part a multiple
+  // of G chunks: every lane's chunks lie inside the row and the rotation needs no tests
+  sh.ld = 4 * sh.G * sh.cpl;
+  sh.ldv = sh.vform ? 4 * ((pitch_for(sh.nv) / 4 + sh.G - 1) / sh.G * sh.G) : 0;
+  sh.rowp = sh.ld + sh.ldv;
+  if (((sh.rowp / 4) & 1) == 0) sh.rowp += 4;   // pitch / 4 odd
   sh.np = k.ppg == 2 ? 2 : 1;
   if (k.ppg != 0 && k.ppg != 1 && k.ppg != 2) return false;
   if (sh.np == 2 && (sh.G == 4 || sh.cpl > 4)) return false;   // register budget
