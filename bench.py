@@ -76,8 +76,8 @@ WORKLOADS = {
 # DRAM traffic of one jacobi_svt_kernel launch from an ncu capture of the video workload,
 # valid only for the kernel source it was taken on (see profiles/).
 TRAFFIC = {"source": "paper_1407_1785_gb300/csrc/slice_svt.cu",
-           "sha256": "ce69371304759e34c0cd7fbc1ba70d094db82f23c38f12b6f227cdaa2a8d77c4",
-           "bytes_per_launch": 25212928 + 4718080}
+           "sha256": "226612d4792eb8bab8037ed0dc5da1c795f42ee80681dc4111d12bfe660b22a3",
+           "bytes_per_launch": 25221376 + 10836224}
 
 
 def parse_args():
