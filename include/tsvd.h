@@ -227,8 +227,10 @@ typedef struct tsvd_problem {
  * tnn_complete) or tensor RPCA (as trpca) -- for `count` tensors of any shapes, with the
  * context's options (one rho schedule for all).  With a mixed precision each tensor's sketch
  * width is chosen on the device after every iteration (same rule as the single-tensor
- * solvers, widths up to 112), so the whole batch is still captured into one graph.  All pointers must be device memory on the
- * context's device.  Each tensor's iterations form an independent chain of kernels (its own
+ * solvers, widths up to 112), so the whole batch is still captured into one graph.  In the
+ * plain form each tensor follows warm_start as the single-tensor solvers do (TSVD_WARM_AUTO:
+ * the completion tensors warm start, the RPCA tensors do not).  All pointers must be device
+ * memory on the context's device.  Each tensor's iterations form an independent chain of kernels (its own
  * slice-SVT plan); the chains of all tensors are issued on parallel stream branches and, with
  * use_graphs, captured once into one CUDA graph that later calls with the same problems
  * replay, so the tensors overlap on the GPU.  Plans come from the context's autotune cache

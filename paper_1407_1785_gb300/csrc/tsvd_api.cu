@@ -199,8 +199,11 @@ int slice_weight(const TubeGeom& g, int kf, int kh) {
 
 int vform_of(const tsvd_ctx* c) { return (c->opts.accumulate_v || c->vform_now) ? 1 : 0; }
 
+std::array<int, 4> plan_key(const Problem& p, int nslices, int vform) {
+  return {(int)p.n1, (int)p.n2, nslices, vform};
+}
 std::array<int, 4> plan_key(tsvd_ctx* c, const Problem& p, int nslices) {
-  return {(int)p.n1, (int)p.n2, nslices, vform_of(c)};
+  return plan_key(p, nslices, vform_of(c));
 }
 
 // Slice-SVT plans the autotuner compares (or the single plan fixed by the options).
@@ -226,10 +229,13 @@ std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslic
 }
 
 // The plan a slice-SVT launch uses: the tuned one when there is one, else the options.
-SliceKnobs planned_knobs(tsvd_ctx* c, const Problem& p, int nslices) {
-  auto it = c->tuned.find(plan_key(c, p, nslices));
+SliceKnobs planned_knobs(tsvd_ctx* c, const Problem& p, int nslices, int vform) {
+  auto it = c->tuned.find(plan_key(p, nslices, vform));
   if (it != c->tuned.end()) return it->second;
-  return {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, vform_of(c)};
+  return {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, vform};
+}
+SliceKnobs planned_knobs(tsvd_ctx* c, const Problem& p, int nslices) {
+  return planned_knobs(c, p, nslices, vform_of(c));
 }
 
 std::string device_name(int dev) {
@@ -725,8 +731,11 @@ bool warm_plan_exists(tsvd_ctx* c, const Problem& p) {
 // from V; every kColdEvery-th iteration starts from B and V = I (bounding the drift of V).
 // The rebuild reads B itself (U form), so neither the FP32 pre-rotation nor a V that is
 // unitary only to rounding reaches D_tau(B); they only change how many sweeps converge.
-tsvd_status plain_slice_step(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau, int it) {
+// `kn` (nullable) overrides the context's plan for the shape (a batched tensor's own plan).
+tsvd_status plain_slice_step(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau, int it,
+                             const SliceKnobs* kn = nullptr) {
   SliceArgs s = slice_args(c, p, w, tau);
+  if (kn) s.knobs = *kn;
   if (w.warm) {
     const int nv = w.nv, n1 = (int)p.n1, n2 = (int)p.n2;
     s.vout = w.vwarm;
@@ -1065,21 +1074,26 @@ struct BatchItem {
   std::vector<float2> twid;
   std::vector<int> slices;
   std::vector<unsigned char> isreal;   // mixed form
+  bool warm = false;                   // plain form with the warm-started Jacobi
 };
 
 // Carves the regions of one tensor from `base` (nullptr: only measure); returns its bytes.
-size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base) {
+size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base, int iters) {
   const TubeGeom& g = it.p.g;
   it.slices.clear();
   for (int kh = 0; kh < g.hh; ++kh)
     for (int kf = 0; kf < g.nf; ++kf)
       if (slice_is_distinct(g, kf, kh)) it.slices.push_back(kf + g.nf * kh);
   it.w.ndistinct = (int)it.slices.size();
-  it.kn = planned_knobs(c, it.p, it.w.ndistinct);
   const size_t spec = (size_t)g.nstore * g.N12 * sizeof(float2);
   const size_t real = (size_t)it.p.N * sizeof(float);
   const bool complete = it.src->kind == TSVD_PROBLEM_COMPLETE;
   const bool mixed = mixed_precision(c);
+  // the warm start as in the single-tensor solves (TSVD_WARM_AUTO: completion only)
+  const int ws = c->opts.warm_start;
+  it.warm = !mixed && iters >= 2 && ws != TSVD_WARM_OFF && (complete || ws == TSVD_WARM_ON) &&
+            warm_plan_exists(c, it.p);
+  it.kn = planned_knobs(c, it.p, it.w.ndistinct, it.warm ? 1 : vform_of(c));
   const size_t jbytes =
       mixed ? 0 : jacobi_svt_scratch_bytes((int)it.p.n1, (int)it.p.n2, it.w.ndistinct, it.kn);
   size_t total = 0;
@@ -1098,6 +1112,13 @@ size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base) {
   it.w.acc = reinterpret_cast<SweepAccum*>(take(sizeof(SweepAccum)));
   it.w.jscratch = jbytes ? take(jbytes) : nullptr;
   it.w.jscratch_bytes = jbytes;
+  it.w.warm = it.warm;
+  it.w.nv = (int)std::min(it.p.n1, it.p.n2);
+  if (it.warm) {
+    it.w.abar = reinterpret_cast<float2*>(take(spec));
+    it.w.vwarm = reinterpret_cast<float2*>(
+        take((size_t)g.nstore * it.w.nv * it.w.nv * sizeof(float2)));
+  }
   it.w.rsvt = mixed;
   if (mixed) {
     // mixed form with the device-chosen width (graph-capturable): widths up to the Gram path's
@@ -1171,9 +1192,7 @@ tsvd_status enqueue_item(tsvd_ctx* c, const BatchItem& it, int iters) {
       ++c->slice_launches;
       TSVD_TRY(record_event(c, 0));
     } else {
-      SliceArgs s = slice_args(c, p, w, tau);
-      s.knobs = it.kn;
-      TSVD_TRY(run_slice(c, s));
+      TSVD_TRY(plain_slice_step(c, p, w, tau, k, &it.kn));
     }
     const double r_next = std::fmin(c->opts.mu * r, c->opts.rho_max);
     if (q.kind == TSVD_PROBLEM_COMPLETE) {
@@ -1597,7 +1616,7 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
   std::vector<size_t> offs((size_t)count);
   for (int i = 0; i < count; ++i) {
     offs[(size_t)i] = total;
-    total += carve_item(c, items[(size_t)i], nullptr);
+    total += carve_item(c, items[(size_t)i], nullptr, iters);
   }
   const size_t bad_off = total;
   total += align_up((size_t)count * sizeof(int));
@@ -1623,7 +1642,7 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
   TSVD_CUDA(c, cudaMemsetAsync(bad, 0, (size_t)count * sizeof(int), c->stream));
   for (int i = 0; i < count; ++i) {
     BatchItem& it = items[(size_t)i];
-    carve_item(c, it, c->ws + offs[(size_t)i]);
+    carve_item(c, it, c->ws + offs[(size_t)i], iters);
     const TubeGeom& g = it.p.g;
     it.twid.resize((size_t)(g.nh + g.nf));
     for (int pass = 0; pass < 2; ++pass) {   // same FP64 tables as the single-tensor calls
@@ -1711,7 +1730,7 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
                               q.order == 4 ? q.dims[3] : 1, (int64_t)(intptr_t)q.M,
                               (int64_t)(intptr_t)q.omega, (int64_t)(intptr_t)q.out0,
                               (int64_t)(intptr_t)q.out1, lbits, it.kn.ctas, it.kn.lanes,
-                              it.kn.ppg, it.kn.vform};
+                              it.kn.ppg, it.kn.vform, it.warm ? 1 : 0};
       key.insert(key.end(), std::begin(vals), std::end(vals));
     }
     auto body = [&]() -> tsvd_status {

@@ -211,11 +211,14 @@ def test_graph_replay_matches_direct_launches(kind):
         assert np.array_equal(x, outs[0][0]) and np.array_equal(y, outs[0][1])
 
 
-def test_batched_uneven_problems_match_oracle():
+@pytest.mark.parametrize("warm", ["off", "auto", "on"])
+def test_batched_uneven_problems_match_oracle(warm):
     """A batch of uneven tensors (completion and RPCA, 3-way and 4-way) in one call: every
-    tensor matches the oracle's solve; a second call replays the captured batch graph and
-    gives the same bits."""
+    tensor matches the oracle's solve, with the warm-started Jacobi off, on for the
+    completions only (the default) or on for all; a second call replays the captured batch
+    graph and gives the same bits."""
     from paper_1407_1785_gb300 import libtsvd
+    warm_start = {"off": libtsvd.WARM_OFF, "auto": libtsvd.WARM_AUTO, "on": libtsvd.WARM_ON}[warm]
     torch = _torch()
     specs = [("complete", (30, 41, 8), 3, 0.4), ("rpca", (52, 36, 6), 2, 0.1),
              ("complete", (64, 20, 11), 4, 0.5), ("rpca", (20, 70, 9), 2, 0.08),
@@ -248,7 +251,8 @@ def test_batched_uneven_problems_match_oracle():
         q["out1"] = torch.empty_like(q["M"])
         probs.append(q)
         keep.append(M)
-    with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream) as ctx:
+    with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
+                         warm_start=warm_start) as ctx:
         first = None
         for call in range(2):
             st = ctx.solve_batched(probs, iters, stats=True)
