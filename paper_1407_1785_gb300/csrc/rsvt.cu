@@ -363,37 +363,42 @@ __global__ void __launch_bounds__(1024) eig_svt_kernel(float2* G, float2* T, flo
     }
   const int kp = k + (k & 1);
   const int npair = kp / 2;
-  const float big = sqrtf(tol / (2.f * (float)k));
+  const float tol2 = tol * tol;
+  const float big2 = tol / (2.f * (float)k);
   int sweeps = 0, converged = 0;
   __syncthreads();
   for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
     if (tid == 0) s_flags = 0;
     __syncthreads();
     for (int r = 0; r < kp - 1; ++r) {
-      // rotation parameters, one thread per pair
+      // rotation parameters, one thread per pair (t, 1/r and the phase with the approximate
+      // reciprocal square root and division: cs - 1 = -t sn / (1 + r) keeps cs^2 + sn^2 = 1
+      // up to ~1.5 t^2 times their relative error)
       if (tid < npair) {
         int p, q;
         circle_pair(r, tid, kp, p, q);
         float4 ro = make_float4(0.f, 0.f, 0.f, 0.f);
         if (p < k && q < k) {
-          const float al = H[p + (size_t)p * ldh].x, be = H[q + (size_t)q * ldh].x;
+          const float al = fmaxf(H[p + (size_t)p * ldh].x, 0.f);
+          const float be = fmaxf(H[q + (size_t)q * ldh].x, 0.f);
           const float2 c = H[p + (size_t)q * ldh];   // H_pq = col_p^H col_q
-          const float g = sqrtf(c.x * c.x + c.y * c.y);
-          const float sab = sqrtf(fmaxf(al, 0.f)) * sqrtf(fmaxf(be, 0.f));
-          if (g > tol * sab) {
-            const float inv_g = 1.f / g;
+          const float c2 = c.x * c.x + c.y * c.y;
+          const float ab = al * be;
+          if (c2 > tol2 * ab) {
+            const float inv_g = c2 >= 1e-30f ? rsqrtf(c2) : 1.f / sqrtf(c2);
             const float zeta = (be - al) * (0.5f * inv_g);
-            float t;
-            if (fabsf(zeta) > 1e18f)
-              t = 0.5f / zeta;
-            else
-              t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+            const float az = fabsf(zeta);
+            const float z1 = fmaf(zeta, zeta, 1.f);
+            const float t0 = __fdividef(1.f, az + z1 * rsqrtf(z1));
+            float t = az > 1e18f ? __fdividef(0.5f, az) : t0;
+            t = zeta >= 0.f ? t : -t;
             if (t != 0.f) {
-              const float rr = sqrtf(1.f + t * t);
-              const float sn = t / rr;
-              const float cm = -(t * sn) / (1.f + rr);
+              const float q1 = fmaf(t, t, 1.f);
+              const float rs = rsqrtf(q1);
+              const float sn = t * rs;
+              const float cm = __fdividef(-(t * sn), 1.f + q1 * rs);
               ro = make_float4(cm, sn * (c.x * inv_g), sn * (c.y * inv_g), 1.f);
-              atomicOr(&s_flags, g > big * sab ? 3 : 1);
+              atomicOr(&s_flags, c2 > big2 * ab ? 3 : 1);
             }
           }
         }
@@ -402,12 +407,13 @@ __global__ void __launch_bounds__(1024) eig_svt_kernel(float2* G, float2* T, flo
       }
       __syncthreads();
       // columns: [x, y] <- [x + cm x - conj(kk) y, y + cm y + kk x] on H and W; a warp per
-      // pair, a lane per row
+      // pair, a lane per row; packed FP32x2: (re, im) of an entry in one register pair
       for (int i = warp; i < npair; i += nwarps) {
         const float4 ro = rot[i];
         if (ro.w == 0.f) continue;
         const int2 pq = prs[i];
-        const float cm = ro.x, kr = ro.y, ki = ro.z;
+        const float2 CM = make_float2(ro.x, ro.x), KR = make_float2(ro.y, ro.y),
+                     NKR = make_float2(-ro.y, -ro.y), KI = make_float2(-ro.z, ro.z);
         for (int m = lane; m < k; m += 32) {
 #pragma unroll
           for (int mat = 0; mat < 2; ++mat) {
@@ -415,11 +421,9 @@ __global__ void __launch_bounds__(1024) eig_svt_kernel(float2* G, float2* T, flo
             float2& x = X[m + (size_t)pq.x * ldh];
             float2& y = X[m + (size_t)pq.y * ldh];
             const float2 xv = x, yv = y;
-            // conj(kk) y = (kr yr + ki yi, kr yi - ki yr);  kk x = (kr xr - ki xi, kr xi + ki xr)
-            x = make_float2(xv.x + cm * xv.x - (kr * yv.x + ki * yv.y),
-                            xv.y + cm * xv.y - (kr * yv.y - ki * yv.x));
-            y = make_float2(yv.x + cm * yv.x + (kr * xv.x - ki * xv.y),
-                            yv.y + cm * yv.y + (kr * xv.y + ki * xv.x));
+            // -conj(kk) y = (-kr yr - ki yi, -kr yi + ki yr);  kk x = (kr xr - ki xi, kr xi + ki xr)
+            x = __ffma2_rn(KI, make_float2(yv.y, yv.x), __ffma2_rn(NKR, yv, __ffma2_rn(CM, xv, xv)));
+            y = __ffma2_rn(KI, make_float2(xv.y, xv.x), __ffma2_rn(KR, xv, __ffma2_rn(CM, yv, yv)));
           }
         }
       }
@@ -429,15 +433,15 @@ __global__ void __launch_bounds__(1024) eig_svt_kernel(float2* G, float2* T, flo
         const float4 ro = rot[i];
         if (ro.w == 0.f) continue;
         const int2 pq = prs[i];
-        const float cm = ro.x, kr = ro.y, ki = ro.z;
+        const float2 CM = make_float2(ro.x, ro.x), KR = make_float2(ro.y, ro.y),
+                     NKR = make_float2(-ro.y, -ro.y), KI = make_float2(ro.z, -ro.z);
         for (int m = lane; m < k; m += 32) {
           float2& x = H[pq.x + (size_t)m * ldh];
           float2& y = H[pq.y + (size_t)m * ldh];
           const float2 xv = x, yv = y;
-          x = make_float2(xv.x + cm * xv.x - (kr * yv.x - ki * yv.y),
-                          xv.y + cm * xv.y - (kr * yv.y + ki * yv.x));
-          y = make_float2(yv.x + cm * yv.x + (kr * xv.x + ki * xv.y),
-                          yv.y + cm * yv.y + (kr * xv.y - ki * xv.x));
+          // -kk y = (-kr yr + ki yi, -kr yi - ki yr);  conj(kk) x = (kr xr + ki xi, kr xi - ki xr)
+          x = __ffma2_rn(KI, make_float2(yv.y, yv.x), __ffma2_rn(NKR, yv, __ffma2_rn(CM, xv, xv)));
+          y = __ffma2_rn(KI, make_float2(xv.y, xv.x), __ffma2_rn(KR, xv, __ffma2_rn(CM, yv, yv)));
         }
       }
       __syncthreads();
