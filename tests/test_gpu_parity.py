@@ -90,7 +90,9 @@ def gap_threshold(allsv, q):
 
 @pytest.mark.parametrize("shape", [(32, 32, 16), (33, 17, 7), (17, 33, 8), (40, 24, 1),
                                    (5, 64, 2), (1, 9, 5), (9, 1, 4), (64, 48, 13), (3, 130, 6),
-                                   (150, 20, 9), (144, 176, 4), (200, 190, 3)])
+                                   (150, 20, 9), (144, 176, 4), (200, 190, 3),
+                                   # long tubes: tube-tile row groups of 2, 4 and 8 rows, padding
+                                   (5, 4, 33), (3, 4, 64), (8, 6, 100), (6, 5, 130), (4, 3, 255)])
 def test_tsvt_parity_3d(gpu_ctx, shape):
     Y = synth.normal(11, 0, int(np.prod(shape))).reshape(shape, order="F")
     sv = slice_singular_values(Y.astype(np.float32))
@@ -103,7 +105,7 @@ def test_tsvt_parity_3d(gpu_ctx, shape):
 
 
 @pytest.mark.parametrize("shape", [(9, 7, 3, 6), (16, 12, 3, 5), (8, 8, 4, 4), (6, 10, 5, 1),
-                                   (7, 5, 1, 6)])
+                                   (7, 5, 1, 6), (4, 3, 5, 40), (3, 3, 2, 130)])
 def test_tsvt_parity_4d(gpu_ctx, shape):
     Y = synth.normal(12, 0, int(np.prod(shape))).reshape(shape, order="F")
     sv = slice_singular_values(Y.astype(np.float32))
