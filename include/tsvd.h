@@ -94,7 +94,7 @@ typedef struct tsvd_opts {
   int accumulate_v;   /* 1: also rotate V during the Jacobi sweeps and rebuild each slice as
                          W diag((s - tau)/s) V^H instead of U diag((s - tau)/s) U^H A;
                          default 0 */
-  int lanes_per_pair; /* lanes that share one vector pair: 4, 8 or 16; 0 (default) = chosen */
+  int lanes_per_pair; /* lanes that share one vector pair: 4, 8, 16 or 32; 0 (default) = chosen */
   int autotune;       /* 1 (default): the first slice-SVT launch of each new slice shape in a
                          context times the valid (ctas_per_slice, lanes_per_pair) plans on the
                          real input (sweeps capped at 4) and keeps the fastest; choices fixed

@@ -861,6 +861,7 @@ bool plan_with_ctas(int n1, int n2, int C, const SliceKnobs& k, SliceShape& sh, 
   sh.np = k.ppg == 2 ? 2 : 1;
   if (k.ppg != 0 && k.ppg != 1 && k.ppg != 2) return false;
   if (sh.np == 2 && (sh.G == 4 || sh.cpl > 4)) return false;   // register budget
+  if (sh.G == 32 && (sh.np == 2 || sh.cpl > 4)) return false;   // no such kernel instances
   sh.C = C;
   sh.nb = 2 * C;
   sh.bs = (sh.nv + sh.nb - 1) / sh.nb;
@@ -996,6 +997,7 @@ cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st) {
   TSVD_CASE(8, 3, 1) TSVD_CASE(8, 4, 1) TSVD_CASE(8, 6, 1) TSVD_CASE(8, 8, 1)
   TSVD_CASE(16, 1, 1) TSVD_CASE(16, 2, 1) TSVD_CASE(16, 3, 1) TSVD_CASE(16, 4, 1)
   TSVD_CASE(16, 6, 1) TSVD_CASE(16, 8, 1)
+  TSVD_CASE(32, 1, 1) TSVD_CASE(32, 2, 1) TSVD_CASE(32, 3, 1) TSVD_CASE(32, 4, 1)
   TSVD_CASE(8, 1, 2) TSVD_CASE(8, 2, 2) TSVD_CASE(8, 3, 2) TSVD_CASE(8, 4, 2)
   TSVD_CASE(16, 1, 2) TSVD_CASE(16, 2, 2) TSVD_CASE(16, 3, 2) TSVD_CASE(16, 4, 2)
 #undef TSVD_CASE

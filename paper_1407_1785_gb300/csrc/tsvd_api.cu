@@ -212,7 +212,7 @@ std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslic
   std::vector<SliceKnobs> out;
   if (c->opts.autotune) {
     const int ctas[4] = {1, 2, 4, 8};
-    const int lanes[3] = {4, 8, 16};
+    const int lanes[4] = {4, 8, 16, 32};
     for (int C : ctas) {
       if (base.ctas && C != base.ctas) continue;
       for (int L : lanes) {
@@ -620,8 +620,8 @@ tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
   if (o.accumulate_v != 0 && o.accumulate_v != 1)
     return fail(c, TSVD_EINVAL, "accumulate_v must be 0 or 1");
   if (o.lanes_per_pair != 0 && o.lanes_per_pair != 4 && o.lanes_per_pair != 8 &&
-      o.lanes_per_pair != 16)
-    return fail(c, TSVD_EINVAL, "lanes_per_pair must be 0, 4, 8 or 16");
+      o.lanes_per_pair != 16 && o.lanes_per_pair != 32)
+    return fail(c, TSVD_EINVAL, "lanes_per_pair must be 0, 4, 8, 16 or 32");
   if (o.autotune != 0 && o.autotune != 1) return fail(c, TSVD_EINVAL, "autotune must be 0 or 1");
   if (o.use_graphs != 0 && o.use_graphs != 1)
     return fail(c, TSVD_EINVAL, "use_graphs must be 0 or 1");
