@@ -118,7 +118,7 @@ typedef struct tsvd_opts {
   int warm_start;     /* plain form, tnn_complete / trpca: TSVD_WARM_ON starts each slice's
                          Jacobi SVD from the previous iteration's right singular vectors V
                          (the slice is pre-rotated to B V and the rotations accumulate into V,
-                         the V form), with a cold start every 16 iterations; the rebuild
+                         the V form), with a cold start every 64 iterations; the rebuild
                          still projects B itself (U form), so the result is the same SVT,
                          reached in fewer sweeps.  TSVD_WARM_OFF: every SVD starts from B.
                          TSVD_WARM_AUTO (default): on for tnn_complete, off for trpca, whose

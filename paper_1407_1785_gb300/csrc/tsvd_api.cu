@@ -717,7 +717,7 @@ tsvd_status run_slice(tsvd_ctx* c, const SliceArgs& a) {
 }
 
 // ---- plain form with warm start
-constexpr int kColdEvery = 16;   // iterations between cold starts of the warm-started Jacobi
+constexpr int kColdEvery = 64;   // iterations between cold starts of the warm-started Jacobi
 
 // Whether the V form (needed by the warm start) has a plan for this slice shape.
 bool warm_plan_exists(tsvd_ctx* c, const Problem& p) {
