@@ -105,13 +105,16 @@ struct SliceShape {
   int C;      // CTAs per slice (cluster size)
   int nb;     // vector blocks = 2C
   int bs;     // vectors per block
+  int kcap;   // kept vectors per rebuild group: 2 bs, or as many rows of ld floats as the
+              // 2 bs rows of rowp floats hold (a cluster's U-form rebuild imports those)
   size_t xbuf_floats;   // exchange buffer per slice (floats)
 };
 
 __host__ __device__ inline size_t slice_smem_bytes(const SliceShape& sh) {
   const size_t nl = 2 * (size_t)sh.bs;   // vectors held by one CTA
+  const size_t kc = (size_t)sh.kcap;
   return 2 * nl * sh.rowp * sizeof(float) + (size_t)sh.len * sh.nc * sizeof(float2) +
-         nl * sh.nc * sizeof(float2) + nl * (2 * sizeof(float) + sizeof(int));
+         kc * sh.nc * sizeof(float2) + nl * sizeof(float) + kc * (sizeof(float) + sizeof(int));
 }
 
 // x' = x + (cs-1) x - conj(k) y ;  y' = y + (cs-1) y + k x on two entries of each plane
@@ -390,8 +393,16 @@ __device__ __forceinline__ size_t b_index(const SliceShape& sh, int n1, int p, i
   return sh.rows ? (size_t)c + (size_t)n1 * p : (size_t)p + (size_t)n1 * c;
 }
 
+// Register budget of a thread: the register file over the largest CTA for a chunk count
+// (the launch trims the CTA when the allocation granularity leaves fewer threads).
+__host__ __device__ constexpr int max_regs_for(int chunks) {
+  return (65536 / (max_warps_for(chunks) * 32)) / 8 * 8 > 255
+             ? 255
+             : (65536 / (max_warps_for(chunks) * 32)) / 8 * 8;
+}
+
 template <int G, int CPL, int NP>
-__global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
+__global__ void __maxnreg__(max_regs_for(CPL * NP))
     jacobi_svt_kernel(SliceArgs a, SliceShape sh) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int len = sh.len, ld = sh.ld, rowp = sh.rowp, nc = sh.nc, bs = sh.bs, nb = sh.nb;
@@ -401,9 +412,9 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
   float* Wi = Wr + (size_t)nl * rowp;
   float2* Bc = reinterpret_cast<float2*>(Wi + (size_t)nl * rowp);
   float2* Cc = Bc + (size_t)len * nc;
-  float* sig = reinterpret_cast<float*>(Cc + (size_t)nl * nc);
+  float* sig = reinterpret_cast<float*>(Cc + (size_t)sh.kcap * nc);
   float* dsc = sig + nl;
-  int* keep = reinterpret_cast<int*>(dsc + nl);
+  int* keep = reinterpret_cast<int*>(dsc + sh.kcap);
   __shared__ int s_flag[2];
   __shared__ int s_rank;
   __shared__ double s_nuc;
@@ -666,16 +677,20 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
       Z[b_index(sh, n1, p, col)] = make_float2(0.f, 0.f);
     }
   }
-  for (int g0 = 0; g0 < rank_all; g0 += nl) {
-    const int rank = C > 1 ? min(nl, rank_all - g0) : rank_loc;
+  // kept rows in shared memory: the local rows (pitch rowp) with one CTA; imported rows with a
+  // cluster, at pitch ld in the U form (only the vector part is read), kcap of them per group
+  const int kpit = (C > 1 && uform) ? ld : rowp;
+  const int gcap = (C > 1 && uform) ? sh.kcap : nl;
+  for (int g0 = 0; g0 < rank_all; g0 += gcap) {
+    const int rank = C > 1 ? min(gcap, rank_all - g0) : rank_loc;
     if (C > 1) {
       // import kept vectors g0 .. g0 + rank - 1 into local slots 0 .. rank - 1
       __syncthreads();
       for (int k = warp; k < rank; k += nwarps) {
         const float* sr = xbuf + (size_t)2 * (g0 + k) * rowp;
         for (int e = lane * 4; e < xw; e += 128) {
-          *reinterpret_cast<float4*>(Wr + (size_t)k * rowp + e) = *reinterpret_cast<const float4*>(sr + e);
-          *reinterpret_cast<float4*>(Wi + (size_t)k * rowp + e) =
+          *reinterpret_cast<float4*>(Wr + (size_t)k * kpit + e) = *reinterpret_cast<const float4*>(sr + e);
+          *reinterpret_cast<float4*>(Wi + (size_t)k * kpit + e) =
               *reinterpret_cast<const float4*>(sr + rowp + e);
         }
         if (lane == 0) {
@@ -695,7 +710,7 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
           const int k = idx / ncur, cc = idx % ncur;
           const int v = keep[k];
           const float d = dsc[v];
-          const size_t o = (size_t)v * rowp + ld + c0 + cc;
+          const size_t o = (size_t)v * kpit + ld + c0 + cc;
           Cc[(size_t)k * nc + cc] = make_float2(d * Wr[o], -d * Wi[o]);
         }
         __syncthreads();
@@ -713,41 +728,43 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
           Bc[p + (size_t)len * cc] = Ab[b_index(sh, n1, p, c0 + cc)];
         }
         __syncthreads();
-        // C(k, cc) = d_k u_k^H B(:, c0+cc): one warp per kept vector, its lanes striding
-        // over the entries (consecutive banks), then a butterfly sum over the warp
-        for (int k = warp; k < rank; k += nwarps) {
-          const int v = keep[k];
-          const float* ur = Wr + (size_t)v * rowp;
-          const float* ui = Wi + (size_t)v * rowp;
-          float accr[kNC], acci[kNC];
+        // C(k, cc) = d_k u_k^H B(:, c0+cc): one warp per kept vector, its lanes striding over
+        // the entries (consecutive banks), then a butterfly sum over the warp
+        {
+          for (int k = warp; k < rank; k += nwarps) {
+            const int v = keep[k];
+            const float* ur = Wr + (size_t)v * kpit;
+            const float* ui = Wi + (size_t)v * kpit;
+            float accr[kNC], acci[kNC];
 #pragma unroll
-          for (int cc = 0; cc < kNC; ++cc) accr[cc] = acci[cc] = 0.f;
-          for (int p = lane; p < len; p += 32) {
-            const float xr = ur[p], xi = ui[p];
+            for (int cc = 0; cc < kNC; ++cc) accr[cc] = acci[cc] = 0.f;
+            for (int p = lane; p < len; p += 32) {
+              const float xr = ur[p], xi = ui[p];
 #pragma unroll
-            for (int cc = 0; cc < kNC; ++cc) {
-              if (cc < ncur) {
-                const float2 b = Bc[p + (size_t)len * cc];
-                accr[cc] += xr * b.x + xi * b.y;
-                acci[cc] += xr * b.y - xi * b.x;
+              for (int cc = 0; cc < kNC; ++cc) {
+                if (cc < ncur) {
+                  const float2 b = Bc[p + (size_t)len * cc];
+                  accr[cc] += xr * b.x + xi * b.y;
+                  acci[cc] += xr * b.y - xi * b.x;
+                }
               }
             }
-          }
 #pragma unroll
-          for (int cc = 0; cc < kNC; ++cc) {
-            accr[cc] = group_sum<32>(accr[cc]);
-            acci[cc] = group_sum<32>(acci[cc]);
-          }
-          const float d = dsc[v];
-          if (lane < ncur) {
-            float cr = 0.f, ci = 0.f;
+            for (int cc = 0; cc < kNC; ++cc) {
+              accr[cc] = group_sum<32>(accr[cc]);
+              acci[cc] = group_sum<32>(acci[cc]);
+            }
+            const float d = dsc[v];
+            if (lane < ncur) {
+              float cr = 0.f, ci = 0.f;
 #pragma unroll
-            for (int cc = 0; cc < kNC; ++cc)
-              if (cc == lane) {
-                cr = accr[cc];
-                ci = acci[cc];
-              }
-            Cc[(size_t)k * nc + lane] = make_float2(d * cr, d * ci);
+              for (int cc = 0; cc < kNC; ++cc)
+                if (cc == lane) {
+                  cr = accr[cc];
+                  ci = acci[cc];
+                }
+              Cc[(size_t)k * nc + lane] = make_float2(d * cr, d * ci);
+            }
           }
         }
         __syncthreads();
@@ -759,7 +776,7 @@ __global__ void __launch_bounds__(max_warps_for(CPL * NP) * 32)
         for (int cc = 0; cc < kNC; ++cc) accr[cc] = acci[cc] = 0.f;
         for (int k = 0; k < rank; ++k) {
           const int v = keep[k];
-          const float xr = Wr[(size_t)v * rowp + p], xi = Wi[(size_t)v * rowp + p];
+          const float xr = Wr[(size_t)v * kpit + p], xi = Wi[(size_t)v * kpit + p];
 #pragma unroll
           for (int cc = 0; cc < kNC; ++cc) {
             if (cc < ncur) {
@@ -865,6 +882,7 @@ bool plan_with_ctas(int n1, int n2, int C, const SliceKnobs& k, SliceShape& sh, 
   sh.C = C;
   sh.nb = 2 * C;
   sh.bs = (sh.nv + sh.nb - 1) / sh.nb;
+  sh.kcap = C > 1 ? 2 * sh.bs * sh.rowp / sh.ld : 2 * sh.bs;
   sh.xbuf_floats = C > 1 ? (size_t)2 * sh.nb * 2 * sh.bs * sh.rowp : 0;
   for (int nc = kNC; nc >= 1; nc >>= 1) {
     sh.nc = nc;
@@ -925,6 +943,13 @@ cudaError_t launch_gc(const SliceArgs& a, const SliceShape& sh, size_t smem, int
   cudaError_t e = cudaFuncSetAttribute(jacobi_svt_kernel<G, CPL, NP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // the register budget can allow fewer threads than the warp cap: the kernel takes any
+  // multiple of 32 (it runs a local round's pairs in as many trips as its groups need)
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, jacobi_svt_kernel<G, CPL, NP>);
+  if (e != cudaSuccess) return e;
+  if (threads > fa.maxThreadsPerBlock) threads = fa.maxThreadsPerBlock / 32 * 32;
+  if (threads < 32) return cudaErrorInvalidConfiguration;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.nslices * sh.C), 1, 1);
   cfg.blockDim = dim3((unsigned)threads, 1, 1);
