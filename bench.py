@@ -76,8 +76,8 @@ WORKLOADS = {
 # DRAM traffic of one jacobi_svt_kernel launch from an ncu capture of the video workload,
 # valid only for the kernel source it was taken on (see profiles/).
 TRAFFIC = {"source": "paper_1407_1785_gb300/csrc/slice_svt.cu",
-           "sha256": "226612d4792eb8bab8037ed0dc5da1c795f42ee80681dc4111d12bfe660b22a3",
-           "bytes_per_launch": 25221376 + 10836224}
+           "sha256": "2e3a587e2da225351c88ce8d24ec613d3482a24d483e296c172b993ff092b2db",
+           "bytes_per_launch": 21763328 + 9811200}
 
 
 def parse_args():
