@@ -17,7 +17,10 @@
 // 16-byte core matrices, consecutive 8-row groups 128 bytes apart (stride-dimension offset),
 // consecutive K core matrices one plane height apart (leading-dimension offset).  One
 // thread then issues the chunk's MMAs and commits them to the chunk buffer's mbarrier; two
-// chunk buffers alternate so loading chunk c+1 overlaps the MMAs of chunk c.  The epilogue
+// chunk buffers alternate so loading chunk c+1 overlaps the MMAs of chunk c.  With 3XTF32
+// each thread copies its share of the raw complex entries with cp.async into three private
+// slots, two chunks ahead, and converts chunk c from its slot: the global latency overlaps
+// two chunks of conversion and MMA issue instead of sitting in front of each chunk.  The epilogue
 // reads T1..T3 with tcgen05.ld (warp w reads TMEM lanes 32 (w mod 4) .. +31, i.e. its rows of
 // the tile, and half of the columns) and writes C.
 //
@@ -62,7 +65,14 @@ struct Layout {
   static constexpr int PLANE_B = BN * C::BK * C::EB;
   static constexpr int NPLANE = 3 * C::NSPLIT;
   static constexpr int STAGE = NPLANE * (PLANE_A + PLANE_B);
-  static constexpr int SMEM = 2 * STAGE + 64;                // + mbarriers and TMEM address
+  // 3XTF32: raw complex operand chunks copied asynchronously (cp.async) into per-thread slots,
+  // up to two chunks ahead of the one being converted; the other engines' planes leave no
+  // room for them and load through registers
+  static constexpr int RAW_STAGES = ENG == RSVT_GEMM_3XTF32 ? 3 : 0;
+  static constexpr int RAW_A = BM * C::BK * 8;               // bytes of one raw A chunk
+  static constexpr int RAW_B = BN * C::BK * 8;
+  static constexpr int RAW = RAW_STAGES * (RAW_A + RAW_B);
+  static constexpr int SMEM = 2 * STAGE + RAW + 64;          // + mbarriers and TMEM address
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -125,6 +135,20 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if ((it & 255) == 255 && now_ns() - t0 > kWaitNs) return false;
   }
   return false;
+}
+
+// 8-byte asynchronous global -> shared copy; with pred false it writes zeros and reads nothing.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(pred ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -222,6 +246,60 @@ __device__ __forceinline__ void stage_operand(unsigned char* planes, int plane_b
   }
 }
 
+// Asynchronous copy of a thread's share of one operand tile (chunk l0) into its raw slots
+// raw[(u EPC + q) NTHR + tid]: the thread that converts an entry is the one that copied it,
+// so the copies need no barrier, only the thread's own cp.async.wait_group.
+template <int ENG, int R>
+__device__ __forceinline__ void issue_operand(float2* raw, const float2* base, int64_t sr,
+                                              int64_t sl, int row0, int nrows, int l0, int K) {
+  using C = Cfg<ENG>;
+  constexpr int PER = R * Layout<ENG>::KG / NTHR;
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int item = threadIdx.x + NTHR * u;
+    const int r = item % R, kg = item / R;
+    const int row = row0 + r;
+#pragma unroll
+    for (int q = 0; q < C::EPC; ++q) {
+      const int l = l0 + kg * C::EPC + q;
+      const bool ok = row < nrows && l < K;
+      const float2* src = ok ? base + (int64_t)row * sr + (int64_t)l * sl : base;
+      cp_async8(raw + (size_t)(u * C::EPC + q) * NTHR + threadIdx.x, src, ok);
+    }
+  }
+}
+
+// Converts a thread's raw share into the planes (conjugating on the way).
+template <int ENG, int R>
+__device__ __forceinline__ void convert_operand(const float2* raw, int conj, unsigned char* planes,
+                                                int plane_bytes) {
+  using C = Cfg<ENG>;
+  constexpr int PER = R * Layout<ENG>::KG / NTHR;
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int item = threadIdx.x + NTHR * u;
+    const int r = item % R, kg = item / R;
+    float2 x[C::EPC];
+#pragma unroll
+    for (int q = 0; q < C::EPC; ++q) {
+      x[q] = raw[(size_t)(u * C::EPC + q) * NTHR + threadIdx.x];
+      if (conj) x[q].y = -x[q].y;
+    }
+    Row<ENG> row;
+    make_planes<ENG>(x, row);
+    const int off = (kg * (R / 8) + r / 8) * 128 + (r % 8) * 16;
+#pragma unroll
+    for (int pl = 0; pl < 3 * C::NSPLIT; ++pl) {
+      uint4 val;
+      val.x = row.w[pl][0];
+      val.y = row.w[pl][1];
+      val.z = row.w[pl][2];
+      val.w = row.w[pl][3];
+      *reinterpret_cast<uint4*>(planes + (size_t)pl * plane_bytes + off) = val;
+    }
+  }
+}
+
 template <int ENG>
 __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(CGemm g) {
   using C = Cfg<ENG>;
@@ -241,8 +319,11 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(CGemm g) {
   const float2* B = g.b.p + (int64_t)(g.b.idx ? g.b.idx[bz] : bz) * g.b.bs;
   float2* Cp = const_cast<float2*>(g.c.p) + (int64_t)(g.c.idx ? g.c.idx[bz] : bz) * g.c.bs;
   const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * L::STAGE);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * L::STAGE + 32);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * L::STAGE + L::RAW);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * L::STAGE + L::RAW + 32);
+  float2* raw = reinterpret_cast<float2*>(smem + 2 * L::STAGE);   // RAW_STAGES x (A, B)
+  auto raw_a = [&](int c) { return raw + (size_t)(c % 3) * ((L::RAW_A + L::RAW_B) / 8); };
+  auto raw_b = [&](int c) { return raw_a(c) + L::RAW_A / 8; };
   const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
 
   if (warp == 0) {
@@ -267,9 +348,28 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(CGemm g) {
   constexpr int KSTEPS = C::BK / C::KMMA;
   const int nk = (g.K + C::BK - 1) / C::BK;
   bool timed_out = false;
+  if constexpr (L::RAW_STAGES > 0) {
+    // chunks 0 and 1 in flight before the loop; one commit group per chunk (empty past nk)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c < nk) {
+        issue_operand<ENG, BM>(raw_a(c), A, g.a.s0, g.a.s1, i0, g.M, c * C::BK, g.K);
+        issue_operand<ENG, BN>(raw_b(c), B, g.b.s1, g.b.s0, j0, g.N, c * C::BK, g.K);
+      }
+      cp_async_commit();
+    }
+  }
   int kc = 0;
   for (; kc < nk; ++kc) {
     const int buf = kc & 1;
+    if constexpr (L::RAW_STAGES > 0) {
+      // chunk kc + 2 into the slot chunk kc - 1 used (converted by this thread last time)
+      if (kc + 2 < nk) {
+        issue_operand<ENG, BM>(raw_a(kc + 2), A, g.a.s0, g.a.s1, i0, g.M, (kc + 2) * C::BK, g.K);
+        issue_operand<ENG, BN>(raw_b(kc + 2), B, g.b.s1, g.b.s0, j0, g.N, (kc + 2) * C::BK, g.K);
+      }
+      cp_async_commit();
+    }
     if (kc >= 2) {
       const bool ok = mbar_wait(buf ? bar1 : bar0, (uint32_t)(((kc >> 1) - 1) & 1));
       if (__syncthreads_or(!ok)) {
@@ -280,9 +380,15 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(CGemm g) {
     unsigned char* st = smem + (size_t)buf * L::STAGE;
     unsigned char* pa = st;
     unsigned char* pb = st + L::NPLANE * L::PLANE_A;
-    const int l0 = kc * C::BK;
-    stage_operand<ENG, BM>(pa, L::PLANE_A, A, g.a.s0, g.a.s1, g.a.conj, i0, g.M, l0, g.K);
-    stage_operand<ENG, BN>(pb, L::PLANE_B, B, g.b.s1, g.b.s0, g.b.conj, j0, g.N, l0, g.K);
+    if constexpr (L::RAW_STAGES > 0) {
+      cp_async_wait<2>();   // this thread's copies of chunk kc have landed
+      convert_operand<ENG, BM>(raw_a(kc), g.a.conj, pa, L::PLANE_A);
+      convert_operand<ENG, BN>(raw_b(kc), g.b.conj, pb, L::PLANE_B);
+    } else {
+      const int l0 = kc * C::BK;
+      stage_operand<ENG, BM>(pa, L::PLANE_A, A, g.a.s0, g.a.s1, g.a.conj, i0, g.M, l0, g.K);
+      stage_operand<ENG, BN>(pb, L::PLANE_B, B, g.b.s1, g.b.s0, g.b.conj, j0, g.N, l0, g.K);
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -312,6 +418,8 @@ __global__ void __launch_bounds__(NTHR, 1) cgemm_tc_kernel(CGemm g) {
           : "memory");
     }
   }
+  // no asynchronous copy may still be landing in shared memory when the CTA moves on or exits
+  if constexpr (L::RAW_STAGES > 0) cp_async_wait<0>();
   // wait for the last committed chunk (its commit covers every earlier MMA)
   const int last = (timed_out ? kc : nk) - 1;
   bool ok = true;
