@@ -522,16 +522,22 @@ __global__ void __launch_bounds__(256) rsvt_refill_kernel(float2* P, const float
   const int tid = threadIdx.x, nthr = blockDim.x;
   __shared__ float s_max;
   const float* sg = sig + (size_t)s * kmax;
-  if (tid == 0) {
+  if (tid < 32) {
+    // sigma_max and the count above max(tau, floor sigma_max) by one warp (both exact in any
+    // order)
     float m = 0.f;
-    for (int v = 0; v < k; ++v) m = fmaxf(m, sg[v]);
+    for (int v = tid; v < k; v += 32) m = fmaxf(m, sg[v]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     const float thr = fmaxf(tau, floor_rel * m);
     int cnt = 0;
-    for (int v = 0; v < k; ++v) cnt += sg[v] > thr ? 1 : 0;
-    s_max = m;
-    if (rstat && k > 0) {
-      atomicMax(&rstat->rank_max, cnt);
-      if (cnt >= k) atomicAdd(&rstat->saturated, 1);
+    for (int v = tid; v < k; v += 32) cnt += sg[v] > thr ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (tid == 0) {
+      s_max = m;
+      if (rstat && k > 0) {
+        atomicMax(&rstat->rank_max, cnt);
+        if (cnt >= k) atomicAdd(&rstat->saturated, 1);
+      }
     }
   }
   __syncthreads();
