@@ -64,6 +64,9 @@ WORKLOADS = {
                   desc="grayscale video completion 144x176x100, 20% observed"),
     "rpca": dict(kind="rpca", iters=200, cpu_iters=2,
                  desc="tensor RPCA 240x320x60, tubal rank 10, 10% entrywise corruption"),
+    "rpca_tube": dict(kind="rpca", iters=200, cpu_iters=2,
+                      desc="tube-sparse tensor RPCA (eq. sparse2) on a 144x256x80 panning "
+                           "video, 10% of pixel tubes corrupted in 10-frame blocks"),
     "color": dict(kind="complete", iters=150, cpu_iters=1,
                   desc="colour video completion 288x352x3x60, 15% observed"),
     "lowrank": dict(kind="complete", iters=100, cpu_iters=100,
@@ -245,6 +248,10 @@ def build_workload(name, seed):
     if name == "rpca":
         M, L0, S0, sup, lam = synth.workload_rpca(seed=seed)
         return dict(kind="rpca", dims=M.shape, M=M.astype(np.float32), lam=lam, truth=L0)
+    if name == "rpca_tube":
+        M, L0, S0, sup, lam = synth.workload_rpca_tube(seed=seed)
+        return dict(kind="rpca", dims=M.shape, M=M.astype(np.float32), lam=lam, truth=L0,
+                    tube=True)
     if name == "batch":
         items = []
         for b, sp in enumerate(synth.workload_batch_shapes(seed=seed)):
@@ -261,6 +268,12 @@ def build_workload(name, seed):
                                   lam=lam, truth=L))
         return dict(kind="batch", items=items)
     raise ValueError(name)
+
+
+def ctx_options(wl):
+    """Context options a workload needs besides precision (the tube-wise sparse term)."""
+    from paper_1407_1785_gb300 import libtsvd
+    return {"sparse_mode": libtsvd.SPARSE_TUBE} if wl.get("tube") else {}
 
 
 def to_device(wl):
@@ -330,7 +343,8 @@ def oracle_sample(wl, iters_sample):
         if it["kind"] == "complete":
             oracle.tnn_complete(M, it["omega"], iters_sample)
         else:
-            oracle.trpca(M, it["lam"], iters_sample)
+            oracle.trpca(M, it["lam"], iters_sample,
+                         sparse_mode=oracle.SPARSE_TUBE if it.get("tube") else oracle.SPARSE_ENTRY)
     dt = time.perf_counter() - t0
     frac = sum(int(np.prod(it["dims"])) for it in take) / n_voxels(wl)
     what = (f"first {iters_sample} ADMM iterations of the same workload" if wl["kind"] != "batch"
@@ -436,7 +450,7 @@ def instrumented_pass(dw, iters, prec_name, stream, flush, barrier, steps, cache
     short drain per record, so the throughput figures come from an uninstrumented region."""
     from paper_1407_1785_gb300 import libtsvd
     ctx = libtsvd.Context(device=stream.device.index, stream=stream.cuda_stream, timing=1,
-                          precision=PRECISIONS[prec_name], autotune_cache=cache)
+                          precision=PRECISIONS[prec_name], autotune_cache=cache, **ctx_options(dw))
     solve = solver(ctx, dw, iters)
     solve()                                                # warm-up (plan from the cache)
     t_ms, stats = timed_solves(solve, steps, flush, stream, barrier)
@@ -449,7 +463,7 @@ def mixed_form(args, dw, iters, prec_name, e_plain, stream, flush, barrier, peak
     """Times the mixed form on the same workload; returns the "mixed" object."""
     from paper_1407_1785_gb300 import libtsvd
     ctx = libtsvd.Context(device=stream.device.index, stream=stream.cuda_stream,
-                          precision=PRECISIONS[prec_name], autotune_cache=cache)
+                          precision=PRECISIONS[prec_name], autotune_cache=cache, **ctx_options(dw))
     solve = solver(ctx, dw, iters)
     for _ in range(max(args.warmup, 1)):
         solve()
@@ -525,7 +539,7 @@ def run_ours(args):
     # the timed context and the instrumented one share the autotuned plans
     cache = os.path.join(tempfile.mkdtemp(prefix="tsvd_tune_"), "plans.txt").encode()
     ctx = libtsvd.Context(device=local, stream=stream.cuda_stream,
-                          precision=PRECISIONS[prec], autotune_cache=cache)
+                          precision=PRECISIONS[prec], autotune_cache=cache, **ctx_options(wl))
     solve = solver(ctx, dw, iters)
     for _ in range(max(args.warmup, 0)):
         solve()
@@ -570,7 +584,7 @@ def run_ours(args):
         mh = torch.from_numpy(synth.to_colmajor(wl["M"])).pin_memory()
         xh = torch.empty(N, dtype=torch.float32).pin_memory()
         ctx_e2e = libtsvd.Context(device=local, stream=stream.cuda_stream,
-                                  precision=PRECISIONS[prec])
+                                  precision=PRECISIONS[prec], **ctx_options(wl))
         dims = wl["dims"]
         if wl["kind"] == "complete":
             oh = torch.from_numpy(synth.to_colmajor(wl["omega"], np.uint8)).pin_memory()

@@ -181,7 +181,7 @@ def tube_corruption(shape, frac: float, seed: int, block: int = 10, std: float =
 
 
 # ---------------------------------------------------------------------------------------------
-# The five workloads (shapes, sampling rates and corruption levels used in tests and benches).
+# The workloads (shapes, sampling rates and corruption levels used in tests and benches).
 # ---------------------------------------------------------------------------------------------
 
 def workload_lowrank_completion(seed: int = 1, n1=32, n2=32, n3=16, rank=3, p=0.5):
@@ -205,6 +205,17 @@ def workload_rpca(seed: int = 1, n1=240, n2=320, n3=60, rank=10, frac=0.1):
     L = lowrank_tensor(n1, n2, n3, rank, seed)
     S, sup = sparse_corruption(L.shape, frac, seed)
     lam = 1.0 / math.sqrt(max(n1, n2) * n3)
+    return L + S, L, S, sup, lam
+
+
+def workload_rpca_tube(seed: int = 1, n1=144, n2=256, n3=80, frac=0.1, block=10, std=1.0):
+    """Tube-sparse tensor RPCA on video (the Sec. 5 experiment's setting, at the size of its
+    144 x 256 x 80 clip): L = a panning-texture video, S = Gaussian noise (std 1) on a fraction
+    `frac` of the pixel tubes, the noisy pixels fixed within each block of `block` frames;
+    lambda = 1/sqrt(max(n1, n2)) for the l_{1,1,2} term of eq. sparse2."""
+    L = translating_texture(n1, n2, n3, seed)
+    S, sup = tube_corruption(L.shape, frac, seed, block=block, std=std)
+    lam = 1.0 / math.sqrt(max(n1, n2))
     return L + S, L, S, sup, lam
 
 

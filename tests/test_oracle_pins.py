@@ -367,3 +367,18 @@ def test_rpca_tube_mode_finds_corrupted_tubes():
     tube_found = np.linalg.norm(S, axis=2) > 1e-3
     tube_true = np.linalg.norm(S0, axis=2) > 0
     assert np.array_equal(tube_found, tube_true)
+
+
+def test_rpca_tube_workload_generator():
+    """The tube-sparse RPCA workload (Sec. 5 setting): noisy pixel locations constant within
+    each 10-frame block, about 10% of the tubes per block, lambda = 1/sqrt(max(n1, n2)), and
+    L the panning video itself."""
+    M, L0, S0, sup, lam = synth.workload_rpca_tube(seed=3, n1=24, n2=40, n3=25)
+    assert M.shape == (24, 40, 25) and lam == 1.0 / np.sqrt(40)
+    assert np.array_equal(M, L0 + S0)
+    assert np.array_equal(L0, synth.translating_texture(24, 40, 25, 3))
+    for b0 in (0, 10, 20):
+        blk = sup[:, :, b0:min(b0 + 10, 25)]
+        assert np.all(blk == blk[:, :, :1])            # same pixels for the whole block
+        assert 0.05 < blk[:, :, 0].mean() < 0.15
+    assert np.array_equal(S0 != 0, sup.astype(bool))
