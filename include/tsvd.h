@@ -187,6 +187,21 @@ const char* tsvd_last_error(const tsvd_ctx* ctx);
 tsvd_status tsvt(tsvd_ctx* ctx, const float* Y, float* Z, int order, const int64_t* dims,
                  float tau, int32_t* multirank, double* tnn);
 
+/* Truncated t-SVD (Algorithm 1; Theorem 2.3.1): Y = U * S * V^T with the first k singular
+ * tubes, where * is the t-product (Def. 2.1.1) and V^T the tensor transpose.  Per Fourier
+ * slice the singular values are taken in decreasing order and the first k kept, so for
+ * k = min(n1, n2) U * S * V^T reproduces Y (the economy t-SVD: U^T * U = I), and for smaller k
+ * it is M_k, the best approximation of Theorem 2.3.1.  k = 0 means min(n1, n2).
+ * Outputs (real, column-major, device or host, not aliasing Y): U dims (n1, k, n3[, n4]),
+ * S dims (k, k, n3[, n4]) f-diagonal, V dims (n2, k, n3[, n4]).  The factors are unique up
+ * to a phase per (slice, column) in the Fourier domain; U * S * V^T is unique when the k-th
+ * and (k+1)-th singular values of every slice differ.  A column whose singular value is 0 is
+ * returned as zeros in U (n1 >= n2) or V (n1 < n2).  Plain form (one-sided Jacobi, FP32)
+ * whatever the context's precision; waits for its stream.  Errors: EINVAL (k < 0 or
+ * k > min(n1, n2), NULL or aliasing buffers), EUNSUPPORTED, ENOTCONV, ENOMEM. */
+tsvd_status tsvd_factor(tsvd_ctx* ctx, const float* Y, int order, const int64_t* dims, int k,
+                        float* U, float* S, float* V);
+
 /* TNN tensor completion (Sec. 4: min ||X||_TNN s.t. P_Omega(X) = P_Omega(M), eq.
  * originalTNN) by the ADMM of eq. proj / eq. shrink / dual ascent with scaled dual Q and
  * penalty schedule rho_{k+1} = min(mu rho_k, rho_max) from opts:

@@ -581,7 +581,7 @@ __global__ void __maxnreg__(max_regs_for(CPL * NP))
       const float* wr = Wr + (size_t)v * rowp;
       const float* wi = Wi + (size_t)v * rowp;
       for (int e = lane; e < len; e += 32)
-        wo[(size_t)e + (size_t)n1 * gv] = make_float2(wr[e], si * wi[e]);
+        wo[(size_t)e + (size_t)len * gv] = make_float2(wr[e], si * wi[e]);
       if (lane == 0 && a.sigout) a.sigout[(size_t)s * a.sig_stride + gv] = sig[v];
     }
   }
@@ -1003,7 +1003,7 @@ cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st) {
   if (!plan_slice(a.n1, a.n2, a.nslices, a.knobs, sh, smem)) return cudaErrorInvalidValue;
   if (sh.C > 1 && (a.scratch == nullptr || a.scratch_bytes < scratch_for(sh, a.N12, a.nslices)))
     return cudaErrorInvalidValue;
-  if (a.wout && (sh.rows || a.wout_stride < (int64_t)a.n1 * a.n2)) return cudaErrorInvalidValue;
+  if (a.wout && a.wout_stride < (int64_t)a.n1 * a.n2) return cudaErrorInvalidValue;
   if ((a.vin || a.vout) && (!sh.vform || a.vstride < (int64_t)sh.nv * sh.nv))
     return cudaErrorInvalidValue;
   const int gpw = 32 / sh.G;

@@ -54,6 +54,9 @@ struct tsvd_ctx {
   cudaEvent_t fork = nullptr;
   // plain form: the current solve runs the V form (warm start), for the plan lookups
   bool vform_now = false;
+  // tsvd_factor: converged vectors, rotations, Fourier-domain factors and output staging
+  char* fbuf = nullptr;
+  size_t fbuf_cap = 0;
   // mixed form: per-iteration sketch statistics copied to pinned host memory (a ring read
   // two iterations late, so the host never waits for the iteration it just enqueued)
   static constexpr int kRing = 4;
@@ -1299,6 +1302,7 @@ tsvd_status tsvd_destroy(tsvd_ctx* c) {
   for (auto& evs : c->rs_stage)
     for (cudaEvent_t e : evs) cudaEventDestroy(e);
   if (c->rs_host) cudaFreeHost(c->rs_host);
+  if (c->fbuf) cudaFree(c->fbuf);
   delete c;
   return st;
 }
@@ -1365,6 +1369,149 @@ tsvd_status tsvt(tsvd_ctx* c, const float* Y, float* Z, int order, const int64_t
     TSVD_CUDA(c, cudaMemcpyAsync(Z, w.stage_out0, bytes, cudaMemcpyDeviceToHost, c->stream));
   bool conv = true;
   TSVD_TRY(read_slice_stats(c, p, w, multirank, tnn, nullptr, &conv));
+  if (!conv) return fail(c, TSVD_ENOTCONV, "a slice SVD reached max_sweeps = %d", c->opts.max_sweeps);
+  return TSVD_OK;
+}
+
+// Truncated t-SVD (Algorithm 1, Theorem 2.3.1): forward tube pass, the one-sided Jacobi of
+// every distinct Fourier slice in the V form (V = I at the start) returning its converged
+// vectors, singular values and rotations, the Fourier-domain factors ordered by decreasing
+// singular value (factor.cu), and one inverse tube pass per factor.  The threshold of the
+// slice pass is the largest float, so its own rebuild keeps nothing.
+tsvd_status tsvd_factor(tsvd_ctx* c, const float* Y, int order, const int64_t* dims, int k,
+                        float* U, float* S, float* V) {
+  if (!c) return TSVD_EINVAL;
+  begin_call(c);
+  if (!Y || !U || !S || !V) return fail(c, TSVD_EINVAL, "Y, U, S and V must not be NULL");
+  if ((const void*)U == Y || (const void*)S == Y || (const void*)V == Y || U == S || U == V ||
+      S == V)
+    return fail(c, TSVD_EINVAL, "Y, U, S and V must be distinct buffers");
+  Problem p;
+  TSVD_TRY(make_problem(c, order, dims, p));
+  if (!jacobi_svt_supported((int)p.n1, (int)p.n2))
+    return fail(c, TSVD_EUNSUPPORTED, "a %lld x %lld complex slice does not fit one SM's shared memory",
+                (long long)p.n1, (long long)p.n2);
+  const int n1 = (int)p.n1, n2 = (int)p.n2;
+  const int nv = std::min(n1, n2), len = std::max(n1, n2);
+  if (k < 0 || k > nv) return fail(c, TSVD_EINVAL, "k = %d outside [0, min(n1, n2) = %d]", k, nv);
+  if (k == 0) k = nv;
+  if (!warm_plan_exists(c, p))
+    return fail(c, TSVD_EUNSUPPORTED, "no slice plan keeps the rotations of a %d x %d slice", n1, n2);
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
+  const int ky = pointer_kind(Y, c->device), ku = pointer_kind(U, c->device);
+  const int ks = pointer_kind(S, c->device), kv = pointer_kind(V, c->device);
+  if (ky < 0 || ku < 0 || ks < 0 || kv < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
+  // the plans (and the scratch sized for them) are those of the V form
+  c->vform_now = true;
+  WsRequest rq;
+  rq.stage_in = ky == 1;
+  Workspace w;
+  TSVD_TRY(prepare_workspace(c, p, rq, w));
+  const TubeGeom& g = p.g;
+  const size_t ns = (size_t)g.nstore, nsl = (size_t)p.nslices;
+  const size_t nU = (size_t)n1 * k, nV = (size_t)n2 * k, nS = (size_t)k * k;
+  const size_t b_w = align_up(ns * len * nv * sizeof(float2));
+  const size_t b_j = align_up(ns * nv * nv * sizeof(float2));
+  const size_t b_s = align_up(ns * nv * sizeof(float));
+  const size_t b_fu = align_up(ns * nU * sizeof(float2)), b_fv = align_up(ns * nV * sizeof(float2));
+  const size_t b_fs = align_up(ns * nS * sizeof(float2));
+  const size_t b_ou = ku == 1 ? align_up(nsl * nU * sizeof(float)) : 0;
+  const size_t b_os = ks == 1 ? align_up(nsl * nS * sizeof(float)) : 0;
+  const size_t b_ov = kv == 1 ? align_up(nsl * nV * sizeof(float)) : 0;
+  const size_t need = b_w + b_j + b_s + b_fu + b_fv + b_fs + b_ou + b_os + b_ov;
+  if (need > c->fbuf_cap) {
+    if (c->fbuf) {
+      TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+      cudaFree(c->fbuf);
+      c->fbuf = nullptr;
+      c->fbuf_cap = 0;
+    }
+    void* ptr = nullptr;
+    const cudaError_t e = cudaMalloc(&ptr, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, TSVD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", need, cudaGetErrorString(e));
+    }
+    c->fbuf = static_cast<char*>(ptr);
+    c->fbuf_cap = need;
+  }
+  char* b = c->fbuf;
+  float2* fW = reinterpret_cast<float2*>(b);
+  float2* fJ = reinterpret_cast<float2*>(b += b_w);
+  float* fsig = reinterpret_cast<float*>(b += b_j);
+  float2* fU = reinterpret_cast<float2*>(b += b_s);
+  float2* fV = reinterpret_cast<float2*>(b += b_fu);
+  float2* fS = reinterpret_cast<float2*>(b += b_fv);
+  b += b_fs;
+  // outputs in host memory are written to staging first
+  float* oU = U;
+  float* oS = S;
+  float* oV = V;
+  if (ku == 1) {
+    oU = reinterpret_cast<float*>(b);
+    b += b_ou;
+  }
+  if (ks == 1) {
+    oS = reinterpret_cast<float*>(b);
+    b += b_os;
+  }
+  if (kv == 1) oV = reinterpret_cast<float*>(b);
+
+  const float* y = Y;
+  if (ky == 1) {
+    TSVD_CUDA(c, cudaMemcpyAsync(w.stage_in, Y, (size_t)p.N * sizeof(float),
+                                 cudaMemcpyHostToDevice, c->stream));
+    y = w.stage_in;
+  }
+  TubeArgs f = tube_args(p, w, TUBE_FWD);
+  f.in = y;
+  f.spec_out = w.spec_a;
+  TSVD_TRY(run_tube(c, f, "tube pass (forward)"));
+  const float tau_none = 3.0e38f;   // keeps no singular value: the slice pass only factors
+  TSVD_TRY(tune_slices(c, p, w, tau_none));
+  SliceArgs sa = slice_args(c, p, w, tau_none);
+  sa.wout = fW;
+  sa.wout_stride = (int64_t)len * nv;
+  sa.sigout = fsig;
+  sa.sig_stride = nv;
+  sa.vout = fJ;
+  sa.vstride = (int64_t)nv * nv;
+  TSVD_TRY(run_slice(c, sa));
+  FactorArgs fa;
+  fa.W = fW;
+  fa.sig = fsig;
+  fa.J = fJ;
+  fa.slices = w.slices;
+  fa.nslices = w.ndistinct;
+  fa.n1 = n1;
+  fa.n2 = n2;
+  fa.k = k;
+  fa.Uh = fU;
+  fa.Sh = fS;
+  fa.Vh = fV;
+  TSVD_TRY(launch(c, launch_factor_assemble(fa, c->cur), "t-SVD factors"));
+  // each factor is a tensor with the same tube geometry and its own tube count
+  const struct {
+    const float2* spec;
+    float* out;
+    size_t tubes;
+  } outs[3] = {{fU, oU, nU}, {fS, oS, nS}, {fV, oV, nV}};
+  for (const auto& o : outs) {
+    TubeArgs t = tube_args(p, w, TUBE_INV);
+    t.g.N12 = (int64_t)o.tubes;
+    t.spec_in = o.spec;
+    t.out0 = o.out;
+    TSVD_TRY(run_tube(c, t, "tube pass (inverse)"));
+  }
+  if (ku == 1)
+    TSVD_CUDA(c, cudaMemcpyAsync(U, oU, nsl * nU * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (ks == 1)
+    TSVD_CUDA(c, cudaMemcpyAsync(S, oS, nsl * nS * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (kv == 1)
+    TSVD_CUDA(c, cudaMemcpyAsync(V, oV, nsl * nV * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  bool conv = true;
+  TSVD_TRY(read_slice_stats(c, p, w, nullptr, nullptr, nullptr, &conv));
   if (!conv) return fail(c, TSVD_ENOTCONV, "a slice SVD reached max_sweeps = %d", c->opts.max_sweeps);
   return TSVD_OK;
 }

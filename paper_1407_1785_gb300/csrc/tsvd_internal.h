@@ -103,10 +103,10 @@ struct SliceArgs {
                           // partial rebuilds of multi-CTA slices); nullable = one CTA per slice
   size_t scratch_bytes;
   SliceKnobs knobs;
-  // Optional outputs of the converged vectors W = B V = U diag(sigma) (only when the vectors
-  // are the columns, n1 >= n2): entry e of vector v of slice s (the index the slice list
-  // gives) is written, conjugated when wout_conj, to wout[s * wout_stride + e + n1 * v], and
-  // sigma_v to sigout[s * sig_stride + v].
+  // Optional outputs of the converged vectors W = B V = U diag(sigma) (vectors = columns,
+  // n1 >= n2) or W = B^T V (vectors = rows): entry e < len = max(n1, n2) of vector v of slice s
+  // (the index the slice list gives) is written, conjugated when wout_conj, to
+  // wout[s * wout_stride + e + len * v], and sigma_v to sigout[s * sig_stride + v].
   float2* wout = nullptr;
   int64_t wout_stride = 0;
   int wout_conj = 0;
@@ -128,6 +128,22 @@ struct SliceArgs {
 
 // Returns cudaErrorInvalidValue when a slice does not fit the kernel's shared memory.
 cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st);
+
+// Fourier-domain factors of the truncated t-SVD from the converged Jacobi of every distinct
+// slice (factor.cu): W (len x nv per stored slice, as SliceArgs::wout writes it), sigma (nv per
+// slice) and the accumulated rotations J (nv x nv, as SliceArgs::vout writes it from V = I).
+struct FactorArgs {
+  const float2* W;
+  const float* sig;
+  const float2* J;
+  const int* slices;    // distinct stored slices
+  int nslices;
+  int n1, n2, k;        // k <= min(n1, n2) factors kept
+  float2* Uh;           // n1 x k per stored slice
+  float2* Sh;           // k x k per stored slice (f-diagonal)
+  float2* Vh;           // n2 x k per stored slice
+};
+cudaError_t launch_factor_assemble(const FactorArgs& a, cudaStream_t st);
 // Whether launch_jacobi_svt supports an n1 x n2 slice (with scratch available).
 bool jacobi_svt_supported(int n1, int n2);
 // Whether the knobs give a valid plan for `nslices` n1 x n2 slices.

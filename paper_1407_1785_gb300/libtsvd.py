@@ -29,8 +29,8 @@ SCALE_AVG, SCALE_SUM = 0, 1
 
 # Every symbol include/tsvd.h declares.
 EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_last_error",
-                    "tsvt", "tnn_complete", "trpca", "tsvd_solve_batched", "tsvt_static",
-                    "tsvd_cgemm")
+                    "tsvt", "tsvd_factor", "tnn_complete", "trpca", "tsvd_solve_batched",
+                    "tsvt_static", "tsvd_cgemm")
 OP_N, OP_T, OP_C = 0, 1, 2
 WARM_OFF, WARM_ON, WARM_AUTO = 0, 1, 2
 PROBLEM_COMPLETE, PROBLEM_RPCA = 1, 2
@@ -109,6 +109,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tsvd_last_error.restype = ctypes.c_char_p
     L.tsvt.argtypes = [P, P, P, ctypes.c_int, i64p, ctypes.c_float, P, P]
     L.tsvt.restype = ctypes.c_int
+    L.tsvd_factor.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_int, P, P, P]
+    L.tsvd_factor.restype = ctypes.c_int
     L.tnn_complete.argtypes = [P, P, P, ctypes.c_int, i64p, ctypes.c_int, P, P,
                                ctypes.POINTER(Stats)]
     L.tnn_complete.restype = ctypes.c_int
@@ -215,6 +217,19 @@ class Context:
         allow = (TSVD_OK, TSVD_ENOTCONV) if allow_notconv else (TSVD_OK,)
         self._check("tsvt", st, allow)
         return st, (tnn.value if with_tnn else None)
+
+    def factor(self, Y, dims: Sequence[int], k: int, U, S, V):
+        """Truncated t-SVD of Y: U (n1, k, ...), S (k, k, ...), V (n2, k, ...); k = 0 keeps
+        min(n1, n2) singular tubes."""
+        st = self._L.tsvd_factor(self._h, _ptr(Y), len(dims), _dims(dims), int(k), _ptr(U),
+                                 _ptr(S), _ptr(V))
+        self._check("tsvd_factor", st)
+        return st
+
+    def raw_factor(self, Y, dims: Sequence[int], k: int, U, S, V) -> int:
+        """tsvd_factor status without raising (argument checks in the tests)."""
+        return self._L.tsvd_factor(self._h, _ptr(Y), len(dims), _dims(dims), int(k), _ptr(U),
+                                   _ptr(S), _ptr(V))
 
     def tnn_complete(self, M_obs, omega, dims: Sequence[int], iters: int, X_out, Z_out=None,
                      stats: bool = False):
