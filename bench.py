@@ -74,6 +74,9 @@ WORKLOADS = {
     "factor": dict(kind="factor", iters=1, cpu_iters=1,
                    desc="economy t-SVD (Algorithm 1) of the 144x176x100 video, all "
                         "min(n1, n2) singular tubes"),
+    "compress": dict(kind="compress", iters=1, cpu_iters=1,
+                     desc="t-SVD compression (Sec. 3, Methods 1 and 2) of the 144x176x100 "
+                          "video: RSE against the compression ratio"),
     "batch": dict(kind="batch", iters=100, cpu_iters=10,
                   desc="64 uneven tensors (n1, n2 in [48, 256], n3 in [8, 64]), half "
                        "completion / half RPCA, one batched call"),
@@ -725,6 +728,8 @@ def run_factor(args, reference=False):
     rank, world, local = dist_info()
     spec = WORKLOADS["factor"]
     if reference:
+        spec = WORKLOADS[args.workload]
+        unit = "factorizations/s" if args.workload == "factor" else "compressions/s"
         if rank != 0:
             return 0
         import oracle
@@ -737,15 +742,15 @@ def run_factor(args, reference=False):
             oracle.tsvd(Y)
         dt = time.perf_counter() - t0
         v = args.steps / dt
-        cpu = {"value": v, "unit": "factorizations/s", "cores": oracle.num_threads(),
+        cpu = {"value": v, "unit": unit, "cores": oracle.num_threads(),
                "kind": "oracle", "sample": "full t-SVD of the same tensor per step (FP64 C oracle)"}
         print(json.dumps({"metric": METRIC, "impl": "reference", "value": v,
-                          "unit": "factorizations/s", "n_gpus": world, "steps": args.steps,
+                          "unit": unit, "n_gpus": world, "steps": args.steps,
                           "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                           "dtype": "f64", "data": "synthetic",
                           "config": {"workload": spec["desc"]}, "cpu_baseline": cpu,
-                          "e2e": {"value": v, "unit": "factorizations/s",
+                          "e2e": {"value": v, "unit": unit,
                                   "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
               flush=True)
         return 0
@@ -837,9 +842,108 @@ def run_factor(args, reference=False):
     return 0
 
 
+def run_compress(args):
+    """t-SVD compression of the video: one step = one Method 1 compression at k2 = 10 n3 (ratio
+    ~9); the line also carries the RSE-against-ratio curve of both methods (k3 tubes for
+    Method 2, k2 = k3 n3 entries for Method 1: the same ratio)."""
+    import torch
+    import torch.distributed as dist
+    from paper_1407_1785_gb300 import libtsvd, synth
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    spec = WORKLOADS["compress"]
+    Y = factor_input(1 + rank)
+    n1, n2, n3 = Y.shape
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.tsvd(Y.astype(np.float64))
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "compressions/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": "the full t-SVD both methods truncate, same tensor "
+                                           "(FP64 C oracle)", "seconds": dt}
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    y = torch.from_numpy(synth.to_colmajor(Y)).cuda()
+    z = torch.empty_like(y)
+    ctx = libtsvd.Context(device=local, stream=stream.cuda_stream)
+    nrm = float(np.linalg.norm(Y))
+    curve = []
+    for k3 in (1, 2, 5, 10, 20, 40):
+        for method, k, name in ((libtsvd.COMPRESS_TUBAL, k3, "t-SVD-tubal (Method 2)"),
+                                (libtsvd.COMPRESS_GLOBAL, k3 * n3, "t-SVD (Method 1)")):
+            kept, ratio = ctx.compress(y, Y.shape, method, k, z)
+            R = synth.from_colmajor(z.cpu().numpy(), Y.shape)
+            rse = float(np.linalg.norm(R - Y) / nrm)
+            curve.append({"method": name, "k": int(k), "kept": int(kept), "ratio": ratio,
+                          "rse_db": 20 * math.log10(max(rse, 1e-300))})
+    k2 = 10 * n3
+
+    def step():
+        ctx.compress(y, Y.shape, libtsvd.COMPRESS_GLOBAL, k2, z)
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_ms, _ = timed_solves(step, args.steps, flush, stream, barrier)
+    clocks = sampler.stop()
+    t_ms = max_over_ranks(t_ms)
+    yh = torch.from_numpy(synth.to_colmajor(Y)).pin_memory()
+    zh = torch.empty(yh.numel()).pin_memory()
+    ctx.compress(yh, Y.shape, libtsvd.COMPRESS_GLOBAL, k2, zh)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.compress(yh, Y.shape, libtsvd.COMPRESS_GLOBAL, k2, zh)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    ctx.close()
+    peaks = measured_peaks()
+    flops = jacobi_gvl_flops(n1, n2, half_slices(Y.shape))
+    achieved = flops / (t_ms / 1000.0 / args.steps) / 1e12
+    line = {
+        "metric": METRIC, "value": world * args.steps / (t_ms / 1000.0), "unit": "compressions/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": spec["desc"], "seed": 1, "method_timed": "Method 1, k2 = 10 n3",
+                   "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "curve": curve,
+        "roofline": {"bound": "alu", "kernel": "jacobi_svt_kernel", "achieved": achieved,
+                     "peak": alu_peak(peaks), "unit": "TFLOP/s", "frac": achieved / alu_peak(peaks),
+                     "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x max SM clock",
+                     "alg_flops_per_call": flops,
+                     "times_from": "whole call (forward pass, slice SVDs, singular values to the "
+                                   "host, rebuild, inverse pass), CUDA events"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * args.steps / e2e_s, "unit": "compressions/s",
+                "h2d_bytes_per_step": int(yh.numel() * 4), "d2h_bytes_per_step": int(zh.numel() * 4)},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
-    if args.workload == "factor":
+    if args.workload == "compress" and args.impl != "reference":
+        return run_compress(args)
+    if args.workload in ("factor", "compress"):
         return run_factor(args, reference=args.impl == "reference")
     if args.impl == "reference":
         return run_reference(args)

@@ -202,6 +202,20 @@ tsvd_status tsvt(tsvd_ctx* ctx, const float* Y, float* Z, int order, const int64
 tsvd_status tsvd_factor(tsvd_ctx* ctx, const float* Y, int order, const int64_t* dims, int k,
                         float* U, float* S, float* V);
 
+/* t-SVD compression (Sec. 3).  Z = the tensor rebuilt from the kept Fourier-domain singular
+ * terms: method TSVD_COMPRESS_GLOBAL (Method 1, t-SVD compression) keeps the k largest
+ * f-diagonal entries of S-hat over all min(n1, n2) * prod(dims[2..]) of them -- every entry
+ * equal to the k-th largest is kept too, so conjugate Fourier slices keep the same terms and Z
+ * is real (*kept_total may exceed k); TSVD_COMPRESS_TUBAL (Method 2, t-SVD-tubal compression)
+ * keeps the first k singular tubes (Z = M_k of Theorem 2.3.1, as tsvd_factor with k).
+ * 1 <= k <= min(n1, n2) * prod(dims[2..]) (GLOBAL) or min(n1, n2) (TUBAL).  Z (dims-shaped,
+ * may alias Y); kept_total (nullable, host): the entries kept (GLOBAL) or k (TUBAL); ratio
+ * (nullable, host): the compression ratio of Sec. 3, n1 n2 prod(dims[2..]) / (kept (n1 + n2 + 1))
+ * or n1 n2 / (k (n1 + n2 + 1)).  Plain form; waits for its stream.  Errors as tsvd_factor. */
+enum { TSVD_COMPRESS_GLOBAL = 1, TSVD_COMPRESS_TUBAL = 2 };
+tsvd_status tsvd_compress(tsvd_ctx* ctx, const float* Y, int order, const int64_t* dims,
+                          int method, int64_t k, float* Z, int64_t* kept_total, double* ratio);
+
 /* TNN tensor completion (Sec. 4: min ||X||_TNN s.t. P_Omega(X) = P_Omega(M), eq.
  * originalTNN) by the ADMM of eq. proj / eq. shrink / dual ascent with scaled dual Q and
  * penalty schedule rho_{k+1} = min(mu rho_k, rho_max) from opts:

@@ -12,6 +12,10 @@
 // (k x k), column-major, at slice s of buffers laid out like the tensor's stored spectrum.
 // A vector whose singular value is 0 has no defined left (columns) or right (rows) partner:
 // that column is written as zeros.
+//
+// The compression of Sec. 3 (Methods 1 and 2) keeps, per slice, a number of the largest terms
+// sigma_g u_g v_g^H chosen on the host and rebuilds the slice from W and J directly (W
+// already carries sigma).
 #include "tsvd_internal.h"
 
 namespace tsvd {
@@ -79,7 +83,70 @@ __global__ void __launch_bounds__(kThreads) factor_assemble_kernel(FactorArgs a)
   }
 }
 
+// Compression rebuild: Z-hat = sum of the kept[s] largest terms sigma_g u_g v_g^H of the slice,
+// from W = U diag(sigma) and J: columns  Z(i, j) = sum_g W(i, g) conj(J(j, g));
+//                                rows     Z(i, j) = sum_g conj(J(i, g)) W(j, g).
+__global__ void __launch_bounds__(kThreads) compress_rebuild_kernel(FactorArgs a,
+                                                                    const int* kept,
+                                                                    float2* Zh) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = a.slices[blockIdx.x];
+  const int nv = a.n1 < a.n2 ? a.n1 : a.n2;
+  const int len = a.n1 < a.n2 ? a.n2 : a.n1;
+  const bool rows = a.n1 < a.n2;
+  float* sg = reinterpret_cast<float*>(smem_raw);
+  int* perm = reinterpret_cast<int*>(sg + nv);
+  const float* sig = a.sig + (size_t)s * nv;
+  const int kk = min(max(kept[s], 0), nv);
+  for (int g = threadIdx.x; g < nv; g += blockDim.x) sg[g] = sig[g];
+  __syncthreads();
+  for (int g = threadIdx.x; g < nv; g += blockDim.x) {
+    const float v = sg[g];
+    int r = 0;
+    for (int h = 0; h < nv; ++h) r += (sg[h] > v || (sg[h] == v && h < g)) ? 1 : 0;
+    perm[r] = g;
+  }
+  __syncthreads();
+  const float2* W = a.W + (size_t)s * len * nv;
+  const float2* J = a.J + (size_t)s * nv * nv;
+  float2* Z = Zh + (size_t)s * a.n1 * a.n2;
+  for (int idx = threadIdx.x; idx < a.n1 * a.n2; idx += blockDim.x) {
+    const int i = idx % a.n1, j = idx / a.n1;
+    float zr = 0.f, zi = 0.f;
+    for (int r = 0; r < kk; ++r) {
+      const int g = perm[r];
+      float2 x, y;   // Z(i, j) += x * y
+      if (rows) {
+        const float2 jv = J[i + (size_t)nv * g];
+        x = make_float2(jv.x, -jv.y);
+        y = W[j + (size_t)len * g];
+      } else {
+        x = W[i + (size_t)len * g];
+        const float2 jv = J[j + (size_t)nv * g];
+        y = make_float2(jv.x, -jv.y);
+      }
+      zr += x.x * y.x - x.y * y.y;
+      zi += x.x * y.y + x.y * y.x;
+    }
+    Z[idx] = make_float2(zr, zi);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_compress_rebuild(const FactorArgs& a, const int* kept, float2* Zh,
+                                    cudaStream_t st) {
+  if (a.nslices <= 0) return cudaSuccess;
+  const int nv = a.n1 < a.n2 ? a.n1 : a.n2;
+  const size_t smem = (size_t)nv * (sizeof(float) + sizeof(int));
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(compress_rebuild_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  compress_rebuild_kernel<<<a.nslices, kThreads, smem, st>>>(a, kept, Zh);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_factor_assemble(const FactorArgs& a, cudaStream_t st) {
   if (a.nslices <= 0) return cudaSuccess;

@@ -1373,53 +1373,47 @@ tsvd_status tsvt(tsvd_ctx* c, const float* Y, float* Z, int order, const int64_t
   return TSVD_OK;
 }
 
-// Truncated t-SVD (Algorithm 1, Theorem 2.3.1): forward tube pass, the one-sided Jacobi of
-// every distinct Fourier slice in the V form (V = I at the start) returning its converged
-// vectors, singular values and rotations, the Fourier-domain factors ordered by decreasing
-// singular value (factor.cu), and one inverse tube pass per factor.  The threshold of the
-// slice pass is the largest float, so its own rebuild keeps nothing.
-tsvd_status tsvd_factor(tsvd_ctx* c, const float* Y, int order, const int64_t* dims, int k,
-                        float* U, float* S, float* V) {
-  if (!c) return TSVD_EINVAL;
-  begin_call(c);
-  if (!Y || !U || !S || !V) return fail(c, TSVD_EINVAL, "Y, U, S and V must not be NULL");
-  if ((const void*)U == Y || (const void*)S == Y || (const void*)V == Y || U == S || U == V ||
-      S == V)
-    return fail(c, TSVD_EINVAL, "Y, U, S and V must be distinct buffers");
+// The slice SVDs behind tsvd_factor and tsvd_compress: forward tube pass, then the one-sided
+// Jacobi of every distinct Fourier slice in the V form (V = I at the start) with a threshold
+// above every singular value (its own rebuild keeps nothing), writing the converged vectors W,
+// their norms sigma and the rotations J into the context's factor buffer, followed by
+// `extra` further bytes for the caller (fw.extra).
+struct FactorWork {
   Problem p;
+  Workspace w;
+  int n1 = 0, n2 = 0, nv = 0, len = 0;
+  float2* W = nullptr;
+  float2* J = nullptr;
+  float* sig = nullptr;
+  char* extra = nullptr;
+};
+
+tsvd_status factor_slices(tsvd_ctx* c, const float* Y, int order, const int64_t* dims,
+                          size_t extra, FactorWork& fw) {
+  Problem& p = fw.p;
   TSVD_TRY(make_problem(c, order, dims, p));
   if (!jacobi_svt_supported((int)p.n1, (int)p.n2))
     return fail(c, TSVD_EUNSUPPORTED, "a %lld x %lld complex slice does not fit one SM's shared memory",
                 (long long)p.n1, (long long)p.n2);
-  const int n1 = (int)p.n1, n2 = (int)p.n2;
-  const int nv = std::min(n1, n2), len = std::max(n1, n2);
-  if (k < 0 || k > nv) return fail(c, TSVD_EINVAL, "k = %d outside [0, min(n1, n2) = %d]", k, nv);
-  if (k == 0) k = nv;
+  fw.n1 = (int)p.n1;
+  fw.n2 = (int)p.n2;
+  fw.nv = std::min(fw.n1, fw.n2);
+  fw.len = std::max(fw.n1, fw.n2);
   if (!warm_plan_exists(c, p))
-    return fail(c, TSVD_EUNSUPPORTED, "no slice plan keeps the rotations of a %d x %d slice", n1, n2);
-  DeviceGuard dg(c->device);
-  if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
-  const int ky = pointer_kind(Y, c->device), ku = pointer_kind(U, c->device);
-  const int ks = pointer_kind(S, c->device), kv = pointer_kind(V, c->device);
-  if (ky < 0 || ku < 0 || ks < 0 || kv < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
+    return fail(c, TSVD_EUNSUPPORTED, "no slice plan keeps the rotations of a %d x %d slice",
+                fw.n1, fw.n2);
+  const int ky = pointer_kind(Y, c->device);
+  if (ky < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
   // the plans (and the scratch sized for them) are those of the V form
   c->vform_now = true;
   WsRequest rq;
   rq.stage_in = ky == 1;
-  Workspace w;
-  TSVD_TRY(prepare_workspace(c, p, rq, w));
-  const TubeGeom& g = p.g;
-  const size_t ns = (size_t)g.nstore, nsl = (size_t)p.nslices;
-  const size_t nU = (size_t)n1 * k, nV = (size_t)n2 * k, nS = (size_t)k * k;
-  const size_t b_w = align_up(ns * len * nv * sizeof(float2));
-  const size_t b_j = align_up(ns * nv * nv * sizeof(float2));
-  const size_t b_s = align_up(ns * nv * sizeof(float));
-  const size_t b_fu = align_up(ns * nU * sizeof(float2)), b_fv = align_up(ns * nV * sizeof(float2));
-  const size_t b_fs = align_up(ns * nS * sizeof(float2));
-  const size_t b_ou = ku == 1 ? align_up(nsl * nU * sizeof(float)) : 0;
-  const size_t b_os = ks == 1 ? align_up(nsl * nS * sizeof(float)) : 0;
-  const size_t b_ov = kv == 1 ? align_up(nsl * nV * sizeof(float)) : 0;
-  const size_t need = b_w + b_j + b_s + b_fu + b_fv + b_fs + b_ou + b_os + b_ov;
+  TSVD_TRY(prepare_workspace(c, p, rq, fw.w));
+  const size_t ns = (size_t)p.g.nstore;
+  const size_t b_w = align_up(ns * fw.len * fw.nv * sizeof(float2));
+  const size_t b_j = align_up(ns * fw.nv * fw.nv * sizeof(float2));
+  const size_t b_s = align_up(ns * fw.nv * sizeof(float));
+  const size_t need = b_w + b_j + b_s + align_up(extra);
   if (need > c->fbuf_cap) {
     if (c->fbuf) {
       TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1436,14 +1430,85 @@ tsvd_status tsvd_factor(tsvd_ctx* c, const float* Y, int order, const int64_t* d
     c->fbuf = static_cast<char*>(ptr);
     c->fbuf_cap = need;
   }
-  char* b = c->fbuf;
-  float2* fW = reinterpret_cast<float2*>(b);
-  float2* fJ = reinterpret_cast<float2*>(b += b_w);
-  float* fsig = reinterpret_cast<float*>(b += b_j);
-  float2* fU = reinterpret_cast<float2*>(b += b_s);
-  float2* fV = reinterpret_cast<float2*>(b += b_fu);
-  float2* fS = reinterpret_cast<float2*>(b += b_fv);
-  b += b_fs;
+  fw.W = reinterpret_cast<float2*>(c->fbuf);
+  fw.J = reinterpret_cast<float2*>(c->fbuf + b_w);
+  fw.sig = reinterpret_cast<float*>(c->fbuf + b_w + b_j);
+  fw.extra = c->fbuf + b_w + b_j + b_s;
+  const float* y = Y;
+  if (ky == 1) {
+    TSVD_CUDA(c, cudaMemcpyAsync(fw.w.stage_in, Y, (size_t)p.N * sizeof(float),
+                                 cudaMemcpyHostToDevice, c->stream));
+    y = fw.w.stage_in;
+  }
+  TubeArgs f = tube_args(p, fw.w, TUBE_FWD);
+  f.in = y;
+  f.spec_out = fw.w.spec_a;
+  TSVD_TRY(run_tube(c, f, "tube pass (forward)"));
+  const float tau_none = 3.0e38f;   // keeps no singular value: the slice pass only factors
+  TSVD_TRY(tune_slices(c, p, fw.w, tau_none));
+  SliceArgs sa = slice_args(c, p, fw.w, tau_none);
+  sa.wout = fw.W;
+  sa.wout_stride = (int64_t)fw.len * fw.nv;
+  sa.sigout = fw.sig;
+  sa.sig_stride = fw.nv;
+  sa.vout = fw.J;
+  sa.vstride = (int64_t)fw.nv * fw.nv;
+  return run_slice(c, sa);
+}
+
+FactorArgs factor_args(const FactorWork& fw, int k) {
+  FactorArgs fa{};
+  fa.W = fw.W;
+  fa.sig = fw.sig;
+  fa.J = fw.J;
+  fa.slices = fw.w.slices;
+  fa.nslices = fw.w.ndistinct;
+  fa.n1 = fw.n1;
+  fa.n2 = fw.n2;
+  fa.k = k;
+  return fa;
+}
+
+// Truncated t-SVD (Algorithm 1, Theorem 2.3.1): the slice SVDs, the Fourier-domain factors
+// ordered by decreasing singular value (factor.cu), one inverse tube pass per factor.
+tsvd_status tsvd_factor(tsvd_ctx* c, const float* Y, int order, const int64_t* dims, int k,
+                        float* U, float* S, float* V) {
+  if (!c) return TSVD_EINVAL;
+  begin_call(c);
+  if (!Y || !U || !S || !V) return fail(c, TSVD_EINVAL, "Y, U, S and V must not be NULL");
+  if ((const void*)U == Y || (const void*)S == Y || (const void*)V == Y || U == S || U == V ||
+      S == V)
+    return fail(c, TSVD_EINVAL, "Y, U, S and V must be distinct buffers");
+  if (!dims || (order != 3 && order != 4)) return fail(c, TSVD_EINVAL, "bad order or dims");
+  for (int d = 0; d < order; ++d)
+    if (dims[d] < 1) return fail(c, TSVD_EINVAL, "dims[%d] = %lld < 1", d, (long long)dims[d]);
+  const int nv0 = (int)std::min(dims[0], dims[1]);
+  if (k < 0 || k > nv0) return fail(c, TSVD_EINVAL, "k = %d outside [0, min(n1, n2) = %d]", k, nv0);
+  if (k == 0) k = nv0;
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
+  const int ku = pointer_kind(U, c->device), ks = pointer_kind(S, c->device);
+  const int kv = pointer_kind(V, c->device);
+  if (ku < 0 || ks < 0 || kv < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
+  int64_t nsl = 1;
+  for (int d = 2; d < order; ++d) nsl *= dims[d];
+  const size_t nU = (size_t)dims[0] * k, nV = (size_t)dims[1] * k, nS = (size_t)k * k;
+  int64_t nst = 1;   // stored Fourier slices, as make_problem counts them
+  for (int d = 2; d < order - 1; ++d) nst *= dims[d];
+  nst *= dims[order - 1] / 2 + 1;
+  const size_t b_fu = align_up((size_t)nst * nU * sizeof(float2));
+  const size_t b_fs = align_up((size_t)nst * nS * sizeof(float2));
+  const size_t b_fv = align_up((size_t)nst * nV * sizeof(float2));
+  const size_t b_ou = ku == 1 ? align_up((size_t)nsl * nU * sizeof(float)) : 0;
+  const size_t b_os = ks == 1 ? align_up((size_t)nsl * nS * sizeof(float)) : 0;
+  const size_t b_ov = kv == 1 ? align_up((size_t)nsl * nV * sizeof(float)) : 0;
+  FactorWork fw;
+  TSVD_TRY(factor_slices(c, Y, order, dims, b_fu + b_fs + b_fv + b_ou + b_os + b_ov, fw));
+  char* b = fw.extra;
+  float2* fU = reinterpret_cast<float2*>(b);
+  float2* fS = reinterpret_cast<float2*>(b += b_fu);
+  float2* fV = reinterpret_cast<float2*>(b += b_fs);
+  b += b_fv;
   // outputs in host memory are written to staging first
   float* oU = U;
   float* oS = S;
@@ -1457,36 +1522,7 @@ tsvd_status tsvd_factor(tsvd_ctx* c, const float* Y, int order, const int64_t* d
     b += b_os;
   }
   if (kv == 1) oV = reinterpret_cast<float*>(b);
-
-  const float* y = Y;
-  if (ky == 1) {
-    TSVD_CUDA(c, cudaMemcpyAsync(w.stage_in, Y, (size_t)p.N * sizeof(float),
-                                 cudaMemcpyHostToDevice, c->stream));
-    y = w.stage_in;
-  }
-  TubeArgs f = tube_args(p, w, TUBE_FWD);
-  f.in = y;
-  f.spec_out = w.spec_a;
-  TSVD_TRY(run_tube(c, f, "tube pass (forward)"));
-  const float tau_none = 3.0e38f;   // keeps no singular value: the slice pass only factors
-  TSVD_TRY(tune_slices(c, p, w, tau_none));
-  SliceArgs sa = slice_args(c, p, w, tau_none);
-  sa.wout = fW;
-  sa.wout_stride = (int64_t)len * nv;
-  sa.sigout = fsig;
-  sa.sig_stride = nv;
-  sa.vout = fJ;
-  sa.vstride = (int64_t)nv * nv;
-  TSVD_TRY(run_slice(c, sa));
-  FactorArgs fa;
-  fa.W = fW;
-  fa.sig = fsig;
-  fa.J = fJ;
-  fa.slices = w.slices;
-  fa.nslices = w.ndistinct;
-  fa.n1 = n1;
-  fa.n2 = n2;
-  fa.k = k;
+  FactorArgs fa = factor_args(fw, k);
   fa.Uh = fU;
   fa.Sh = fS;
   fa.Vh = fV;
@@ -1498,7 +1534,7 @@ tsvd_status tsvd_factor(tsvd_ctx* c, const float* Y, int order, const int64_t* d
     size_t tubes;
   } outs[3] = {{fU, oU, nU}, {fS, oS, nS}, {fV, oV, nV}};
   for (const auto& o : outs) {
-    TubeArgs t = tube_args(p, w, TUBE_INV);
+    TubeArgs t = tube_args(fw.p, fw.w, TUBE_INV);
     t.g.N12 = (int64_t)o.tubes;
     t.spec_in = o.spec;
     t.out0 = o.out;
@@ -1511,8 +1547,109 @@ tsvd_status tsvd_factor(tsvd_ctx* c, const float* Y, int order, const int64_t* d
   if (kv == 1)
     TSVD_CUDA(c, cudaMemcpyAsync(V, oV, nsl * nV * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   bool conv = true;
-  TSVD_TRY(read_slice_stats(c, p, w, nullptr, nullptr, nullptr, &conv));
+  TSVD_TRY(read_slice_stats(c, fw.p, fw.w, nullptr, nullptr, nullptr, &conv));
   if (!conv) return fail(c, TSVD_ENOTCONV, "a slice SVD reached max_sweeps = %d", c->opts.max_sweeps);
+  return TSVD_OK;
+}
+
+// t-SVD compression (Sec. 3, Methods 1 and 2): the slice SVDs, the per-slice numbers of kept
+// terms chosen here from the singular values, the slices rebuilt from their kept terms
+// (factor.cu) and one inverse tube pass.
+tsvd_status tsvd_compress(tsvd_ctx* c, const float* Y, int order, const int64_t* dims, int method,
+                          int64_t k, float* Z, int64_t* kept_total, double* ratio) {
+  if (!c) return TSVD_EINVAL;
+  begin_call(c);
+  if (!Y || !Z) return fail(c, TSVD_EINVAL, "Y and Z must not be NULL");
+  if (method != TSVD_COMPRESS_GLOBAL && method != TSVD_COMPRESS_TUBAL)
+    return fail(c, TSVD_EINVAL, "method must be TSVD_COMPRESS_GLOBAL or TSVD_COMPRESS_TUBAL");
+  if (!dims || (order != 3 && order != 4)) return fail(c, TSVD_EINVAL, "bad order or dims");
+  for (int d = 0; d < order; ++d)
+    if (dims[d] < 1) return fail(c, TSVD_EINVAL, "dims[%d] = %lld < 1", d, (long long)dims[d]);
+  int64_t nsl = 1;
+  for (int d = 2; d < order; ++d) nsl *= dims[d];
+  const int64_t n0 = std::min(dims[0], dims[1]);
+  const int64_t kmax = method == TSVD_COMPRESS_GLOBAL ? n0 * nsl : n0;
+  if (k < 1 || k > kmax)
+    return fail(c, TSVD_EINVAL, "k = %lld outside [1, %lld]", (long long)k, (long long)kmax);
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
+  const int kz = pointer_kind(Z, c->device);
+  if (kz < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
+  int64_t nst = 1;
+  for (int d = 2; d < order - 1; ++d) nst *= dims[d];
+  nst *= dims[order - 1] / 2 + 1;
+  const size_t b_k = align_up((size_t)nst * sizeof(int));
+  const size_t b_z = kz == 1 ? align_up((size_t)nsl * dims[0] * dims[1] * sizeof(float)) : 0;
+  FactorWork fw;
+  TSVD_TRY(factor_slices(c, Y, order, dims, b_k + b_z, fw));
+  const TubeGeom& g = fw.p.g;
+  const int nv = fw.nv;
+  int* kept_dev = reinterpret_cast<int*>(fw.extra);
+  float* z = kz == 1 ? reinterpret_cast<float*>(fw.extra + b_k) : Z;
+  // singular values of the distinct slices -> kept terms per stored slice
+  std::vector<float> sig((size_t)g.nstore * nv);
+  TSVD_CUDA(c, cudaMemcpyAsync(sig.data(), fw.sig, sig.size() * sizeof(float),
+                               cudaMemcpyDeviceToHost, c->stream));
+  TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<int> kept((size_t)g.nstore, 0);
+  int64_t total = 0;
+  if (method == TSVD_COMPRESS_TUBAL) {
+    // Method 2: the first k singular tubes, i.e. the k largest singular values of every slice
+    std::fill(kept.begin(), kept.end(), (int)k);
+    total = k;
+  } else {
+    // Method 1: the k largest f-diagonal entries of S-hat over all n0 * nslices of them (a
+    // distinct stored slice stands for 1 or 2 full-spectrum slices); entries equal to the
+    // k-th largest are all kept, so conjugate slices keep the same terms and Z stays real
+    std::vector<std::pair<float, int>> all;
+    all.reserve((size_t)fw.w.ndistinct * nv);
+    for (int kh = 0; kh < g.hh; ++kh)
+      for (int kf = 0; kf < g.nf; ++kf) {
+        if (!slice_is_distinct(g, kf, kh)) continue;
+        const int q = kf + g.nf * kh, wgt = slice_weight(g, kf, kh);
+        for (int v = 0; v < nv; ++v) all.push_back({sig[(size_t)q * nv + v], wgt});
+      }
+    std::sort(all.begin(), all.end(),
+              [](const std::pair<float, int>& a, const std::pair<float, int>& b) {
+                return a.first > b.first;
+              });
+    int64_t acc = 0;
+    float thr = 0.f;
+    for (const auto& e : all) {
+      acc += e.second;
+      thr = e.first;
+      if (acc >= k) break;
+    }
+    for (int kh = 0; kh < g.hh; ++kh)
+      for (int kf = 0; kf < g.nf; ++kf) {
+        if (!slice_is_distinct(g, kf, kh)) continue;
+        const int q = kf + g.nf * kh;
+        int cnt = 0;
+        for (int v = 0; v < nv; ++v) cnt += sig[(size_t)q * nv + v] >= thr ? 1 : 0;
+        kept[(size_t)q] = cnt;
+        total += (int64_t)cnt * slice_weight(g, kf, kh);
+      }
+  }
+  TSVD_CUDA(c, cudaMemcpyAsync(kept_dev, kept.data(), kept.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, c->stream));
+  FactorArgs fa = factor_args(fw, 1);
+  TSVD_TRY(launch(c, launch_compress_rebuild(fa, kept_dev, fw.w.spec_b, c->cur),
+                  "compression rebuild"));
+  TubeArgs inv = tube_args(fw.p, fw.w, TUBE_INV);
+  inv.spec_in = fw.w.spec_b;
+  inv.out0 = z;
+  TSVD_TRY(run_tube(c, inv, "tube pass (inverse)"));
+  if (kz == 1)
+    TSVD_CUDA(c, cudaMemcpyAsync(Z, z, (size_t)fw.p.N * sizeof(float), cudaMemcpyDeviceToHost,
+                                 c->stream));
+  bool conv = true;
+  TSVD_TRY(read_slice_stats(c, fw.p, fw.w, nullptr, nullptr, nullptr, &conv));
+  if (!conv) return fail(c, TSVD_ENOTCONV, "a slice SVD reached max_sweeps = %d", c->opts.max_sweeps);
+  const double n1 = (double)dims[0], n2 = (double)dims[1];
+  if (kept_total) *kept_total = total;
+  if (ratio)
+    *ratio = method == TSVD_COMPRESS_TUBAL ? n1 * n2 / ((double)total * (n1 + n2 + 1.0))
+                                           : n1 * n2 * (double)nsl / ((double)total * (n1 + n2 + 1.0));
   return TSVD_OK;
 }
 

@@ -144,6 +144,10 @@ struct FactorArgs {
   float2* Vh;           // n2 x k per stored slice
 };
 cudaError_t launch_factor_assemble(const FactorArgs& a, cudaStream_t st);
+// Z-hat of every distinct slice from its kept[s] (per stored slice) largest singular terms
+// (uses W, sig, J, slices, nslices, n1, n2 of `a`); Zh laid out like the stored spectrum.
+cudaError_t launch_compress_rebuild(const FactorArgs& a, const int* kept, float2* Zh,
+                                    cudaStream_t st);
 // Whether launch_jacobi_svt supports an n1 x n2 slice (with scratch available).
 bool jacobi_svt_supported(int n1, int n2);
 // Whether the knobs give a valid plan for `nslices` n1 x n2 slices.

@@ -29,10 +29,11 @@ SCALE_AVG, SCALE_SUM = 0, 1
 
 # Every symbol include/tsvd.h declares.
 EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_last_error",
-                    "tsvt", "tsvd_factor", "tnn_complete", "trpca", "tsvd_solve_batched",
-                    "tsvt_static", "tsvd_cgemm")
+                    "tsvt", "tsvd_factor", "tsvd_compress", "tnn_complete", "trpca",
+                    "tsvd_solve_batched", "tsvt_static", "tsvd_cgemm")
 OP_N, OP_T, OP_C = 0, 1, 2
 WARM_OFF, WARM_ON, WARM_AUTO = 0, 1, 2
+COMPRESS_GLOBAL, COMPRESS_TUBAL = 1, 2
 PROBLEM_COMPLETE, PROBLEM_RPCA = 1, 2
 
 
@@ -111,6 +112,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tsvt.restype = ctypes.c_int
     L.tsvd_factor.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_int, P, P, P]
     L.tsvd_factor.restype = ctypes.c_int
+    L.tsvd_compress.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int64, P,
+                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+    L.tsvd_compress.restype = ctypes.c_int
     L.tnn_complete.argtypes = [P, P, P, ctypes.c_int, i64p, ctypes.c_int, P, P,
                                ctypes.POINTER(Stats)]
     L.tnn_complete.restype = ctypes.c_int
@@ -225,6 +229,20 @@ class Context:
                                  _ptr(S), _ptr(V))
         self._check("tsvd_factor", st)
         return st
+
+    def compress(self, Y, dims: Sequence[int], method: int, k: int, Z):
+        """t-SVD compression (Method 1: COMPRESS_GLOBAL, Method 2: COMPRESS_TUBAL) of Y into Z.
+        Returns (entries kept, compression ratio)."""
+        kept = ctypes.c_int64(0)
+        ratio = ctypes.c_double(0.0)
+        st = self._L.tsvd_compress(self._h, _ptr(Y), len(dims), _dims(dims), int(method), int(k),
+                                   _ptr(Z), ctypes.byref(kept), ctypes.byref(ratio))
+        self._check("tsvd_compress", st)
+        return kept.value, ratio.value
+
+    def raw_compress(self, Y, dims: Sequence[int], method: int, k: int, Z) -> int:
+        return self._L.tsvd_compress(self._h, _ptr(Y), len(dims), _dims(dims), int(method),
+                                     int(k), _ptr(Z), None, None)
 
     def raw_factor(self, Y, dims: Sequence[int], k: int, U, S, V) -> int:
         """tsvd_factor status without raising (argument checks in the tests)."""

@@ -61,6 +61,7 @@ def test_null_arguments_are_rejected_without_touching_a_device():
     dims = (ctypes.c_int64 * 3)(4, 4, 4)
     assert L.tsvt(None, None, None, 3, dims, 1.0, None, None) == libtsvd.TSVD_EINVAL
     assert L.tsvd_factor(None, None, 3, dims, 0, None, None, None) == libtsvd.TSVD_EINVAL
+    assert L.tsvd_compress(None, None, 3, dims, 1, 1, None, None, None) == libtsvd.TSVD_EINVAL
     assert L.tnn_complete(None, None, None, 3, dims, 1, None, None, None) == libtsvd.TSVD_EINVAL
     assert L.trpca(None, None, 3, dims, 1.0, 1, None, None, None) == libtsvd.TSVD_EINVAL
 

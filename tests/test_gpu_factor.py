@@ -1,4 +1,5 @@
-"""tsvd_factor(): the truncated t-SVD (Algorithm 1, Theorem 2.3.1) through the C ABI.
+"""tsvd_factor(): the truncated t-SVD (Algorithm 1, Theorem 2.3.1), and tsvd_compress(): the
+t-SVD compression of Sec. 3 (Methods 1 and 2), through the C ABI.
 
 The factors are unique only up to a phase per (Fourier slice, column), so the tests compare
 what is unique -- U * S * V^T against Y and against the FP64 oracle's truncated t-SVD M_k, the
@@ -213,3 +214,99 @@ def test_factor_argument_errors(fctx):
     assert fctx.raw_factor(y, dims, 0, y, s, v) == libtsvd.TSVD_EINVAL      # output aliases Y
     assert fctx.raw_factor(y, (6, 0, 3), 0, u, s, v) == libtsvd.TSVD_EINVAL
     assert fctx.raw_factor(y, dims, 0, u, s, v) == libtsvd.TSVD_OK
+
+
+# ------------------------------------------------------------------ compression (Sec. 3)
+
+def gpu_compress(ctx, Y, method, k):
+    torch = _torch()
+    y = torch.from_numpy(colmajor(Y)).cuda()
+    z = torch.empty_like(y)
+    kept, ratio = ctx.compress(y, Y.shape, method, k, z)
+    return uncolmajor(z.cpu().numpy(), Y.shape), kept, ratio
+
+
+def oracle_compress(Y, method, k):
+    """Sec. 3 on the oracle's t-SVD (Algorithm 1, 3-way): the f-diagonal of S-hat over all n3
+    slices; Method 1 keeps the k largest entries (all entries equal to the k-th), Method 2 the
+    first k of every slice.  Returns (Z, entries kept)."""
+    Uo, So, Vo = oracle.tsvd(np.asarray(Y, np.float64))
+    Uh, Sh, Vh = (np.fft.fft(X, axis=2) for X in (Uo, So, Vo))
+    n1, n2, n3 = Y.shape
+    n0 = min(n1, n2)
+    sig = np.real(np.stack([np.diagonal(Sh[:, :, q])[:n0] for q in range(n3)], axis=1))
+    if method == libtsvd.COMPRESS_TUBAL:
+        keep = np.zeros_like(sig, dtype=bool)
+        keep[:k] = True
+    else:
+        thr = np.sort(sig.ravel())[::-1][k - 1]
+        keep = sig >= thr
+    Zh = np.zeros((n1, n2, n3), complex)
+    for q in range(n3):
+        idx = np.nonzero(keep[:, q])[0]
+        Zh[:, :, q] = (Uh[:, idx, q] * sig[idx, q]) @ np.conj(Vh[:, idx, q]).T
+    return np.real(np.fft.ifft(Zh, axis=2)), int(keep.sum())
+
+
+@pytest.mark.parametrize("shape", [(36, 28, 7), (28, 44, 8)])
+def test_compression_methods_match_oracle(fctx, shape):
+    """A tubal-rank-3 tensor plus noise: Method 1 with k = 3 n3 and Method 2 with k = 3 keep
+    the signal terms (a wide gap at the cut) and equal the oracle's compression; the ratios are
+    the formulas of Sec. 3."""
+    n1, n2, n3 = shape
+    Y = synth.lowrank_tensor(n1, n2, n3, 3, seed=66)
+    Y = (Y + 0.05 * synth.normal(67, 5, Y.size).reshape(shape, order="F")).astype(np.float32)
+    for method, k in ((libtsvd.COMPRESS_GLOBAL, 3 * n3), (libtsvd.COMPRESS_TUBAL, 3)):
+        Z, kept, ratio = gpu_compress(fctx, Y, method, k)
+        Zo, kept_o = oracle_compress(Y, method, k)
+        assert relerr(Z, Zo) <= 1e-4, method
+        if method == libtsvd.COMPRESS_GLOBAL:
+            assert kept == kept_o == k
+            assert ratio == pytest.approx(n1 * n2 * n3 / (k * (n1 + n2 + 1)), rel=1e-12)
+        else:
+            assert kept == k
+            assert ratio == pytest.approx(n1 * n2 / (k * (n1 + n2 + 1)), rel=1e-12)
+    # Method 2 is the truncated t-SVD of tsvd_factor
+    U, S, V = gpu_factor(fctx, Y, 3)
+    Z2, _, _ = gpu_compress(fctx, Y, libtsvd.COMPRESS_TUBAL, 3)
+    assert relerr(Z2, product_fourier(U, S, V)) <= TOL
+
+
+@pytest.mark.parametrize("shape,k", [((30, 20, 9), 1), ((30, 20, 9), 57), ((20, 33, 8), 100),
+                                     ((12, 10, 3, 6), 90), ((30, 20, 9), 180)])
+def test_global_compression_keeps_the_largest_entries(fctx, shape, k):
+    """Method 1 on Gaussian tensors (3-way and 4-way), any k: at least k entries kept (ties at
+    the cut kept whole), and the error energy is the energy of the discarded Fourier singular
+    values (Parseval, Theorem 2.3.1's identity per entry): Z keeps the largest ones.  k = n0 n3
+    keeps everything."""
+    Y = synth.normal(68, 0, int(np.prod(shape))).reshape(shape, order="F").astype(np.float32)
+    Z, kept, ratio = gpu_compress(fctx, Y, libtsvd.COMPRESS_GLOBAL, k)
+    sv = np.sort(slice_svals(Y).ravel())[::-1]
+    nsl = int(np.prod(shape[2:]))
+    assert k <= kept <= k + 2
+    assert ratio == pytest.approx(shape[0] * shape[1] * nsl / (kept * (shape[0] + shape[1] + 1)),
+                                  rel=1e-12)
+    err2 = np.sum((Y.astype(np.float64) - Z) ** 2)
+    assert err2 == pytest.approx(np.sum(sv[kept:] ** 2) / nsl, rel=1e-3, abs=1e-6 * np.sum(sv ** 2))
+    if kept == sv.size:
+        assert relerr(Z, Y) <= TOL
+
+
+def test_compression_host_buffers_in_place_and_errors(fctx):
+    """Host buffers, Z aliasing Y, and the argument checks."""
+    shape = (24, 18, 6)
+    Y = synth.normal(69, 0, int(np.prod(shape))).reshape(shape, order="F").astype(np.float32)
+    Zd, kept_d, _ = gpu_compress(fctx, Y, libtsvd.COMPRESS_GLOBAL, 40)
+    h = colmajor(Y).copy()
+    kept_h, _ = fctx.compress(h, shape, libtsvd.COMPRESS_GLOBAL, 40, h)     # in place, host
+    assert kept_h == kept_d
+    assert np.array_equal(uncolmajor(h, shape), Zd)
+    torch = _torch()
+    y = torch.from_numpy(colmajor(Y)).cuda()
+    z = torch.empty_like(y)
+    n0 = min(shape[:2])
+    assert fctx.raw_compress(y, shape, 3, 1, z) == libtsvd.TSVD_EINVAL
+    assert fctx.raw_compress(y, shape, libtsvd.COMPRESS_GLOBAL, 0, z) == libtsvd.TSVD_EINVAL
+    assert fctx.raw_compress(y, shape, libtsvd.COMPRESS_GLOBAL, n0 * 6 + 1, z) == libtsvd.TSVD_EINVAL
+    assert fctx.raw_compress(y, shape, libtsvd.COMPRESS_TUBAL, n0 + 1, z) == libtsvd.TSVD_EINVAL
+    assert fctx.raw_compress(y, shape, libtsvd.COMPRESS_TUBAL, n0, z) == libtsvd.TSVD_OK
