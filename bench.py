@@ -85,8 +85,8 @@ WORKLOADS = {
 # DRAM traffic of one jacobi_svt_kernel launch from an ncu capture of the video workload,
 # valid only for the kernel source it was taken on (see profiles/).
 TRAFFIC = {"source": "paper_1407_1785_gb300/csrc/slice_svt.cu",
-           "sha256": "2e3a587e2da225351c88ce8d24ec613d3482a24d483e296c172b993ff092b2db",
-           "bytes_per_launch": 21763328 + 9811200}
+           "sha256": "21c090a1f89b98bb2d32052c08722cd18c9f1190226e1a8ca3914b9624739d58",
+           "bytes_per_launch": 21770240 + 9728512}
 
 
 def parse_args():

@@ -74,13 +74,11 @@ __global__ void __launch_bounds__(256) cgemm_fp32_kernel(CGemm g) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const bool a_rows = g.a.s0 == 1;
   const bool b_ctr = g.b.s0 == 1;
-  // a complex multiply-add as two packed FP32x2 FMAs:
-  //   (re, im) += (ar, ar) (br, bi) + (-ai, ai) (bi, br)
-  float2 acc[4][4];
+  float accr[4][4], acci[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+    for (int c = 0; c < 4; ++c) accr[r][c] = acci[r][c] = 0.f;
   for (int l0 = 0; l0 < g.K; l0 += TK) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -118,14 +116,12 @@ __global__ void __launch_bounds__(256) cgemm_fp32_kernel(CGemm g) {
 #pragma unroll
       for (int c = 0; c < 4; ++c) b[c] = Bs[l][tx + 16 * c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const float2 ar = make_float2(a[r].x, a[r].x), ai = make_float2(-a[r].y, a[r].y);
+      for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          acc[r][c] = __ffma2_rn(ar, b[c], acc[r][c]);
-          acc[r][c] = __ffma2_rn(ai, make_float2(b[c].y, b[c].x), acc[r][c]);
+          accr[r][c] = fmaf(a[r].x, b[c].x, fmaf(-a[r].y, b[c].y, accr[r][c]));
+          acci[r][c] = fmaf(a[r].x, b[c].y, fmaf(a[r].y, b[c].x, acci[r][c]));
         }
-      }
     }
     __syncthreads();
   }
@@ -136,7 +132,7 @@ __global__ void __launch_bounds__(256) cgemm_fp32_kernel(CGemm g) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int j = j0 + tx + 16 * c;
-      if (j < g.N) C[i * g.c.s0 + j * g.c.s1] = acc[r][c];
+      if (j < g.N) C[i * g.c.s0 + j * g.c.s1] = make_float2(accr[r][c], acci[r][c]);
     }
   }
 }
