@@ -546,14 +546,15 @@ __global__ void __launch_bounds__(256) rsvt_refill_kernel(float2* P, const float
   const unsigned long long key =
       mix64(seed ^ ((unsigned long long)(unsigned)iter << 32) ^ (unsigned long long)s);
   float2* Ps = P + (size_t)s * nw * kmax;
-  for (int c = 0; c < kfill; ++c) {
-    const bool need = c >= k || !(sg[c] > 1e-6f * smax);
-    if (!need) continue;
-    for (int e = tid; e < nw; e += nthr) {
-      const unsigned long long ctr = 2ull * ((unsigned long long)c * nw + e);
-      Ps[(size_t)e + (size_t)nw * c] =
-          make_float2(urand(key, ctr), real ? 0.f : urand(key, ctr + 1ull));
-    }
+  // columns to refill, then all their entries spread over the whole CTA
+  __shared__ unsigned char need[128];
+  for (int c = tid; c < kfill; c += nthr) need[c] = (c >= k || !(sg[c] > 1e-6f * smax)) ? 1 : 0;
+  __syncthreads();
+  for (int idx = tid; idx < kfill * nw; idx += nthr) {
+    const int c = idx / nw, e = idx - c * nw;
+    if (!need[c]) continue;
+    const unsigned long long ctr = 2ull * ((unsigned long long)c * nw + e);
+    Ps[(size_t)e + (size_t)nw * c] = make_float2(urand(key, ctr), real ? 0.f : urand(key, ctr + 1ull));
   }
 }
 
@@ -643,6 +644,7 @@ cudaError_t launch_rsvt_state_init(RsvtStat* st_dev, int k0, cudaStream_t st) {
 }
 
 cudaError_t launch_rsvt_refill(const RsvtArgs& a, int k, int kfill, cudaStream_t st) {
+  if (kfill > rsvt_max_k()) return cudaErrorInvalidValue;   // the kernel's column flags
   if (a.nslices <= 0) return cudaSuccess;
   // k = 0 (initialisation) refills every column whatever the device width says
   rsvt_refill_kernel<<<a.nslices, 256, 0, st>>>(a.P, a.sig, a.slices, a.isreal, a.nw, a.kmax, k,
