@@ -11,6 +11,8 @@ batched workload an iteration advances all 64 tensors).  Workloads (`--workload`
            10% entrywise corruption U[-5, 5], lambda = 1/sqrt(320*60), 200 iterations
   color    colour video completion 288x352x3x60 (per-channel textures), 15% observed,
            150 iterations, FFT along modes 3 and 4
+  multiview  5-way multi-view colour video completion 144x176x3x2x40 (a texture per channel
+           and view), 20% observed, 150 iterations, FFT along modes 3, 4 and 5
   lowrank  tubal-rank-3 32x32x16, 50% observed, 100 iterations
   batch    64 tensors of uneven shapes (n1, n2 in [48, 256], n3 in [8, 64]), half completion
            and half RPCA, 100 iterations, one batched call
@@ -69,6 +71,9 @@ WORKLOADS = {
                            "video, 10% of pixel tubes corrupted in 10-frame blocks"),
     "color": dict(kind="complete", iters=150, cpu_iters=1,
                   desc="colour video completion 288x352x3x60, 15% observed"),
+    "multiview": dict(kind="complete", iters=150, cpu_iters=1,
+                      desc="5-way multi-view colour video completion 144x176x3x2x40, 20% "
+                           "observed, DFT along modes 3-5"),
     "lowrank": dict(kind="complete", iters=100, cpu_iters=100,
                     desc="low-tubal-rank completion 32x32x16, rank 3, 50% observed"),
     "factor": dict(kind="factor", iters=1, cpu_iters=1,
@@ -219,13 +224,14 @@ def file_sha256(path):
 
 
 def half_slices(dims):
-    """Distinct Fourier slices the t-SVT computes (conjugate symmetry of the last mode)."""
-    if len(dims) == 3:
-        return dims[2] // 2 + 1
-    n3, n4 = dims[2], dims[3]
-    hh = n4 // 2 + 1
-    self_cols = 1 + (1 if n4 % 2 == 0 else 0)
-    return n3 * hh - self_cols * ((n3 - 1) // 2)
+    """Distinct Fourier slices the t-SVT computes: the half spectrum of the last mode, and on
+    its self-conjugate columns (index 0 and n/2) one of each conjugate pair of indices of
+    modes 3..N-1."""
+    nf = int(np.prod(dims[2:-1])) if len(dims) > 3 else 1
+    nh = dims[-1]
+    self_cols = 1 + (1 if nh % 2 == 0 else 0)
+    self_f = int(np.prod([1 + (1 if n % 2 == 0 else 0) for n in dims[2:-1]]))
+    return nf * (nh // 2 + 1) - self_cols * ((nf - self_f) // 2)
 
 
 def jacobi_gvl_flops(n1, n2, nslices):
@@ -241,7 +247,7 @@ def tube_bytes(dims):
     write W)."""
     N = int(np.prod(dims))
     n12 = dims[0] * dims[1]
-    stored = (dims[2] if len(dims) == 4 else 1) * (dims[-1] // 2 + 1)
+    stored = int(np.prod(dims[2:-1])) * (dims[-1] // 2 + 1)
     sc = 8.0 * n12 * stored
     return 2 * sc + 3 * 4.0 * N
 
@@ -252,8 +258,9 @@ def build_workload(name, seed):
     """Host inputs of one workload: dict with kind, dims, M, omega / lam, truth; for the batch
     a list of such dicts under "items"."""
     from paper_1407_1785_gb300 import synth
-    if name in ("video", "color", "lowrank"):
+    if name in ("video", "color", "multiview", "lowrank"):
         gen = {"video": synth.workload_video_completion, "color": synth.workload_color_video,
+               "multiview": synth.workload_multiview_video,
                "lowrank": synth.workload_lowrank_completion}[name]
         X, om = gen(seed=seed)
         return dict(kind="complete", dims=X.shape, M=(X * om).astype(np.float32), omega=om,

@@ -5,11 +5,12 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- * Tensors.  A real tensor of order 3 (n1 x n2 x n3) or 4 (n1 x n2 x n3 x n4) is a dense FP32
- *   array in MATLAB column-major order: entry (i1, i2, i3[, i4]) (0-based) lives at
- *   i1 + n1*(i2 + n2*(i3 + n3*i4)).  `order` is 3 or 4 and `dims` points to `order` int64
- *   extents, each >= 1.  The transformed modes are 3 (and 4): the Fourier slices of Sec. 2
- *   are taken along them (Algorithm 1, "fft along modes 3..N").
+ * Tensors.  A real tensor of order N = 3..6 (n1 x n2 x n3 x ... x nN) is a dense FP32 array in
+ *   MATLAB column-major order: entry (i1, i2, i3, ...) (0-based) lives at
+ *   i1 + n1*(i2 + n2*(i3 + n3*(...))).  `order` is N and `dims` points to N int64 extents,
+ *   each >= 1.  The transformed modes are 3..N: the Fourier slices of Sec. 2 are taken along
+ *   them (Algorithm 1, "fft along modes 3..N"); for N >= 5 the product n3 * ... * n(N-1) is at
+ *   most 64.  tsvd_solve_batched and tsvt_static take N = 3 or 4.
  * Memory.  Every tensor pointer may be either a device pointer (on the context's device) or
  *   host memory (pinned or pageable); the library asks the CUDA runtime which it is.  Device
  *   tensors are used in place and the call returns as soon as the work is queued on the
@@ -20,7 +21,7 @@
  *   call that fills one of them waits for its stream.
  * Errors.  Every call returns a tsvd_status and never aborts; tsvd_last_error() holds a
  *   one-line reason for the last failure on that context.  TSVD_EINVAL: a null required
- *   pointer, order not 3 or 4, an extent < 1, a non-finite observed entry or a bad scalar.
+ *   pointer, order outside 3..6, an extent < 1, a non-finite observed entry or a bad scalar.
  *   TSVD_EUNSUPPORTED: a shape the kernels do not handle (reported before any work).
  *   TSVD_ECUDA: a CUDA runtime error.  TSVD_ENOTCONV: a tsvt() call whose Jacobi SVD of some
  *   Fourier slice reached max_sweeps (the result is still written); inside the ADMM solvers
@@ -66,7 +67,8 @@ enum { TSVD_PRECISION_FP32 = 0, TSVD_PRECISION_TF32 = 1, TSVD_PRECISION_BF16 = 2
        TSVD_PRECISION_3XTF32 = 3, TSVD_PRECISION_RAND_FP32 = 4 };
 
 /* Sparse penalty of tensor RPCA: entrywise l1 (soft threshold at lambda/rho) or the
- * tube-wise l_{1,1,2} norm of Sec. 5 (eq. sparse2; for order 4 the group is S(i,j,:,:)). */
+ * tube-wise l_{1,1,2} norm of Sec. 5 (eq. sparse2; for order >= 4 the group is every entry
+ * sharing (i, j), S(i,j,:,...,:)). */
 enum { TSVD_SPARSE_ENTRY = 0, TSVD_SPARSE_TUBE = 1 };
 
 /* Threshold of the ADMM low-rank step for penalty rho.  AVG: tau = 1/rho applied to the
@@ -181,7 +183,7 @@ const char* tsvd_last_error(const tsvd_ctx* ctx);
  * values of the unnormalised DFT slices.  Y and Z: dims-shaped tensors (may alias).  Unlike
  * the solvers, tsvt() always waits for its stream before returning (it reports ENOTCONV).
  * multirank (nullable, host): receives the rank of every Fourier slice of Z, prod(dims[2..])
- * int32 in column-major (k3[, k4]) order.  tnn (nullable, host): receives the TNN of Y, the
+ * int32 in column-major (k3, k4, ...) order.  tnn (nullable, host): receives the TNN of Y, the
  * sum of the singular values of all Fourier slices (Thm 2.4.1).  Errors: EINVAL (tau < 0 or
  * not finite), EUNSUPPORTED, ENOTCONV. */
 tsvd_status tsvt(tsvd_ctx* ctx, const float* Y, float* Z, int order, const int64_t* dims,

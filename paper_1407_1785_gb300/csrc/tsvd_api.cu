@@ -136,28 +136,34 @@ struct Problem {
 
 tsvd_status make_problem(tsvd_ctx* c, int order, const int64_t* dims, Problem& p) {
   if (!dims) return fail(c, TSVD_EINVAL, "dims is NULL");
-  if (order != 3 && order != 4) return fail(c, TSVD_EINVAL, "order must be 3 or 4 (got %d)", order);
+  if (order < 3 || order > 6) return fail(c, TSVD_EINVAL, "order must be 3 to 6 (got %d)", order);
   for (int d = 0; d < order; ++d)
     if (dims[d] < 1) return fail(c, TSVD_EINVAL, "dims[%d] = %lld < 1", d, (long long)dims[d]);
   p.order = order;
   p.n1 = dims[0];
   p.n2 = dims[1];
-  p.n3 = dims[2];
-  p.n4 = order == 4 ? dims[3] : 1;
-  if (p.n1 > (1 << 30) || p.n2 > (1 << 30) || p.n3 > (1 << 20) || p.n4 > (1 << 20))
-    return fail(c, TSVD_EUNSUPPORTED, "extent too large");
-  p.nslices = p.n3 * p.n4;
+  for (int d = 2; d < order; ++d)
+    if (dims[d] > (1 << 20)) return fail(c, TSVD_EUNSUPPORTED, "extent too large");
+  if (p.n1 > (1 << 30) || p.n2 > (1 << 30)) return fail(c, TSVD_EUNSUPPORTED, "extent too large");
+  // modes 3..N-1 take the full DFT (their flattened index kf, mode 3 fastest), mode N the
+  // half-spectrum DFT
+  int64_t nf = 1;
+  for (int d = 2; d < order - 1; ++d) nf *= dims[d];
+  if (order >= 5 && nf > 64)
+    return fail(c, TSVD_EUNSUPPORTED, "modes 3..%d hold %lld entries per tube section (at most 64)",
+                order - 1, (long long)nf);
+  if (nf > (1 << 20)) return fail(c, TSVD_EUNSUPPORTED, "extent too large");
+  p.n3 = order == 3 ? dims[2] : nf;
+  p.n4 = order == 3 ? 1 : dims[order - 1];
+  p.nslices = nf * dims[order - 1];
   p.N = p.n1 * p.n2 * p.nslices;
   p.g.N12 = p.n1 * p.n2;
-  if (order == 3) {
-    p.g.nf = 1;
-    p.g.nh = (int)p.n3;
-  } else {
-    p.g.nf = (int)p.n3;
-    p.g.nh = (int)p.n4;
-  }
+  p.g.nf = (int)nf;
+  p.g.nh = (int)dims[order - 1];
   p.g.hh = p.g.nh / 2 + 1;
   p.g.nstore = p.g.nf * p.g.hh;
+  p.g.nfm = order - 3;
+  for (int d = 0; d < p.g.nfm; ++d) p.g.fdim[d] = (int)dims[2 + d];
   if (!tube_pass_supported(p.g))
     return fail(c, TSVD_EUNSUPPORTED, "tube of %lld entries exceeds the tube-pass limit",
                 (long long)p.nslices);
@@ -177,26 +183,49 @@ tsvd_status make_problem(tsvd_ctx* c, int order, const int64_t* dims, Problem& p
 
 // Stored slice (kf, kh) is computed by the t-SVT unless it is the conjugate partner of an
 // earlier stored slice: only possible on the self-conjugate columns kh = 0, nh/2.
+// Flat full index of the conjugate partner of full index kf: (-k3 mod n3, -k4 mod n4, ...).
+int full_partner(const TubeGeom& g, int kf) {
+  if (g.nfm <= 1) return (g.nf - kf) % g.nf;
+  int r = 0, mul = 1, rem = kf;
+  for (int d = 0; d < g.nfm; ++d) {
+    const int n = g.fdim[d], k = rem % n;
+    rem /= n;
+    r += ((n - k) % n) * mul;
+    mul *= n;
+  }
+  return r;
+}
+
+// float2 entries of the twiddle region: the half-mode and full-mode tables, and for more than
+// one full mode the DFT matrix and the partner table (ints in float2 slots).
+size_t twid_count(const TubeGeom& g) {
+  size_t n = (size_t)g.nh + g.nf;
+  if (g.nfm >= 2) n += (size_t)g.nf * g.nf + ((size_t)g.nf + 1) / 2;
+  return n;
+}
+
+// On the self-conjugate half-mode columns (kh = 0, nh/2) a slice and its partner are
+// conjugates: only the one with the smaller full index is computed.
 bool slice_is_distinct(const TubeGeom& g, int kf, int kh) {
   const bool selfcol = (kh == 0) || (2 * kh == g.nh);
-  return !(selfcol && 2 * kf > g.nf);
+  return !(selfcol && full_partner(g, kf) < kf);
 }
 
 // Stored slice that holds full-spectrum slice (kf, kfull) itself or its conjugate.
 int stored_slice_of(const TubeGeom& g, int kf, int kfull) {
   int f = kf, h = kfull;
   if (h >= g.hh) {  // conjugate partner (-kf, -kh)
-    f = (g.nf - kf) % g.nf;
+    f = full_partner(g, kf);
     h = g.nh - kfull;
   }
-  if (!slice_is_distinct(g, f, h)) f = g.nf - f;
+  if (!slice_is_distinct(g, f, h)) f = full_partner(g, f);
   return f + g.nf * h;
 }
 
 // Number of full-spectrum slices a distinct stored slice stands for (1 or 2).
 int slice_weight(const TubeGeom& g, int kf, int kh) {
   const bool selfcol = (kh == 0) || (2 * kh == g.nh);
-  const bool selfrow = (kf == 0) || (2 * kf == g.nf);
+  const bool selfrow = full_partner(g, kf) == kf;
   return (selfcol && selfrow) ? 1 : 2;
 }
 
@@ -350,7 +379,7 @@ SliceKnobs rsvt_knobs(const tsvd_ctx* c) {
 // A stored slice is real when it is its own conjugate partner.
 bool slice_is_real(const TubeGeom& g, int kf, int kh) {
   const bool fh = kh == 0 || 2 * kh == g.nh;
-  const bool ff = kf == 0 || 2 * kf == g.nf;
+  const bool ff = full_partner(g, kf) == kf;
   return fh && ff;
 }
 
@@ -396,7 +425,7 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
   take(5, rq.stage_om ? (size_t)p.N : 0);
   take(6, rq.stage_out0 ? real : 0);
   take(7, rq.stage_out1 ? real : 0);
-  take(8, (size_t)(g.nh + g.nf) * sizeof(float2));
+  take(8, twid_count(g) * sizeof(float2));
   take(9, (size_t)g.nstore * sizeof(int));
   take(10, (size_t)g.nstore * sizeof(SliceStat));
   take(11, sizeof(SweepAccum));
@@ -492,9 +521,36 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
       dst[m] = make_float2((float)cr, (float)sr);
     }
   };
-  c->twid_host.resize((size_t)(g.nh + g.nf));
+  c->twid_host.assign(twid_count(g), make_float2(0.f, 0.f));
   table(g.nh, c->twid_host.data());
   table(g.nf, c->twid_host.data() + g.nh);
+  if (g.nfm >= 2) {
+    // the multi-dimensional DFT over modes 3..N-1 as an nf x nf matrix: the product of the
+    // modes' exact twiddles, in FP64; then the conjugate partner of every full index
+    std::vector<std::vector<float2>> mt((size_t)g.nfm);
+    for (int d = 0; d < g.nfm; ++d) {
+      mt[(size_t)d].resize((size_t)g.fdim[d]);
+      table(g.fdim[d], mt[(size_t)d].data());
+    }
+    float2* fm = c->twid_host.data() + g.nh + g.nf;
+    for (int o = 0; o < g.nf; ++o)
+      for (int f = 0; f < g.nf; ++f) {
+        double re = 1.0, im = 0.0;
+        int ro = o, rf = f;
+        for (int d = 0; d < g.nfm; ++d) {
+          const int n = g.fdim[d], od = ro % n, fd = rf % n;
+          ro /= n;
+          rf /= n;
+          const float2 w = mt[(size_t)d][(size_t)((od * fd) % n)];
+          const double nr = re * w.x - im * w.y, ni = re * w.y + im * w.x;
+          re = nr;
+          im = ni;
+        }
+        fm[(size_t)o * g.nf + f] = make_float2((float)re, (float)im);
+      }
+    int* fp = reinterpret_cast<int*>(fm + (size_t)g.nf * g.nf);
+    for (int kf = 0; kf < g.nf; ++kf) fp[kf] = full_partner(g, kf);
+  }
   TSVD_CUDA(c, cudaMemcpyAsync(w.twid, c->twid_host.data(), c->twid_host.size() * sizeof(float2),
                                cudaMemcpyHostToDevice, c->stream));
   TSVD_CUDA(c, cudaMemcpyAsync(w.slices, c->slices_host.data(),
@@ -514,6 +570,10 @@ TubeArgs tube_args(const Problem& p, const Workspace& w, int mode) {
   a.mode = mode;
   a.twid_h = w.twid;
   a.twid_f = w.twid + p.g.nh;
+  if (p.g.nfm >= 2) {
+    a.fmat = w.twid + p.g.nh + p.g.nf;
+    a.fpart = reinterpret_cast<const int*>(w.twid + p.g.nh + p.g.nf + (size_t)p.g.nf * p.g.nf);
+  }
   a.ratio = 1.f;
   return a;
 }
@@ -1479,7 +1539,7 @@ tsvd_status tsvd_factor(tsvd_ctx* c, const float* Y, int order, const int64_t* d
   if ((const void*)U == Y || (const void*)S == Y || (const void*)V == Y || U == S || U == V ||
       S == V)
     return fail(c, TSVD_EINVAL, "Y, U, S and V must be distinct buffers");
-  if (!dims || (order != 3 && order != 4)) return fail(c, TSVD_EINVAL, "bad order or dims");
+  if (!dims || order < 3 || order > 6) return fail(c, TSVD_EINVAL, "bad order or dims");
   for (int d = 0; d < order; ++d)
     if (dims[d] < 1) return fail(c, TSVD_EINVAL, "dims[%d] = %lld < 1", d, (long long)dims[d]);
   const int nv0 = (int)std::min(dims[0], dims[1]);
@@ -1562,7 +1622,7 @@ tsvd_status tsvd_compress(tsvd_ctx* c, const float* Y, int order, const int64_t*
   if (!Y || !Z) return fail(c, TSVD_EINVAL, "Y and Z must not be NULL");
   if (method != TSVD_COMPRESS_GLOBAL && method != TSVD_COMPRESS_TUBAL)
     return fail(c, TSVD_EINVAL, "method must be TSVD_COMPRESS_GLOBAL or TSVD_COMPRESS_TUBAL");
-  if (!dims || (order != 3 && order != 4)) return fail(c, TSVD_EINVAL, "bad order or dims");
+  if (!dims || order < 3 || order > 6) return fail(c, TSVD_EINVAL, "bad order or dims");
   for (int d = 0; d < order; ++d)
     if (dims[d] < 1) return fail(c, TSVD_EINVAL, "dims[%d] = %lld < 1", d, (long long)dims[d]);
   int64_t nsl = 1;
@@ -1879,6 +1939,8 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
     it.src = &q;
     if (q.kind != TSVD_PROBLEM_COMPLETE && q.kind != TSVD_PROBLEM_RPCA)
       return fail(c, TSVD_EINVAL, "problem %d: bad kind %d", i, q.kind);
+    if (q.order != 3 && q.order != 4)
+      return fail(c, TSVD_EINVAL, "problem %d: batched tensors are 3-way or 4-way", i);
     tsvd_status st = make_problem(c, q.order, q.dims, it.p);
     if (st != TSVD_OK) return fail(c, st, "problem %d: %s", i, c->err.c_str());
     const bool complete = q.kind == TSVD_PROBLEM_COMPLETE;

@@ -15,10 +15,12 @@ namespace tsvd {
 // (float2, column-major), i.e. spectrum entry (t, kf, kh) at t + N12*(kf + nf*kh).
 struct TubeGeom {
   int64_t N12;   // number of tubes (n1*n2)
-  int nf;        // full-DFT mode length (1 for 3-way)
-  int nh;        // half-spectrum mode length
+  int nf;        // full-DFT index length: the product of modes 3..N-1 (1 for 3-way)
+  int nh;        // half-spectrum mode length (mode N)
   int hh;        // nh/2 + 1
   int nstore;    // nf*hh stored Fourier slices
+  int nfm = 0;                  // number of full-DFT modes (N - 3)
+  int fdim[4] = {0, 0, 0, 0};   // their sizes, mode 3 first (its index varies fastest in kf)
 };
 
 // Work modes of the tube pass.
@@ -36,6 +38,12 @@ struct TubeArgs {
   float2* spec_out;       // Vhat (nullable in the last pass)
   const float2* twid_h;   // nh entries (cos, sin)(2 pi m / nh)
   const float2* twid_f;   // nf entries
+  // more than one full-DFT mode (order >= 5): the nf x nf matrix of the multi-dimensional
+  // DFT, fmat[o * nf + f] = exp(+2 pi i sum_d o_d f_d / n_d), and the conjugate partner of
+  // every full index (the flat index of (-k3 mod n3, ...)); nullptr for order <= 4, where the
+  // kernels use twid_f and the partner nf - kf
+  const float2* fmat = nullptr;
+  const int* fpart = nullptr;
   const float* in;        // TUBE_FWD: input tensor; COMPLETE: Yn (NaN = unobserved); RPCA: M
   float* state;           // COMPLETE: V = X + Q;  RPCA: W (scaled dual)
   float* out0;            // INV: output; COMPLETE: X (when write_out); RPCA: L (when last)

@@ -43,7 +43,8 @@ __device__ __forceinline__ Smem carve(unsigned char* raw, const TubeGeom& g) {
 // Spectrum (this thread's column of sp) -> real tube (column of re).  Inverse DFT along the
 // full mode, then complex-to-real along the half mode, scaled by 1/(nf*nh).
 template <int TB>
-__device__ void inverse_tube(const Smem& s, const TubeGeom& g, int tid) {
+__device__ void inverse_tube(const Smem& s, const TubeGeom& g, int tid,
+                             const float2* __restrict__ fm) {
   const int nf = g.nf, nh = g.nh, hh = g.hh;
   float2* sp = s.sp + tid;
   float2* tmp = s.tmp + tid;
@@ -54,7 +55,7 @@ __device__ void inverse_tube(const Smem& s, const TubeGeom& g, int tid) {
         int m = 0;
         for (int kf = 0; kf < nf; ++kf) {
           const float2 x = sp[(size_t)(kf + nf * kh) * TB];
-          const float2 w = s.tw_f[m];
+          const float2 w = fm ? fm[(size_t)jf * nf + kf] : s.tw_f[m];
           ar += x.x * w.x - x.y * w.y;
           ai += x.x * w.y + x.y * w.x;
           m += jf;
@@ -88,7 +89,8 @@ __device__ void inverse_tube(const Smem& s, const TubeGeom& g, int tid) {
 // Real tube (column of re) -> half spectrum (column of sp): real-to-complex DFT along the
 // half mode, then the full complex DFT along the other mode.
 template <int TB>
-__device__ void forward_tube(const Smem& s, const TubeGeom& g, int tid) {
+__device__ void forward_tube(const Smem& s, const TubeGeom& g, int tid,
+                             const float2* __restrict__ fm) {
   const int nf = g.nf, nh = g.nh, hh = g.hh;
   const float* re = s.re + tid;
   float2* sp = s.sp + tid;
@@ -115,7 +117,7 @@ __device__ void forward_tube(const Smem& s, const TubeGeom& g, int tid) {
         int m = 0;
         for (int jf = 0; jf < nf; ++jf) {
           const float2 x = sp[(size_t)(jf + nf * kh) * TB];
-          const float2 w = s.tw_f[m];
+          const float2 w = fm ? fm[(size_t)kf * nf + jf] : s.tw_f[m];
           // x * e^{-i theta}
           ar += x.x * w.x + x.y * w.y;
           ai += x.y * w.x - x.x * w.y;
@@ -129,19 +131,21 @@ __device__ void forward_tube(const Smem& s, const TubeGeom& g, int tid) {
   }
 }
 
-// Load the stored half spectrum of tube t.  For kh = 0 and kh = nh/2 the slices with
-// kf > nf/2 are the complex conjugates of slices nf - kf (the t-SVT only computes the
-// distinct member of each pair), so they are taken from the partner.
+// Load the stored half spectrum of tube t.  For kh = 0 and kh = nh/2 the slices whose
+// conjugate partner has the smaller full index (kf > nf/2 for one full mode: partner nf - kf;
+// several full modes: the table fp) are the complex conjugates of that partner (the t-SVT only
+// computes the distinct member of each pair), so they are taken from the partner.
 template <int TB>
 __device__ void load_spectrum(const Smem& s, const TubeGeom& g, const float2* __restrict__ spec,
-                              int64_t t, int tid) {
+                              int64_t t, int tid, const int* __restrict__ fp) {
   const int nf = g.nf, nh = g.nh, hh = g.hh;
   for (int kh = 0; kh < hh; ++kh) {
     const bool selfcol = (kh == 0) || (2 * kh == nh);
     for (int kf = 0; kf < nf; ++kf) {
       float2 v;
-      if (selfcol && 2 * kf > nf) {
-        v = spec[(size_t)((nf - kf) + nf * kh) * g.N12 + t];
+      const int pk = fp ? fp[kf] : (nf - kf) % nf;
+      if (selfcol && pk < kf) {
+        v = spec[(size_t)(pk + nf * kh) * g.N12 + t];
         v.y = -v.y;
       } else {
         v = spec[(size_t)(kf + nf * kh) * g.N12 + t];
@@ -175,20 +179,20 @@ __global__ void __launch_bounds__(TB) tube_pass_kernel(TubeArgs a) {
   switch (a.mode) {
     case TUBE_FWD: {
       for (int j = 0; j < nreal; ++j) re[(size_t)j * TB] = a.in[t + N12 * j];
-      forward_tube<TB>(s, g, tid);
+      forward_tube<TB>(s, g, tid, a.fmat);
       store_spectrum<TB>(s, g, a.spec_out, t, tid);
       break;
     }
     case TUBE_INV: {
-      load_spectrum<TB>(s, g, a.spec_in, t, tid);
-      inverse_tube<TB>(s, g, tid);
+      load_spectrum<TB>(s, g, a.spec_in, t, tid, a.fpart);
+      inverse_tube<TB>(s, g, tid, a.fmat);
       for (int j = 0; j < nreal; ++j) a.out0[t + N12 * j] = re[(size_t)j * TB];
       break;
     }
     case TUBE_COMPLETE: {
       if (!a.first) {
-        load_spectrum<TB>(s, g, a.spec_in, t, tid);
-        inverse_tube<TB>(s, g, tid);
+        load_spectrum<TB>(s, g, a.spec_in, t, tid, a.fpart);
+        inverse_tube<TB>(s, g, tid, a.fmat);
       }
       for (int j = 0; j < nreal; ++j) {
         const int64_t e = t + N12 * j;
@@ -204,13 +208,13 @@ __global__ void __launch_bounds__(TB) tube_pass_kernel(TubeArgs a) {
         re[(size_t)j * TB] = v;
         if (a.write_out) a.out0[e] = x;
       }
-      forward_tube<TB>(s, g, tid);
+      forward_tube<TB>(s, g, tid, a.fmat);
       store_spectrum<TB>(s, g, a.spec_out, t, tid);
       break;
     }
     case TUBE_RPCA: {
-      load_spectrum<TB>(s, g, a.spec_in, t, tid);
-      inverse_tube<TB>(s, g, tid);
+      load_spectrum<TB>(s, g, a.spec_in, t, tid, a.fpart);
+      inverse_tube<TB>(s, g, tid, a.fmat);
       const float kappa = a.kappa;
       float f = 0.f;
       if (a.tube_sparse) {
@@ -256,7 +260,7 @@ __global__ void __launch_bounds__(TB) tube_pass_kernel(TubeArgs a) {
         }
       }
       if (!a.last) {
-        forward_tube<TB>(s, g, tid);
+        forward_tube<TB>(s, g, tid, a.fmat);
         store_spectrum<TB>(s, g, a.spec_out, t, tid);
       }
       break;
@@ -393,7 +397,7 @@ __device__ __forceinline__ void tile_product(const float* __restrict__ fr, int l
 // Full-mode DFT of length nf of every (kh, tube) column of the spectrum tile, in place:
 // sign +1 (inverse, no scaling) or -1 (forward).
 __device__ void tile_full_dft(const TileSmem& s, const TubeGeom& g, const float2* __restrict__ twf,
-                              float sign) {
+                              float sign, const float2* __restrict__ fm) {
   const int nf = g.nf, hh = g.hh, q4 = tile_q4(g);
   for (int idx = threadIdx.x; idx < hh * TT; idx += TILE_THREADS) {
     const int kh = idx / TT, t = idx % TT;
@@ -406,7 +410,7 @@ __device__ void tile_full_dft(const TileSmem& s, const TubeGeom& g, const float2
       float ar = 0.f, ai = 0.f;
       int m = 0;
       for (int f = 0; f < nf; ++f) {
-        const float2 w = twf[m];
+        const float2 w = fm ? fm[(size_t)o * nf + f] : twf[m];
         const float ws = sign * w.y;
         ar += x[f].x * w.x - x[f].y * ws;
         ai += x[f].x * ws + x[f].y * w.x;
@@ -425,9 +429,10 @@ __device__ void tile_full_dft(const TileSmem& s, const TubeGeom& g, const float2
 
 // Spectrum tile (loaded, weighted) -> real tile.
 template <int RM>
-__device__ void tile_inverse(const TileSmem& s, const TubeGeom& g, const float2* twf) {
+__device__ void tile_inverse(const TileSmem& s, const TubeGeom& g, const float2* twf,
+                             const float2* fm) {
   if (g.nf > 1) {
-    tile_full_dft(s, g, twf, 1.f);
+    tile_full_dft(s, g, twf, 1.f, fm);
     __syncthreads();
   }
   const int nh4 = tile_nh4(g), q4 = tile_q4(g);
@@ -439,14 +444,15 @@ __device__ void tile_inverse(const TileSmem& s, const TubeGeom& g, const float2*
 
 // Real tile -> spectrum tile.
 template <int RM>
-__device__ void tile_forward(const TileSmem& s, const TubeGeom& g, const float2* twf) {
+__device__ void tile_forward(const TileSmem& s, const TubeGeom& g, const float2* twf,
+                             const float2* fm) {
   const int nh4 = tile_nh4(g), q4 = tile_q4(g);
   for (int f = 0; f < g.nf; ++f)
     tile_product<RM, true>(s.fr, s.ldq, s.ldq, s.zt + (size_t)f * nh4 * TT,
                            s.yt + (size_t)f * q4 * TT, 2 * g.hh, nh4);
   __syncthreads();
   if (g.nf > 1) {
-    tile_full_dft(s, g, twf, -1.f);
+    tile_full_dft(s, g, twf, -1.f, fm);
     __syncthreads();
   }
 }
@@ -454,7 +460,8 @@ __device__ void tile_forward(const TileSmem& s, const TubeGeom& g, const float2*
 // Loads the stored spectrum of the tile (conjugate partners on the self-conjugate columns)
 // and applies the C2R weights c_kh / (nf nh).
 __device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
-                                   const float2* __restrict__ spec, int64_t t0) {
+                                   const float2* __restrict__ spec, int64_t t0,
+                                   const int* __restrict__ fp) {
   const int nf = g.nf, nh = g.nh, hh = g.hh, q4 = tile_q4(g);
   const float inv = 1.f / (float)(nf * nh);
   const int total = nf * hh * TT;
@@ -471,8 +478,9 @@ __device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
         const int q = idx / TT;
         const int kf = q % nf, kh = q / nf;
         const bool selfcol = (kh == 0) || (2 * kh == nh);
-        if (selfcol && 2 * kf > nf) {
-          v[u] = spec[(size_t)((nf - kf) + nf * kh) * g.N12 + t0 + t];
+        const int pk = fp ? fp[kf] : (nf - kf) % nf;
+        if (selfcol && pk < kf) {
+          v[u] = spec[(size_t)(pk + nf * kh) * g.N12 + t0 + t];
           v[u].y = -v[u].y;
         } else {
           v[u] = spec[(size_t)q * g.N12 + t0 + t];
@@ -546,9 +554,9 @@ __global__ void __launch_bounds__(TILE_THREADS) tube_tile_kernel(TubeArgs a) {
   }
   const bool need_inv = a.mode == TUBE_INV || a.mode == TUBE_RPCA ||
                         (a.mode == TUBE_COMPLETE && !a.first);
-  if (need_inv) tile_load_spectrum(s, g, a.spec_in, t0);
+  if (need_inv) tile_load_spectrum(s, g, a.spec_in, t0, a.fpart);
   __syncthreads();
-  if (need_inv) tile_inverse<RM>(s, g, a.twid_f);
+  if (need_inv) tile_inverse<RM>(s, g, a.twid_f, a.fmat);
 
   // element (j, t) of the tile; t = tid % TT is fixed per thread (TILE_THREADS % TT == 0).
   // Tube offset j = jf + nf*jh of the tensor (mode 3 fastest) is tile row jf*nh4 + jh.
@@ -706,7 +714,7 @@ __global__ void __launch_bounds__(TILE_THREADS) tube_tile_kernel(TubeArgs a) {
                         (a.mode == TUBE_RPCA && !a.last);
   if (!need_fwd) return;
   __syncthreads();
-  tile_forward<RM>(s, g, a.twid_f);
+  tile_forward<RM>(s, g, a.twid_f, a.fmat);
   tile_store_spectrum(s, g, a.spec_out, t0);
 }
 

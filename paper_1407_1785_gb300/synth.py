@@ -229,6 +229,18 @@ def workload_color_video(seed: int = 1, n1=288, n2=352, n3=3, n4=60, p=0.15):
     return X, omega
 
 
+def workload_multiview_video(seed: int = 1, n1=144, n2=176, nc=3, nv=2, nt=40, p=0.2):
+    """5-way multi-view colour video completion: 144x176 frames x 3 channels x 2 views x 40
+    frames, an independent translating texture per (channel, view), 20% of entries observed.
+    The t-SVD takes the DFT along modes 3, 4 and 5."""
+    X = np.empty((n1, n2, nc, nv, nt))
+    for v in range(nv):
+        for c in range(nc):
+            X[:, :, c, v, :] = translating_texture(n1, n2, nt, seed, channel=c + nc * v)
+    omega = sampling_mask(X.shape, p, seed)
+    return X, omega
+
+
 def workload_batch_shapes(seed: int = 1, count: int = 64):
     """Shapes of the uneven batch: n1, n2 uniform in [48, 256], n3 uniform in [8, 64],
     tubal rank uniform in [2, 12]; even index -> completion with observed fraction in

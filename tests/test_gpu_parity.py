@@ -534,7 +534,7 @@ def test_invalid_arguments(gpu_ctx):
     m = torch.zeros(4 * 4 * 4, device="cuda")
     om = torch.ones(4 * 4 * 4, dtype=torch.uint8, device="cuda")
     x = torch.empty_like(m)
-    assert gpu_ctx.raw_tnn_complete(m, om, 5, (4, 4, 4, 1, 1), 3, x) == libtsvd.TSVD_EINVAL
+    assert gpu_ctx.raw_tnn_complete(m, om, 7, (4, 4, 4, 1, 1, 1, 1), 3, x) == libtsvd.TSVD_EINVAL
     assert gpu_ctx.raw_tnn_complete(m, om, 3, (4, 0, 4), 3, x) == libtsvd.TSVD_EINVAL
     assert gpu_ctx.raw_tnn_complete(m, om, 3, (4, 4, 4), -1, x) == libtsvd.TSVD_EINVAL
     m[5] = float("nan")

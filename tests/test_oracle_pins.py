@@ -24,7 +24,7 @@ def _rng(seed=0):
 # ---------------------------------------------------------------- DFT (Sec. 2.1, Algorithm 1)
 
 @pytest.mark.parametrize("shape", [(3, 4, 1), (3, 4, 2), (2, 3, 7), (4, 2, 8), (2, 2, 3, 4),
-                                   (3, 2, 5, 3)])
+                                   (3, 2, 5, 3), (2, 3, 2, 3, 4), (2, 2, 3, 2, 2, 3)])
 def test_dft_matches_numpy_fft(shape):
     x = _rng(1).standard_normal(shape)
     axes = tuple(range(2, len(shape)))
@@ -184,7 +184,8 @@ def test_tsvt_is_matrix_svt_of_block_circulant(shape, tau):
 
 
 @pytest.mark.parametrize("shape,tau", [((5, 4, 6), 1.5), ((3, 5, 7), 0.8), ((3, 4, 3, 4), 1.0),
-                                       ((2, 3, 4, 5), 0.5), ((3, 3, 2, 1), 0.4)])
+                                       ((2, 3, 4, 5), 0.5), ((3, 3, 2, 1), 0.4),
+                                       ((3, 4, 2, 3, 4), 1.0), ((4, 3, 3, 2, 2, 3), 0.8)])
 def test_tsvt_matches_library_fft_svd(shape, tau):
     """Same result through numpy's FFT over the tube modes and numpy's SVD per slice."""
     Y = _rng(12).standard_normal(shape)
