@@ -40,3 +40,17 @@ def svt_matrix(Y, tau):
     """Textbook singular value thresholding of a matrix via numpy's SVD."""
     U, s, Vh = np.linalg.svd(Y, full_matrices=False)
     return (U * np.maximum(s - tau, 0.0)) @ Vh
+
+
+def lowrank_fourier(shape, rank, seed):
+    """A real tensor of tubal rank <= rank of any order >= 3: A * B with A (n1 x r x ...),
+    B (r x n2 x ...) seeded N(0, 1), the t-product taken slice by slice after numpy's FFT over
+    every mode from 3 on (Def. 2.1.1 extended to order p by the DFT along each such mode)."""
+    from paper_1407_1785_gb300 import synth
+    n1, n2, rest = shape[0], shape[1], tuple(shape[2:])
+    nr = int(np.prod(rest))
+    A = synth.normal(seed, 1, n1 * rank * nr).reshape((n1, rank) + rest, order="F")
+    B = synth.normal(seed, 2, rank * n2 * nr).reshape((rank, n2) + rest, order="F")
+    axes = tuple(range(2, len(shape)))
+    Ch = np.einsum("ik...,kj...->ij...", np.fft.fftn(A, axes=axes), np.fft.fftn(B, axes=axes))
+    return np.real(np.fft.ifftn(Ch, axes=axes))

@@ -12,7 +12,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import colmajor, relerr, uncolmajor
+from helpers import colmajor, lowrank_fourier as lowrank_nd, relerr, uncolmajor
 
 import oracle
 from paper_1407_1785_gb300 import libtsvd, synth
@@ -56,17 +56,6 @@ def gap_threshold(sv, q):
     u = np.unique(sv.ravel())
     i = min(max(int(q * len(u)), 1), len(u) - 1)
     return float(0.5 * (u[i - 1] + u[i]))
-
-
-def lowrank_nd(shape, rank, seed):
-    """A tensor of tubal rank <= rank: A * B with Gaussian A (n1 x r x ...), B (r x n2 x ...),
-    the product taken slice by slice in the Fourier domain (Def. 2.1.1 over every mode >= 3)."""
-    n1, n2, rest = shape[0], shape[1], tuple(shape[2:])
-    A = synth.normal(seed, 1, n1 * rank * int(np.prod(rest))).reshape((n1, rank) + rest, order="F")
-    B = synth.normal(seed, 2, rank * n2 * int(np.prod(rest))).reshape((rank, n2) + rest, order="F")
-    Ah, Bh = fourier(A), fourier(B)
-    Ch = np.einsum("ik...,kj...->ij...", Ah, Bh)
-    return np.real(np.fft.ifftn(Ch, axes=tuple(range(2, len(shape)))))
 
 
 @pytest.fixture(scope="module")

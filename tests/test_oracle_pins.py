@@ -9,7 +9,7 @@ dual scaling) fails at least one of them.
 import numpy as np
 import pytest
 
-from helpers import bcirc, relerr, rse_db, svt_matrix
+from helpers import bcirc, lowrank_fourier, relerr, rse_db, svt_matrix
 
 import oracle
 from paper_1407_1785_gb300 import synth
@@ -271,6 +271,18 @@ def test_shrink_tube_is_group_prox():
     assert np.all(S[1, 2, :] == 0)
 
 
+def test_shrink_tube_groups_every_mode_from_3_on():
+    """For order 5 the tube of (i, j) is S(i, j, :, :, :): the group soft threshold (the
+    closed form of the prox above) with norms over modes 3 to 5."""
+    D = _rng(16).standard_normal((3, 2, 2, 3, 4))
+    D[2, 1] = 0.0
+    kappa = 4.65
+    nrm = np.sqrt((D ** 2).sum(axis=(2, 3, 4), keepdims=True))
+    expect = np.where(nrm > kappa, 1.0 - kappa / np.where(nrm > 0, nrm, 1.0), 0.0) * D
+    assert np.allclose(oracle.shrink(D, kappa, oracle.SPARSE_TUBE), expect, atol=1e-14)
+    assert np.any(nrm > kappa) and np.any((nrm < kappa) & (nrm > 0))
+
+
 # ---------------------------------------------------------------- ADMM completion (Sec. 4)
 
 def test_completion_exact_recovery_lowrank():
@@ -315,6 +327,28 @@ def test_completion_zero_iterations_is_projection():
     Xr, Z = oracle.tnn_complete(X, om, 0)
     assert np.array_equal(Xr, np.where(om == 1, X, 0.0))
     assert np.all(Z == 0)
+
+
+@pytest.mark.parametrize("shape", [(12, 10, 2, 3, 4), (14, 12, 2, 2, 3, 3)])
+def test_completion_order_5_and_6(shape):
+    """Orders 5 and 6: a low-tubal-rank tensor (built with numpy's FFT) is recovered from 60%
+    of its entries, and the scaled dual stays a subgradient of the TNN in every slice of the
+    multi-dimensional DFT (spectral norm <= 1)."""
+    X = lowrank_fourier(shape, 2, 17)
+    om = synth.sampling_mask(shape, 0.6, seed=17)
+    Xr, _ = oracle.tnn_complete(X * om, om, 80)
+    assert np.array_equal(Xr[om == 1], X[om == 1])
+    assert rse_db(Xr, X) < -80.0
+    _, Z, Q, rho = oracle.tnn_complete(X * om, om, 6, rho0=0.05, mu=1.3, with_dual=True)
+    axes = tuple(range(2, len(shape)))
+    G = np.fft.fftn(rho * Q, axes=axes)
+    Zh = np.fft.fftn(Z, axes=axes)
+    for idx in np.ndindex(*shape[2:]):
+        sl = (slice(None), slice(None)) + idx
+        g = np.linalg.norm(G[sl], 2)
+        assert g <= 1 + 1e-8
+        if np.linalg.norm(Zh[sl]) > 1e-8:
+            assert abs(g - 1) < 1e-8
 
 
 # ---------------------------------------------------------------- tensor RPCA (Sec. 5)
