@@ -218,6 +218,19 @@ enum { TSVD_COMPRESS_GLOBAL = 1, TSVD_COMPRESS_TUBAL = 2 };
 tsvd_status tsvd_compress(tsvd_ctx* ctx, const float* Y, int order, const int64_t* dims,
                           int method, int64_t k, float* Z, int64_t* kept_total, double* ratio);
 
+/* t-product C = A * B (Def. 2.1.1): tube (i, j) of C is the sum over l of the circular
+ * convolutions of the tubes A(i, l, :) and B(l, j, :); for order > 3 the convolution runs over
+ * every mode from 3 on, i.e. C-hat = A-hat B-hat in every slice of the DFT along modes 3..N
+ * (Sec. 2.1).  A: dims (n1, n2, n3, ...), order 3 to 6 with the limits of tsvt(); B: (n2, n4,
+ * n3, ...); C: (n1, n4, n3, ...); real FP32, column-major, device or host memory; C must not
+ * alias A or B.  The slice products follow the context's precision (FP32 on CUDA cores for
+ * TSVD_PRECISION_FP32 and RAND_FP32; 3M tensor-core products for TF32, BF16, 3XTF32).
+ * Asynchronous on the context's stream for device buffers; with any buffer in host memory the
+ * call returns after C is written.  Errors: EINVAL (NULL or aliasing buffers, bad order or
+ * dims, n4 < 1), EUNSUPPORTED, ENOMEM. */
+tsvd_status tsvd_tproduct(tsvd_ctx* ctx, const float* A, const float* B, float* C, int order,
+                          const int64_t* dims, int64_t n4);
+
 /* TNN tensor completion (Sec. 4: min ||X||_TNN s.t. P_Omega(X) = P_Omega(M), eq.
  * originalTNN) by the ADMM of eq. proj / eq. shrink / dual ascent with scaled dual Q and
  * penalty schedule rho_{k+1} = min(mu rho_k, rho_max) from opts:

@@ -204,6 +204,55 @@ size_t twid_count(const TubeGeom& g) {
   return n;
 }
 
+// The twiddle region of a tube geometry, in FP64 and rounded once: (cos, sin)(2 pi m / n) for
+// the half mode (n = nh) and the full mode (n = nf), exact at the quarter points; for more
+// than one full mode also the nf x nf matrix of their multi-dimensional DFT (the product of
+// the modes' twiddles) and the conjugate partner of every full index.
+void fill_twiddles(const TubeGeom& g, std::vector<float2>& out) {
+  auto table = [](int n, float2* dst) {
+    for (int m = 0; m < n; ++m) {
+      double cr, sr;
+      if (m == 0) { cr = 1; sr = 0; }
+      else if (2 * m == n) { cr = -1; sr = 0; }
+      else if (4 * m == n) { cr = 0; sr = 1; }
+      else if (4 * m == 3 * n) { cr = 0; sr = -1; }
+      else {
+        const double a = 2.0 * M_PI * (double)m / (double)n;
+        cr = std::cos(a);
+        sr = std::sin(a);
+      }
+      dst[m] = make_float2((float)cr, (float)sr);
+    }
+  };
+  out.assign(twid_count(g), make_float2(0.f, 0.f));
+  table(g.nh, out.data());
+  table(g.nf, out.data() + g.nh);
+  if (g.nfm < 2) return;
+  std::vector<std::vector<float2>> mt((size_t)g.nfm);
+  for (int d = 0; d < g.nfm; ++d) {
+    mt[(size_t)d].resize((size_t)g.fdim[d]);
+    table(g.fdim[d], mt[(size_t)d].data());
+  }
+  float2* fm = out.data() + g.nh + g.nf;
+  for (int o = 0; o < g.nf; ++o)
+    for (int f = 0; f < g.nf; ++f) {
+      double re = 1.0, im = 0.0;
+      int ro = o, rf = f;
+      for (int d = 0; d < g.nfm; ++d) {
+        const int n = g.fdim[d], od = ro % n, fd = rf % n;
+        ro /= n;
+        rf /= n;
+        const float2 w = mt[(size_t)d][(size_t)((od * fd) % n)];
+        const double nr = re * w.x - im * w.y, ni = re * w.y + im * w.x;
+        re = nr;
+        im = ni;
+      }
+      fm[(size_t)o * g.nf + f] = make_float2((float)re, (float)im);
+    }
+  int* fp = reinterpret_cast<int*>(fm + (size_t)g.nf * g.nf);
+  for (int kf = 0; kf < g.nf; ++kf) fp[kf] = full_partner(g, kf);
+}
+
 // On the self-conjugate half-mode columns (kh = 0, nh/2) a slice and its partner are
 // conjugates: only the one with the smaller full index is computed.
 bool slice_is_distinct(const TubeGeom& g, int kf, int kh) {
@@ -505,52 +554,7 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
     TSVD_CUDA(c, cudaMemsetAsync(w.rstat, 0, tsvd_ctx::kRing * sizeof(RsvtStat), c->stream));
   }
 
-  // twiddles (cos, sin)(2 pi m / n) in FP64, exact at the quarter points
-  auto table = [](int n, float2* dst) {
-    for (int m = 0; m < n; ++m) {
-      double cr, sr;
-      if (m == 0) { cr = 1; sr = 0; }
-      else if (2 * m == n) { cr = -1; sr = 0; }
-      else if (4 * m == n) { cr = 0; sr = 1; }
-      else if (4 * m == 3 * n) { cr = 0; sr = -1; }
-      else {
-        const double a = 2.0 * M_PI * (double)m / (double)n;
-        cr = std::cos(a);
-        sr = std::sin(a);
-      }
-      dst[m] = make_float2((float)cr, (float)sr);
-    }
-  };
-  c->twid_host.assign(twid_count(g), make_float2(0.f, 0.f));
-  table(g.nh, c->twid_host.data());
-  table(g.nf, c->twid_host.data() + g.nh);
-  if (g.nfm >= 2) {
-    // the multi-dimensional DFT over modes 3..N-1 as an nf x nf matrix: the product of the
-    // modes' exact twiddles, in FP64; then the conjugate partner of every full index
-    std::vector<std::vector<float2>> mt((size_t)g.nfm);
-    for (int d = 0; d < g.nfm; ++d) {
-      mt[(size_t)d].resize((size_t)g.fdim[d]);
-      table(g.fdim[d], mt[(size_t)d].data());
-    }
-    float2* fm = c->twid_host.data() + g.nh + g.nf;
-    for (int o = 0; o < g.nf; ++o)
-      for (int f = 0; f < g.nf; ++f) {
-        double re = 1.0, im = 0.0;
-        int ro = o, rf = f;
-        for (int d = 0; d < g.nfm; ++d) {
-          const int n = g.fdim[d], od = ro % n, fd = rf % n;
-          ro /= n;
-          rf /= n;
-          const float2 w = mt[(size_t)d][(size_t)((od * fd) % n)];
-          const double nr = re * w.x - im * w.y, ni = re * w.y + im * w.x;
-          re = nr;
-          im = ni;
-        }
-        fm[(size_t)o * g.nf + f] = make_float2((float)re, (float)im);
-      }
-    int* fp = reinterpret_cast<int*>(fm + (size_t)g.nf * g.nf);
-    for (int kf = 0; kf < g.nf; ++kf) fp[kf] = full_partner(g, kf);
-  }
+  fill_twiddles(g, c->twid_host);
   TSVD_CUDA(c, cudaMemcpyAsync(w.twid, c->twid_host.data(), c->twid_host.size() * sizeof(float2),
                                cudaMemcpyHostToDevice, c->stream));
   TSVD_CUDA(c, cudaMemcpyAsync(w.slices, c->slices_host.data(),
@@ -1169,7 +1173,7 @@ size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base, int iters) {
   it.w.spec_b = reinterpret_cast<float2*>(take(spec));
   it.w.state = reinterpret_cast<float*>(take(real));
   it.w.yn = complete ? reinterpret_cast<float*>(take(real)) : nullptr;
-  it.w.twid = reinterpret_cast<float2*>(take((size_t)(g.nh + g.nf) * sizeof(float2)));
+  it.w.twid = reinterpret_cast<float2*>(take(twid_count(g) * sizeof(float2)));
   it.w.slices = reinterpret_cast<int*>(take((size_t)g.nstore * sizeof(int)));
   it.w.stat = reinterpret_cast<SliceStat*>(take((size_t)g.nstore * sizeof(SliceStat)));
   it.w.acc = reinterpret_cast<SweepAccum*>(take(sizeof(SweepAccum)));
@@ -1448,6 +1452,27 @@ struct FactorWork {
   char* extra = nullptr;
 };
 
+// The context's buffer for the factor, compression and t-product calls, grown to `need` bytes
+// (the old one is freed after the stream drains).
+tsvd_status grow_fbuf(tsvd_ctx* c, size_t need) {
+  if (need <= c->fbuf_cap) return TSVD_OK;
+  if (c->fbuf) {
+    TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaFree(c->fbuf);
+    c->fbuf = nullptr;
+    c->fbuf_cap = 0;
+  }
+  void* ptr = nullptr;
+  const cudaError_t e = cudaMalloc(&ptr, need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, TSVD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", need, cudaGetErrorString(e));
+  }
+  c->fbuf = static_cast<char*>(ptr);
+  c->fbuf_cap = need;
+  return TSVD_OK;
+}
+
 tsvd_status factor_slices(tsvd_ctx* c, const float* Y, int order, const int64_t* dims,
                           size_t extra, FactorWork& fw) {
   Problem& p = fw.p;
@@ -1473,23 +1498,7 @@ tsvd_status factor_slices(tsvd_ctx* c, const float* Y, int order, const int64_t*
   const size_t b_w = align_up(ns * fw.len * fw.nv * sizeof(float2));
   const size_t b_j = align_up(ns * fw.nv * fw.nv * sizeof(float2));
   const size_t b_s = align_up(ns * fw.nv * sizeof(float));
-  const size_t need = b_w + b_j + b_s + align_up(extra);
-  if (need > c->fbuf_cap) {
-    if (c->fbuf) {
-      TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
-      cudaFree(c->fbuf);
-      c->fbuf = nullptr;
-      c->fbuf_cap = 0;
-    }
-    void* ptr = nullptr;
-    const cudaError_t e = cudaMalloc(&ptr, need);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(c, TSVD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", need, cudaGetErrorString(e));
-    }
-    c->fbuf = static_cast<char*>(ptr);
-    c->fbuf_cap = need;
-  }
+  TSVD_TRY(grow_fbuf(c, b_w + b_j + b_s + align_up(extra)));
   fw.W = reinterpret_cast<float2*>(c->fbuf);
   fw.J = reinterpret_cast<float2*>(c->fbuf + b_w);
   fw.sig = reinterpret_cast<float*>(c->fbuf + b_w + b_j);
@@ -1710,6 +1719,103 @@ tsvd_status tsvd_compress(tsvd_ctx* c, const float* Y, int order, const int64_t*
   if (ratio)
     *ratio = method == TSVD_COMPRESS_TUBAL ? n1 * n2 / ((double)total * (n1 + n2 + 1.0))
                                            : n1 * n2 * (double)nsl / ((double)total * (n1 + n2 + 1.0));
+  return TSVD_OK;
+}
+
+// t-product C = A * B (Def. 2.1.1; for order > 3 the product of the Fourier slices over every
+// mode from 3 on): forward tube passes of A and B, one complex product per stored Fourier
+// slice, one inverse tube pass.  Slices on the self-conjugate columns whose partner has the
+// smaller full index are computed too (the inverse pass reads their partners instead).
+tsvd_status tsvd_tproduct(tsvd_ctx* c, const float* A, const float* B, float* C, int order,
+                          const int64_t* dims, int64_t n4) {
+  if (!c) return TSVD_EINVAL;
+  begin_call(c);
+  if (!A || !B || !C) return fail(c, TSVD_EINVAL, "A, B and C must not be NULL");
+  if ((const void*)C == A || (const void*)C == B)
+    return fail(c, TSVD_EINVAL, "C must not alias A or B");
+  if (!dims || order < 3 || order > 6) return fail(c, TSVD_EINVAL, "bad order or dims");
+  for (int d = 0; d < order; ++d)
+    if (dims[d] < 1) return fail(c, TSVD_EINVAL, "dims[%d] = %lld < 1", d, (long long)dims[d]);
+  if (n4 < 1 || n4 > (1 << 30)) return fail(c, TSVD_EINVAL, "n4 = %lld outside [1, 2^30]", (long long)n4);
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
+  const int ka = pointer_kind(A, c->device), kb = pointer_kind(B, c->device);
+  const int kc = pointer_kind(C, c->device);
+  if (ka < 0 || kb < 0 || kc < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
+  Problem p;   // the tube geometry of A (B and C share its modes 3..N)
+  TSVD_TRY(make_problem(c, order, dims, p));
+  const int64_t n1 = p.n1, n2 = p.n2, nsl = p.nslices, nst = p.g.nstore;
+  if (n1 > INT32_MAX || n2 > INT32_MAX) return fail(c, TSVD_EUNSUPPORTED, "slice too large");
+  const size_t rA = (size_t)(n1 * n2), rB = (size_t)(n2 * n4), rC = (size_t)(n1 * n4);
+  const size_t b_tw = align_up(twid_count(p.g) * sizeof(float2));
+  const size_t b_fa = align_up((size_t)nst * rA * sizeof(float2));
+  const size_t b_fb = align_up((size_t)nst * rB * sizeof(float2));
+  const size_t b_fc = align_up((size_t)nst * rC * sizeof(float2));
+  const size_t b_sa = ka == 1 ? align_up((size_t)nsl * rA * sizeof(float)) : 0;
+  const size_t b_sb = kb == 1 ? align_up((size_t)nsl * rB * sizeof(float)) : 0;
+  const size_t b_sc = kc == 1 ? align_up((size_t)nsl * rC * sizeof(float)) : 0;
+  TSVD_TRY(grow_fbuf(c, b_tw + b_fa + b_fb + b_fc + b_sa + b_sb + b_sc));
+  char* b = c->fbuf;
+  Workspace w;
+  w.twid = reinterpret_cast<float2*>(b);
+  float2* fA = reinterpret_cast<float2*>(b += b_tw);
+  float2* fB = reinterpret_cast<float2*>(b += b_fa);
+  float2* fC = reinterpret_cast<float2*>(b += b_fb);
+  b += b_fc;
+  const float* a = A;
+  const float* bb = B;
+  float* out = C;
+  if (ka == 1) {
+    float* st = reinterpret_cast<float*>(b);
+    b += b_sa;
+    TSVD_CUDA(c, cudaMemcpyAsync(st, A, nsl * rA * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    a = st;
+  }
+  if (kb == 1) {
+    float* st = reinterpret_cast<float*>(b);
+    b += b_sb;
+    TSVD_CUDA(c, cudaMemcpyAsync(st, B, nsl * rB * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    bb = st;
+  }
+  if (kc == 1) out = reinterpret_cast<float*>(b);
+  fill_twiddles(p.g, c->twid_host);
+  TSVD_CUDA(c, cudaMemcpyAsync(w.twid, c->twid_host.data(), c->twid_host.size() * sizeof(float2),
+                               cudaMemcpyHostToDevice, c->stream));
+  const struct {
+    const float* in;
+    float2* spec;
+    size_t tubes;
+  } ins[2] = {{a, fA, rA}, {bb, fB, rB}};
+  for (const auto& x : ins) {
+    TubeArgs t = tube_args(p, w, TUBE_FWD);
+    t.g.N12 = (int64_t)x.tubes;
+    t.in = x.in;
+    t.spec_out = x.spec;
+    TSVD_TRY(run_tube(c, t, "tube pass (forward)"));
+  }
+  // C-hat_s = A-hat_s B-hat_s for every stored slice s, in batches of at most 65535
+  const int engine = c->opts.precision == TSVD_PRECISION_FP32 ? RSVT_GEMM_FP32 : rsvt_engine(c);
+  for (int64_t s0 = 0; s0 < nst; s0 += 65535) {
+    CGemm g;
+    g.M = (int)n1;
+    g.N = (int)n4;
+    g.K = (int)n2;
+    g.batch = (int)std::min<int64_t>(65535, nst - s0);
+    g.a = CMat{fA + (size_t)s0 * rA, nullptr, (int64_t)rA, 1, n1, 0};
+    g.b = CMat{fB + (size_t)s0 * rB, nullptr, (int64_t)rB, 1, n2, 0};
+    g.c = CMat{fC + (size_t)s0 * rC, nullptr, (int64_t)rC, 1, n1, 0};
+    TSVD_TRY(record_event(c, 0));
+    TSVD_TRY(launch(c, launch_cgemm(g, engine, c->stream), "slice products"));
+    TSVD_TRY(record_event(c, 0));
+  }
+  TubeArgs t = tube_args(p, w, TUBE_INV);
+  t.g.N12 = (int64_t)rC;
+  t.spec_in = fC;
+  t.out0 = out;
+  TSVD_TRY(run_tube(c, t, "tube pass (inverse)"));
+  if (kc == 1)
+    TSVD_CUDA(c, cudaMemcpyAsync(C, out, nsl * rC * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (ka == 1 || kb == 1 || kc == 1) TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
   return TSVD_OK;
 }
 
@@ -1990,24 +2096,7 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
     BatchItem& it = items[(size_t)i];
     carve_item(c, it, c->ws + offs[(size_t)i], iters);
     const TubeGeom& g = it.p.g;
-    it.twid.resize((size_t)(g.nh + g.nf));
-    for (int pass = 0; pass < 2; ++pass) {   // same FP64 tables as the single-tensor calls
-      const int n = pass ? g.nf : g.nh;
-      float2* dst = it.twid.data() + (pass ? g.nh : 0);
-      for (int m = 0; m < n; ++m) {
-        double cr, sr;
-        if (m == 0) { cr = 1; sr = 0; }
-        else if (2 * m == n) { cr = -1; sr = 0; }
-        else if (4 * m == n) { cr = 0; sr = 1; }
-        else if (4 * m == 3 * n) { cr = 0; sr = -1; }
-        else {
-          const double a = 2.0 * M_PI * (double)m / (double)n;
-          cr = std::cos(a);
-          sr = std::sin(a);
-        }
-        dst[m] = make_float2((float)cr, (float)sr);
-      }
-    }
+    fill_twiddles(g, it.twid);   // same FP64 tables as the single-tensor calls
     TSVD_CUDA(c, cudaMemcpyAsync(it.w.twid, it.twid.data(), it.twid.size() * sizeof(float2),
                                  cudaMemcpyHostToDevice, c->stream));
     TSVD_CUDA(c, cudaMemcpyAsync(it.w.slices, it.slices.data(), it.slices.size() * sizeof(int),

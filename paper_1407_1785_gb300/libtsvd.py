@@ -29,7 +29,8 @@ SCALE_AVG, SCALE_SUM = 0, 1
 
 # Every symbol include/tsvd.h declares.
 EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_last_error",
-                    "tsvt", "tsvd_factor", "tsvd_compress", "tnn_complete", "trpca",
+                    "tsvt", "tsvd_factor", "tsvd_compress", "tsvd_tproduct", "tnn_complete",
+                    "trpca",
                     "tsvd_solve_batched", "tsvt_static", "tsvd_cgemm")
 OP_N, OP_T, OP_C = 0, 1, 2
 WARM_OFF, WARM_ON, WARM_AUTO = 0, 1, 2
@@ -115,6 +116,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tsvd_compress.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int64, P,
                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
     L.tsvd_compress.restype = ctypes.c_int
+    L.tsvd_tproduct.argtypes = [P, P, P, P, ctypes.c_int, i64p, ctypes.c_int64]
+    L.tsvd_tproduct.restype = ctypes.c_int
     L.tnn_complete.argtypes = [P, P, P, ctypes.c_int, i64p, ctypes.c_int, P, P,
                                ctypes.POINTER(Stats)]
     L.tnn_complete.restype = ctypes.c_int
@@ -248,6 +251,17 @@ class Context:
         """tsvd_factor status without raising (argument checks in the tests)."""
         return self._L.tsvd_factor(self._h, _ptr(Y), len(dims), _dims(dims), int(k), _ptr(U),
                                    _ptr(S), _ptr(V))
+
+    def tproduct(self, A, B, C, dims: Sequence[int], n4: int):
+        """t-product C = A * B: A dims (n1, n2, ...), B (n2, n4, ...), C (n1, n4, ...)."""
+        st = self._L.tsvd_tproduct(self._h, _ptr(A), _ptr(B), _ptr(C), len(dims), _dims(dims),
+                                   int(n4))
+        self._check("tsvd_tproduct", st)
+        return st
+
+    def raw_tproduct(self, A, B, C, dims: Sequence[int], n4: int) -> int:
+        return self._L.tsvd_tproduct(self._h, _ptr(A), _ptr(B), _ptr(C), len(dims),
+                                     _dims(dims), int(n4))
 
     def tnn_complete(self, M_obs, omega, dims: Sequence[int], iters: int, X_out, Z_out=None,
                      stats: bool = False):

@@ -62,6 +62,7 @@ def test_null_arguments_are_rejected_without_touching_a_device():
     assert L.tsvt(None, None, None, 3, dims, 1.0, None, None) == libtsvd.TSVD_EINVAL
     assert L.tsvd_factor(None, None, 3, dims, 0, None, None, None) == libtsvd.TSVD_EINVAL
     assert L.tsvd_compress(None, None, 3, dims, 1, 1, None, None, None) == libtsvd.TSVD_EINVAL
+    assert L.tsvd_tproduct(None, None, None, None, 3, dims, 4) == libtsvd.TSVD_EINVAL
     assert L.tnn_complete(None, None, None, 3, dims, 1, None, None, None) == libtsvd.TSVD_EINVAL
     assert L.trpca(None, None, 3, dims, 1.0, 1, None, None, None) == libtsvd.TSVD_EINVAL
 
