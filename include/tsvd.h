@@ -194,8 +194,8 @@ tsvd_status tsvt(tsvd_ctx* ctx, const float* Y, float* Z, int order, const int64
  * slice the singular values are taken in decreasing order and the first k kept, so for
  * k = min(n1, n2) U * S * V^T reproduces Y (the economy t-SVD: U^T * U = I), and for smaller k
  * it is M_k, the best approximation of Theorem 2.3.1.  k = 0 means min(n1, n2).
- * Outputs (real, column-major, device or host, not aliasing Y): U dims (n1, k, n3[, n4]),
- * S dims (k, k, n3[, n4]) f-diagonal, V dims (n2, k, n3[, n4]).  The factors are unique up
+ * Outputs (real, column-major, device or host, not aliasing Y): U dims (n1, k, n3, ...),
+ * S dims (k, k, n3, ...) f-diagonal, V dims (n2, k, n3, ...).  The factors are unique up
  * to a phase per (slice, column) in the Fourier domain; U * S * V^T is unique when the k-th
  * and (k+1)-th singular values of every slice differ.  A column whose singular value is 0 is
  * returned as zeros in U (n1 >= n2) or V (n1 < n2).  Plain form (one-sided Jacobi, FP32)

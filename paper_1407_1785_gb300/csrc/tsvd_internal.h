@@ -6,11 +6,11 @@
 
 namespace tsvd {
 
-// Geometry of the tube passes.  A real tensor of order 3 or 4 is stored MATLAB column-major;
+// Geometry of the tube passes.  A real tensor of order 3 to 6 is stored MATLAB column-major;
 // the "tube" of pixel t = i + n1*j is the set of entries t + N12*(jf + nf*jh).  The last
-// transformed mode (length nh) is transformed real-to-complex and only its first
-// hh = nh/2+1 frequencies are kept; the other transformed mode (4-way case, length nf) is a
-// full complex DFT.  A 3-way tensor has nf = 1, nh = n3.
+// mode (length nh) is transformed real-to-complex and only its first hh = nh/2+1 frequencies
+// are kept; modes 3..N-1 (flat index jf, mode 3 fastest, nf entries in all) take a full
+// complex DFT.  A 3-way tensor has nf = 1, nh = n3.
 // Fourier slice (kf, kh) is stored at slice index kf + nf*kh, as an n1 x n2 complex matrix
 // (float2, column-major), i.e. spectrum entry (t, kf, kh) at t + N12*(kf + nf*kh).
 struct TubeGeom {
