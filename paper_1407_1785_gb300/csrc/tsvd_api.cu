@@ -134,7 +134,10 @@ struct Problem {
   TubeGeom g{};
 };
 
-tsvd_status make_problem(tsvd_ctx* c, int order, const int64_t* dims, Problem& p) {
+// Validates dims and fills the geometry.  need_svd: the call runs slice SVDs (their size
+// limits apply); the t-product runs none.
+tsvd_status make_problem(tsvd_ctx* c, int order, const int64_t* dims, Problem& p,
+                         bool need_svd = true) {
   if (!dims) return fail(c, TSVD_EINVAL, "dims is NULL");
   if (order < 3 || order > 6) return fail(c, TSVD_EINVAL, "order must be 3 to 6 (got %d)", order);
   for (int d = 0; d < order; ++d)
@@ -156,6 +159,8 @@ tsvd_status make_problem(tsvd_ctx* c, int order, const int64_t* dims, Problem& p
   p.n3 = order == 3 ? dims[2] : nf;
   p.n4 = order == 3 ? 1 : dims[order - 1];
   p.nslices = nf * dims[order - 1];
+  if (p.n1 * p.n2 > (INT64_MAX / 16) / p.nslices)
+    return fail(c, TSVD_EUNSUPPORTED, "tensor too large");
   p.N = p.n1 * p.n2 * p.nslices;
   p.g.N12 = p.n1 * p.n2;
   p.g.nf = (int)nf;
@@ -167,6 +172,7 @@ tsvd_status make_problem(tsvd_ctx* c, int order, const int64_t* dims, Problem& p
   if (!tube_pass_supported(p.g))
     return fail(c, TSVD_EUNSUPPORTED, "tube of %lld entries exceeds the tube-pass limit",
                 (long long)p.nslices);
+  if (!need_svd) return TSVD_OK;
   if (mixed_precision(c)) {
     // the randomized SVT only runs Jacobi on the projected nw x k matrices
     const int nw = (int)std::min(p.n1, p.n2);
@@ -1743,9 +1749,10 @@ tsvd_status tsvd_tproduct(tsvd_ctx* c, const float* A, const float* B, float* C,
   const int kc = pointer_kind(C, c->device);
   if (ka < 0 || kb < 0 || kc < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
   Problem p;   // the tube geometry of A (B and C share its modes 3..N)
-  TSVD_TRY(make_problem(c, order, dims, p));
+  TSVD_TRY(make_problem(c, order, dims, p, false));
   const int64_t n1 = p.n1, n2 = p.n2, nsl = p.nslices, nst = p.g.nstore;
-  if (n1 > INT32_MAX || n2 > INT32_MAX) return fail(c, TSVD_EUNSUPPORTED, "slice too large");
+  if (std::max(n1, n2) * n4 > (INT64_MAX / 16) / nsl)
+    return fail(c, TSVD_EUNSUPPORTED, "tensor too large");
   const size_t rA = (size_t)(n1 * n2), rB = (size_t)(n2 * n4), rC = (size_t)(n1 * n4);
   const size_t b_tw = align_up(twid_count(p.g) * sizeof(float2));
   const size_t b_fa = align_up((size_t)nst * rA * sizeof(float2));

@@ -80,6 +80,14 @@ def test_tproduct_matches_oracle(ctx, sa, n4):
     assert relerr(C, oracle_tproduct(A, B)) <= TOL
 
 
+def test_tproduct_slices_beyond_the_svd_limits(ctx):
+    """The t-product runs no slice SVD: 600 x 700 slices (larger than any slice the t-SVT
+    takes) are fine."""
+    A = rand((600, 700, 3), 78)
+    B = rand((700, 30, 3), 79)
+    assert relerr(gpu_tproduct(ctx, A, B), oracle_tproduct(A, B)) <= TOL
+
+
 def test_tproduct_identity_and_host_buffers(ctx):
     """A * I = A for the identity tensor (first frontal slice I, the rest 0; Def. 2.1.3), and
     host buffers give the bits of device buffers."""
