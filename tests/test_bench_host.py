@@ -1,0 +1,59 @@
+"""Host-side accounting of bench.py (CPU): the counts and byte figures its roofline lines are
+built from, against brute force over the Fourier indices."""
+import itertools
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def distinct_brute(dims):
+    """Fourier slices of a real tensor up to conjugation, taking the first half (and the
+    middle) of the last mode: the slices whose SVD the t-SVT computes."""
+    modes = dims[2:]
+    nh = modes[-1]
+    seen, count = set(), 0
+    for k in itertools.product(*[range(n) for n in modes]):
+        if k[-1] > nh // 2:
+            continue
+        partner = tuple((-x) % n for x, n in zip(k, modes))
+        if partner in seen:
+            continue
+        seen.add(k)
+        count += 1
+    return count
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 1), (4, 4, 7), (4, 4, 8), (2, 2, 100), (2, 2, 3, 60),
+                                  (2, 2, 4, 6), (2, 2, 1, 5), (2, 2, 3, 2, 40), (2, 2, 2, 2, 2),
+                                  (2, 2, 2, 4, 2, 6), (2, 2, 3, 3, 3, 3), (2, 2, 8, 8, 3)])
+def test_distinct_slices_match_brute_force(dims):
+    assert bench.half_slices(dims) == distinct_brute(dims)
+
+
+def test_distinct_slices_cover_the_spectrum():
+    """Every Fourier slice is a distinct slice or the conjugate of one: the distinct count is
+    (P + s) / 2 where s counts the self-conjugate slices (indices with 2k = 0 mod n on every
+    mode)."""
+    for dims in [(2, 2, 6), (2, 2, 5, 4), (2, 2, 3, 2, 40), (2, 2, 2, 3, 4, 5)]:
+        modes = dims[2:]
+        P = int(np.prod(modes))
+        s = int(np.prod([1 + (n % 2 == 0) for n in modes]))
+        assert bench.half_slices(dims) == (P + s) // 2
+
+
+@pytest.mark.parametrize("dims", [(144, 176, 100), (288, 352, 3, 60), (144, 176, 3, 2, 40)])
+def test_tube_bytes_is_two_spectra_and_three_real_tensors(dims):
+    n12 = dims[0] * dims[1]
+    stored = int(np.prod(dims[2:-1])) * (dims[-1] // 2 + 1)
+    N = int(np.prod(dims))
+    assert bench.tube_bytes(dims) == 2 * 8 * n12 * stored + 3 * 4 * N
+    if dims == (144, 176, 100):
+        assert bench.tube_bytes(dims) == pytest.approx(51.1e6, rel=1e-3)
