@@ -76,8 +76,12 @@ def lib() -> ctypes.CDLL:
         L.orc_tproduct.argtypes = [c_i64, c_i64, c_i64, c_i64, P, P, P]
         L.orc_ttranspose.argtypes = [c_i64, c_i64, c_i64, P, P]
         L.orc_tsvd.argtypes = [c_i64, c_i64, c_i64, P, P, P, P]
+        L.orc_tproduct_nd.argtypes = [c_int, i64p, c_i64, P, P, P]
+        L.orc_ttranspose_nd.argtypes = [c_int, i64p, P, P]
+        L.orc_tsvd_nd.argtypes = [c_int, i64p, P, P, P, P]
         for name in ("orc_dft", "orc_svd", "orc_tsvt", "orc_tnn_complete", "orc_trpca",
-                     "orc_shrink", "orc_tproduct", "orc_ttranspose", "orc_tsvd"):
+                     "orc_shrink", "orc_tproduct", "orc_ttranspose", "orc_tsvd",
+                     "orc_tproduct_nd", "orc_ttranspose_nd", "orc_tsvd_nd"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -217,33 +221,50 @@ def shrink(D: np.ndarray, kappa: float, mode: int = SPARSE_ENTRY) -> np.ndarray:
 
 
 def tproduct(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """t-product A * B (Def. 2.1.1; for order > 3 through the DFT along every mode from 3 on):
+    A (n1, n2, ...), B (n2, n4, ...) -> (n1, n4, ...)."""
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
-    n1, n2, n3 = A.shape
-    n2b, n4, n3b = B.shape
-    assert n2 == n2b and n3 == n3b
+    assert A.ndim >= 3 and B.ndim == A.ndim
+    assert A.shape[1] == B.shape[0] and A.shape[2:] == B.shape[2:]
+    n1, n2, n4, rest = A.shape[0], A.shape[1], B.shape[1], A.shape[2:]
     a, b = _f64(A), _f64(B)
-    c = np.zeros(n1 * n4 * n3, np.float64)
-    _check("tproduct", lib().orc_tproduct(n1, n2, n4, n3, _ptr(a), _ptr(b), _ptr(c)))
-    return _unflat(c, (n1, n4, n3))
+    c = np.zeros(n1 * n4 * int(np.prod(rest)), np.float64)
+    if A.ndim == 3:
+        _check("tproduct", lib().orc_tproduct(n1, n2, n4, rest[0], _ptr(a), _ptr(b), _ptr(c)))
+    else:
+        _check("tproduct", lib().orc_tproduct_nd(A.ndim, _dims(A.shape), n4, _ptr(a), _ptr(b),
+                                                 _ptr(c)))
+    return _unflat(c, (n1, n4) + rest)
 
 
 def ttranspose(A: np.ndarray) -> np.ndarray:
+    """Tensor transpose (Def. 2.1.2): (n1, n2, ...) -> (n2, n1, ...)."""
     A = np.asarray(A, dtype=np.float64)
-    n1, n2, n3 = A.shape
+    assert A.ndim >= 3
+    n1, n2, rest = A.shape[0], A.shape[1], A.shape[2:]
     a = _f64(A)
     t = np.zeros_like(a)
-    _check("ttranspose", lib().orc_ttranspose(n1, n2, n3, _ptr(a), _ptr(t)))
-    return _unflat(t, (n2, n1, n3))
+    if A.ndim == 3:
+        _check("ttranspose", lib().orc_ttranspose(n1, n2, rest[0], _ptr(a), _ptr(t)))
+    else:
+        _check("ttranspose", lib().orc_ttranspose_nd(A.ndim, _dims(A.shape), _ptr(a), _ptr(t)))
+    return _unflat(t, (n2, n1) + rest)
 
 
 def tsvd(M: np.ndarray):
-    """Full t-SVD M = U * S * V^T; returns real (U, S, V)."""
+    """Full t-SVD M = U * S * V^T (order 3 to 6); returns real (U, S, V)."""
     M = np.asarray(M, dtype=np.float64)
-    n1, n2, n3 = M.shape
+    assert M.ndim >= 3
+    n1, n2, rest = M.shape[0], M.shape[1], M.shape[2:]
+    ns = int(np.prod(rest))
     m = _f64(M)
-    U = np.zeros(n1 * n1 * n3)
-    S = np.zeros(n1 * n2 * n3)
-    V = np.zeros(n2 * n2 * n3)
-    _check("tsvd", lib().orc_tsvd(n1, n2, n3, _ptr(m), _ptr(U), _ptr(S), _ptr(V)))
-    return (_unflat(U, (n1, n1, n3)), _unflat(S, (n1, n2, n3)), _unflat(V, (n2, n2, n3)))
+    U = np.zeros(n1 * n1 * ns)
+    S = np.zeros(n1 * n2 * ns)
+    V = np.zeros(n2 * n2 * ns)
+    if M.ndim == 3:
+        _check("tsvd", lib().orc_tsvd(n1, n2, rest[0], _ptr(m), _ptr(U), _ptr(S), _ptr(V)))
+    else:
+        _check("tsvd", lib().orc_tsvd_nd(M.ndim, _dims(M.shape), _ptr(m), _ptr(U), _ptr(S),
+                                         _ptr(V)))
+    return (_unflat(U, (n1, n1) + rest), _unflat(S, (n1, n2) + rest), _unflat(V, (n2, n2) + rest))

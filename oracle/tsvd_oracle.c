@@ -18,7 +18,8 @@
  *   - tensor RPCA ADMM: eq. low_rank, eq. sparse (closed form eq. sparse2) and eq. dual of
  *     Sec. 5;
  *   - t-product (Def. 2.1.1 via the FFT route of Sec. 2.1), tensor transpose (Def. 2.1.2),
- *     full t-SVD (Theorem 2.2.1 / Algorithm 1).
+ *     full t-SVD (Theorem 2.2.1 / Algorithm 1), for order 3 and, through Algorithm 1's loop
+ *     over modes 3..N, for orders up to 6.
  *
  * Layout: every tensor is MATLAB column-major; entry (i1,i2,i3[,i4]) lives at
  * i1 + n1*(i2 + n2*(i3 + n3*i4)).  Complex values are C99 double complex.
@@ -94,8 +95,8 @@ static int check_dims(int order, const int64_t* dims)
 }
 
 /* ------------------------------------------------------------------------------------------
- * DFT along one mode (Sec. 2.1: "performing the fast Fourier transformation (FFT) along the
- * tube fibers"; Algorithm 1: D <- fft(M,[],i) for i = 3..N).  A naive sum per fiber:
+ * DFT along one mode (Sec. 2.1 computes the t-product and the t-SVD with FFTs along the tubes;
+ * Algorithm 1 transforms along each mode i = 3..N in turn).  A naive sum per fiber:
  *     forward  y[k] = sum_t x[t] exp(-2 pi i t k / n)
  *     inverse  y[t] = (1/n) sum_k x[k] exp(+2 pi i t k / n)
  * The phase index t*k is reduced modulo n before the angle is formed.
@@ -536,40 +537,59 @@ int orc_trpca(int order, const int64_t* dims, const double* M, double lambda, in
  * ---------------------------------------------------------------------------------------- */
 
 /* t-product C = A * B (Def. 2.1.1), computed by the FFT route of Sec. 2.1: DFT both along
- * mode 3, multiply matching frontal slices, inverse DFT.  A is n1 x n2 x n3, B is n2 x n4 x n3,
- * C is n1 x n4 x n3. */
-int orc_tproduct(int64_t n1, int64_t n2, int64_t n4, int64_t n3, const double* A, const double* B,
-                 double* C)
+ * modes 3..N (for N = 3 the mode-3 DFT of the definition; for N > 3 the loop of Algorithm 1
+ * over every mode from 3 on, so that the product is the multi-dimensional circular
+ * convolution of the tubes), multiply matching Fourier slices, inverse DFT.  A has dims
+ * (n1, n2, n3, ...), B (n2, n4, n3, ...), C (n1, n4, n3, ...). */
+int orc_tproduct_nd(int order, const int64_t* dims, int64_t n4, const double* A, const double* B,
+                    double* C)
 {
-    if (n1 < 1 || n2 < 1 || n3 < 1 || n4 < 1 || !A || !B || !C) return ORC_EINVAL;
-    const int64_t da[3] = {n1, n2, n3}, db[3] = {n2, n4, n3}, dc[3] = {n1, n4, n3};
-    cplx* Ah = (cplx*)malloc(sizeof(cplx) * (size_t)(n1 * n2 * n3));
-    cplx* Bh = (cplx*)malloc(sizeof(cplx) * (size_t)(n2 * n4 * n3));
-    cplx* Ch = (cplx*)calloc((size_t)(n1 * n4 * n3), sizeof(cplx));
-    for (int64_t i = 0; i < n1 * n2 * n3; ++i) Ah[i] = A[i];
-    for (int64_t i = 0; i < n2 * n4 * n3; ++i) Bh[i] = B[i];
-    dft_tubes(Ah, 3, da, 0);
-    dft_tubes(Bh, 3, db, 0);
-    for (int64_t k = 0; k < n3; ++k)
+    if (order < 3 || !check_dims(order, dims) || n4 < 1 || !A || !B || !C) return ORC_EINVAL;
+    const int64_t n1 = dims[0], n2 = dims[1], ns = prod_dims(dims, 2, order);
+    int64_t db[ORC_MAX_ORDER], dc[ORC_MAX_ORDER];
+    for (int d = 0; d < order; ++d) db[d] = dc[d] = dims[d];
+    db[0] = n2;
+    db[1] = n4;
+    dc[1] = n4;
+    cplx* Ah = (cplx*)malloc(sizeof(cplx) * (size_t)(n1 * n2 * ns));
+    cplx* Bh = (cplx*)malloc(sizeof(cplx) * (size_t)(n2 * n4 * ns));
+    cplx* Ch = (cplx*)calloc((size_t)(n1 * n4 * ns), sizeof(cplx));
+    if (!Ah || !Bh || !Ch) { free(Ah); free(Bh); free(Ch); return ORC_ENOMEM; }
+    for (int64_t i = 0; i < n1 * n2 * ns; ++i) Ah[i] = A[i];
+    for (int64_t i = 0; i < n2 * n4 * ns; ++i) Bh[i] = B[i];
+    dft_tubes(Ah, order, dims, 0);
+    dft_tubes(Bh, order, db, 0);
+    for (int64_t k = 0; k < ns; ++k)
         for (int64_t j = 0; j < n4; ++j)
             for (int64_t l = 0; l < n2; ++l) {
                 const cplx b = Bh[l + j * n2 + k * n2 * n4];
                 for (int64_t i = 0; i < n1; ++i)
                     Ch[i + j * n1 + k * n1 * n4] += Ah[i + l * n1 + k * n1 * n2] * b;
             }
-    dft_tubes(Ch, 3, dc, 1);
-    for (int64_t i = 0; i < n1 * n4 * n3; ++i) C[i] = creal(Ch[i]);
+    dft_tubes(Ch, order, dc, 1);
+    for (int64_t i = 0; i < n1 * n4 * ns; ++i) C[i] = creal(Ch[i]);
     free(Ah); free(Bh); free(Ch);
     return ORC_OK;
 }
 
-/* Tensor transpose (Def. 2.1.2): transpose every frontal slice, then reverse the order of
- * slices 2..n3.  A is n1 x n2 x n3, AT is n2 x n1 x n3. */
-int orc_ttranspose(int64_t n1, int64_t n2, int64_t n3, const double* A, double* AT)
+int orc_tproduct(int64_t n1, int64_t n2, int64_t n4, int64_t n3, const double* A, const double* B,
+                 double* C)
 {
-    if (n1 < 1 || n2 < 1 || n3 < 1 || !A || !AT) return ORC_EINVAL;
-    for (int64_t k = 0; k < n3; ++k) {
-        const int64_t src = (k == 0) ? 0 : n3 - k;
+    const int64_t da[3] = {n1, n2, n3};
+    return orc_tproduct_nd(3, da, n4, A, B, C);
+}
+
+/* Tensor transpose (Def. 2.1.2): transpose every frontal slice, then reverse the order of
+ * slices 2..n3; for order N > 3 the slice at (k3, ..., kN) takes the transposed slice at
+ * (-k3 mod n3, ..., -kN mod nN), the conjugate partner, so that the transpose is the
+ * conjugate transpose of every Fourier slice for any order.  A has dims (n1, n2, ...), AT
+ * (n2, n1, ...). */
+int orc_ttranspose_nd(int order, const int64_t* dims, const double* A, double* AT)
+{
+    if (order < 3 || !check_dims(order, dims) || !A || !AT) return ORC_EINVAL;
+    const int64_t n1 = dims[0], n2 = dims[1], ns = prod_dims(dims, 2, order);
+    for (int64_t k = 0; k < ns; ++k) {
+        const int64_t src = conj_partner(order, dims, k);
         for (int64_t j = 0; j < n2; ++j)
             for (int64_t i = 0; i < n1; ++i)
                 AT[j + i * n2 + k * n2 * n1] = A[i + j * n1 + src * n1 * n2];
@@ -577,25 +597,40 @@ int orc_ttranspose(int64_t n1, int64_t n2, int64_t n3, const double* A, double* 
     return ORC_OK;
 }
 
-/* Full t-SVD M = U * S * V^T (Theorem 2.2.1) by Algorithm 1: DFT along mode 3, full SVD of
- * each Fourier slice (shared by conjugate partners, real on self-conjugate slices), inverse
- * DFT of the three factor tensors.  U is n1 x n1 x n3, S is n1 x n2 x n3, V is n2 x n2 x n3,
- * all real.  Returns ORC_EIMAG if an inverse-transformed factor is not real. */
-int orc_tsvd(int64_t n1, int64_t n2, int64_t n3, const double* M, double* U, double* S, double* V)
+int orc_ttranspose(int64_t n1, int64_t n2, int64_t n3, const double* A, double* AT)
 {
-    if (n1 < 1 || n2 < 1 || n3 < 1 || !M || !U || !S || !V) return ORC_EINVAL;
+    const int64_t da[3] = {n1, n2, n3};
+    return orc_ttranspose_nd(3, da, A, AT);
+}
+
+/* Full t-SVD M = U * S * V^T (Theorem 2.2.1) by Algorithm 1: DFT along modes 3..N, full SVD
+ * of each Fourier slice (shared by conjugate partners, real on self-conjugate slices),
+ * inverse DFT of the three factor tensors.  M has dims (n1, n2, n3, ...); U (n1, n1, ...),
+ * S (n1, n2, ...), V (n2, n2, ...), all real.  Returns ORC_EIMAG if an inverse-transformed
+ * factor is not real. */
+int orc_tsvd_nd(int order, const int64_t* dims, const double* M, double* U, double* S, double* V)
+{
+    if (order < 3 || !check_dims(order, dims) || !M || !U || !S || !V) return ORC_EINVAL;
+    const int64_t n1 = dims[0], n2 = dims[1], ns = prod_dims(dims, 2, order);
     const int64_t k0 = n1 < n2 ? n1 : n2;
-    const int64_t dm[3] = {n1, n2, n3}, du[3] = {n1, n1, n3}, dv[3] = {n2, n2, n3};
-    cplx* Mh = (cplx*)malloc(sizeof(cplx) * (size_t)(n1 * n2 * n3));
-    cplx* Uh = (cplx*)malloc(sizeof(cplx) * (size_t)(n1 * n1 * n3));
-    cplx* Sh = (cplx*)calloc((size_t)(n1 * n2 * n3), sizeof(cplx));
-    cplx* Vh = (cplx*)malloc(sizeof(cplx) * (size_t)(n2 * n2 * n3));
+    int64_t du[ORC_MAX_ORDER], dv[ORC_MAX_ORDER];
+    for (int d = 0; d < order; ++d) du[d] = dv[d] = dims[d];
+    du[1] = n1;
+    dv[0] = n2;
+    cplx* Mh = (cplx*)malloc(sizeof(cplx) * (size_t)(n1 * n2 * ns));
+    cplx* Uh = (cplx*)malloc(sizeof(cplx) * (size_t)(n1 * n1 * ns));
+    cplx* Sh = (cplx*)calloc((size_t)(n1 * n2 * ns), sizeof(cplx));
+    cplx* Vh = (cplx*)malloc(sizeof(cplx) * (size_t)(n2 * n2 * ns));
     double* sg = (double*)malloc(sizeof(double) * (size_t)k0);
-    for (int64_t i = 0; i < n1 * n2 * n3; ++i) Mh[i] = M[i];
-    dft_tubes(Mh, 3, dm, 0);
+    if (!Mh || !Uh || !Sh || !Vh || !sg) {
+        free(Mh); free(Uh); free(Sh); free(Vh); free(sg);
+        return ORC_ENOMEM;
+    }
+    for (int64_t i = 0; i < n1 * n2 * ns; ++i) Mh[i] = M[i];
+    dft_tubes(Mh, order, dims, 0);
     int status = ORC_OK;
-    for (int64_t k = 0; k < n3; ++k) {
-        const int64_t p = (n3 - k) % n3;
+    for (int64_t k = 0; k < ns; ++k) {
+        const int64_t p = conj_partner(order, dims, k);
         cplx* Uk = Uh + k * n1 * n1;
         cplx* Vk = Vh + k * n2 * n2;
         cplx* Sk = Sh + k * n1 * n2;
@@ -614,14 +649,20 @@ int orc_tsvd(int64_t n1, int64_t n2, int64_t n3, const double* M, double* U, dou
         if (svd_full(n1, n2, A, Uk, sg, Vk) < 0) status = ORC_ENOTCONV;
         for (int64_t i = 0; i < k0; ++i) Sk[i + i * n1] = sg[i];
     }
-    dft_tubes(Uh, 3, du, 1);
-    dft_tubes(Sh, 3, dm, 1);
-    dft_tubes(Vh, 3, dv, 1);
+    dft_tubes(Uh, order, du, 1);
+    dft_tubes(Sh, order, dims, 1);
+    dft_tubes(Vh, order, dv, 1);
     double im = 0, re = 0;
-    for (int64_t i = 0; i < n1 * n1 * n3; ++i) { U[i] = creal(Uh[i]); re += creal(Uh[i]) * creal(Uh[i]); im += cimag(Uh[i]) * cimag(Uh[i]); }
-    for (int64_t i = 0; i < n1 * n2 * n3; ++i) { S[i] = creal(Sh[i]); re += creal(Sh[i]) * creal(Sh[i]); im += cimag(Sh[i]) * cimag(Sh[i]); }
-    for (int64_t i = 0; i < n2 * n2 * n3; ++i) { V[i] = creal(Vh[i]); re += creal(Vh[i]) * creal(Vh[i]); im += cimag(Vh[i]) * cimag(Vh[i]); }
+    for (int64_t i = 0; i < n1 * n1 * ns; ++i) { U[i] = creal(Uh[i]); re += creal(Uh[i]) * creal(Uh[i]); im += cimag(Uh[i]) * cimag(Uh[i]); }
+    for (int64_t i = 0; i < n1 * n2 * ns; ++i) { S[i] = creal(Sh[i]); re += creal(Sh[i]) * creal(Sh[i]); im += cimag(Sh[i]) * cimag(Sh[i]); }
+    for (int64_t i = 0; i < n2 * n2 * ns; ++i) { V[i] = creal(Vh[i]); re += creal(Vh[i]) * creal(Vh[i]); im += cimag(Vh[i]) * cimag(Vh[i]); }
     if (sqrt(im) > 1e-12 * sqrt(re) && status == ORC_OK) status = ORC_EIMAG;
     free(Mh); free(Uh); free(Sh); free(Vh); free(sg);
     return status;
+}
+
+int orc_tsvd(int64_t n1, int64_t n2, int64_t n3, const double* M, double* U, double* S, double* V)
+{
+    const int64_t dm[3] = {n1, n2, n3};
+    return orc_tsvd_nd(3, dm, M, U, S, V);
 }

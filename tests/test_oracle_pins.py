@@ -122,6 +122,46 @@ def test_transpose_and_identity():
     assert np.allclose(oracle.ttranspose(oracle.ttranspose(A)), A)
 
 
+def _tproduct_bruteforce_nd(A, B):
+    """Order-N t-product by its definition as a circular convolution of the tubes over every
+    mode from 3 on: C(i, j, t) = sum_l sum_s A(i, l, s) B(l, j, (t - s) mod dims)."""
+    modes = A.shape[2:]
+    C = np.zeros((A.shape[0], B.shape[1]) + modes)
+    for t in np.ndindex(*modes):
+        for s_ in np.ndindex(*modes):
+            d = tuple((a - b) % n for a, b, n in zip(t, s_, modes))
+            C[(slice(None), slice(None)) + t] += (A[(slice(None), slice(None)) + s_]
+                                                  @ B[(slice(None), slice(None)) + d])
+    return C
+
+
+@pytest.mark.parametrize("modes", [(2, 3), (3, 2, 2), (2, 2, 1, 3)])
+def test_tproduct_order_4_to_6_is_circular_convolution(modes):
+    r = _rng(8)
+    A = r.standard_normal((3, 2) + modes)
+    B = r.standard_normal((2, 4) + modes)
+    assert np.allclose(oracle.tproduct(A, B), _tproduct_bruteforce_nd(A, B), atol=1e-12)
+
+
+@pytest.mark.parametrize("modes", [(3, 4), (2, 3, 2), (2, 2, 3, 2)])
+def test_transpose_and_identity_order_4_to_6(modes):
+    """(A*B)^T = B^T * A^T, I * A = A, (A^T)^T = A, and the transpose is the conjugate
+    transpose of every Fourier slice."""
+    r = _rng(9)
+    A = r.standard_normal((3, 4) + modes)
+    B = r.standard_normal((4, 2) + modes)
+    lhs = oracle.ttranspose(oracle.tproduct(A, B))
+    rhs = oracle.tproduct(oracle.ttranspose(B), oracle.ttranspose(A))
+    assert np.allclose(lhs, rhs, atol=1e-12)
+    I = np.zeros((3, 3) + modes)
+    I[(slice(None), slice(None)) + (0,) * len(modes)] = np.eye(3)
+    assert np.allclose(oracle.tproduct(I, A), A, atol=1e-12)
+    assert np.allclose(oracle.ttranspose(oracle.ttranspose(A)), A)
+    axes = tuple(range(2, A.ndim))
+    Ah, ATh = np.fft.fftn(A, axes=axes), np.fft.fftn(oracle.ttranspose(A), axes=axes)
+    assert np.allclose(ATh, np.conj(np.swapaxes(Ah, 0, 1)), atol=1e-12)
+
+
 # ---------------------------------------------------------------- t-SVD (Theorem 2.2.1)
 
 @pytest.mark.parametrize("shape", [(4, 3, 5), (3, 4, 6), (3, 3, 1), (2, 4, 2)])
@@ -140,6 +180,32 @@ def test_tsvd_reconstruction_and_orthogonality(shape):
     for i in range(min(n1, n2)):
         off[i, i, :] = 0
     assert np.abs(off).max() < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(4, 3, 2, 3), (3, 4, 3, 2, 2), (3, 2, 2, 2, 1, 3)])
+def test_tsvd_order_4_to_6(shape):
+    """Algorithm 1 over modes 3..N: U * S * V^T = M, U^T * U = I, V^T * V = I, S f-diagonal,
+    and the diagonal of every Fourier slice of S is numpy's singular values of that slice of M
+    (decreasing)."""
+    M = _rng(17).standard_normal(shape)
+    U, S, V = oracle.tsvd(M)
+    n1, n2, modes = shape[0], shape[1], shape[2:]
+    rec = oracle.tproduct(oracle.tproduct(U, S), oracle.ttranspose(V))
+    assert np.allclose(rec, M, atol=1e-11)
+    for X, n in ((U, n1), (V, n2)):
+        I = np.zeros((n, n) + modes)
+        I[(slice(None), slice(None)) + (0,) * len(modes)] = np.eye(n)
+        assert np.allclose(oracle.tproduct(oracle.ttranspose(X), X), I, atol=1e-11)
+    off = S.copy()
+    for i in range(min(n1, n2)):
+        off[i, i] = 0
+    assert np.abs(off).max() < 1e-12
+    axes = tuple(range(2, M.ndim))
+    Mh, Sh = np.fft.fftn(M, axes=axes), np.fft.fftn(S, axes=axes)
+    for idx in np.ndindex(*modes):
+        sl = (slice(None), slice(None)) + idx
+        sv = np.linalg.svd(Mh[sl], compute_uv=False)
+        assert np.allclose(np.diagonal(Sh[sl])[:sv.size], sv, atol=1e-10)
 
 
 def test_truncated_tsvd_theorem_2_3_1():
