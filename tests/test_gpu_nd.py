@@ -244,9 +244,15 @@ def test_factor_nd(ctx, shape, k):
     Sh = fourier(S)
     diag = np.stack([Sh[i, i] for i in range(kk)])
     assert np.abs(np.real(diag) - sv[:kk]).max() <= TOL * sv.max()
+    # the singular tubes of the oracle's order-N t-SVD (Algorithm 1 over modes 3..N)
+    So = fourier(oracle.tsvd(Y.astype(np.float64))[1])
+    diag_o = np.stack([So[i, i] for i in range(kk)])
+    assert np.abs(diag - diag_o).max() <= TOL * sv.max()
     R = product_fourier(U, S, V)
     if k == 0:
         assert relerr(R, Y) <= TOL
+        # and the oracle's order-N t-product multiplies the factors back to Y
+        assert relerr(oracle.tproduct(oracle.tproduct(U, S), oracle.ttranspose(V)), Y) <= TOL
     else:
         # per-slice best rank-k approximation: error energy = discarded sigma^2 / #slices
         nsl = int(np.prod(shape[2:]))
