@@ -285,6 +285,8 @@ class Context:
         omega (completion), lam (RPCA), out0, out1 (device buffers)."""
         arr = (Problem * len(problems))()
         for i, q in enumerate(problems):
+            if len(q["dims"]) not in (3, 4):
+                raise ValueError(f"problem {i}: batched tensors are 3-way or 4-way")
             d = list(q["dims"]) + [1] * (4 - len(q["dims"]))
             arr[i].kind = PROBLEM_COMPLETE if q["kind"] == "complete" else PROBLEM_RPCA
             arr[i].order = len(q["dims"])
