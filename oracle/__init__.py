@@ -36,6 +36,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 OK, EINVAL, ENOMEM, ENOTCONV, EIMAG = 0, 1, 2, 4, 7
 SCALE_AVG, SCALE_SUM = 0, 1
 SPARSE_ENTRY, SPARSE_TUBE = 0, 1
+COMPRESS_GLOBAL, COMPRESS_TUBAL = 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -79,9 +80,10 @@ def lib() -> ctypes.CDLL:
         L.orc_tproduct_nd.argtypes = [c_int, i64p, c_i64, P, P, P]
         L.orc_ttranspose_nd.argtypes = [c_int, i64p, P, P]
         L.orc_tsvd_nd.argtypes = [c_int, i64p, P, P, P, P]
+        L.orc_compress.argtypes = [c_int, i64p, P, c_int, c_i64, P, i64p]
         for name in ("orc_dft", "orc_svd", "orc_tsvt", "orc_tnn_complete", "orc_trpca",
                      "orc_shrink", "orc_tproduct", "orc_ttranspose", "orc_tsvd",
-                     "orc_tproduct_nd", "orc_ttranspose_nd", "orc_tsvd_nd"):
+                     "orc_tproduct_nd", "orc_ttranspose_nd", "orc_tsvd_nd", "orc_compress"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -268,3 +270,16 @@ def tsvd(M: np.ndarray):
         _check("tsvd", lib().orc_tsvd_nd(M.ndim, _dims(M.shape), _ptr(m), _ptr(U), _ptr(S),
                                          _ptr(V)))
     return (_unflat(U, (n1, n1) + rest), _unflat(S, (n1, n2) + rest), _unflat(V, (n2, n2) + rest))
+
+
+def compress(M: np.ndarray, method: int, k: int):
+    """t-SVD compression of Sec. 3 (Method 1: COMPRESS_GLOBAL, the k largest Fourier singular
+    values over all slices, ties at the cut kept; Method 2: COMPRESS_TUBAL, the first k
+    singular tubes).  Returns (Z, entries kept)."""
+    M = np.asarray(M, dtype=np.float64)
+    m = _f64(M)
+    z = np.zeros_like(m)
+    kept = ctypes.c_int64(0)
+    _check("compress", lib().orc_compress(M.ndim, _dims(M.shape), _ptr(m), int(method), int(k),
+                                          _ptr(z), ctypes.byref(kept)))
+    return _unflat(z, M.shape), kept.value

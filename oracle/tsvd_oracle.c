@@ -19,7 +19,8 @@
  *     Sec. 5;
  *   - t-product (Def. 2.1.1 via the FFT route of Sec. 2.1), tensor transpose (Def. 2.1.2),
  *     full t-SVD (Theorem 2.2.1 / Algorithm 1), for order 3 and, through Algorithm 1's loop
- *     over modes 3..N, for orders up to 6.
+ *     over modes 3..N, for orders up to 6;
+ *   - t-SVD compression, Methods 1 and 2 of Sec. 3.
  *
  * Layout: every tensor is MATLAB column-major; entry (i1,i2,i3[,i4]) lives at
  * i1 + n1*(i2 + n2*(i3 + n3*i4)).  Complex values are C99 double complex.
@@ -665,4 +666,95 @@ int orc_tsvd(int64_t n1, int64_t n2, int64_t n3, const double* M, double* U, dou
 {
     const int64_t dm[3] = {n1, n2, n3};
     return orc_tsvd_nd(3, dm, M, U, S, V);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * t-SVD compression (Sec. 3).  The t-SVD of Algorithm 1 gives, in every Fourier slice, the
+ * f-diagonal entries of S-hat (the slice's singular values).  Method 1 (t-SVD compression)
+ * keeps the k largest of those entries over all slices; an entry equal to the k-th largest is
+ * kept too, so that a slice and its conjugate partner, which have equal singular values, keep
+ * the same terms and the result stays real.  Method 2 (t-SVD-tubal compression) keeps the
+ * first k of every slice, i.e. the first k singular tubes.  Z is the inverse DFT of
+ * Z-hat = sum over the kept terms of sigma u v^H; *kept receives the number of entries kept.
+ * ---------------------------------------------------------------------------------------- */
+enum { ORC_COMPRESS_GLOBAL = 1, ORC_COMPRESS_TUBAL = 2 };
+
+static int cmp_desc(const void* a, const void* b)
+{
+    const double x = *(const double*)a, y = *(const double*)b;
+    return (x < y) - (x > y);
+}
+
+int orc_compress(int order, const int64_t* dims, const double* M, int method, int64_t k,
+                 double* Z, int64_t* kept)
+{
+    if (order < 3 || !check_dims(order, dims) || !M || !Z) return ORC_EINVAL;
+    const int64_t n1 = dims[0], n2 = dims[1], ns = prod_dims(dims, 2, order);
+    const int64_t k0 = n1 < n2 ? n1 : n2;
+    if (method == ORC_COMPRESS_TUBAL ? (k < 1 || k > k0)
+        : method == ORC_COMPRESS_GLOBAL ? (k < 1 || k > k0 * ns) : 1)
+        return ORC_EINVAL;
+    cplx* Mh = (cplx*)malloc(sizeof(cplx) * (size_t)(n1 * n2 * ns));
+    cplx* Uh = (cplx*)malloc(sizeof(cplx) * (size_t)(n1 * n1 * ns));
+    cplx* Vh = (cplx*)malloc(sizeof(cplx) * (size_t)(n2 * n2 * ns));
+    cplx* Zh = (cplx*)calloc((size_t)(n1 * n2 * ns), sizeof(cplx));
+    double* sg = (double*)malloc(sizeof(double) * (size_t)(k0 * ns));
+    double* sorted = (double*)malloc(sizeof(double) * (size_t)(k0 * ns));
+    if (!Mh || !Uh || !Vh || !Zh || !sg || !sorted) {
+        free(Mh); free(Uh); free(Vh); free(Zh); free(sg); free(sorted);
+        return ORC_ENOMEM;
+    }
+    for (int64_t i = 0; i < n1 * n2 * ns; ++i) Mh[i] = M[i];
+    dft_tubes(Mh, order, dims, 0);
+    int status = ORC_OK;
+    /* the SVD of every Fourier slice, shared by conjugate partners as in the t-SVD */
+    for (int64_t s = 0; s < ns; ++s) {
+        const int64_t p = conj_partner(order, dims, s);
+        cplx* Us = Uh + s * n1 * n1;
+        cplx* Vs = Vh + s * n2 * n2;
+        if (p < s) {
+            for (int64_t i = 0; i < n1 * n1; ++i) Us[i] = conj(Uh[p * n1 * n1 + i]);
+            for (int64_t i = 0; i < n2 * n2; ++i) Vs[i] = conj(Vh[p * n2 * n2 + i]);
+            for (int64_t i = 0; i < k0; ++i) sg[s * k0 + i] = sg[p * k0 + i];
+            continue;
+        }
+        cplx* A = Mh + s * n1 * n2;
+        if (p == s)
+            for (int64_t i = 0; i < n1 * n2; ++i) A[i] = creal(A[i]);
+        if (svd_full(n1, n2, A, Us, sg + s * k0, Vs) < 0) status = ORC_ENOTCONV;
+    }
+    /* the kept entries: a threshold at the k-th largest (Method 1) or the first k (Method 2) */
+    double thr = 0.0;
+    if (method == ORC_COMPRESS_GLOBAL) {
+        memcpy(sorted, sg, sizeof(double) * (size_t)(k0 * ns));
+        qsort(sorted, (size_t)(k0 * ns), sizeof(double), cmp_desc);
+        thr = sorted[k - 1];
+    }
+    int64_t count = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+        const cplx* Us = Uh + s * n1 * n1;
+        const cplx* Vs = Vh + s * n2 * n2;
+        cplx* Zs = Zh + s * n1 * n2;
+        for (int64_t g = 0; g < k0; ++g) {
+            const double sv = sg[s * k0 + g];
+            const int keep = method == ORC_COMPRESS_TUBAL ? (g < k) : (sv >= thr);
+            if (!keep) continue;
+            ++count;
+            for (int64_t j = 0; j < n2; ++j) {
+                const cplx v = conj(Vs[j + g * n2]) * sv;
+                for (int64_t i = 0; i < n1; ++i) Zs[i + j * n1] += Us[i + g * n1] * v;
+            }
+        }
+    }
+    dft_tubes(Zh, order, dims, 1);
+    double im = 0, re = 0;
+    for (int64_t i = 0; i < n1 * n2 * ns; ++i) {
+        Z[i] = creal(Zh[i]);
+        re += creal(Zh[i]) * creal(Zh[i]);
+        im += cimag(Zh[i]) * cimag(Zh[i]);
+    }
+    if (sqrt(im) > 1e-12 * (sqrt(re) + 1e-300) && im > 0 && status == ORC_OK) status = ORC_EIMAG;
+    if (kept) *kept = count;
+    free(Mh); free(Uh); free(Vh); free(Zh); free(sg); free(sorted);
+    return status;
 }

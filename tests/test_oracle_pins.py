@@ -230,6 +230,54 @@ def test_truncated_tsvd_theorem_2_3_1():
         assert np.linalg.norm((M - alpha * C).ravel()) ** 2 >= err2 - 1e-9
 
 
+# ---------------------------------------------------------------- compression (Sec. 3)
+
+def _fourier_svals(M):
+    axes = tuple(range(2, M.ndim))
+    Mh = np.fft.fftn(M, axes=axes)
+    return np.stack([np.linalg.svd(Mh[(slice(None), slice(None)) + idx], compute_uv=False)
+                     for idx in np.ndindex(*M.shape[2:])], axis=1)   # (min(n1, n2), slices)
+
+
+@pytest.mark.parametrize("shape", [(6, 5, 7), (5, 7, 8), (4, 5, 2, 3, 4)])
+def test_compress_tubal_is_truncated_tsvd(shape):
+    """Method 2 with k tubes is M_k of Theorem 2.3.1: the first k columns of U, S, V
+    multiplied back, and its error energy is the discarded singular values' (Parseval, the
+    squares summed over every Fourier slice divided by their number)."""
+    M = _rng(18).standard_normal(shape)
+    k = 2
+    Z, kept = oracle.compress(M, oracle.COMPRESS_TUBAL, k)
+    assert kept == k * int(np.prod(shape[2:]))
+    U, S, V = oracle.tsvd(M)
+    Mk = oracle.tproduct(oracle.tproduct(U[:, :k], S[:k, :k]), oracle.ttranspose(V[:, :k]))
+    assert np.allclose(Z, Mk, atol=1e-11)
+    sv = _fourier_svals(M)
+    nsl = sv.shape[1]
+    assert np.sum((M - Z) ** 2) == pytest.approx(np.sum(sv[k:] ** 2) / nsl, rel=1e-10)
+    Zall, _ = oracle.compress(M, oracle.COMPRESS_TUBAL, min(shape[:2]))
+    assert np.allclose(Zall, M, atol=1e-11)
+
+
+@pytest.mark.parametrize("shape,k", [((6, 5, 7), 9), ((5, 7, 8), 17), ((4, 5, 2, 3, 4), 30),
+                                     ((4, 5, 2, 3, 4), 96)])
+def test_compress_global_keeps_the_largest_entries(shape, k):
+    """Method 1 keeps every Fourier singular value at least as large as the k-th largest
+    (numpy's SVD of every slice), so at least k entries, and the error energy is that of the
+    rest (Parseval); keeping all of them returns M."""
+    M = _rng(19).standard_normal(shape)
+    Z, kept = oracle.compress(M, oracle.COMPRESS_GLOBAL, k)
+    sv = _fourier_svals(M)
+    flat = np.sort(sv.ravel())[::-1]
+    thr = flat[k - 1]
+    expect = int(np.sum(sv >= thr * (1 - 1e-12)))
+    assert kept >= k and kept == expect
+    nsl = sv.shape[1]
+    assert np.sum((M - Z) ** 2) == pytest.approx(np.sum(flat[kept:] ** 2) / nsl, rel=1e-9,
+                                                 abs=1e-12)
+    if k == flat.size:
+        assert np.allclose(Z, M, atol=1e-11)
+
+
 # ---------------------------------------------------------------- TNN and t-SVT (Thm 2.4.1, Lemma)
 
 @pytest.mark.parametrize("shape", [(3, 4, 5), (4, 3, 4), (2, 2, 1), (3, 2, 2)])
