@@ -57,3 +57,21 @@ def test_tube_bytes_is_two_spectra_and_three_real_tensors(dims):
     assert bench.tube_bytes(dims) == 2 * 8 * n12 * stored + 3 * 4 * N
     if dims == (144, 176, 100):
         assert bench.tube_bytes(dims) == pytest.approx(51.1e6, rel=1e-3)
+
+
+def test_reference_arm_prints_one_json_line():
+    """`bench.py --impl reference` (the oracle on the host cores) runs without a GPU and
+    prints the contract's line for the reference implementation."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "lowrank", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "iters/s"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1
