@@ -498,6 +498,33 @@ def test_rpca_scaled_dual_bounds(mode):
             assert np.allclose(G[on], -lam * S[on] / sn[on][:, None], rtol=1e-8, atol=1e-12)
 
 
+@pytest.mark.parametrize("mode", [oracle.SPARSE_ENTRY, oracle.SPARSE_TUBE])
+def test_rpca_order_5_duals(mode):
+    """Order 5: after the S-step rho W is -lambda times a subgradient of the sparse penalty
+    at S (entrywise, or per tube with the tube of (i, j) spanning modes 3 to 5)."""
+    shape = (7, 6, 2, 3, 2)
+    M = lowrank_fourier(shape, 2, 21)
+    Sx, _ = synth.sparse_corruption(shape, 0.15, seed=21)
+    lam = 0.3
+    L, S, W, rho = oracle.trpca(M + Sx, lam, 8, rho0=0.05, mu=1.3, sparse_mode=mode,
+                                with_dual=True)
+    G = rho * W
+    axes = (2, 3, 4)
+    if mode == oracle.SPARSE_ENTRY:
+        assert np.abs(G).max() <= lam * (1 + 1e-9)
+        on = S != 0
+        assert on.any()
+        assert np.allclose(G[on], -lam * np.sign(S[on]), rtol=1e-9, atol=1e-12)
+    else:
+        gn = np.sqrt((G ** 2).sum(axis=axes))
+        sn = np.sqrt((S ** 2).sum(axis=axes))
+        assert gn.max() <= lam * (1 + 1e-9)
+        on = sn > 0
+        assert on.any()
+        assert np.allclose(G[on], -lam * S[on] / sn[on][:, None, None, None], rtol=1e-8,
+                           atol=1e-12)
+
+
 def test_rpca_separates_sparse_corruption():
     L0 = synth.lowrank_tensor(20, 18, 8, 2, seed=7)
     S0, sup = synth.sparse_corruption(L0.shape, 0.05, seed=7, lo=-20, hi=20)
