@@ -232,11 +232,31 @@ def test_truncated_tsvd_theorem_2_3_1():
 
 # ---------------------------------------------------------------- compression (Sec. 3)
 
+
 def _fourier_svals(M):
     axes = tuple(range(2, M.ndim))
     Mh = np.fft.fftn(M, axes=axes)
     return np.stack([np.linalg.svd(Mh[(slice(None), slice(None)) + idx], compute_uv=False)
                      for idx in np.ndindex(*M.shape[2:])], axis=1)   # (min(n1, n2), slices)
+
+
+def test_truncated_tsvd_theorem_2_3_1_order_5():
+    """Theorem 2.3.1 with the DFT over modes 3 to 5: M_k's error is the Parseval sum of the
+    dropped Fourier singular values, and no scaled random X * Y of inner size k does better."""
+    shape, k = (5, 4, 2, 3, 2), 2
+    M = _rng(22).standard_normal(shape)
+    U, S, V = oracle.tsvd(M)
+    Mk = oracle.tproduct(oracle.tproduct(U[:, :k], S[:k, :k]), oracle.ttranspose(V[:, :k]))
+    err2 = np.linalg.norm((M - Mk).ravel()) ** 2
+    sv = _fourier_svals(M)
+    assert abs(err2 - np.sum(sv[k:] ** 2) / sv.shape[1]) < 1e-9 * max(1.0, err2)
+    r = _rng(23)
+    for _ in range(20):
+        X = r.standard_normal((shape[0], k) + shape[2:])
+        Y = r.standard_normal((k, shape[1]) + shape[2:])
+        C = oracle.tproduct(X, Y)
+        alpha = np.vdot(C.ravel(), M.ravel()) / max(np.vdot(C.ravel(), C.ravel()), 1e-300)
+        assert np.linalg.norm((M - alpha * C).ravel()) ** 2 >= err2 - 1e-9
 
 
 @pytest.mark.parametrize("shape", [(6, 5, 7), (5, 7, 8), (4, 5, 2, 3, 4)])
