@@ -232,7 +232,6 @@ def test_truncated_tsvd_theorem_2_3_1():
 
 # ---------------------------------------------------------------- compression (Sec. 3)
 
-
 def _fourier_svals(M):
     axes = tuple(range(2, M.ndim))
     Mh = np.fft.fftn(M, axes=axes)
