@@ -336,6 +336,27 @@ def test_tsvt_matches_library_fft_svd(shape, tau):
         assert rk[idx] == int((s > tau).sum())
 
 
+@pytest.mark.parametrize("shape", [(4, 3, 5), (3, 4, 2, 3, 2)])
+def test_tsvt_is_a_firmly_nonexpansive_prox(shape):
+    """The t-SVT is the proximal map of a convex function (Thm 2.4.1 with the Lemma), so it
+    is firmly non-expansive: ||P(X) - P(Y)||^2 <= <P(X) - P(Y), X - Y>; and its result's TNN
+    is the sum of the thresholded singular values."""
+    r = _rng(24)
+    for _ in range(5):
+        X = r.standard_normal(shape)
+        Y = X + 0.3 * r.standard_normal(shape)
+        tau = 0.8
+        PX, PY = oracle.tsvt(X, tau), oracle.tsvt(Y, tau)
+        d = (PX - PY).ravel()
+        assert d @ d <= d @ (X - Y).ravel() + 1e-12
+    sv = []
+    Xh = np.fft.fftn(X, axes=tuple(range(2, X.ndim)))
+    for idx in np.ndindex(*shape[2:]):
+        sv.append(np.linalg.svd(Xh[(slice(None), slice(None)) + idx], compute_uv=False))
+    _, _, tnn = oracle.tsvt(PX, 0.0, with_info=True)
+    assert tnn == pytest.approx(np.sum(np.maximum(np.concatenate(sv) - tau, 0.0)), rel=1e-10)
+
+
 def test_svt_lemma_optimality_and_certificate():
     """D_tau(Y) minimises 1/2 ||X - Y||^2 + tau ||X||_* (Lemma of Sec. 4.1); n3 = 1 makes the
     t-SVT the matrix SVT of the single frontal slice."""
