@@ -5,8 +5,10 @@ One step = one complete ADMM solve of a seeded synthetic workload with its input
 resident on the GPU; `value` is ADMM iterations per second over the whole job (for the
 batched workload an iteration advances all 64 tensors).  Workloads (`--workload`):
 
+  batch    64 tensors of uneven shapes (n1, n2 in [48, 256], n3 in [8, 64]), half completion
+           and half RPCA, 100 iterations, one batched call                 [default]
   video    grayscale video completion 144x176x100 (translating texture + N(0, 0.01^2)
-           noise), 20% of entries observed, 150 iterations            [default]
+           noise), 20% of entries observed, 150 iterations
   rpca     tensor RPCA, L = tubal-rank-10 t-product of N(0,1) factors 240x320x60,
            10% entrywise corruption U[-5, 5], lambda = 1/sqrt(320*60), 200 iterations
   color    colour video completion 288x352x3x60 (per-channel textures), 15% observed,
@@ -20,9 +22,12 @@ batched workload an iteration advances all 64 tensors).  Workloads (`--workload`
 `--precision` picks the slice SVT of the headline line: fp32 (plain one-sided Jacobi) or a
 mixed form (tf32, bf16, 3xtf32: tensor-core products; rand_fp32: CUDA-core products).  For
 the plain headline, `--mixed` (default 3xtf32) also times that mixed form on the same
-workload and steps and reports it (batch: mean over the tensors), with its final recovery error and
-whether it meets the equal-error rule (e_mixed <= e_plain + 0.01 e_plain + 1e-5: no worse
-than the plain form's recovery error beyond 1%), under the key "mixed".
+workload and steps and reports it, with its final recovery error and whether it meets the
+equal-error rule (e_mixed <= e_plain + 0.01 e_plain + 1e-5: no worse than the plain form's
+recovery error beyond 1%), under the key "mixed"; for the batch the rule is applied to every
+tensor and the verdict lists the tensors that miss it.  With the default batch workload the
+line also carries, under "color", the plain and mixed forms of the 288x352x3x60 colour video
+(the largest single tensor) timed the same way (`--no-color` skips it).
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                         [--workload NAME] [--precision P] [--mixed P|none]
@@ -53,7 +58,6 @@ import numpy as np
 
 METRIC = "t-SVT ADMM iters/s & HBM/TC roofline %, mixed/batched vs plain FP32 at equal err"
 FLUSH_BYTES = 256 << 20      # > 129 MB L2
-SMS = 152
 FP32_LANES_PER_SM = 128
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / BF16 tensor rates
 PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "3xtf32": 3, "rand_fp32": 4}
@@ -100,13 +104,15 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="video")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batch")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32")
     ap.add_argument("--mixed", choices=sorted(PRECISIONS) + ["none"], default="3xtf32")
     ap.add_argument("--iters", type=int, default=0, help="ADMM iterations per step (0 = the "
                     "workload's count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=0)
+    ap.add_argument("--no-color", action="store_true",
+                    help="batch workload: skip the colour-video lines reported alongside")
     return ap.parse_args()
 
 
@@ -273,19 +279,7 @@ def build_workload(name, seed):
         return dict(kind="rpca", dims=M.shape, M=M.astype(np.float32), lam=lam, truth=L0,
                     tube=True)
     if name == "batch":
-        items = []
-        for b, sp in enumerate(synth.workload_batch_shapes(seed=seed)):
-            s = seed * 1000 + b
-            L = synth.lowrank_tensor(sp["n1"], sp["n2"], sp["n3"], sp["rank"], seed=s)
-            if sp["kind"] == "complete":
-                om = synth.sampling_mask(L.shape, sp["p"], seed=s)
-                items.append(dict(kind="complete", dims=L.shape,
-                                  M=(L * om).astype(np.float32), omega=om, truth=L))
-            else:
-                S, _ = synth.sparse_corruption(L.shape, sp["frac"], seed=s)
-                lam = 1.0 / math.sqrt(max(sp["n1"], sp["n2"]) * sp["n3"])
-                items.append(dict(kind="rpca", dims=L.shape, M=(L + S).astype(np.float32),
-                                  lam=lam, truth=L))
+        items = synth.workload_batch(seed=seed)
         return dict(kind="batch", items=items)
     raise ValueError(name)
 
@@ -435,8 +429,29 @@ def sum_stats(stats, key):
     return sum(s[key] for s in stats)
 
 
+def add_fp32_peak(peaks, device):
+    """Measures the device's FP32 CUDA-core throughput (tsvd_measure_fp32_peak: the best of a
+    scalar and a packed FP32x2 FMA loop) into peaks["fp32_tflops"]; falls back to the count
+    SMs x 128 lanes x 2 flop x max SM clock, with the SM count from the device, if the
+    measurement fails."""
+    from paper_1407_1785_gb300 import libtsvd
+    try:
+        fma, fma2 = libtsvd.measure_fp32_peak(device)
+        peaks["fp32_tflops"] = max(fma, fma2)
+        peaks["fp32_fma_tflops"], peaks["fp32_fma2_tflops"] = fma, fma2
+        peaks["fp32_source"] = ("measured: FP32 FMA loop (tsvd_measure_fp32_peak, best of "
+                                "scalar and packed FP32x2)")
+    except Exception as e:      # noqa: BLE001 -- report the derived figure instead
+        import torch
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+        peaks["fp32_tflops"] = sms * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e-6
+        peaks["fp32_source"] = (f"derived ({e}): {sms} SMs x 128 FP32 lanes x 2 flop/FMA x "
+                                "max SM clock")
+    return peaks
+
+
 def alu_peak(peaks):
-    return SMS * FP32_LANES_PER_SM * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12
+    return peaks["fp32_tflops"]
 
 
 def mixed_rooflines(stats, prec_name, peaks):
@@ -449,13 +464,13 @@ def mixed_rooflines(stats, prec_name, peaks):
     roof_svd = {"bound": "alu", "kernel": "jacobi_svt_kernel (n x k projections)",
                 "achieved": svd_tf, "peak": peak, "unit": "TFLOP/s", "frac": svd_tf / peak,
                 "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x max SM clock",
+                "peak_source": peaks["fp32_source"],
                 "alg": "Golub-Van Loan 4 (4 n k^2 + 8 k^3) per n x k projection",
                 "ms": s_ms}
     if prec_name == "rand_fp32":
         roof_gemm = {"bound": "alu", "kernel": "cgemm_fp32_kernel", "achieved": gemm_tf,
                      "peak": peak, "unit": "TFLOP/s", "frac": gemm_tf / peak, "traffic": None,
-                     "peak_source": "derived FP32 CUDA-core peak",
+                     "peak_source": peaks["fp32_source"],
                      "alg": "8 m n k per complex product", "ms": g_ms}
     else:
         roof_gemm = {"bound": "tensor", "kernel": f"cgemm_tc_kernel ({prec_name})",
@@ -482,44 +497,89 @@ def instrumented_pass(dw, iters, prec_name, stream, flush, barrier, steps, cache
     return t_ms, stats
 
 
+def equal_error_verdict(e_mixed, e_plain):
+    """The equal-error rule per tensor: e_mixed <= e_plain + 0.01 e_plain + 1e-5."""
+    ok = [em <= ep + 0.01 * ep + 1e-5 for em, ep in zip(e_mixed, e_plain)]
+    worst = max(range(len(ok)), key=lambda i: e_mixed[i] / max(e_plain[i], 1e-300))
+    return {"equal_error": all(ok), "tensors_meeting": int(sum(ok)), "tensors": len(ok),
+            "missing": [i for i, v in enumerate(ok) if not v],
+            "worst_ratio": e_mixed[worst] / max(e_plain[worst], 1e-300), "worst_tensor": worst}
+
+
 def mixed_form(args, dw, iters, prec_name, e_plain, stream, flush, barrier, peaks, t_plain_ms,
-               cache):
-    """Times the mixed form on the same workload; returns the "mixed" object."""
+               cache, steps=None):
+    """Times the mixed form on the same workload; returns the "mixed" object.  e_plain: the
+    plain form's recovery error of every tensor."""
     from paper_1407_1785_gb300 import libtsvd
+    steps = steps or args.steps
     ctx = libtsvd.Context(device=stream.device.index, stream=stream.cuda_stream,
                           precision=PRECISIONS[prec_name], autotune_cache=cache, **ctx_options(dw))
     solve = solver(ctx, dw, iters)
     for _ in range(max(args.warmup, 1)):
         solve()
-    t_ms, tstats = timed_solves(solve, args.steps, flush, stream, barrier)
+    t_ms, tstats = timed_solves(solve, steps, flush, stream, barrier)
     ctx.close()
-    e = statistics.mean(recovery_errors(dw))
-    tp_ms, stats = instrumented_pass(dw, iters, prec_name, stream, flush, barrier, args.steps,
-                                     cache)
-    n_it = iters * args.steps
+    errs = recovery_errors(dw)
+    verdict = equal_error_verdict(errs, e_plain)
+    out = {
+        "precision": prec_name, "value": iters * steps / (t_ms / 1000.0),
+        "unit": "iters/s", "ms_per_step": t_ms / steps, "steps": steps,
+        "speedup_vs_plain": t_plain_ms / t_ms,
+        "final_rse_db": 20 * math.log10(statistics.mean(errs)),
+        "plain_rse_db": 20 * math.log10(statistics.mean(e_plain)),
+        # equal error: not worse than the plain form's recovery error beyond 1% (+1e-5), for
+        # every tensor
+        **verdict,
+        "sketch_width_last": tstats[-1]["rsvt_k_last"],
+        "saturated_slice_svts": tstats[-1]["rsvt_saturated"],
+        "gpu_launches": sum_stats(tstats, "launches"),
+    }
+    if dw["kind"] == "batch":
+        out["final_rse_db_per_tensor"] = [round(20 * math.log10(max(e, 1e-300)), 3) for e in errs]
+        return out       # the batched form records no per-stage events
+    tp_ms, stats = instrumented_pass(dw, iters, prec_name, stream, flush, barrier, steps, cache)
+    n_it = iters * steps
     parts = {"small_svd": sum_stats(stats, "rsvt_svd_ms"),
              "slice_products": sum_stats(stats, "rsvt_gemm_ms"),
              "cholqr2": sum_stats(stats, "rsvt_orth_ms"),
              "tube_pass": sum_stats(stats, "tube_ms")}
     parts["other"] = max(tp_ms - sum(parts.values()), 0.0)
     roof_svd, roof_gemm = mixed_rooflines(stats, prec_name, peaks)
-    dominant = max(("small_svd", "slice_products", "cholqr2", "tube_pass"), key=parts.get)
-    return {
-        "precision": prec_name, "value": iters * args.steps / (t_ms / 1000.0),
-        "unit": "iters/s", "ms_per_step": t_ms / args.steps,
-        "speedup_vs_plain": t_plain_ms / t_ms,
-        "final_rse_db": 20 * math.log10(e), "plain_rse_db": 20 * math.log10(e_plain),
-        # equal error: not worse than the plain form's recovery error beyond 1% (+1e-5)
-        "equal_error": e <= e_plain + 0.01 * e_plain + 1e-5,
-        "sketch_width_last": stats[-1]["rsvt_k_last"],
-        "saturated_slice_svts": stats[-1]["rsvt_saturated"],
+    out.update({
         "ms_per_iter": {k: v / n_it for k, v in parts.items()},
-        "dominant": dominant,
+        "dominant": max(("small_svd", "slice_products", "cholqr2", "tube_pass"), key=parts.get),
         "roofline_small_svd": roof_svd,
         "roofline_slice_products": roof_gemm,
-        "gpu_launches": sum_stats(tstats, "launches"),
         "stage_times_from": "instrumented pass of the same solves (CUDA events per stage)",
-    }
+    })
+    return out
+
+
+def side_workload(args, name, stream, flush, barrier, peaks, cache, steps):
+    """Plain and mixed form of another workload on the same GPU, timed like the headline
+    (inputs resident, L2 flushed between solves); returns its summary object."""
+    from paper_1407_1785_gb300 import libtsvd
+    spec = WORKLOADS[name]
+    iters = spec["iters"]
+    wl = build_workload(name, 1)
+    dw = to_device(wl)
+    ctx = libtsvd.Context(device=stream.device.index, stream=stream.cuda_stream,
+                          precision=PRECISIONS["fp32"], autotune_cache=cache, **ctx_options(wl))
+    solve = solver(ctx, dw, iters)
+    for _ in range(max(args.warmup, 1)):
+        solve()
+    t_ms, stats = timed_solves(solve, steps, flush, stream, barrier)
+    ctx.close()
+    errs = recovery_errors(dw)
+    out = {"workload": spec["desc"], "admm_iters_per_step": iters, "steps": steps,
+           "plain": {"value": iters * steps / (t_ms / 1000.0), "unit": "iters/s",
+                     "ms_per_step": t_ms / steps, "final_rse_db": 20 * math.log10(errs[0]),
+                     "jacobi_sweeps_per_slice_svd": (sum_stats(stats, "total_sweeps") /
+                                                     max(sum_stats(stats, "slice_svds"), 1))}}
+    if args.mixed not in ("none", "fp32"):
+        out["mixed"] = mixed_form(args, dw, iters, args.mixed, errs, stream, flush, barrier,
+                                  peaks, t_ms, cache, steps=steps)
+    return out
 
 
 def run_ours(args):
@@ -579,8 +639,10 @@ def run_ours(args):
     value = units * iters * args.steps / (t_ms / 1000.0)
     errs = recovery_errors(dw)
     launches = sum_stats(stats, "launches")
-    # per-kernel device times from an instrumented pass of the same solves
-    tp_ms, pstats = instrumented_pass(dw, iters, prec, stream, flush, barrier, args.steps, cache)
+    # per-kernel device times from an instrumented pass of the same solves (fewer steps: the
+    # per-launch events only split the time, the throughput comes from the region above)
+    isteps = min(args.steps, 5)
+    tp_ms, pstats = instrumented_pass(dw, iters, prec, stream, flush, barrier, isteps, cache)
     slice_ms, tube_ms = sum_stats(pstats, "slice_ms"), sum_stats(pstats, "tube_ms")
     slice_launches = sum_stats(pstats, "slice_launches")
 
@@ -624,17 +686,34 @@ def run_ours(args):
             h2d, d2h = mh.numel() * 4, 2 * xh.numel() * 4
     e2e_step()                                             # warm-up (workspace)
     barrier()
+    esteps = min(args.steps, 5)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(esteps):
         e2e_step()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": units * iters * args.steps / e2e_s, "unit": "iters/s",
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    e2e = {"value": units * iters * esteps / e2e_s, "unit": "iters/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": esteps}
 
-    peaks = measured_peaks()
+    peaks = add_fp32_peak(measured_peaks(), local)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    n_it = iters * args.steps
-    if prec == "fp32":
+    n_it = iters * isteps
+    if prec == "fp32" and batch:
+        # the tensors' chains overlap on stream branches, so per-launch events do not add up
+        # to device time: the achieved rate is the algorithmic flops of all slice SVDs of one
+        # batch iteration over the wall time of one batch iteration of the timed region (tube
+        # passes and warm-start products included, so a lower bound on the kernel's)
+        flops = sum(jacobi_gvl_flops(it["dims"][0], it["dims"][1], half_slices(it["dims"]))
+                    for it in items)
+        it_s = t_ms / 1000.0 / (iters * args.steps)
+        achieved = flops / it_s / 1e12
+        roofline = {"bound": "alu", "kernel": "batched plain solve (jacobi_svt_kernel, tube "
+                    "passes, warm-start products)", "achieved": achieved,
+                    "peak": alu_peak(peaks), "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak(peaks), "traffic": None,
+                    "peak_source": peaks["fp32_source"],
+                    "alg_flops_per_iteration": flops, "ms_per_batch_iteration": it_s * 1e3,
+                    "times_from": "wall time of the timed region (CUDA events on the stream)"}
+    elif prec == "fp32":
         # algorithmic flops of one iteration (all tensors), per-iteration slice time
         flops = sum(jacobi_gvl_flops(it["dims"][0], it["dims"][1], half_slices(it["dims"]))
                     for it in items)
@@ -646,7 +725,7 @@ def run_ours(args):
         roofline = {"bound": "alu", "kernel": "jacobi_svt_kernel", "achieved": achieved,
                     "peak": alu_peak(peaks), "unit": "TFLOP/s",
                     "frac": achieved / alu_peak(peaks), "traffic": traffic,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x max SM clock",
+                    "peak_source": peaks["fp32_source"],
                     "alg_flops_per_iteration": flops,
                     "avg_launch_ms": slice_ms / max(slice_launches, 1),
                     "share_of_step": slice_ms / tp_ms,
@@ -656,7 +735,7 @@ def run_ours(args):
         roofline = roof_svd if roof_svd["ms"] >= roof_gemm["ms"] else roof_gemm
     t_bytes = sum(tube_bytes(it["dims"]) for it in items)
     roofline_tube = None
-    if tube_ms > 0:
+    if tube_ms > 0 and not batch:
         gbs = t_bytes * n_it / (tube_ms / 1000.0) / 1e9
         roofline_tube = {"bound": "hbm", "kernel": "tube_pass_kernel", "achieved": gbs,
                          "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
@@ -666,12 +745,13 @@ def run_ours(args):
 
     mixed = None
     if prec == "fp32" and args.mixed not in ("none", "fp32"):
-        # batch: recovery errors averaged over the tensors
-        mixed = mixed_form(args, dw, iters, args.mixed, statistics.mean(errs), stream, flush,
-                           barrier, peaks, t_ms, cache)
-        if batch:   # the batched form records no per-stage events
-            for key in ("ms_per_iter", "dominant", "roofline_small_svd", "roofline_slice_products"):
-                mixed.pop(key, None)
+        mixed = mixed_form(args, dw, iters, args.mixed, errs, stream, flush, barrier, peaks,
+                           t_ms, cache)
+    color = None
+    if batch and world == 1 and not args.no_color:
+        # the largest single tensor (288x352x3x60 colour video), plain and mixed, alongside
+        color = side_workload(args, "color", stream, flush, barrier, peaks, cache,
+                              steps=min(args.steps, 3))
 
     e_db = [20 * math.log10(max(e, 1e-300)) for e in errs]
     line = {
@@ -693,6 +773,7 @@ def run_ours(args):
     }
     if batch:
         line["final_rse_db_max"] = max(e_db)
+        line["final_rse_db_per_tensor"] = [round(v, 3) for v in e_db]
     if prec == "fp32":
         line["jacobi_sweeps_per_slice_svd"] = (sum_stats(stats, "total_sweeps") /
                                                max(sum_stats(stats, "slice_svds"), 1))
@@ -708,6 +789,8 @@ def run_ours(args):
                                "tube_pass": tube_ms / n_it}
     if mixed is not None:
         line["mixed"] = mixed
+    if color is not None:
+        line["color"] = color
     ctx.close()
     if ctx_e2e is not None:
         ctx_e2e.close()
@@ -817,7 +900,7 @@ def run_factor(args, reference=False):
         ctx.factor(yh, dims, 0, uh, sh, vh)
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     ctx.close()
-    peaks = measured_peaks()
+    peaks = add_fp32_peak(measured_peaks(), local)
     flops = jacobi_gvl_flops(n1, n2, half_slices(dims))
     achieved = flops / (t_ms / 1000.0 / args.steps) / 1e12
     line = {
@@ -831,7 +914,7 @@ def run_factor(args, reference=False):
         "roofline": {"bound": "alu", "kernel": "jacobi_svt_kernel", "achieved": achieved,
                      "peak": alu_peak(peaks), "unit": "TFLOP/s", "frac": achieved / alu_peak(peaks),
                      "traffic": None,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x max SM clock",
+                     "peak_source": peaks["fp32_source"],
                      "alg_flops_per_call": flops,
                      "times_from": "whole call (forward pass, slice SVDs in the V form, factor "
                                    "assembly, three inverse passes), CUDA events"},
@@ -914,7 +997,7 @@ def run_compress(args):
         ctx.compress(yh, Y.shape, libtsvd.COMPRESS_GLOBAL, k2, zh)
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     ctx.close()
-    peaks = measured_peaks()
+    peaks = add_fp32_peak(measured_peaks(), local)
     flops = jacobi_gvl_flops(n1, n2, half_slices(Y.shape))
     achieved = flops / (t_ms / 1000.0 / args.steps) / 1e12
     line = {
@@ -929,7 +1012,7 @@ def run_compress(args):
         "roofline": {"bound": "alu", "kernel": "jacobi_svt_kernel", "achieved": achieved,
                      "peak": alu_peak(peaks), "unit": "TFLOP/s", "frac": achieved / alu_peak(peaks),
                      "traffic": None,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x max SM clock",
+                     "peak_source": peaks["fp32_source"],
                      "alg_flops_per_call": flops,
                      "times_from": "whole call (forward pass, slice SVDs, singular values to the "
                                    "host, rebuild, inverse pass), CUDA events"},

@@ -284,6 +284,16 @@ typedef struct tsvd_problem {
 tsvd_status tsvd_solve_batched(tsvd_ctx* ctx, int count, const tsvd_problem* problems, int iters,
                                tsvd_stats* stats);
 
+/* The batched solve restricted to one method: TNN completion of `count` tensors (Sec. 4, as
+ * tnn_complete; every problem of kind TSVD_PROBLEM_COMPLETE) or tensor RPCA of `count`
+ * tensors (Sec. 5, as trpca; every problem of kind TSVD_PROBLEM_RPCA).  Same arguments,
+ * memory rules, scheduling and errors as tsvd_solve_batched, plus EINVAL when a problem is of
+ * the other kind. */
+tsvd_status tnn_complete_batched(tsvd_ctx* ctx, int count, const tsvd_problem* problems,
+                                 int iters, tsvd_stats* stats);
+tsvd_status trpca_batched(tsvd_ctx* ctx, int count, const tsvd_problem* problems, int iters,
+                          tsvd_stats* stats);
+
 /* Operand forms of tsvd_cgemm: as stored, transposed, conjugate-transposed. */
 enum { TSVD_OP_N = 0, TSVD_OP_T = 1, TSVD_OP_C = 2 };
 
@@ -303,6 +313,15 @@ tsvd_status tsvd_cgemm(tsvd_ctx* ctx, int transa, int transb, int m, int n, int 
                        int64_t ldb, int64_t stride_b, float* C, int64_t ldc, int64_t stride_c,
                        int batch);
 
+/* Measurement aid (not a step of the paper's method): the FP32 CUDA-core throughput of device
+ * `device` in TFLOP/s (2 flops per fused multiply-add), measured with a loop of independent
+ * scalar FMAs (*tflops_fma) and of packed FP32x2 FMAs (*tflops_fma2, the instruction form of
+ * the Jacobi kernels), each the best of 5 launches of 16 blocks of 1024 threads per SM timed
+ * with CUDA events.  This is the denominator of the FP32 ("alu") rooflines of the slice SVT.
+ * Allocates 4 bytes of device memory and a stream for the duration of the call and waits for
+ * them.  Errors: EINVAL (NULL outputs), ECUDA. */
+tsvd_status tsvd_measure_fp32_peak(int device, double* tflops_fma, double* tflops_fma2);
+
 /* The paper has no counterpart to this entry point; it exists for callers that cannot
  * allocate device memory.  Some callers cannot call cudaMalloc: a process that has handed the
  * whole device memory budget to its own pool allocator (a later cudaMalloc fails or fragments
@@ -314,15 +333,19 @@ tsvd_status tsvd_cgemm(tsvd_ctx* ctx, int transa, int transb, int m, int n, int 
  * Y, Z: device pointers on the current device (host memory is rejected), dims-shaped as for
  * tsvt(); Y and Z may alias.  The work is queued on `cuda_stream` (a cudaStream_t, NULL =
  * legacy default stream) and the call returns without waiting; no multi-rank, TNN or
- * convergence report.
+ * convergence report: TSVD_OK means the work was queued, not that every slice SVD converged
+ * within the default 40 sweeps (tsvt() reports that case as TSVD_ENOTCONV).  Each call's
+ * tables (twiddles, distinct-slice list) are written into the array by its first kernel from
+ * the launch arguments; no host buffer is read on the GPU.
  * Limit: 2 * 8 * n1*n2*P_half bytes of spectra plus small tables must fit in 64 MiB, where
  * P_half = floor(n3/2)+1 (order 3) or n3*(floor(n4/2)+1) (order 4); larger problems return
  * TSVD_ENOMEM before any work.  Every GPU that loads the library holds the 64 MiB until the
  * process exits.  The first call on a device (with that device current) looks up the array's
- * device address once; make it before any stream capture.  All calls on a device share the
- * array: calls that overlap on the GPU race and corrupt each other, so order them (one stream,
- * or events).  Errors: EINVAL (null or host pointer, bad order/dims/tau), EUNSUPPORTED,
- * ENOMEM (over the limit), ECUDA. */
+ * device address once; make it before any stream capture.  That address is cached for the
+ * process: resetting the device (cudaDeviceReset) while the library is loaded is not
+ * supported.  All calls on a device share the array: calls that overlap on the GPU race and
+ * corrupt each other, so order them (one stream, or events).  Errors: EINVAL (null or host
+ * pointer, bad order/dims/tau), EUNSUPPORTED, ENOMEM (over the limit), ECUDA. */
 tsvd_status tsvt_static(const float* Y, float* Z, int order, const int64_t* dims, float tau,
                         void* cuda_stream);
 

@@ -20,7 +20,7 @@ LIB_DIR = os.path.join(PKG, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libtsvd.so")
 
 SOURCES = ["tsvd_api.cu", "tube_pass.cu", "slice_svt.cu", "tsvd_noalloc.cu", "rsvt.cu",
-           "tc_gemm.cu", "factor.cu"]
+           "tc_gemm.cu", "factor.cu", "peak_probe.cu"]
 HEADERS = ["tsvd_internal.h"]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]

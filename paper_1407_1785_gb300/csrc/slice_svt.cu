@@ -62,7 +62,6 @@ namespace {
 constexpr int kNC = 8;            // rebuild chunk width (columns of B per chunk)
 constexpr int kMinWarps = 4;
 constexpr int kMinBlock = 16;     // fewest vectors per block before a slice is split further
-constexpr int kSMs = 152;
 constexpr size_t kStaticSmemReserve = 1024;   // static __shared__ of the kernel, with margin
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -828,7 +827,7 @@ int max_optin_smem() {
   return max_optin;
 }
 
-// Lanes per pair and 4-entry chunks per lane for a vector pitch of ld floats.
+// Lanes per pair and 4-entry chunks per lane for vectors of ld floats (a multiple of 4).
 // `prefer` = 0 picks the narrowest group with at most 2 chunks per lane, else 16 lanes;
 // `prefer` = 4, 8 or 16 asks for that group width (more chunks per lane = more independent
 // work per lane, fewer lanes = fewer shuffle levels and more pairs per warp).
@@ -853,26 +852,19 @@ bool pick_group(int ld, int prefer, int& G, int& cpl) {
   return fit(16);
 }
 
-// A pitch of at least n floats: a multiple of 4 with pitch/4 odd (fewer bank conflicts on
-// strided access).
-int pitch_for(int n) {
-  int p = (n + 3) / 4 * 4;
-  if (((p / 4) & 1) == 0) p += 4;
-  return p;
-}
-
 bool plan_with_ctas(int n1, int n2, int C, const SliceKnobs& k, SliceShape& sh, size_t& smem) {
   const int max_optin = max_optin_smem();
   sh.rows = n1 < n2 ? 1 : 0;
   sh.nv = n1 < n2 ? n1 : n2;
   sh.len = n1 < n2 ? n2 : n1;
-  sh.ld = pitch_for(sh.len);
   sh.vform = k.vform ? 1 : 0;
-  if (!pick_group(sh.ld, k.lanes, sh.G, sh.cpl)) return false;
+  // lanes and chunks for the vector's own 4-entry chunks (the row pitch is made odd below;
+  // sizing the chunks from an odd pitch instead padded e.g. a 128-entry vector to 192)
+  if (!pick_group(4 * ((sh.len + 3) / 4), k.lanes, sh.G, sh.cpl)) return false;
   // rows padded so that the vector part is exactly G * cpl chunks and the V part a multiple
   // of G chunks: every lane's chunks lie inside the row and the rotation needs no tests
   sh.ld = 4 * sh.G * sh.cpl;
-  sh.ldv = sh.vform ? 4 * ((pitch_for(sh.nv) / 4 + sh.G - 1) / sh.G * sh.G) : 0;
+  sh.ldv = sh.vform ? 4 * (((sh.nv + 3) / 4 + sh.G - 1) / sh.G * sh.G) : 0;
   sh.rowp = sh.ld + sh.ldv;
   if (((sh.rowp / 4) & 1) == 0) sh.rowp += 4;   // pitch / 4 odd
   sh.np = k.ppg == 2 ? 2 : 1;
@@ -907,7 +899,8 @@ bool plan_slice(int n1, int n2, int nslices, const SliceKnobs& k, SliceShape& sh
     SliceShape t;
     size_t sm;
     if (!plan_with_ctas(n1, n2, C, k, t, sm)) continue;
-    const int waves = (nslices * C + kSMs - 1) / kSMs;
+    const int sms = device_sm_count();
+    const int waves = (nslices * C + sms - 1) / sms;
     const double cost = (double)waves / C;
     if (cost < best - 1e-12) {
       best = cost;

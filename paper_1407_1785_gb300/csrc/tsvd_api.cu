@@ -187,21 +187,6 @@ tsvd_status make_problem(tsvd_ctx* c, int order, const int64_t* dims, Problem& p
   return TSVD_OK;
 }
 
-// Stored slice (kf, kh) is computed by the t-SVT unless it is the conjugate partner of an
-// earlier stored slice: only possible on the self-conjugate columns kh = 0, nh/2.
-// Flat full index of the conjugate partner of full index kf: (-k3 mod n3, -k4 mod n4, ...).
-int full_partner(const TubeGeom& g, int kf) {
-  if (g.nfm <= 1) return (g.nf - kf) % g.nf;
-  int r = 0, mul = 1, rem = kf;
-  for (int d = 0; d < g.nfm; ++d) {
-    const int n = g.fdim[d], k = rem % n;
-    rem /= n;
-    r += ((n - k) % n) * mul;
-    mul *= n;
-  }
-  return r;
-}
-
 // float2 entries of the twiddle region: the half-mode and full-mode tables, and for more than
 // one full mode the DFT matrix and the partner table (ints in float2 slots).
 size_t twid_count(const TubeGeom& g) {
@@ -216,19 +201,7 @@ size_t twid_count(const TubeGeom& g) {
 // the modes' twiddles) and the conjugate partner of every full index.
 void fill_twiddles(const TubeGeom& g, std::vector<float2>& out) {
   auto table = [](int n, float2* dst) {
-    for (int m = 0; m < n; ++m) {
-      double cr, sr;
-      if (m == 0) { cr = 1; sr = 0; }
-      else if (2 * m == n) { cr = -1; sr = 0; }
-      else if (4 * m == n) { cr = 0; sr = 1; }
-      else if (4 * m == 3 * n) { cr = 0; sr = -1; }
-      else {
-        const double a = 2.0 * M_PI * (double)m / (double)n;
-        cr = std::cos(a);
-        sr = std::sin(a);
-      }
-      dst[m] = make_float2((float)cr, (float)sr);
-    }
+    for (int m = 0; m < n; ++m) dst[m] = twiddle_value(m, n);
   };
   out.assign(twid_count(g), make_float2(0.f, 0.f));
   table(g.nh, out.data());
@@ -257,13 +230,6 @@ void fill_twiddles(const TubeGeom& g, std::vector<float2>& out) {
     }
   int* fp = reinterpret_cast<int*>(fm + (size_t)g.nf * g.nf);
   for (int kf = 0; kf < g.nf; ++kf) fp[kf] = full_partner(g, kf);
-}
-
-// On the self-conjugate half-mode columns (kh = 0, nh/2) a slice and its partner are
-// conjugates: only the one with the smaller full index is computed.
-bool slice_is_distinct(const TubeGeom& g, int kf, int kh) {
-  const bool selfcol = (kh == 0) || (2 * kh == g.nh);
-  return !(selfcol && full_partner(g, kf) < kf);
 }
 
 // Stored slice that holds full-spectrum slice (kf, kfull) itself or its conjugate.
@@ -2037,11 +2003,23 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
   return TSVD_OK;
 }
 
-tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, int iters,
-                               tsvd_stats* stats) {
+}  // extern "C"
+
+namespace {
+
+// The batched solve behind tsvd_solve_batched (only_kind = 0: any mix of problems) and
+// tnn_complete_batched / trpca_batched (every problem must be of kind only_kind).
+tsvd_status solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, int iters,
+                          tsvd_stats* stats, int only_kind) {
   if (!c) return TSVD_EINVAL;
   begin_call(c);
   if (count < 0 || (count > 0 && !problems)) return fail(c, TSVD_EINVAL, "bad problem list");
+  if (only_kind)
+    for (int i = 0; i < count; ++i)
+      if (problems[i].kind != only_kind)
+        return fail(c, TSVD_EINVAL, "problem %d: kind %d in a %s call", i, problems[i].kind,
+                    only_kind == TSVD_PROBLEM_COMPLETE ? "tnn_complete_batched"
+                                                       : "trpca_batched");
   if (iters < 0) return fail(c, TSVD_EINVAL, "iters must be >= 0");
   DeviceGuard dg(c->device);
   if (!dg.ok) return fail(c, TSVD_ECUDA, "cudaSetDevice(%d) failed", c->device);
@@ -2230,6 +2208,25 @@ tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* probl
   }
   TSVD_CUDA(c, cudaGetLastError());
   return TSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, int iters,
+                               tsvd_stats* stats) {
+  return solve_batched(c, count, problems, iters, stats, 0);
+}
+
+tsvd_status tnn_complete_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, int iters,
+                                 tsvd_stats* stats) {
+  return solve_batched(c, count, problems, iters, stats, TSVD_PROBLEM_COMPLETE);
+}
+
+tsvd_status trpca_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, int iters,
+                          tsvd_stats* stats) {
+  return solve_batched(c, count, problems, iters, stats, TSVD_PROBLEM_RPCA);
 }
 
 tsvd_status tsvd_cgemm(tsvd_ctx* c, int transa, int transb, int m, int n, int k,

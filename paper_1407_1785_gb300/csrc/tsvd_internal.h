@@ -6,6 +6,10 @@
 
 namespace tsvd {
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, cached per
+// device); the planners size grids and waves with it.
+int device_sm_count();
+
 // Geometry of the tube passes.  A real tensor of order 3 to 6 is stored MATLAB column-major;
 // the "tube" of pixel t = i + n1*j is the set of entries t + N12*(jf + nf*jh).  The last
 // mode (length nh) is transformed real-to-complex and only its first hh = nh/2+1 frequencies
@@ -22,6 +26,51 @@ struct TubeGeom {
   int nfm = 0;                  // number of full-DFT modes (N - 3)
   int fdim[4] = {0, 0, 0, 0};   // their sizes, mode 3 first (its index varies fastest in kf)
 };
+
+// (cos, sin)(2 pi m / n) computed in FP64 and rounded once to FP32, exact at the quarter
+// points: the twiddle factor of every DFT table of the library (host and device).
+__host__ __device__ inline float2 twiddle_value(int m, int n) {
+  double c, s;
+  if (m == 0) {
+    c = 1.0;
+    s = 0.0;
+  } else if (2 * m == n) {
+    c = -1.0;
+    s = 0.0;
+  } else if (4 * m == n) {
+    c = 0.0;
+    s = 1.0;
+  } else if (4 * m == 3 * n) {
+    c = 0.0;
+    s = -1.0;
+  } else {
+    const double a = 2.0 * 3.14159265358979323846 * (double)m / (double)n;
+    c = cos(a);
+    s = sin(a);
+  }
+  return make_float2((float)c, (float)s);
+}
+
+// Flat full index of the conjugate partner of full index kf: (-k3 mod n3, -k4 mod n4, ...).
+__host__ __device__ inline int full_partner(const TubeGeom& g, int kf) {
+  if (g.nfm <= 1) return (g.nf - kf) % g.nf;
+  int r = 0, mul = 1, rem = kf;
+  for (int d = 0; d < g.nfm; ++d) {
+    const int n = g.fdim[d], k = rem % n;
+    rem /= n;
+    r += ((n - k) % n) * mul;
+    mul *= n;
+  }
+  return r;
+}
+
+// Stored slice (kf, kh) is computed by the t-SVT unless it is the conjugate partner of an
+// earlier stored slice: only possible on the self-conjugate columns kh = 0, nh/2, where a
+// slice and its partner are conjugates and the one with the smaller full index is computed.
+__host__ __device__ inline bool slice_is_distinct(const TubeGeom& g, int kf, int kh) {
+  const bool selfcol = (kh == 0) || (2 * kh == g.nh);
+  return !(selfcol && full_partner(g, kf) < kf);
+}
 
 // Work modes of the tube pass.
 enum TubeMode : int {

@@ -16,19 +16,21 @@
 //  * In host code the array's name is only a host-side handle, not a device address.  The
 //    first tsvt_static() call on a device (with that device current) looks the address up
 //    once with cudaGetSymbolAddress and caches it per device; make that first call before
-//    any stream capture.
+//    any stream capture.  The cached address belongs to the device's primary context, so
+//    resetting the device (cudaDeviceReset) while the library is loaded is not supported.
 //  * Every call on a device shares the one array and it keeps the last call's contents.
-//    Nothing in it needs to start at zero: each call rewrites the tables, the forward pass
-//    writes every stored slice of the input spectrum and the SVT kernel writes every slice
-//    that the inverse pass reads.  Calls that overlap on the GPU (different streams, or
-//    different host threads without ordering) race on the array and corrupt each other.
+//    Nothing in it needs to start at zero: each call's first kernel writes the twiddle table
+//    and the list of distinct Fourier slices from its launch arguments (no host buffer is
+//    read), the forward pass writes every stored slice of the input spectrum and the SVT
+//    kernel writes every slice that the inverse pass reads.  Calls that overlap on the GPU
+//    (different streams, or different host threads without ordering) race on the array and
+//    corrupt each other.
 //  * No cudaMalloc, cudaFree or allocating library routine is called.
 #include "tsvd.h"
 #include "tsvd_internal.h"
 
 #include <cmath>
 #include <mutex>
-#include <vector>
 
 using namespace tsvd;
 
@@ -77,19 +79,18 @@ bool on_device(const void* p, int dev) {
   return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
-void twiddles(int n, float2* dst) {
-  for (int m = 0; m < n; ++m) {
-    double c, s;
-    if (m == 0) { c = 1; s = 0; }
-    else if (2 * m == n) { c = -1; s = 0; }
-    else if (4 * m == n) { c = 0; s = 1; }
-    else if (4 * m == 3 * n) { c = 0; s = -1; }
-    else {
-      const double a = 2.0 * M_PI * (double)m / (double)n;
-      c = std::cos(a);
-      s = std::sin(a);
-    }
-    dst[m] = make_float2((float)c, (float)s);
+// The tables a call needs, written by the device from the launch arguments: the twiddles
+// (cos, sin)(2 pi m / n) of the half mode (n = nh) and of the full mode (n = nf, order 4), and
+// the distinct stored slices in increasing order, by the same rules as tsvt() (twiddle_value,
+// slice_is_distinct).
+__global__ void static_tables_kernel(TubeGeom g, float2* __restrict__ twid, int* __restrict__ slices) {
+  for (int m = threadIdx.x; m < g.nh + g.nf; m += blockDim.x)
+    twid[m] = m < g.nh ? twiddle_value(m, g.nh) : twiddle_value(m - g.nh, g.nf);
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int kh = 0; kh < g.hh; ++kh)
+      for (int kf = 0; kf < g.nf; ++kf)
+        if (slice_is_distinct(g, kf, kh)) slices[n++] = kf + g.nf * kh;
   }
 }
 
@@ -117,17 +118,19 @@ extern "C" tsvd_status tsvt_static(const float* Y, float* Z, int order, const in
   g.nh = order == 4 ? (int)dims[3] : (int)dims[2];
   g.hh = g.nh / 2 + 1;
   g.nstore = g.nf * g.hh;
+  if (order == 4) {   // one full-DFT mode (mode 3), as tsvt() sets it up
+    g.nfm = 1;
+    g.fdim[0] = g.nf;
+  }
   if (!tube_pass_supported(g) || !jacobi_svt_supported((int)dims[0], (int)dims[1]))
     return TSVD_EUNSUPPORTED;
 
   // scratch layout: spectrum A | spectrum B | twiddles (nh + nf) | distinct slice list |
   // slice-SVT exchange buffers (multi-CTA slices)
   int ndistinct = 0;
-  for (int kh = 0; kh < g.hh; ++kh) {
-    const bool selfcol = (kh == 0) || (2 * kh == g.nh);
+  for (int kh = 0; kh < g.hh; ++kh)
     for (int kf = 0; kf < g.nf; ++kf)
-      if (!(selfcol && 2 * kf > g.nf)) ++ndistinct;
-  }
+      if (slice_is_distinct(g, kf, kh)) ++ndistinct;
   const size_t spec = align_up((size_t)g.nstore * (size_t)g.N12 * sizeof(float2));
   const size_t tw = align_up((size_t)(g.nh + g.nf) * sizeof(float2));
   const size_t lst = align_up((size_t)g.nstore * sizeof(int));
@@ -151,23 +154,8 @@ extern "C" tsvd_status tsvt_static(const float* Y, float* Z, int order, const in
   int* slices = reinterpret_cast<int*>(b + 2 * spec + tw);
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
-  std::vector<float2> tw_host((size_t)(g.nh + g.nf));
-  twiddles(g.nh, tw_host.data());
-  twiddles(g.nf, tw_host.data() + g.nh);
-  std::vector<int> list;
-  for (int kh = 0; kh < g.hh; ++kh) {
-    const bool selfcol = (kh == 0) || (2 * kh == g.nh);
-    for (int kf = 0; kf < g.nf; ++kf)
-      if (!(selfcol && 2 * kf > g.nf)) list.push_back(kf + g.nf * kh);
-  }
-  // pageable sources: the copies have consumed them when cudaMemcpyAsync returns
-  if (cudaMemcpyAsync(twid, tw_host.data(), tw_host.size() * sizeof(float2),
-                      cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemcpyAsync(slices, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice,
-                      stream) != cudaSuccess) {
-    cudaGetLastError();
-    return TSVD_ECUDA;
-  }
+  static_tables_kernel<<<1, 256, 0, stream>>>(g, twid, slices);
+  if ((st = from_launch(cudaGetLastError())) != TSVD_OK) return st;
 
   TubeArgs f{};
   f.g = g;
@@ -183,7 +171,7 @@ extern "C" tsvd_status tsvt_static(const float* Y, float* Z, int order, const in
   s.ahat = spec_a;
   s.zhat = spec_b;
   s.slices = slices;
-  s.nslices = (int)list.size();
+  s.nslices = ndistinct;
   s.n1 = (int)dims[0];
   s.n2 = (int)dims[1];
   s.N12 = g.N12;

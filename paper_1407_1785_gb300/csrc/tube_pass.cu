@@ -787,12 +787,31 @@ __global__ void project_observed_kernel(const float* __restrict__ M, const uint8
 
 unsigned elementwise_grid(int64_t N) {
   int64_t b = (N + 255) / 256;
-  if (b > 152 * 16) b = 152 * 16;
+  const int64_t cap = (int64_t)device_sm_count() * 16;
+  if (b > cap) b = cap;
   if (b < 1) b = 1;
   return (unsigned)b;
 }
 
 }  // namespace
+
+int device_sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (cached[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      return 1;
+    }
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
 
 bool tube_pass_supported(const TubeGeom& g) {
   return tile_rm(g) > 0 || tube_smem_bytes(g, 32) <= 220 * 1024;

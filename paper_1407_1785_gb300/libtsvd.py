@@ -31,7 +31,8 @@ SCALE_AVG, SCALE_SUM = 0, 1
 EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_last_error",
                     "tsvt", "tsvd_factor", "tsvd_compress", "tsvd_tproduct", "tnn_complete",
                     "trpca",
-                    "tsvd_solve_batched", "tsvt_static", "tsvd_cgemm")
+                    "tsvd_solve_batched", "tnn_complete_batched", "trpca_batched",
+                    "tsvt_static", "tsvd_cgemm", "tsvd_measure_fp32_peak")
 OP_N, OP_T, OP_C = 0, 1, 2
 WARM_OFF, WARM_ON, WARM_AUTO = 0, 1, 2
 COMPRESS_GLOBAL, COMPRESS_TUBAL = 1, 2
@@ -129,6 +130,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tsvd_solve_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
                                      ctypes.POINTER(Stats)]
     L.tsvd_solve_batched.restype = ctypes.c_int
+    for name in ("tnn_complete_batched", "trpca_batched"):
+        getattr(L, name).argtypes = L.tsvd_solve_batched.argtypes
+        getattr(L, name).restype = ctypes.c_int
+    L.tsvd_measure_fp32_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double)]
+    L.tsvd_measure_fp32_peak.restype = ctypes.c_int
     i64 = ctypes.c_int64
     L.tsvd_cgemm.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                              ctypes.c_int, P, i64, i64, P, i64, i64, P, i64, i64, ctypes.c_int]
@@ -142,6 +149,16 @@ def tsvt_static(Y, Z, dims: Sequence[int], tau: float, stream: Optional[int] = N
     device buffers on the current device; returns the tsvd_status code."""
     return load().tsvt_static(_ptr(Y), _ptr(Z), len(dims), _dims(dims), float(tau),
                               ctypes.c_void_p(stream or 0))
+
+
+def measure_fp32_peak(device: int = 0):
+    """Measured FP32 CUDA-core throughput (TFLOP/s) of the device: (scalar FMA loop, packed
+    FP32x2 FMA loop).  Raises on failure."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = load().tsvd_measure_fp32_peak(int(device), ctypes.byref(a), ctypes.byref(b))
+    if st != TSVD_OK:
+        raise TsvdError("tsvd_measure_fp32_peak", st, "measurement failed")
+    return a.value, b.value
 
 
 def default_opts() -> Opts:
@@ -280,9 +297,26 @@ class Context:
         self._check("trpca", st)
         return s.as_dict() if stats else None
 
-    def solve_batched(self, problems, iters: int, stats: bool = False):
+    def solve_batched(self, problems, iters: int, stats: bool = False,
+                      entry: str = "tsvd_solve_batched"):
         """problems: sequence of dicts with keys kind ('complete' | 'rpca'), dims, M,
-        omega (completion), lam (RPCA), out0, out1 (device buffers)."""
+        omega (completion), lam (RPCA), out0, out1 (device buffers).  `entry` picks the C
+        entry point: tsvd_solve_batched (any mix), tnn_complete_batched or trpca_batched."""
+        st = self.raw_solve_batched(problems, iters, stats, entry)
+        self._check(entry, st[0])
+        return st[1]
+
+    def tnn_complete_batched(self, problems, iters: int, stats: bool = False):
+        return self.solve_batched(problems, iters, stats, "tnn_complete_batched")
+
+    def trpca_batched(self, problems, iters: int, stats: bool = False):
+        return self.solve_batched(problems, iters, stats, "trpca_batched")
+
+    def raw_solve_batched(self, problems, iters: int, stats: bool = False,
+                          entry: str = "tsvd_solve_batched"):
+        """(status, stats dict or None) without raising."""
+        if entry not in ("tsvd_solve_batched", "tnn_complete_batched", "trpca_batched"):
+            raise ValueError(f"unknown batched entry point {entry}")
         arr = (Problem * len(problems))()
         for i, q in enumerate(problems):
             if len(q["dims"]) not in (3, 4):
@@ -297,10 +331,9 @@ class Context:
             arr[i].out0 = _ptr(q["out0"])
             arr[i].out1 = _ptr(q.get("out1"))
         s = Stats()
-        st = self._L.tsvd_solve_batched(self._h, len(problems), arr, int(iters),
-                                        ctypes.byref(s) if stats else None)
-        self._check("tsvd_solve_batched", st)
-        return s.as_dict() if stats else None
+        st = getattr(self._L, entry)(self._h, len(problems), arr, int(iters),
+                                     ctypes.byref(s) if stats else None)
+        return st, (s.as_dict() if stats and st == TSVD_OK else None)
 
     def cgemm(self, transa, transb, m, n, k, A, lda, stride_a, B, ldb, stride_b, C, ldc,
               stride_c, batch):

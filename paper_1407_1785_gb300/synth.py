@@ -259,3 +259,40 @@ def workload_batch_shapes(seed: int = 1, count: int = 64):
             out.append(dict(kind="rpca", n1=n1, n2=n2, n3=n3, rank=rank,
                             frac=0.05 + 0.10 * u[b, 4]))
     return out
+
+
+def workload_batch(seed: int = 1, count: int = 64):
+    """The uneven batch itself: for tensor b of `workload_batch_shapes`, with per-tensor seed
+    s = 1000 seed + b, L = a tubal-rank-r t-product of N(0,1) factors; completion tensors
+    observe L on Omega ~ Bernoulli(p); RPCA tensors see M = L + S with S an entrywise
+    corruption (fraction `frac`, values uniform in [-5, 5]) and lambda = 1/sqrt(max(n1, n2) n3).
+    Returns a list of dicts with kind, dims, M (float32, Omega-projected for completion),
+    omega (completion) or lam (RPCA), and truth (the float64 L)."""
+    items = []
+    for b, sp in enumerate(workload_batch_shapes(seed=seed, count=count)):
+        s = seed * 1000 + b
+        L = lowrank_tensor(sp["n1"], sp["n2"], sp["n3"], sp["rank"], seed=s)
+        if sp["kind"] == "complete":
+            om = sampling_mask(L.shape, sp["p"], seed=s)
+            items.append(dict(kind="complete", dims=L.shape, M=(L * om).astype(np.float32),
+                              omega=om, truth=L))
+        else:
+            S, _ = sparse_corruption(L.shape, sp["frac"], seed=s)
+            lam = 1.0 / math.sqrt(max(sp["n1"], sp["n2"]) * sp["n3"])
+            items.append(dict(kind="rpca", dims=L.shape, M=(L + S).astype(np.float32),
+                              lam=lam, truth=L))
+    return items
+
+
+def sample_indices(n: int, k: int, seed: int = 20260101) -> np.ndarray:
+    """k distinct flat (column-major) indices of an n-entry tensor, sorted, drawn from the
+    counter-based generator (the first k distinct values of floor(u n) in draw order): where
+    stored expected values are a sample of a large output."""
+    k = min(k, n)
+    draws = 4 * k + 64
+    while True:
+        v = (uniform(seed, STREAM_BATCH + 1, draws) * n).astype(np.int64)
+        _, first = np.unique(v, return_index=True)
+        if first.size >= k:
+            return np.sort(v[np.sort(first)[:k]])
+        draws *= 2

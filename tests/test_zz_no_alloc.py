@@ -1,7 +1,9 @@
 """tsvt_static(): the t-SVT for callers that cannot allocate device memory (a process whose
 device memory belongs to its own pool allocator, or a loop that must not pay cudaMalloc's
 implicit synchronisation).  Its scratch is a fixed array inside the library; the test checks
-it against tsvt(), which allocates its own workspace, through the C ABI.
+it through the C ABI against tsvt(), which allocates its own workspace, and against the FP64
+oracle's t-SVT (Lemma of Sec. 4.1 per Fourier slice), and checks that a repeated call takes
+no device memory.
 
 This file is collected last on purpose, so that a run stopping at the first failure has
 already run every other test."""
@@ -10,6 +12,7 @@ import pytest
 
 from helpers import colmajor, relerr, uncolmajor
 
+import oracle
 from paper_1407_1785_gb300 import libtsvd, synth
 
 pytestmark = pytest.mark.gpu
@@ -32,6 +35,17 @@ def _run_pair(ctx, torch, shape, seed, tau):
     floor = 1e-3 * np.linalg.norm(Y)
     assert np.all(np.isfinite(Zs))
     assert relerr(Zs, Zr, floor=floor) <= TSVT_TOL
+    Zo = oracle.tsvt(Y.astype(np.float64), tau)
+    Zo_floor = max(np.linalg.norm(Zo), floor)
+    assert relerr(Zs, Zo, floor=Zo_floor) <= TSVT_TOL
+    # the same call again: the scratch address is cached and the kernels are loaded, so a
+    # call that allocated device memory would show as a drop of the free memory
+    free0 = torch.cuda.mem_get_info()[0]
+    st = libtsvd.tsvt_static(y, z, shape, tau, stream.cuda_stream)
+    torch.cuda.synchronize()
+    assert st == libtsvd.TSVD_OK
+    assert torch.cuda.mem_get_info()[0] >= free0
+    assert np.array_equal(uncolmajor(z.cpu().numpy(), shape), Zs)
 
 
 def test_static_scratch_tsvt_matches_tsvt():
@@ -43,6 +57,8 @@ def test_static_scratch_tsvt_matches_tsvt():
         _run_pair(ctx, torch, (40, 28, 12), seed=21, tau=2.0)
         _run_pair(ctx, torch, (17, 33, 3, 5), seed=22, tau=1.0)
         _run_pair(ctx, torch, (144, 176, 100), seed=23, tau=5.0)
+        # back to the first shape after the large one left its spectra in the array
+        _run_pair(ctx, torch, (40, 28, 12), seed=24, tau=2.0)
 
 
 def test_static_scratch_rejects_oversize_and_host_buffers():
