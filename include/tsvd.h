@@ -127,6 +127,14 @@ typedef struct tsvd_opts {
                          sparse residual changes the small singular vectors at every
                          iteration, so a warm start saves fewer sweeps than the V form's
                          extra rotations cost. */
+  int batch_persistent; /* plain form, batched solves: 1 (default) runs each ADMM iteration of
+                         the whole batch as one persistent kernel launch that takes the slice
+                         SVTs of all tensors (largest first) and then their tube passes from
+                         device work queues, a tube pass starting once its tensor's slices are
+                         done; the cluster size and which tensors run one CTA per slice are
+                         autotuned per batch shape (timed on the first iteration) and kept in
+                         the context.  0: one chain of kernels per tensor on parallel stream
+                         branches. */
 } tsvd_opts;
 
 /* Counters of one ADMM solve (host struct). */

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(LIB_DIR, "libtsvd.so")
 
 SOURCES = ["tsvd_api.cu", "tube_pass.cu", "slice_svt.cu", "tsvd_noalloc.cu", "rsvt.cu",
            "tc_gemm.cu", "factor.cu", "peak_probe.cu"]
-HEADERS = ["tsvd_internal.h"]
+HEADERS = ["tsvd_internal.h", "tube_tile.cuh"]
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -51,8 +51,11 @@
 // A slice whose matrix is exactly real (the self-conjugate Fourier slices) stays exactly
 // real: every inner product then has a zero imaginary part and every rotation is real.
 #include "tsvd_internal.h"
+#include "tube_tile.cuh"
 
+#include <algorithm>
 #include <cooperative_groups.h>
+#include <cstring>
 
 namespace cg = cooperative_groups;
 
@@ -400,10 +403,92 @@ __host__ __device__ constexpr int max_regs_for(int chunks) {
              : (65536 / (max_warps_for(chunks) * 32)) / 8 * 8;
 }
 
+// Shared-memory scalars of one slice SVT (static __shared__ in the kernels: the same offset
+// in every CTA of a cluster, so they can be read across the cluster).
+struct SliceShared {
+  int flag[2];
+  int rank;
+  double nuc;
+};
+
+// The vectors of blocks bx (local slot 0) and by (slot 1) of the pre-rotated slice, computed
+// while loading: vector g = sum_l V(l, g) b_l, where b_l is vector l of the slice B (its
+// column, or its row when the vectors are rows) and V the nv x nv matrix Vin -- i.e. column g
+// of B V (columns) or row g of V^T B (rows), the input the V form expects with vin = V.  The
+// V entries of vector g start as column g of V.  The slice's vectors are staged nc at a time
+// in the rebuild's chunk buffer Bc (len x nc) and the matching rows of V in Cc (2 bs x nc).
+__device__ void load_blocks_rotated(float* Wr, float* Wi, const float2* __restrict__ B,
+                                    const float2* __restrict__ Vin, const SliceShape& sh, int n1,
+                                    int bx, int by, float2* Bc, float2* Cc) {
+  const int bs = sh.bs, len = sh.len, rowp = sh.rowp, nv = sh.nv, nc = sh.nc, nl = 2 * bs;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  auto gidx = [&](int k) { return k < bs ? bx * bs + k : by * bs + k - bs; };
+  for (int idx = tid; idx < nl * rowp; idx += nthr) {
+    Wr[idx] = 0.f;
+    Wi[idx] = 0.f;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < nl * nv; idx += nthr) {
+    const int k = idx / nv, i = idx % nv, g = gidx(k);
+    if (g >= nv) continue;
+    const float2 v = Vin[(size_t)i + (size_t)nv * g];
+    Wr[(size_t)k * rowp + sh.ld + i] = v.x;
+    Wi[(size_t)k * rowp + sh.ld + i] = v.y;
+  }
+  const int len4 = (len + 3) / 4;
+  for (int l0 = 0; l0 < nv; l0 += nc) {
+    const int ncur = min(nc, nv - l0);
+    for (int idx = tid; idx < len * ncur; idx += nthr) {
+      int e, cc;
+      if (!sh.rows) {
+        e = idx % len;
+        cc = idx / len;
+      } else {
+        cc = idx % ncur;
+        e = idx / ncur;
+      }
+      Bc[e + (size_t)len * cc] = B[sh.rows ? (size_t)(l0 + cc) + (size_t)n1 * e
+                                           : (size_t)e + (size_t)n1 * (l0 + cc)];
+    }
+    for (int idx = tid; idx < nl * ncur; idx += nthr) {
+      const int k = idx / ncur, cc = idx % ncur, g = gidx(k);
+      Cc[(size_t)k * nc + cc] =
+          g < nv ? Vin[(size_t)(l0 + cc) + (size_t)nv * g] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nl * len4; idx += nthr) {
+      const int k = idx / len4, e0 = 4 * (idx % len4);
+      float* wr = Wr + (size_t)k * rowp + e0;
+      float* wi = Wi + (size_t)k * rowp + e0;
+      float4 ar = *reinterpret_cast<const float4*>(wr), ai = *reinterpret_cast<const float4*>(wi);
+      float accr[4] = {ar.x, ar.y, ar.z, ar.w}, acci[4] = {ai.x, ai.y, ai.z, ai.w};
+      for (int cc = 0; cc < ncur; ++cc) {
+        const float2 c = Cc[(size_t)k * nc + cc];
+        const float2* bcol = Bc + (size_t)len * cc + e0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (e0 + j < len) {
+            const float2 b = bcol[j];
+            accr[j] = fmaf(c.x, b.x, fmaf(-c.y, b.y, accr[j]));
+            acci[j] = fmaf(c.x, b.y, fmaf(c.y, b.x, acci[j]));
+          }
+        }
+      }
+      *reinterpret_cast<float4*>(wr) = make_float4(accr[0], accr[1], accr[2], accr[3]);
+      *reinterpret_cast<float4*>(wi) = make_float4(acci[0], acci[1], acci[2], acci[3]);
+    }
+    __syncthreads();
+  }
+}
+
+// The SVT of slice ordinal `so` of a launch (the slice index is a.slices[so]) by the C = sh.C
+// CTAs of a cluster (this CTA is cluster rank `crank`; C = 1: this CTA alone), with the
+// cluster's block-exchange buffer xbuf (C > 1) and the CTA's dynamic shared memory smem_raw.
+// With a.prerot (V form, a.vin set) the initial vectors are B V / V^T B computed from the
+// slice B = a.ahat itself (load_blocks_rotated) rather than read from a pre-rotated input.
 template <int G, int CPL, int NP>
-__global__ void __maxnreg__(max_regs_for(CPL * NP))
-    jacobi_svt_kernel(SliceArgs a, SliceShape sh) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void svt_slice(const SliceArgs& a, const SliceShape& sh, int so, int crank,
+                          float* xbuf, unsigned char* smem_raw, SliceShared& ss) {
   const int len = sh.len, ld = sh.ld, rowp = sh.rowp, nc = sh.nc, bs = sh.bs, nb = sh.nb;
   const int C = sh.C;
   const int nl = 2 * bs;
@@ -414,13 +499,11 @@ __global__ void __maxnreg__(max_regs_for(CPL * NP))
   float* sig = reinterpret_cast<float*>(Cc + (size_t)sh.kcap * nc);
   float* dsc = sig + nl;
   int* keep = reinterpret_cast<int*>(dsc + sh.kcap);
-  __shared__ int s_flag[2];
-  __shared__ int s_rank;
-  __shared__ double s_nuc;
+  int* s_flag = ss.flag;
+  int& s_rank = ss.rank;
+  double& s_nuc = ss.nuc;
 
   cg::cluster_group cluster = cg::this_cluster();
-  const int crank = C > 1 ? (int)cluster.block_rank() : 0;
-  const int so = blockIdx.x / C;     // slice ordinal in this launch
   const int s = a.slices ? a.slices[so] : so;
   const int n1 = a.n1;
   const int64_t N12 = a.N12;
@@ -429,9 +512,7 @@ __global__ void __maxnreg__(max_regs_for(CPL * NP))
   const float2* __restrict__ Ab = a.brb ? a.brb + (size_t)s * N12 : A;
   const bool uform = !sh.vform || a.brb != nullptr;
   float2* __restrict__ Z = a.zhat + (size_t)s * N12;
-  char* scr = static_cast<char*>(a.scratch);
-  const size_t xbytes = sh.xbuf_floats * sizeof(float);
-  float* xbuf = C > 1 ? reinterpret_cast<float*>(scr + (size_t)so * xbytes) : nullptr;
+  if (C <= 1) xbuf = nullptr;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
 
@@ -439,8 +520,12 @@ __global__ void __maxnreg__(max_regs_for(CPL * NP))
   int bx, by;
   round_robin_pair(0, crank, nb, bx, by);
   const float2* Vin = a.vin ? a.vin + (size_t)s * a.vstride : nullptr;
-  load_block_from_slice(Wr, Wi, A, sh, n1, bx, 0, Vin);
-  load_block_from_slice(Wr, Wi, A, sh, n1, by, 1, Vin);
+  if (a.prerot && Vin && sh.vform) {
+    load_blocks_rotated(Wr, Wi, A, Vin, sh, n1, bx, by, Bc, Cc);
+  } else {
+    load_block_from_slice(Wr, Wi, A, sh, n1, bx, 0, Vin);
+    load_block_from_slice(Wr, Wi, A, sh, n1, by, 1, Vin);
+  }
   __syncthreads();
 
   // ---- Jacobi sweeps
@@ -815,6 +900,20 @@ __global__ void __maxnreg__(max_regs_for(CPL * NP))
   }
 }
 
+template <int G, int CPL, int NP>
+__global__ void __maxnreg__(max_regs_for(CPL * NP))
+    jacobi_svt_kernel(SliceArgs a, SliceShape sh) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SliceShared ss;
+  const int C = sh.C;
+  const int crank = C > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int so = blockIdx.x / C;     // slice ordinal in this launch
+  float* xbuf = C > 1 ? reinterpret_cast<float*>(static_cast<char*>(a.scratch) +
+                                                 (size_t)so * sh.xbuf_floats * sizeof(float))
+                      : nullptr;
+  svt_slice<G, CPL, NP>(a, sh, so, crank, xbuf, smem_raw, ss);
+}
+
 int max_optin_smem() {
   static int max_optin = -1;
   if (max_optin < 0) {
@@ -960,6 +1059,307 @@ cudaError_t launch_gc(const SliceArgs& a, const SliceShape& sh, size_t smem, int
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Persistent batched launch.  One launch per ADMM iteration runs, for every tensor of a batch,
+// the slice SVTs of that iteration (Lemma of Sec. 4.1 per Fourier slice; the slices of all
+// tensors are independent, eq. shrink2) and then the fused tube pass that follows them
+// (completion: eq. proj and the dual update of Sec. 4; RPCA: eq. sparse / sparse2 and eq.
+// dual of Sec. 5).  Work is taken from device queues:
+//   1. cluster items: (tensor, slice) pairs of the tensors planned with C CTAs per slice, in
+//      decreasing cost; crank 0 of a cluster takes the next one and shares it over DSMEM;
+//   2. CTA items: slices of the small tensors planned with one CTA per slice, in decreasing
+//      cost, taken by each CTA once the cluster items are gone;
+//   3. tube tiles: (tensor, 32 tubes) in the order in which the tensors' slices finish.
+// A tube tile of tensor t starts when t's slices of this iteration are all written: a per-tensor
+// counter, raised after each slice, is waited on with a bounded wait (globaltimer, 2 s) that
+// sets an error word instead of hanging.  Only taken items are waited on, and a taken item is
+// held by a running CTA, so the waits always end.
+// ---------------------------------------------------------------------------------------------
+constexpr int kBatchG = 16;                               // lanes per vector pair
+constexpr unsigned long long kBatchWaitNs = 2000000000ull; // bounded wait of a tube tile
+
+struct BatchDesc {
+  BatchTensor t;
+  SliceShape sh;   // slice-SVT plan (sh.C = 1: CTA items, else cluster items)
+  int rm;          // tube tile rows per thread (2, 4, 8)
+  int pad;
+};
+
+struct BatchLaunch {
+  const BatchDesc* desc;
+  const int2* big;
+  const int2* small;
+  const int* tile_start;    // n + 1 prefix of tiles, in tile order
+  const int* tile_tensor;   // tensor at each tile-order position
+  int n, nbig, nsmall, ntiles;
+  BatchIter it;
+  float* xbuf;
+  size_t xbuf_floats;
+  int C;
+};
+
+__device__ __forceinline__ unsigned long long batch_clock() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned batch_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ SliceArgs batch_slice_args(const BatchDesc& d, const BatchIter& it) {
+  const BatchTensor& t = d.t;
+  SliceArgs a{};
+  a.ahat = t.spec_a;
+  a.zhat = t.spec_b;
+  a.slices = t.slices;
+  a.nslices = t.nslices;
+  a.n1 = t.n1;
+  a.n2 = t.n2;
+  a.N12 = t.g.N12;
+  a.tau = (float)(t.scale / it.r);
+  a.tol = it.tol;
+  a.max_sweeps = it.max_sweeps;
+  a.stat = t.stat;
+  a.acc = t.acc;
+  if (t.warm) {
+    // V form from the previous iteration's V (cold every kWarmColdEvery iterations), rebuilt
+    // in the U form from B itself
+    const int nv = min(t.n1, t.n2);
+    a.vout = t.vwarm;
+    a.vstride = (int64_t)nv * nv;
+    a.brb = t.spec_a;
+    if (it.k % kWarmColdEvery != 0) {
+      a.vin = t.vwarm;
+      a.prerot = 1;
+    }
+  }
+  return a;
+}
+
+// The tube pass of tensor t that follows iteration it.k (it.k < 0: the first pass); false
+// when the tensor has none there.
+__device__ bool batch_tube_args(const BatchDesc& d, const BatchIter& it, TubeArgs& a) {
+  const BatchTensor& t = d.t;
+  a = TubeArgs{};
+  a.g = t.g;
+  a.twid_h = t.twid_h;
+  a.twid_f = t.twid_f;
+  a.ratio = 1.f;
+  const bool complete = t.kind == 1;
+  if (it.k < 0) {
+    a.in = t.in;
+    a.spec_out = t.spec_a;
+    if (complete) {
+      a.mode = TUBE_COMPLETE;
+      a.state = t.state;
+      a.first = 1;
+      a.write_out = it.iters == 1;
+      a.out0 = t.out0;
+    } else {
+      a.mode = TUBE_FWD;
+    }
+    return true;
+  }
+  const int k = it.k;
+  if (complete) {
+    if (k + 1 < it.iters) {
+      a.mode = TUBE_COMPLETE;
+      a.in = t.in;
+      a.state = t.state;
+      a.spec_in = t.spec_b;
+      a.spec_out = t.spec_a;
+      a.ratio = (float)(it.r / it.r_next);
+      a.write_out = k + 2 == it.iters;
+      a.out0 = t.out0;
+      return true;
+    }
+    if (t.out1) {
+      a.mode = TUBE_INV;
+      a.spec_in = t.spec_b;
+      a.out0 = t.out1;
+      return true;
+    }
+    return false;
+  }
+  a.mode = TUBE_RPCA;
+  a.in = t.in;
+  a.state = t.state;
+  a.spec_in = t.spec_b;
+  a.spec_out = t.spec_a;
+  a.ratio = (float)(it.r / it.r_next);
+  a.kappa = (float)((double)t.lambda / it.r);
+  a.first = k == 0;
+  a.last = k + 1 == it.iters;
+  a.out0 = t.out0;
+  a.out1 = t.out1;
+  a.tube_sparse = t.tube_sparse;
+  return true;
+}
+
+template <int CMAX>
+__device__ void batch_slice(const SliceArgs& a, const SliceShape& sh, int so, int crank,
+                            float* xbuf, unsigned char* smem_raw, SliceShared& ss) {
+  switch (sh.cpl) {
+    case 1: svt_slice<kBatchG, 1, 1>(a, sh, so, crank, xbuf, smem_raw, ss); break;
+    case 2:
+      if constexpr (CMAX >= 2) svt_slice<kBatchG, 2, 1>(a, sh, so, crank, xbuf, smem_raw, ss);
+      break;
+    case 3:
+      if constexpr (CMAX >= 3) svt_slice<kBatchG, 3, 1>(a, sh, so, crank, xbuf, smem_raw, ss);
+      break;
+    case 4:
+      if constexpr (CMAX >= 4) svt_slice<kBatchG, 4, 1>(a, sh, so, crank, xbuf, smem_raw, ss);
+      break;
+    case 6:
+      if constexpr (CMAX >= 6) svt_slice<kBatchG, 6, 1>(a, sh, so, crank, xbuf, smem_raw, ss);
+      break;
+    case 8:
+      if constexpr (CMAX >= 8) svt_slice<kBatchG, 8, 1>(a, sh, so, crank, xbuf, smem_raw, ss);
+      break;
+    default: break;
+  }
+}
+
+template <int CMAX>
+__global__ void __maxnreg__(max_regs_for(CMAX)) batch_iter_kernel(BatchLaunch L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SliceShared ss;
+  __shared__ int s_item;
+  const BatchIter& it = L.it;
+  const int C = L.C;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = C > 1 ? (int)cluster.block_rank() : 0;
+  float* xbuf = C > 1 ? L.xbuf + (size_t)(blockIdx.x / C) * L.xbuf_floats : nullptr;
+  if (it.k >= 0) {
+    // 1. cluster items (every CTA of a cluster takes the same number of turns)
+    if (C > 1 && L.nbig > 0) {
+      for (;;) {
+        if (crank == 0 && threadIdx.x == 0) s_item = atomicAdd(&it.ctr[0], 1);
+        cluster.sync();
+        const int item = *cluster.map_shared_rank(&s_item, 0);
+        cluster.sync();
+        if (item >= L.nbig) break;
+        const int2 w = L.big[item];
+        const BatchDesc& d = L.desc[w.x];
+        batch_slice<CMAX>(batch_slice_args(d, it), d.sh, w.y, crank, xbuf, smem_raw, ss);
+        __threadfence();
+        cluster.sync();   // every CTA of the cluster has written its columns of the slice
+        if (crank == 0 && threadIdx.x == 0) atomicAdd(&it.done[w.x], 1u);
+      }
+    }
+    // 2. single-CTA items
+    for (;;) {
+      if (threadIdx.x == 0) s_item = atomicAdd(&it.ctr[1], 1);
+      __syncthreads();
+      const int item = s_item;
+      __syncthreads();
+      if (item >= L.nsmall) break;
+      const int2 w = L.small[item];
+      const BatchDesc& d = L.desc[w.x];
+      batch_slice<CMAX>(batch_slice_args(d, it), d.sh, w.y, 0, nullptr, smem_raw, ss);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(&it.done[w.x], 1u);
+    }
+    if (it.slices_only) return;
+  }
+  // 3. tube tiles (threads TILE_THREADS and up skip the tile work)
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&it.ctr[2], 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= L.ntiles) break;
+    int lo = 0, hi = L.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (L.tile_start[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const int tix = L.tile_tensor[lo];
+    const BatchDesc& d = L.desc[tix];
+    TubeArgs ta;
+    if (!batch_tube_args(d, it, ta)) continue;
+    if (it.k >= 0) {
+      if (threadIdx.x == 0) {
+        const unsigned target = (unsigned)(it.k + 1) * (unsigned)d.t.nslices;
+        const unsigned long long t0 = batch_clock();
+        while (batch_ld_acquire(&it.done[tix]) < target) {
+          if (batch_clock() - t0 > kBatchWaitNs) {
+            atomicExch(it.err, 1);
+            break;
+          }
+          __nanosleep(256);
+        }
+      }
+      __syncthreads();
+      __threadfence();
+    }
+    if (threadIdx.x < TILE_THREADS) {
+      const int64_t t0 = (int64_t)(item - L.tile_start[lo]) * TT;
+      switch (d.rm) {
+        case 2: tube_tile_body<2>(ta, t0, smem_raw); break;
+        case 4: tube_tile_body<4>(ta, t0, smem_raw); break;
+        default: tube_tile_body<8>(ta, t0, smem_raw); break;
+      }
+    }
+  }
+}
+
+template <int CMAX>
+cudaError_t batch_occupancy(const BatchPlan& p, int* clusters) {
+  cudaError_t e = cudaFuncSetAttribute(batch_iter_kernel<CMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e != cudaSuccess) return e;
+  if (p.C == 1) {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_iter_kernel<CMAX>, p.threads,
+                                                      p.smem);
+    *clusters = per_sm * device_sm_count();
+    return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(p.C * device_sm_count()), 1, 1);
+  cfg.blockDim = dim3((unsigned)p.threads, 1, 1);
+  cfg.dynamicSmemBytes = p.smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)p.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(clusters, batch_iter_kernel<CMAX>, &cfg);
+}
+
+template <int CMAX>
+cudaError_t batch_launch(const BatchPlan& p, const BatchLaunch& L, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(batch_iter_kernel<CMAX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)p.grid, 1, 1);
+  cfg.blockDim = dim3((unsigned)p.threads, 1, 1);
+  cfg.dynamicSmemBytes = p.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)p.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, batch_iter_kernel<CMAX>, L);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 }  // namespace
 
 bool jacobi_svt_supported(int n1, int n2) {
@@ -1020,6 +1420,124 @@ cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st) {
   TSVD_CASE(16, 1, 2) TSVD_CASE(16, 2, 2) TSVD_CASE(16, 3, 2) TSVD_CASE(16, 4, 2)
 #undef TSVD_CASE
   return cudaErrorInvalidValue;
+}
+
+
+bool batch_plan(const BatchTensor* ts, int n, int C, int small_nv, BatchPlan& plan,
+                std::vector<unsigned char>& table) {
+  if (n <= 0 || (C != 1 && C != 2 && C != 4 && C != 8)) return false;
+  plan = BatchPlan{};
+  plan.C = C;
+  plan.small_nv = small_nv < 0 ? 2 * C * kMinBlock : small_nv;
+  plan.ntensors = n;
+  std::vector<BatchDesc> desc((size_t)n);
+  size_t smem = 0;
+  int cmax = 1;
+  for (int i = 0; i < n; ++i) {
+    const BatchTensor& t = ts[i];
+    BatchDesc& d = desc[(size_t)i];
+    std::memset(&d, 0, sizeof d);
+    d.t = t;
+    const int nv = std::min(t.n1, t.n2);
+    const SliceKnobs k1 = {1, kBatchG, 1, t.warm ? 1 : 0};
+    const SliceKnobs kc = {C, kBatchG, 1, t.warm ? 1 : 0};
+    size_t sm = 0;
+    SliceShape sh;
+    bool ok = false;
+    if (C == 1 || nv < plan.small_nv) ok = plan_with_ctas(t.n1, t.n2, 1, k1, sh, sm);
+    if (!ok && C > 1) ok = plan_with_ctas(t.n1, t.n2, C, kc, sh, sm);
+    if (!ok || sh.G != kBatchG || sh.np != 1) return false;
+    d.sh = sh;
+    d.rm = tile_rm(t.g);
+    if (d.rm == 0) return false;
+    smem = std::max(smem, std::max(sm, tile_smem_bytes(t.g)));
+    cmax = std::max(cmax, sh.cpl);
+    if (sh.C > 1) plan.xbuf_floats = std::max(plan.xbuf_floats, sh.xbuf_floats);
+  }
+  plan.cmax = cmax <= 4 ? 4 : 8;   // (a 2-chunk instance would run at 80 registers and spill)
+  plan.threads = max_warps_for(plan.cmax) * 32;
+  if (plan.threads < TILE_THREADS) return false;
+  plan.smem = smem;
+  if (smem + kStaticSmemReserve > (size_t)max_optin_smem()) return false;
+  // items in decreasing cost: m n^2 per slice, a cold start ~3x the sweeps of a warm one
+  std::vector<double> cost((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const double m = std::max(ts[i].n1, ts[i].n2), nn = std::min(ts[i].n1, ts[i].n2);
+    cost[(size_t)i] = m * nn * nn * (ts[i].warm ? 1.0 : 3.0);
+  }
+  std::vector<int2> big, small;
+  for (int i = 0; i < n; ++i)
+    for (int so = 0; so < ts[i].nslices; ++so)
+      (desc[(size_t)i].sh.C > 1 ? big : small).push_back(make_int2(i, so));
+  auto by_cost = [&](const int2& a, const int2& b) {
+    if (cost[(size_t)a.x] != cost[(size_t)b.x]) return cost[(size_t)a.x] > cost[(size_t)b.x];
+    return a.x != b.x ? a.x < b.x : a.y < b.y;
+  };
+  std::sort(big.begin(), big.end(), by_cost);
+  std::sort(small.begin(), small.end(), by_cost);
+  plan.nbig = (int)big.size();
+  plan.nsmall = (int)small.size();
+  // tube tiles: tensors in the order their last slice item is taken
+  std::vector<int> last((size_t)n, -1), order((size_t)n);
+  for (int j = 0; j < plan.nbig; ++j) last[(size_t)big[(size_t)j].x] = j;
+  for (int j = 0; j < plan.nsmall; ++j) last[(size_t)small[(size_t)j].x] = plan.nbig + j;
+  for (int i = 0; i < n; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return last[(size_t)a] < last[(size_t)b]; });
+  std::vector<int> tstart((size_t)n + 1, 0), ttensor((size_t)n);
+  for (int j = 0; j < n; ++j) {
+    const int i = order[(size_t)j];
+    ttensor[(size_t)j] = i;
+    tstart[(size_t)j + 1] = tstart[(size_t)j] + (int)((ts[i].g.N12 + TT - 1) / TT);
+  }
+  plan.ntiles = tstart[(size_t)n];
+  // device table
+  plan.off_desc = 0;
+  plan.off_big = align16(sizeof(BatchDesc) * (size_t)n);
+  plan.off_small = plan.off_big + align16(sizeof(int2) * big.size());
+  plan.off_tstart = plan.off_small + align16(sizeof(int2) * small.size());
+  plan.off_ttensor = plan.off_tstart + align16(sizeof(int) * ((size_t)n + 1));
+  plan.table_bytes = plan.off_ttensor + align16(sizeof(int) * (size_t)n);
+  table.assign(plan.table_bytes, 0);
+  std::memcpy(table.data() + plan.off_desc, desc.data(), sizeof(BatchDesc) * (size_t)n);
+  if (!big.empty()) std::memcpy(table.data() + plan.off_big, big.data(), sizeof(int2) * big.size());
+  if (!small.empty())
+    std::memcpy(table.data() + plan.off_small, small.data(), sizeof(int2) * small.size());
+  std::memcpy(table.data() + plan.off_tstart, tstart.data(), sizeof(int) * ((size_t)n + 1));
+  std::memcpy(table.data() + plan.off_ttensor, ttensor.data(), sizeof(int) * (size_t)n);
+  // persistent grid: the clusters that fit on the device at once
+  int clusters = 0;
+  cudaError_t e = plan.cmax == 4 ? batch_occupancy<4>(plan, &clusters)
+                                 : batch_occupancy<8>(plan, &clusters);
+  if (e != cudaSuccess || clusters <= 0) {
+    cudaGetLastError();
+    clusters = std::max(1, device_sm_count() / C);
+  }
+  plan.grid = clusters * C;
+  plan.scratch_bytes = C > 1 ? (size_t)clusters * plan.xbuf_floats * sizeof(float) : 0;
+  return true;
+}
+
+cudaError_t launch_batch_iteration(const BatchPlan& p, const void* table_dev, void* scratch,
+                                   const BatchIter& it, cudaStream_t st) {
+  const char* tb = static_cast<const char*>(table_dev);
+  BatchLaunch L;
+  L.desc = reinterpret_cast<const BatchDesc*>(tb + p.off_desc);
+  L.big = reinterpret_cast<const int2*>(tb + p.off_big);
+  L.small = reinterpret_cast<const int2*>(tb + p.off_small);
+  L.tile_start = reinterpret_cast<const int*>(tb + p.off_tstart);
+  L.tile_tensor = reinterpret_cast<const int*>(tb + p.off_ttensor);
+  L.n = p.ntensors;
+  L.nbig = p.nbig;
+  L.nsmall = p.nsmall;
+  L.ntiles = p.ntiles;
+  L.it = it;
+  L.xbuf = static_cast<float*>(scratch);
+  L.xbuf_floats = p.xbuf_floats;
+  L.C = p.C;
+  if (p.C > 1 && p.nbig > 0 && !scratch) return cudaErrorInvalidValue;
+  if (p.cmax == 4) return batch_launch<4>(p, L, st);
+  return batch_launch<8>(p, L, st);
 }
 
 }  // namespace tsvd

@@ -54,6 +54,10 @@ struct tsvd_ctx {
   cudaEvent_t fork = nullptr;
   // plain form: the current solve runs the V form (warm start), for the plan lookups
   bool vform_now = false;
+  // persistent batched solves: tuned (cluster size, single-CTA threshold) per batch shape, and
+  // the host copy of the device table (alive while its copy may be in flight)
+  std::map<std::vector<int64_t>, std::array<int, 2>> batch_tuned;
+  std::vector<unsigned char> batch_table;
   // tsvd_factor: converged vectors, rotations, Fourier-domain factors and output staging
   char* fbuf = nullptr;
   size_t fbuf_cap = 0;
@@ -664,6 +668,8 @@ tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
   if (o.autotune != 0 && o.autotune != 1) return fail(c, TSVD_EINVAL, "autotune must be 0 or 1");
   if (o.use_graphs != 0 && o.use_graphs != 1)
     return fail(c, TSVD_EINVAL, "use_graphs must be 0 or 1");
+  if (o.batch_persistent != 0 && o.batch_persistent != 1)
+    return fail(c, TSVD_EINVAL, "batch_persistent must be 0 or 1");
   return TSVD_OK;
 }
 
@@ -756,7 +762,7 @@ tsvd_status run_slice(tsvd_ctx* c, const SliceArgs& a) {
 }
 
 // ---- plain form with warm start
-constexpr int kColdEvery = 64;   // iterations between cold starts of the warm-started Jacobi
+constexpr int kColdEvery = kWarmColdEvery;   // iterations between cold starts of the warm start
 
 // Whether the V form (needed by the warm start) has a plan for this slice shape.
 bool warm_plan_exists(tsvd_ctx* c, const Problem& p) {
@@ -1117,7 +1123,7 @@ struct BatchItem {
 };
 
 // Carves the regions of one tensor from `base` (nullptr: only measure); returns its bytes.
-size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base, int iters) {
+size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base, int iters, bool persistent = false) {
   const TubeGeom& g = it.p.g;
   it.slices.clear();
   for (int kh = 0; kh < g.hh; ++kh)
@@ -1133,8 +1139,9 @@ size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base, int iters) {
   it.warm = !mixed && iters >= 2 && ws != TSVD_WARM_OFF && (complete || ws == TSVD_WARM_ON) &&
             warm_plan_exists(c, it.p);
   it.kn = planned_knobs(c, it.p, it.w.ndistinct, it.warm ? 1 : vform_of(c));
-  const size_t jbytes =
-      mixed ? 0 : jacobi_svt_scratch_bytes((int)it.p.n1, (int)it.p.n2, it.w.ndistinct, it.kn);
+  // (the persistent batched kernel keeps one exchange buffer per cluster instead)
+  const size_t jbytes = mixed || persistent ? 0
+                        : jacobi_svt_scratch_bytes((int)it.p.n1, (int)it.p.n2, it.w.ndistinct, it.kn);
   size_t total = 0;
   auto take = [&](size_t bytes) {
     char* ptr = base ? base + total : nullptr;
@@ -1154,7 +1161,8 @@ size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base, int iters) {
   it.w.warm = it.warm;
   it.w.nv = (int)std::min(it.p.n1, it.p.n2);
   if (it.warm) {
-    it.w.abar = reinterpret_cast<float2*>(take(spec));
+    // the persistent kernel forms the pre-rotated slices while loading them
+    it.w.abar = persistent ? nullptr : reinterpret_cast<float2*>(take(spec));
     it.w.vwarm = reinterpret_cast<float2*>(
         take((size_t)g.nstore * it.w.nv * it.w.nv * sizeof(float2)));
   }
@@ -1293,6 +1301,7 @@ void tsvd_default_opts(tsvd_opts* o) {
   o->rsvt_kmax = 0;
   o->rsvt_power = 2;
   o->warm_start = TSVD_WARM_AUTO;
+  o->batch_persistent = 1;
 }
 
 tsvd_status tsvd_create(tsvd_ctx** out, int device, void* cuda_stream, const tsvd_opts* opts) {
@@ -2007,6 +2016,196 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
 
 namespace {
 
+// ---- persistent batched solves (plain form)
+BatchTensor batch_tensor(tsvd_ctx* c, const BatchItem& it) {
+  BatchTensor t{};
+  const tsvd_problem& q = *it.src;
+  t.g = it.p.g;
+  t.kind = q.kind;
+  t.n1 = (int)it.p.n1;
+  t.n2 = (int)it.p.n2;
+  t.nslices = it.w.ndistinct;
+  t.warm = it.warm ? 1 : 0;
+  t.scale = threshold_scale(c, it.p);
+  t.lambda = q.lambda;
+  t.tube_sparse = c->opts.sparse_mode == TSVD_SPARSE_TUBE;
+  t.spec_a = it.w.spec_a;
+  t.spec_b = it.w.spec_b;
+  t.state = it.w.state;
+  t.in = q.kind == TSVD_PROBLEM_COMPLETE ? it.w.yn : q.M;
+  t.twid_h = it.w.twid;
+  t.twid_f = it.w.twid ? it.w.twid + it.p.g.nh : nullptr;
+  t.slices = it.w.slices;
+  t.stat = it.w.stat;
+  t.acc = it.w.acc;
+  t.vwarm = it.w.vwarm;
+  t.out0 = q.out0;
+  t.out1 = q.out1;
+  return t;
+}
+
+// Plans a persistent batched solve may use: (cluster size, single-CTA threshold), the
+// threshold 2 C x 16 (blocks of at least 16 vectors) or none (single-CTA slices only where a
+// cluster plan does not fit).
+std::vector<std::array<int, 2>> batch_candidates() {
+  std::vector<std::array<int, 2>> out;
+  for (int C : {2, 4, 8}) {
+    out.push_back({C, 2 * C * 16});
+    out.push_back({C, 0});
+  }
+  return out;
+}
+
+std::vector<int64_t> batch_signature(const std::vector<BatchItem>& items) {
+  std::vector<int64_t> key;
+  for (const BatchItem& it : items) {
+    const int64_t v[] = {it.src->kind, it.p.n1, it.p.n2, it.p.g.nf, it.p.g.nh, it.warm ? 1 : 0};
+    key.insert(key.end(), std::begin(v), std::end(v));
+  }
+  return key;
+}
+
+// The persistent batched solve: tensors' regions carved and initialised, inputs checked.
+// ctr: 3 (iters + 1) queue counters, then one completion counter per tensor, then the error
+// word.  On the first call with a new batch shape every candidate plan is timed on iteration
+// 0's slice SVTs (sweeps capped at 4) and the fastest kept; then the init launch and one
+// launch per iteration run (captured into a graph with use_graphs), and the call waits for
+// the error word.
+tsvd_status persistent_batch(tsvd_ctx* c, const std::vector<BatchItem>& items, int iters,
+                             const std::vector<std::array<int, 2>>& cands, char* table_dev,
+                             char* scratch, int* ctr) {
+  const int count = (int)items.size();
+  unsigned* done = reinterpret_cast<unsigned*>(ctr + 3 * (iters + 1));
+  int* err = reinterpret_cast<int*>(done + count);
+  std::vector<BatchTensor> ts;
+  for (const BatchItem& it : items) ts.push_back(batch_tensor(c, it));
+  BatchPlan plan;
+  auto make = [&](const std::array<int, 2>& cd) -> tsvd_status {
+    if (!batch_plan(ts.data(), count, cd[0], cd[1], plan, c->batch_table))
+      return fail(c, TSVD_EUNSUPPORTED, "no persistent batch plan");
+    TSVD_CUDA(c, cudaMemcpyAsync(table_dev, c->batch_table.data(), plan.table_bytes,
+                                 cudaMemcpyHostToDevice, c->cur));
+    return TSVD_OK;
+  };
+  auto reset = [&]() -> tsvd_status {
+    TSVD_CUDA(c, cudaMemsetAsync(ctr, 0,
+                                 3 * ((size_t)iters + 1) * sizeof(int) + (size_t)count * sizeof(unsigned) +
+                                     sizeof(int),
+                                 c->cur));
+    return TSVD_OK;
+  };
+  BatchIter bi{};
+  bi.iters = iters;
+  bi.tol = c->opts.jacobi_tol;
+  bi.max_sweeps = c->opts.max_sweeps;
+  bi.done = done;
+  bi.err = err;
+  auto run = [&](int k, double r, double r_next, bool slices_only) -> tsvd_status {
+    bi.k = k;
+    bi.r = r;
+    bi.r_next = r_next;
+    bi.ctr = ctr + 3 * (k + 1);
+    bi.slices_only = slices_only ? 1 : 0;
+    TSVD_TRY(record_event(c, 0));
+    TSVD_TRY(launch(c, launch_batch_iteration(plan, table_dev, scratch, bi, c->cur),
+                    "persistent batched iteration"));
+    if (k >= 0) ++c->slice_launches;
+    return record_event(c, 0);
+  };
+  const std::vector<int64_t> sig = batch_signature(items);
+  auto tuned = c->batch_tuned.find(sig);
+  if (tuned == c->batch_tuned.end()) {
+    std::array<int, 2> best = cands[0];
+    if (cands.size() > 1 && c->opts.autotune) {
+      // time iteration 0's slice SVTs of every candidate on the real first spectra
+      c->cur = c->stream;
+      TSVD_TRY(make(cands[0]));
+      TSVD_TRY(reset());
+      TSVD_TRY(run(-1, c->opts.rho0, c->opts.rho0, false));
+      cudaEvent_t e0, e1;
+      TSVD_CUDA(c, cudaEventCreate(&e0));
+      if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, TSVD_ECUDA, "cudaEventCreate failed");
+      }
+      const int ms_keep = bi.max_sweeps;
+      bi.max_sweeps = std::min(4, ms_keep);
+      float best_ms = 1e30f;
+      tsvd_status st = TSVD_OK;
+      for (const auto& cd : cands) {
+        if ((st = make(cd)) != TSVD_OK) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && st == TSVD_OK; ++rep) {   // the first run loads the kernel
+          // iteration 0's queue counters and the completion counters start from zero
+          TSVD_CUDA(c, cudaMemsetAsync(ctr + 3, 0, 3 * sizeof(int), c->cur));
+          TSVD_CUDA(c, cudaMemsetAsync(done, 0, (size_t)count * sizeof(unsigned), c->cur));
+          cudaEventRecord(e0, c->cur);
+          st = run(0, c->opts.rho0, c->opts.rho0, true);
+          cudaEventRecord(e1, c->cur);
+        }
+        if (st != TSVD_OK) break;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms < best_ms) {
+          best_ms = ms;
+          best = cd;
+        }
+      }
+      bi.max_sweeps = ms_keep;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (st != TSVD_OK) return st;
+      TSVD_CUDA(c, cudaGetLastError());
+      // the timing runs added to the per-tensor counters
+      for (const BatchItem& it : items) {
+        TSVD_CUDA(c, cudaMemsetAsync(it.w.acc, 0, sizeof(SweepAccum), c->cur));
+        TSVD_CUDA(c, cudaMemsetAsync(it.w.stat, 0, (size_t)it.p.g.nstore * sizeof(SliceStat), c->cur));
+      }
+      c->launches = 0;
+      c->slice_launches = 0;
+      c->events_used = 0;
+    }
+    tuned = c->batch_tuned.emplace(sig, best).first;
+  }
+  c->cur = c->stream;
+  TSVD_TRY(make(tuned->second));
+  std::vector<int64_t> key = {4, count, iters, (int64_t)(intptr_t)c->ws, (int64_t)c->ws_cap,
+                              c->opts.tnn_scale, c->opts.sparse_mode, c->opts.max_sweeps,
+                              c->opts.timing, tuned->second[0], tuned->second[1]};
+  double d[4] = {c->opts.rho0, c->opts.mu, c->opts.rho_max, (double)c->opts.jacobi_tol};
+  for (double v : d) {
+    int64_t bits;
+    std::memcpy(&bits, &v, sizeof bits);
+    key.push_back(bits);
+  }
+  for (const BatchItem& it : items) {
+    const tsvd_problem& q = *it.src;
+    int64_t lbits = 0;
+    std::memcpy(&lbits, &q.lambda, sizeof q.lambda);
+    const int64_t vals[] = {q.kind, q.order, q.dims[0], q.dims[1], q.dims[2],
+                            q.order == 4 ? q.dims[3] : 1, (int64_t)(intptr_t)q.M,
+                            (int64_t)(intptr_t)q.omega, (int64_t)(intptr_t)q.out0,
+                            (int64_t)(intptr_t)q.out1, lbits, it.warm ? 1 : 0};
+    key.insert(key.end(), std::begin(vals), std::end(vals));
+  }
+  auto body = [&]() -> tsvd_status {
+    TSVD_TRY(reset());
+    double r = c->opts.rho0;
+    TSVD_TRY(run(-1, r, r, false));
+    for (int k = 0; k < iters; ++k) {
+      const double r_next = std::fmin(c->opts.mu * r, c->opts.rho_max);
+      TSVD_TRY(run(k, r, r_next, false));
+      r = r_next;
+    }
+    return TSVD_OK;
+  };
+  TSVD_TRY(run_maybe_graph(c, key, true, body));
+  int err_h = 0;
+  TSVD_CUDA(c, cudaMemcpyAsync(&err_h, err, sizeof err_h, cudaMemcpyDeviceToHost, c->stream));
+  TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (err_h) return fail(c, TSVD_ETIMEOUT, "a persistent batched launch gave up a bounded wait");
+  return TSVD_OK;
+}
+
 // The batched solve behind tsvd_solve_batched (only_kind = 0: any mix of problems) and
 // tnn_complete_batched / trpca_batched (every problem must be of kind only_kind).
 tsvd_status solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, int iters,
@@ -2048,15 +2247,41 @@ tsvd_status solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, 
     if (stats) std::memset(stats, 0, sizeof *stats);
     return TSVD_OK;
   }
-  // one allocation for every tensor's regions plus the batch's non-finite counters
+  // the plain form runs as one persistent launch per iteration when every tensor has a plan
+  bool persist = !mixed_precision(c) && c->opts.batch_persistent && iters > 0;
+  std::vector<std::array<int, 2>> cands;
+  size_t table_cap = 0, scratch_cap = 0;
+  if (persist) {
+    for (BatchItem& it : items) carve_item(c, it, nullptr, iters, true);
+    std::vector<BatchTensor> ts;
+    for (const BatchItem& it : items) ts.push_back(batch_tensor(c, it));
+    for (const auto& cd : batch_candidates()) {
+      BatchPlan pl;
+      std::vector<unsigned char> tab;
+      if (!batch_plan(ts.data(), count, cd[0], cd[1], pl, tab)) continue;
+      cands.push_back(cd);
+      table_cap = std::max(table_cap, pl.table_bytes);
+      scratch_cap = std::max(scratch_cap, pl.scratch_bytes);
+    }
+    persist = !cands.empty();
+  }
+  // one allocation for every tensor's regions plus the batch's non-finite counters (and for
+  // the persistent launch its table, exchange buffers, queue counters and error word)
   size_t total = 0;
   std::vector<size_t> offs((size_t)count);
   for (int i = 0; i < count; ++i) {
     offs[(size_t)i] = total;
-    total += carve_item(c, items[(size_t)i], nullptr, iters);
+    total += carve_item(c, items[(size_t)i], nullptr, iters, persist);
   }
   const size_t bad_off = total;
   total += align_up((size_t)count * sizeof(int));
+  const size_t table_off = total;
+  total += align_up(table_cap);
+  const size_t scratch_off = total;
+  total += align_up(scratch_cap);
+  const size_t ctr_off = total;
+  const size_t nctr = persist ? 3 * ((size_t)iters + 1) : 0;
+  total += align_up(nctr * sizeof(int) + (size_t)count * sizeof(unsigned) + sizeof(int));
   if (total > c->ws_cap) {
     if (c->ws) {
       TSVD_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -2079,7 +2304,7 @@ tsvd_status solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, 
   TSVD_CUDA(c, cudaMemsetAsync(bad, 0, (size_t)count * sizeof(int), c->stream));
   for (int i = 0; i < count; ++i) {
     BatchItem& it = items[(size_t)i];
-    carve_item(c, it, c->ws + offs[(size_t)i], iters);
+    carve_item(c, it, c->ws + offs[(size_t)i], iters, persist);
     const TubeGeom& g = it.p.g;
     fill_twiddles(g, it.twid);   // same FP64 tables as the single-tensor calls
     TSVD_CUDA(c, cudaMemcpyAsync(it.w.twid, it.twid.data(), it.twid.size() * sizeof(float2),
@@ -2119,9 +2344,13 @@ tsvd_status solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, 
         TSVD_CUDA(c, cudaMemsetAsync(q.out1, 0, bytes, c->stream));
       }
     }
+  } else if (persist) {
+    TSVD_TRY(persistent_batch(c, items, iters, cands, c->ws + table_off,
+                              scratch_cap ? c->ws + scratch_off : nullptr,
+                              reinterpret_cast<int*>(c->ws + ctr_off)));
   } else {
-    // stream branches: tensor i runs on branch i mod B, all branches fork from and join the
-    // issuing stream, so the tensors' chains overlap on the GPU
+    // stream branches: every branch forks from and joins the issuing stream, so the tensors'
+    // chains overlap on the GPU
     const int nbr = std::min(count, 16);
     while ((int)c->branches.size() < nbr) {
       cudaStream_t s;
@@ -2153,12 +2382,32 @@ tsvd_status solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, 
                               it.kn.ppg, it.kn.vform, it.warm ? 1 : 0};
       key.insert(key.end(), std::begin(vals), std::end(vals));
     }
+    // tensors to branches by longest processing time first, on the estimated slice-SVT work
+    // of a solve: m n^2 per distinct slice per sweep, ~3x fewer sweeps when warm-started
+    std::vector<int> branch_of((size_t)count, 0), order((size_t)count);
+    {
+      std::vector<double> cost((size_t)count), load((size_t)nbr, 0.0);
+      for (int i = 0; i < count; ++i) {
+        const BatchItem& it = items[(size_t)i];
+        const double m = (double)std::max(it.p.n1, it.p.n2), n = (double)std::min(it.p.n1, it.p.n2);
+        cost[(size_t)i] = m * n * n * it.w.ndistinct * (it.warm ? 1.0 : 3.0) + m * n;
+        order[(size_t)i] = i;
+      }
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int a, int b) { return cost[(size_t)a] > cost[(size_t)b]; });
+      for (int i : order) {
+        const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        branch_of[(size_t)i] = b;
+        load[(size_t)b] += cost[(size_t)i];
+      }
+    }
     auto body = [&]() -> tsvd_status {
       cudaStream_t base = c->cur;
       TSVD_CUDA(c, cudaEventRecord(c->fork, base));
       for (int b = 0; b < nbr; ++b) TSVD_CUDA(c, cudaStreamWaitEvent(c->branches[(size_t)b], c->fork, 0));
-      for (int i = 0; i < count; ++i) {
-        c->cur = c->branches[(size_t)(i % nbr)];
+      // the costliest tensors are issued first on their branches
+      for (int i : order) {
+        c->cur = c->branches[(size_t)branch_of[(size_t)i]];
         const tsvd_status st = enqueue_item(c, items[(size_t)i], iters);
         if (st != TSVD_OK) {
           c->cur = base;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace tsvd {
 
 // Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, cached per
@@ -181,10 +183,82 @@ struct SliceArgs {
   // V that is only unitary to rounding does not enter D_tau(B): the kept u_i span range(W)
   // and u_i^H B is taken from B itself.
   const float2* brb = nullptr;
+  // V form with vin: the kernel forms the pre-rotated vectors B V (columns) or V^T B (rows)
+  // from ahat = B and vin itself while loading them (no separate pre-rotated input)
+  int prerot = 0;
 };
 
 // Returns cudaErrorInvalidValue when a slice does not fit the kernel's shared memory.
 cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st);
+
+// ---- persistent batched launch (plain form): one kernel launch per ADMM iteration runs the
+// slice SVTs of every tensor of a batch, then the tube passes that follow them, from device
+// work queues (slice_svt.cu).
+// One tensor of the batch, as the host describes it.
+struct BatchTensor {
+  TubeGeom g;
+  int kind;                 // TSVD_PROBLEM_COMPLETE (1) or TSVD_PROBLEM_RPCA (2)
+  int n1, n2;
+  int nslices;              // distinct stored slices (the `slices` list)
+  int warm;                 // plain V-form warm start (completion tensors)
+  double scale;             // threshold scale: tau = scale / rho
+  float lambda;             // RPCA
+  int tube_sparse;          // RPCA: eq. sparse2 shrink
+  float2* spec_a;           // V-hat (slice SVT input) and B of the U-form rebuild
+  float2* spec_b;           // Z-hat (slice SVT output)
+  float* state;             // completion V = X + Q; RPCA W
+  const float* in;          // completion Yn (NaN = unobserved); RPCA M
+  const float2* twid_h;
+  const float2* twid_f;
+  const int* slices;
+  SliceStat* stat;
+  SweepAccum* acc;
+  float2* vwarm;            // warm: nstore x nv x nv accumulated right rotations
+  float* out0;              // completion X; RPCA L
+  float* out1;              // completion Z (nullable: not written); RPCA S
+};
+
+// Schedule of a persistent batched launch (filled by batch_plan).
+struct BatchPlan {
+  int C = 1;                // CTAs of a thread-block cluster (1, 2, 4 or 8)
+  int small_nv = 0;         // tensors with min(n1, n2) below this run their slices as
+                            // single-CTA items (if they fit one CTA), the others as cluster items
+  int cmax = 0;             // kernel instance: largest chunks per lane of any tensor's plan
+  int threads = 0;
+  size_t smem = 0;          // dynamic shared memory per CTA
+  int grid = 0;             // CTAs (a multiple of C)
+  int nbig = 0, nsmall = 0, ntiles = 0, ntensors = 0;
+  size_t xbuf_floats = 0;   // exchange buffer per cluster
+  size_t table_bytes = 0;   // device table: descriptors, item lists, tile prefix
+  size_t scratch_bytes = 0; // exchange buffers of all clusters
+  // byte offsets of the table's sections
+  size_t off_desc = 0, off_big = 0, off_small = 0, off_tstart = 0, off_ttensor = 0;
+};
+
+// Per-launch arguments of the persistent batched kernel.
+struct BatchIter {
+  int k;                    // ADMM iteration (the init launch: -1)
+  int iters;
+  double r, r_next;         // rho_k and rho_{k+1}
+  float tol;
+  int max_sweeps;
+  int* ctr;                 // 3 work-queue counters of this launch, zero before it
+  unsigned* done;           // per tensor: slice SVTs finished (monotonic over the solve)
+  int* err;                 // set to 1 when a bounded wait gave up
+  int slices_only = 0;      // skip the tube passes (plan timing)
+};
+
+// Iterations between cold starts of the warm-started plain Jacobi (V reset to I).
+constexpr int kWarmColdEvery = 64;
+
+// Plans the persistent launch for the tensors (C = 0: choose; small_nv < 0: choose) and
+// writes the device table (to be copied to the device verbatim) into `table`.
+bool batch_plan(const BatchTensor* ts, int n, int C, int small_nv, BatchPlan& plan,
+                std::vector<unsigned char>& table);
+// One launch: iteration it.k's slice SVTs of every tensor (it.k >= 0) and the tube passes
+// that follow them (the init launch, it.k = -1: the first tube passes only).
+cudaError_t launch_batch_iteration(const BatchPlan& plan, const void* table_dev, void* scratch,
+                                   const BatchIter& it, cudaStream_t st);
 
 // Fourier-domain factors of the truncated t-SVD from the converged Jacobi of every distinct
 // slice (factor.cu): W (len x nv per stored slice, as SliceArgs::wout writes it), sigma (nv per

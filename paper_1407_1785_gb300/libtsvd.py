@@ -56,7 +56,7 @@ class Opts(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p),
                 ("use_graphs", ctypes.c_int), ("rsvt_oversample", ctypes.c_int),
                 ("rsvt_kmax", ctypes.c_int), ("rsvt_power", ctypes.c_int),
-                ("warm_start", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("batch_persistent", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -216,11 +216,13 @@ def test_graph_replay_matches_direct_launches(kind, tmp_path):
         assert np.array_equal(x, outs[0][0]) and np.array_equal(y, outs[0][1])
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("warm", ["off", "auto", "on"])
-def test_batched_uneven_problems_match_oracle(warm):
+def test_batched_uneven_problems_match_oracle(warm, persistent):
     """A batch of uneven tensors (completion and RPCA, 3-way and 4-way) in one call: every
     tensor matches the oracle's solve, with the warm-started Jacobi off, on for the
-    completions only (the default) or on for all; a second call replays the captured batch
+    completions only (the default) or on for all, as one persistent launch per iteration
+    (the default) or as per-tensor stream branches; a second call replays the captured batch
     graph and gives the same bits."""
     from paper_1407_1785_gb300 import libtsvd
     warm_start = {"off": libtsvd.WARM_OFF, "auto": libtsvd.WARM_AUTO, "on": libtsvd.WARM_ON}[warm]
@@ -257,7 +259,7 @@ def test_batched_uneven_problems_match_oracle(warm):
         probs.append(q)
         keep.append(M)
     with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
-                         warm_start=warm_start) as ctx:
+                         warm_start=warm_start, batch_persistent=persistent) as ctx:
         first = None
         for call in range(2):
             st = ctx.solve_batched(probs, iters, stats=True)
@@ -267,7 +269,8 @@ def test_batched_uneven_problems_match_oracle(warm):
             else:
                 for (a, b), (c, d) in zip(got, first):
                     assert np.array_equal(a, c) and np.array_equal(b, d)
-            assert st["slice_launches"] == iters * len(specs)
+            # one launch per iteration for the whole batch, or one slice SVT per tensor
+            assert st["slice_launches"] == (iters if persistent else iters * len(specs))
             assert st["nonconverged"] == 0
     for (a, b), (ra, rb), M in zip(first, refs, keep):
         assert relerr(a, ra, floor=1e-6) <= ADMM_TOL
