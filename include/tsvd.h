@@ -127,15 +127,25 @@ typedef struct tsvd_opts {
                          sparse residual changes the small singular vectors at every
                          iteration, so a warm start saves fewer sweeps than the V form's
                          extra rotations cost. */
-  int batch_persistent; /* plain form, batched solves: 1 (default) runs each ADMM iteration of
-                         the whole batch as one persistent kernel launch that takes the slice
-                         SVTs of all tensors (largest first) and then their tube passes from
-                         device work queues, a tube pass starting once its tensor's slices are
-                         done; the cluster size and which tensors run one CTA per slice are
-                         autotuned per batch shape (timed on the first iteration) and kept in
-                         the context.  0: one chain of kernels per tensor on parallel stream
-                         branches. */
+  int batch_persistent; /* plain form, batched solves: 1 runs each ADMM iteration of the whole
+                         batch as one persistent kernel launch that takes the slice SVTs of all
+                         tensors (largest first) and then their tube passes from device work
+                         queues, a tube pass starting once its tensor's slices are done; the
+                         cluster size and which tensors run one CTA per slice are autotuned per
+                         batch shape (timed on the first iteration) and kept in the context.
+                         0 (default): one chain of kernels per tensor on parallel stream
+                         branches, which lets every tensor advance at its own pace (faster on
+                         uneven batches, where the persistent form waits each iteration for
+                         its slowest slice). */
+  int slice_form;     /* plain-form Jacobi: TSVD_SLICE_AUTO (default: the autotuner compares
+                         both forms), TSVD_SLICE_PAIRWISE (each local round rotates its vector
+                         pairs directly) or TSVD_SLICE_BLOCK (each round of vector blocks runs
+                         its rotations on the Gram matrix of the CTA's vectors, then applies
+                         their product to the vectors: the same rotations, fewer passes over
+                         the vectors) */
 } tsvd_opts;
+
+enum { TSVD_SLICE_AUTO = 0, TSVD_SLICE_PAIRWISE = 1, TSVD_SLICE_BLOCK = 2 };
 
 /* Counters of one ADMM solve (host struct). */
 typedef struct tsvd_stats {

@@ -110,13 +110,26 @@ struct SliceShape {
   int kcap;   // kept vectors per rebuild group: 2 bs, or as many rows of ld floats as the
               // 2 bs rows of rowp floats hold (a cluster's U-form rebuild imports those)
   size_t xbuf_floats;   // exchange buffer per slice (floats)
+  int block;  // 1: block rounds run on the Gram of the local vectors (block form)
+  int nlp;    // block form: row pitch of the Gram and of the accumulated rotation (odd)
 };
+
+// Floats of the block form's extra shared memory: the Gram G and the accumulated rotation W
+// (nl x nlp, planar re / im each) and, per pair slot, its rotation (float4) and indices (int2).
+__host__ __device__ inline size_t block_smem_floats(const SliceShape& sh) {
+  if (!sh.block) return 0;
+  const size_t nl = 2 * (size_t)sh.bs;
+  return 4 * nl * sh.nlp + 6 * (size_t)sh.bs;
+}
 
 __host__ __device__ inline size_t slice_smem_bytes(const SliceShape& sh) {
   const size_t nl = 2 * (size_t)sh.bs;   // vectors held by one CTA
   const size_t kc = (size_t)sh.kcap;
-  return 2 * nl * sh.rowp * sizeof(float) + (size_t)sh.len * sh.nc * sizeof(float2) +
-         kc * sh.nc * sizeof(float2) + nl * sizeof(float) + kc * (sizeof(float) + sizeof(int));
+  // the block form's region starts 16-byte aligned after the kept-vector indices
+  const size_t base = 2 * nl * sh.rowp * sizeof(float) + (size_t)sh.len * sh.nc * sizeof(float2) +
+                      kc * sh.nc * sizeof(float2) + nl * sizeof(float) +
+                      kc * (sizeof(float) + sizeof(int));
+  return (base + 15) / 16 * 16 + block_smem_floats(sh) * sizeof(float);
 }
 
 // x' = x + (cs-1) x - conj(k) y ;  y' = y + (cs-1) y + k x on two entries of each plane
@@ -155,6 +168,58 @@ __device__ __forceinline__ void group_sum_n(float (&v)[K]) {
   for (int o = G / 2; o > 0; o >>= 1) {
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+}
+
+// The rotation of a vector pair from its 2 x 2 Gram entries al = ||x||^2, be = ||y||^2 and
+// x^H y = cr + i ci: 0 when the pair is orthogonal to the tolerance (|x^H y|^2 <= tol2 al be)
+// or the angle rounds to 0, else 1, or 3 when |cos|^2 = |x^H y|^2 / (al be) > big2; with
+// cm = cs - 1 and k = kr + i ki = sn e^{i phi} (see jacobi_pairs for the arithmetic).
+__device__ __forceinline__ int pair_rotation(float al, float be, float cr, float ci, float tol2,
+                                             float big2, float& cm, float& kr, float& ki) {
+  const float c2 = cr * cr + ci * ci;
+  const float ab = al * be;
+  if (!(c2 > tol2 * ab)) return 0;
+  // ~ 1 / |x^H y| (the exact form below the normal range, where the approximation is not
+  // defined: only vectors of norm ~1e-14 get there)
+  const float inv_g = c2 >= 1e-30f ? rsqrtf(c2) : 1.f / sqrtf(c2);
+  const float zeta = (be - al) * (0.5f * inv_g);
+  const float az = fabsf(zeta);
+  const float z1 = fmaf(zeta, zeta, 1.f);                         // inf past |zeta| ~ 1e19
+  const float t0 = __fdividef(1.f, az + z1 * rsqrtf(z1));
+  float t = az > 1e18f ? __fdividef(0.5f, az) : t0;
+  t = zeta >= 0.f ? t : -t;
+  if (t == 0.f) return 0;
+  const float q1 = fmaf(t, t, 1.f);
+  const float rs = rsqrtf(q1);                                    // ~ 1 / r
+  const float r = q1 * rs;
+  const float sn = t * rs;
+  cm = __fdividef(-(t * sn), 1.f + r);
+  kr = sn * (cr * inv_g);                                         // k = sn e^{i phi}
+  ki = sn * (ci * inv_g);
+  return c2 > big2 * ab ? 3 : 1;
+}
+
+// Local vectors (pp, qq) of pair slot `slot` < bs in local round lr of block round r: round 0
+// pairs every two of the nl = 2 bs local vectors (circle method over nl - 1 rounds), later
+// rounds only the bs x bs cross pairs (bs rounds).
+__device__ __forceinline__ void local_pair(int r, int lr, int slot, int nl, int bs, int& pp,
+                                           int& qq) {
+  if (r == 0) {
+    if (slot == 0) {
+      pp = nl - 1;
+      qq = lr;
+    } else {
+      pp = lr + slot;
+      if (pp >= nl - 1) pp -= nl - 1;
+      qq = lr - slot + nl - 1;
+      if (qq >= nl - 1) qq -= nl - 1;
+    }
+  } else {
+    pp = slot;
+    qq = slot + lr;
+    if (qq >= bs) qq -= bs;
+    qq += bs;
   }
 }
 
@@ -252,27 +317,11 @@ __device__ __forceinline__ int jacobi_pairs(float* __restrict__ Wr, float* __res
   int flags = 0;
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
-    const float al = red[4 * i + 0], be = red[4 * i + 1];
-    const float cr = red[4 * i + 2], ci = red[4 * i + 3];
-    const float c2 = cr * cr + ci * ci;
-    const float ab = al * be;
-    if (!real[i] || !(c2 > tol2 * ab)) continue;
-    // ~ 1 / |x^H y| (the exact form below the normal range, where the approximation is not
-    // defined: only vectors of norm ~1e-14 get there)
-    const float inv_g = c2 >= 1e-30f ? rsqrtf(c2) : 1.f / sqrtf(c2);
-    const float zeta = (be - al) * (0.5f * inv_g);
-    const float az = fabsf(zeta);
-    const float z1 = fmaf(zeta, zeta, 1.f);                         // inf past |zeta| ~ 1e19
-    const float t0 = __fdividef(1.f, az + z1 * rsqrtf(z1));
-    float t = az > 1e18f ? __fdividef(0.5f, az) : t0;
-    t = zeta >= 0.f ? t : -t;
-    if (t == 0.f) continue;
-    const float q1 = fmaf(t, t, 1.f);
-    const float rs = rsqrtf(q1);                                    // ~ 1 / r
-    const float r = q1 * rs;
-    const float sn = t * rs;
-    const float cm = __fdividef(-(t * sn), 1.f + r);
-    const float kr = sn * (cr * inv_g), ki = sn * (ci * inv_g);     // k = sn e^{i phi}
+    if (!real[i]) continue;
+    float cm, kr, ki;
+    const int fl = pair_rotation(red[4 * i + 0], red[4 * i + 1], red[4 * i + 2], red[4 * i + 3],
+                                 tol2, big2, cm, kr, ki);
+    if (!fl) continue;
     const float2 CM = f2(cm, cm), KR = f2(kr, kr), KI = f2(ki, ki), NKR = f2(-kr, -kr),
                  NKI = f2(-ki, -ki);
     float4* xr4 = reinterpret_cast<float4*>(Wr + p[i] * rowp);
@@ -297,7 +346,7 @@ __device__ __forceinline__ int jacobi_pairs(float* __restrict__ Wr, float* __res
       yr4[c] = vyr;
       yi4[c] = vyi;
     }
-    flags |= c2 > big2 * ab ? 3 : 1;
+    flags |= fl;
   }
   return flags;
 }
@@ -481,6 +530,257 @@ __device__ void load_blocks_rotated(float* Wr, float* Wi, const float2* __restri
   }
 }
 
+// ---- block form of a block round.  The rotations of a block round (the local rounds below)
+// act on the CTA's nl = 2 bs local vectors X (columns of a len x nl matrix) only through their
+// inner products, so they can run on the Gram G = X^H X instead: a rotation J of pair (p, q),
+// computed from G_pp, G_qq, G_pq exactly as from the vectors, updates G <- J^H G J (columns p,
+// q, then rows p, q) and accumulates W <- W J; after the round X <- X W.  In exact arithmetic
+// this is the same rotation sequence as the pairwise form (the same sweeps to converge); the
+// len-long vector work becomes one Gram product and one rotation product per block round.
+struct BlockSmem {
+  float* gr;     // G, nl x nlp, real part
+  float* gi;
+  float* wr;     // W, nl x nlp
+  float* wi;
+  float4* prm;   // per pair slot: (cs - 1, Re k, Im k, 1 if rotated)
+  int2* idx;     // per pair slot: (p, q)
+  int nlp;
+};
+
+__device__ __forceinline__ BlockSmem block_carve(unsigned char* smem_raw, const SliceShape& sh) {
+  const size_t nl = 2 * (size_t)sh.bs, kc = (size_t)sh.kcap;
+  const size_t base = 2 * nl * sh.rowp * sizeof(float) + (size_t)sh.len * sh.nc * sizeof(float2) +
+                      kc * sh.nc * sizeof(float2) + nl * sizeof(float) +
+                      kc * (sizeof(float) + sizeof(int));
+  float* f = reinterpret_cast<float*>(smem_raw + (base + 15) / 16 * 16);
+  BlockSmem b;
+  b.nlp = sh.nlp;
+  const size_t m = nl * sh.nlp;
+  b.gr = f;
+  b.gi = f + m;
+  b.wr = f + 2 * m;
+  b.wi = f + 3 * m;
+  b.prm = reinterpret_cast<float4*>(f + 4 * m);   // 4 m is a multiple of 4 (nl even)
+  b.idx = reinterpret_cast<int2*>(b.prm + sh.bs);
+  return b;
+}
+
+// G = X^H X over the first 4 len4 entries of the nl local rows (zero past the vector), and
+// W = I.  Upper-triangle tiles of 4 x 4 entries, each summed by S consecutive lanes over
+// interleaved 4-entry chunks and reduced with shuffles (a fixed order: deterministic).
+__device__ void block_gram(const float* __restrict__ Xr, const float* __restrict__ Xi, int rowp,
+                           int len4, int nl, const BlockSmem& b) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int nlp = b.nlp;
+  for (int e = tid; e < nl * nlp; e += nthr) {
+    const int i = e / nlp, j = e % nlp;
+    b.wr[e] = i == j ? 1.f : 0.f;
+    b.wi[e] = 0.f;
+  }
+  const int nb4 = (nl + 3) / 4;
+  const int ntile = nb4 * (nb4 + 1) / 2;
+  int S = 1;
+  while (S < 32 && 2 * S * ntile <= nthr) S *= 2;
+  const int part = tid % S, grp = tid / S, ngrp = nthr / S;
+  const int ntrip = (ntile + ngrp - 1) / ngrp;
+  for (int trip = 0; trip < ntrip; ++trip) {
+    const int tile = grp + trip * ngrp;
+    const bool live = grp < ngrp && tile < ntile;
+    int pb = 0, qb = 0;
+    if (live) {   // tile -> (pb <= qb), row pb holding nb4 - pb tiles
+      int t = tile;
+      while (t >= nb4 - pb) {
+        t -= nb4 - pb;
+        ++pb;
+      }
+      qb = pb + t;
+    }
+    float ar[4][4], ai[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ar[a][c] = ai[a][c] = 0.f;
+    if (live) {
+      for (int ch = part; ch < len4; ch += S) {
+        float4 qr[4], qi[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int q = 4 * qb + c;
+          const bool ok = q < nl;
+          qr[c] = ok ? *reinterpret_cast<const float4*>(Xr + (size_t)q * rowp + 4 * ch)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+          qi[c] = ok ? *reinterpret_cast<const float4*>(Xi + (size_t)q * rowp + 4 * ch)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int p = 4 * pb + a;
+          if (p >= nl) break;
+          const float4 pr = *reinterpret_cast<const float4*>(Xr + (size_t)p * rowp + 4 * ch);
+          const float4 pi = *reinterpret_cast<const float4*>(Xi + (size_t)p * rowp + 4 * ch);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            // conj(x_p) . x_q
+            float sr = ar[a][c], si = ai[a][c];
+            sr = fmaf(pr.x, qr[c].x, fmaf(pi.x, qi[c].x, sr));
+            si = fmaf(pr.x, qi[c].x, fmaf(-pi.x, qr[c].x, si));
+            sr = fmaf(pr.y, qr[c].y, fmaf(pi.y, qi[c].y, sr));
+            si = fmaf(pr.y, qi[c].y, fmaf(-pi.y, qr[c].y, si));
+            sr = fmaf(pr.z, qr[c].z, fmaf(pi.z, qi[c].z, sr));
+            si = fmaf(pr.z, qi[c].z, fmaf(-pi.z, qr[c].z, si));
+            sr = fmaf(pr.w, qr[c].w, fmaf(pi.w, qi[c].w, sr));
+            si = fmaf(pr.w, qi[c].w, fmaf(-pi.w, qr[c].w, si));
+            ar[a][c] = sr;
+            ai[a][c] = si;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      if (o >= S) continue;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          ar[a][c] += __shfl_xor_sync(0xffffffffu, ar[a][c], o);
+          ai[a][c] += __shfl_xor_sync(0xffffffffu, ai[a][c], o);
+        }
+    }
+    if (live && part == 0) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int p = 4 * pb + a, q = 4 * qb + c;
+          if (p < nl && q < nl && (pb < qb || p <= q)) {
+            b.gr[(size_t)p * nlp + q] = ar[a][c];
+            b.gi[(size_t)p * nlp + q] = ai[a][c];
+            b.gr[(size_t)q * nlp + p] = ar[a][c];
+            b.gi[(size_t)q * nlp + p] = -ai[a][c];
+          }
+        }
+    }
+  }
+}
+
+// The local rounds of block round r on G (and W): per local round, the rotation of every pair
+// slot from the current G, then the column updates of G and W, then the row updates of G.
+// Returns the rotation flags of the slots this thread computed (see pair_rotation).
+__device__ int block_inner(const BlockSmem& b, const SliceShape& sh, int r, int bx, int by,
+                           float tol2, float big2) {
+  const int bs = sh.bs, nl = 2 * bs, nlp = b.nlp;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int nlr = r == 0 ? nl - 1 : bs;
+  int flags = 0;
+  for (int lr = 0; lr < nlr; ++lr) {
+    for (int slot = tid; slot < bs; slot += nthr) {
+      int pp, qq;
+      local_pair(r, lr, slot, nl, bs, pp, qq);
+      const int gp = pp < bs ? bx * bs + pp : by * bs + pp - bs;
+      const int gq = qq < bs ? bx * bs + qq : by * bs + qq - bs;
+      float cm = 0.f, kr = 0.f, ki = 0.f;
+      int fl = 0;
+      if (gp < sh.nv && gq < sh.nv)
+        fl = pair_rotation(b.gr[(size_t)pp * nlp + pp], b.gr[(size_t)qq * nlp + qq],
+                           b.gr[(size_t)pp * nlp + qq], b.gi[(size_t)pp * nlp + qq], tol2, big2,
+                           cm, kr, ki);
+      flags |= fl;
+      b.prm[slot] = make_float4(cm, kr, ki, fl ? 1.f : 0.f);
+      b.idx[slot] = make_int2(pp, qq);
+    }
+    __syncthreads();
+    // columns: [a_p, a_q] <- [a_p + cm a_p - conj(k) a_q, a_q + cm a_q + k a_p] for the rows
+    // of G and of W
+    for (int e = tid; e < 2 * bs * nl; e += nthr) {
+      const int slot = e / (2 * nl), rem = e % (2 * nl);
+      const float4 pr = b.prm[slot];
+      if (pr.w == 0.f) continue;
+      const int2 pq = b.idx[slot];
+      const bool onw = rem >= nl;
+      const int i = onw ? rem - nl : rem;
+      float* mr = onw ? b.wr : b.gr;
+      float* mi = onw ? b.wi : b.gi;
+      const size_t op = (size_t)i * nlp + pq.x, oq = (size_t)i * nlp + pq.y;
+      const float xr = mr[op], xi = mi[op], yr = mr[oq], yi = mi[oq];
+      mr[op] = fmaf(-pr.z, yi, fmaf(-pr.y, yr, fmaf(pr.x, xr, xr)));
+      mi[op] = fmaf(pr.z, yr, fmaf(-pr.y, yi, fmaf(pr.x, xi, xi)));
+      mr[oq] = fmaf(-pr.z, xi, fmaf(pr.y, xr, fmaf(pr.x, yr, yr)));
+      mi[oq] = fmaf(pr.z, xr, fmaf(pr.y, xi, fmaf(pr.x, yi, yi)));
+    }
+    __syncthreads();
+    // rows of G: [g_p, g_q] <- [g_p + cm g_p - k g_q, g_q + cm g_q + conj(k) g_p]
+    for (int e = tid; e < bs * nl; e += nthr) {
+      const int slot = e / nl, j = e % nl;
+      const float4 pr = b.prm[slot];
+      if (pr.w == 0.f) continue;
+      const int2 pq = b.idx[slot];
+      const size_t op = (size_t)pq.x * nlp + j, oq = (size_t)pq.y * nlp + j;
+      const float xr = b.gr[op], xi = b.gi[op], yr = b.gr[oq], yi = b.gi[oq];
+      b.gr[op] = fmaf(pr.z, yi, fmaf(-pr.y, yr, fmaf(pr.x, xr, xr)));
+      b.gi[op] = fmaf(-pr.z, yr, fmaf(-pr.y, yi, fmaf(pr.x, xi, xi)));
+      b.gr[oq] = fmaf(pr.z, xi, fmaf(pr.y, xr, fmaf(pr.x, yr, yr)));
+      b.gi[oq] = fmaf(-pr.z, xr, fmaf(pr.y, xi, fmaf(pr.x, yi, yi)));
+    }
+    __syncthreads();
+  }
+  return flags;
+}
+
+// X <- X W on the nl local rows (all rowp4 4-float chunks of each row: the vector and, in the
+// V form, its V entries), in place: entry e of the new row j is sum_i X(e, i) W(i, j), so each
+// chunk of entries is independent; a warp computes the chunks it owns for every j into
+// registers (lanes = chunks x 4-column blocks of W) and stores them after a warp barrier.
+__device__ void block_update(float* __restrict__ Xr, float* __restrict__ Xi, int rowp, int rowp4,
+                             int nl, const BlockSmem& b) {
+  const int nlp = b.nlp;
+  const int jbs = (nl + 3) / 4;      // <= 32
+  const int ech = 32 / jbs;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lj = lane % jbs, le = lane / jbs;
+  for (int c0 = warp * ech; c0 < rowp4; c0 += nwarps * ech) {
+    const int ch = c0 + le;
+    const bool live = le < ech && ch < rowp4;
+    float accr[4][4], acci[4][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) accr[e][c] = acci[e][c] = 0.f;
+    if (live) {
+      for (int i = 0; i < nl; ++i) {
+        const float4 xr = *reinterpret_cast<const float4*>(Xr + (size_t)i * rowp + 4 * ch);
+        const float4 xi = *reinterpret_cast<const float4*>(Xi + (size_t)i * rowp + 4 * ch);
+        const float xre[4] = {xr.x, xr.y, xr.z, xr.w}, xie[4] = {xi.x, xi.y, xi.z, xi.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int j = 4 * lj + c;
+          const float wr = j < nl ? b.wr[(size_t)i * nlp + j] : 0.f;
+          const float wi = j < nl ? b.wi[(size_t)i * nlp + j] : 0.f;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            accr[e][c] = fmaf(xre[e], wr, fmaf(-xie[e], wi, accr[e][c]));
+            acci[e][c] = fmaf(xre[e], wi, fmaf(xie[e], wr, acci[e][c]));
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (live) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = 4 * lj + c;
+        if (j < nl) {
+          *reinterpret_cast<float4*>(Xr + (size_t)j * rowp + 4 * ch) =
+              make_float4(accr[0][c], accr[1][c], accr[2][c], accr[3][c]);
+          *reinterpret_cast<float4*>(Xi + (size_t)j * rowp + 4 * ch) =
+              make_float4(acci[0][c], acci[1][c], acci[2][c], acci[3][c]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // The SVT of slice ordinal `so` of a launch (the slice index is a.slices[so]) by the C = sh.C
 // CTAs of a cluster (this CTA is cluster rank `crank`; C = 1: this CTA alone), with the
 // cluster's block-exchange buffer xbuf (C > 1) and the CTA's dynamic shared memory smem_raw.
@@ -529,6 +829,7 @@ __device__ void svt_slice(const SliceArgs& a, const SliceShape& sh, int so, int 
   __syncthreads();
 
   // ---- Jacobi sweeps
+  const BlockSmem bsm = block_carve(smem_raw, sh);
   const int gpw = 32 / G;                    // groups per warp
   const int group = warp * gpw + lane / G;   // group index in the CTA
   const int ngroups = nwarps * gpw;
@@ -547,7 +848,14 @@ __device__ void svt_slice(const SliceArgs& a, const SliceShape& sh, int so, int 
     for (int r = 0; r < nb - 1; ++r) {
       round_robin_pair(r, crank, nb, bx, by);
       const int vx0 = bx * bs, vy0 = by * bs;
-      const int nlr = r == 0 ? nl - 1 : bs;   // local rounds
+      const int nlr = sh.block ? 0 : (r == 0 ? nl - 1 : bs);   // local rounds (pairwise form)
+      if (sh.block) {
+        block_gram(Wr, Wi, rowp, (len + 3) / 4, nl, bsm);
+        __syncthreads();
+        rotated |= block_inner(bsm, sh, r, bx, by, tol2, big2);
+        block_update(Wr, Wi, rowp, rowp / 4, nl, bsm);
+        __syncthreads();
+      }
       for (int lr = 0; lr < nlr; ++lr) {
         for (int k0 = 0; k0 < trips; k0 += NP) {
           int p[NP], q[NP];
@@ -557,25 +865,7 @@ __device__ void svt_slice(const SliceArgs& a, const SliceShape& sh, int so, int 
           for (int i = 0; i < NP; ++i) {
             const int slot = group + (k0 + i) * ngroups;
             int pp = nl, qq = nl;
-            if (k0 + i < trips && slot < bs) {
-              // the circle method without integer division: lr < nl - 1 and slot < bs
-              if (r == 0) {
-                if (slot == 0) {
-                  pp = nl - 1;
-                  qq = lr;
-                } else {
-                  pp = lr + slot;
-                  if (pp >= nl - 1) pp -= nl - 1;
-                  qq = lr - slot + nl - 1;
-                  if (qq >= nl - 1) qq -= nl - 1;
-                }
-              } else {
-                pp = slot;
-                qq = slot + lr;
-                if (qq >= bs) qq -= bs;
-                qq += bs;
-              }
-            }
+            if (k0 + i < trips && slot < bs) local_pair(r, lr, slot, nl, bs, pp, qq);
             // a local vector is real if its global index is below nv
             bool rp = pp < nl && qq < nl;
             if (rp) {
@@ -957,22 +1247,36 @@ bool plan_with_ctas(int n1, int n2, int C, const SliceKnobs& k, SliceShape& sh, 
   sh.nv = n1 < n2 ? n1 : n2;
   sh.len = n1 < n2 ? n2 : n1;
   sh.vform = k.vform ? 1 : 0;
-  // lanes and chunks for the vector's own 4-entry chunks (the row pitch is made odd below;
-  // sizing the chunks from an odd pitch instead padded e.g. a 128-entry vector to 192)
-  if (!pick_group(4 * ((sh.len + 3) / 4), k.lanes, sh.G, sh.cpl)) return false;
-  // rows padded so that the vector part is exactly G * cpl chunks and the V part a multiple
-  // of G chunks: every lane's chunks lie inside the row and the rotation needs no tests
-  sh.ld = 4 * sh.G * sh.cpl;
-  sh.ldv = sh.vform ? 4 * (((sh.nv + 3) / 4 + sh.G - 1) / sh.G * sh.G) : 0;
-  sh.rowp = sh.ld + sh.ldv;
-  if (((sh.rowp / 4) & 1) == 0) sh.rowp += 4;   // pitch / 4 odd
-  sh.np = k.ppg == 2 ? 2 : 1;
-  if (k.ppg != 0 && k.ppg != 1 && k.ppg != 2) return false;
-  if (sh.np == 2 && (sh.G == 4 || sh.cpl > 4)) return false;   // register budget
-  if (sh.G == 32 && (sh.np == 2 || sh.cpl > 4)) return false;   // no such kernel instances
+  sh.block = k.block ? 1 : 0;
   sh.C = C;
   sh.nb = 2 * C;
   sh.bs = (sh.nv + sh.nb - 1) / sh.nb;
+  if (sh.block) {
+    // block form: rows of the vector's 4-entry chunks (and its V entries), no lane layout;
+    // it runs in the 16-lane, 4-chunk kernel instance (its register budget), nl <= 128
+    if (2 * sh.bs > 128 || k.ppg > 1) return false;
+    sh.G = 16;
+    sh.cpl = 4;
+    sh.np = 1;
+    sh.ld = 4 * ((sh.len + 3) / 4);
+    sh.ldv = sh.vform ? 4 * ((sh.nv + 3) / 4) : 0;
+    sh.nlp = 2 * sh.bs + 1;
+  } else {
+    // lanes and chunks for the vector's own 4-entry chunks (the row pitch is made odd below;
+    // sizing the chunks from an odd pitch instead padded e.g. a 128-entry vector to 192)
+    if (!pick_group(4 * ((sh.len + 3) / 4), k.lanes, sh.G, sh.cpl)) return false;
+    // rows padded so that the vector part is exactly G * cpl chunks and the V part a multiple
+    // of G chunks: every lane's chunks lie inside the row and the rotation needs no tests
+    sh.ld = 4 * sh.G * sh.cpl;
+    sh.ldv = sh.vform ? 4 * (((sh.nv + 3) / 4 + sh.G - 1) / sh.G * sh.G) : 0;
+    sh.np = k.ppg == 2 ? 2 : 1;
+    if (k.ppg != 0 && k.ppg != 1 && k.ppg != 2) return false;
+    if (sh.np == 2 && (sh.G == 4 || sh.cpl > 4)) return false;   // register budget
+    if (sh.G == 32 && (sh.np == 2 || sh.cpl > 4)) return false;   // no such kernel instances
+    sh.nlp = 0;
+  }
+  sh.rowp = sh.ld + sh.ldv;
+  if (((sh.rowp / 4) & 1) == 0) sh.rowp += 4;   // pitch / 4 odd
   sh.kcap = C > 1 ? 2 * sh.bs * sh.rowp / sh.ld : 2 * sh.bs;
   sh.xbuf_floats = C > 1 ? (size_t)2 * sh.nb * 2 * sh.bs * sh.rowp : 0;
   for (int nc = kNC; nc >= 1; nc >>= 1) {
@@ -1405,6 +1709,8 @@ cudaError_t launch_jacobi_svt(const SliceArgs& a, cudaStream_t st) {
   // enough groups for all pairs of a local round in as few passes as fit, balanced
   const int passes = (sh.bs + maxw * per_warp - 1) / (maxw * per_warp);
   int nwarps = (sh.bs + passes * per_warp - 1) / (passes * per_warp);
+  // block form: a warp per 4 local vectors (the Gram tiles and update chunks spread over them)
+  if (sh.block) nwarps = (2 * sh.bs + 3) / 4;
   if (nwarps < kMinWarps) nwarps = kMinWarps;
   if (nwarps > maxw) nwarps = maxw;
   const int threads = nwarps * 32;

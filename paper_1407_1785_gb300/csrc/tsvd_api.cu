@@ -265,7 +265,9 @@ std::array<int, 4> plan_key(tsvd_ctx* c, const Problem& p, int nslices) {
 
 // Slice-SVT plans the autotuner compares (or the single plan fixed by the options).
 std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslices) {
-  const SliceKnobs base = {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, vform_of(c)};
+  const int form = c->opts.slice_form;
+  const SliceKnobs base = {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, vform_of(c),
+                           form == TSVD_SLICE_BLOCK ? 1 : 0};
   std::vector<SliceKnobs> out;
   if (c->opts.autotune) {
     const int ctas[4] = {1, 2, 4, 8};
@@ -274,11 +276,15 @@ std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslic
       if (base.ctas && C != base.ctas) continue;
       for (int L : lanes) {
         if (base.lanes && L != base.lanes) continue;
-        for (int np = 1; np <= 2; ++np) {
-          const SliceKnobs k = {C, L, np, base.vform};
+        for (int np = 1; np <= 2 && form != TSVD_SLICE_BLOCK; ++np) {
+          const SliceKnobs k = {C, L, np, base.vform, 0};
           if (jacobi_svt_plan_ok((int)p.n1, (int)p.n2, nslices, k)) out.push_back(k);
         }
       }
+      // the block form (no lane layout)
+      const SliceKnobs kb = {C, 0, 1, base.vform, 1};
+      if (form != TSVD_SLICE_PAIRWISE && jacobi_svt_plan_ok((int)p.n1, (int)p.n2, nslices, kb))
+        out.push_back(kb);
     }
   }
   if (out.empty()) out.push_back(base);
@@ -289,7 +295,8 @@ std::vector<SliceKnobs> candidate_knobs(tsvd_ctx* c, const Problem& p, int nslic
 SliceKnobs planned_knobs(tsvd_ctx* c, const Problem& p, int nslices, int vform) {
   auto it = c->tuned.find(plan_key(p, nslices, vform));
   if (it != c->tuned.end()) return it->second;
-  return {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, vform};
+  return {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, vform,
+          c->opts.slice_form == TSVD_SLICE_BLOCK ? 1 : 0};
 }
 SliceKnobs planned_knobs(tsvd_ctx* c, const Problem& p, int nslices) {
   return planned_knobs(c, p, nslices, vform_of(c));
@@ -307,7 +314,7 @@ std::string device_name(int dev) {
 }
 
 // Autotune cache file: one line per plan,
-// "<gpu> <n1> <n2> <slices> <vform> <ctas> <lanes> <pairs in flight>".
+// "<gpu> <n1> <n2> <slices> <vform> <ctas> <lanes> <pairs in flight> <block form>".
 void load_tune_cache(tsvd_ctx* c) {
   c->cache_loaded = true;
   if (!c->opts.autotune_cache) return;
@@ -315,10 +322,10 @@ void load_tune_cache(tsvd_ctx* c) {
   if (!f) return;
   const std::string me = device_name(c->device);
   char gpu[256];
-  int n1, n2, ns, vf, C, L, np;
-  while (std::fscanf(f, "%255s %d %d %d %d %d %d %d", gpu, &n1, &n2, &ns, &vf, &C, &L, &np) ==
-         8) {
-    const SliceKnobs k = {C, L, np, vf};
+  int n1, n2, ns, vf, C, L, np, bl;
+  while (std::fscanf(f, "%255s %d %d %d %d %d %d %d %d", gpu, &n1, &n2, &ns, &vf, &C, &L, &np,
+                     &bl) == 9) {
+    const SliceKnobs k = {C, L, np, vf, bl};
     if (me == gpu && jacobi_svt_plan_ok(n1, n2, ns, k)) c->tuned[{n1, n2, ns, vf}] = k;
   }
   std::fclose(f);
@@ -328,8 +335,8 @@ void store_tune_cache(tsvd_ctx* c, const std::array<int, 4>& key, const SliceKno
   if (!c->opts.autotune_cache) return;
   FILE* f = std::fopen(c->opts.autotune_cache, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d %d %d %d %d\n", device_name(c->device).c_str(), key[0], key[1],
-               key[2], key[3], k.ctas, k.lanes, k.ppg);
+  std::fprintf(f, "%s %d %d %d %d %d %d %d %d\n", device_name(c->device).c_str(), key[0],
+               key[1], key[2], key[3], k.ctas, k.lanes, k.ppg, k.block);
   std::fclose(f);
 }
 
@@ -670,6 +677,9 @@ tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
     return fail(c, TSVD_EINVAL, "use_graphs must be 0 or 1");
   if (o.batch_persistent != 0 && o.batch_persistent != 1)
     return fail(c, TSVD_EINVAL, "batch_persistent must be 0 or 1");
+  if (o.slice_form != TSVD_SLICE_AUTO && o.slice_form != TSVD_SLICE_PAIRWISE &&
+      o.slice_form != TSVD_SLICE_BLOCK)
+    return fail(c, TSVD_EINVAL, "slice_form must be TSVD_SLICE_AUTO, _PAIRWISE or _BLOCK");
   return TSVD_OK;
 }
 
@@ -766,7 +776,8 @@ constexpr int kColdEvery = kWarmColdEvery;   // iterations between cold starts o
 
 // Whether the V form (needed by the warm start) has a plan for this slice shape.
 bool warm_plan_exists(tsvd_ctx* c, const Problem& p) {
-  const SliceKnobs k = {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, 1};
+  const SliceKnobs k = {c->opts.ctas_per_slice, c->opts.lanes_per_pair, 0, 1,
+                        c->opts.slice_form == TSVD_SLICE_BLOCK ? 1 : 0};
   return jacobi_svt_plan_ok((int)p.n1, (int)p.n2, p.g.nstore, k);
 }
 
@@ -1301,7 +1312,7 @@ void tsvd_default_opts(tsvd_opts* o) {
   o->rsvt_kmax = 0;
   o->rsvt_power = 2;
   o->warm_start = TSVD_WARM_AUTO;
-  o->batch_persistent = 1;
+  o->batch_persistent = 0;
 }
 
 tsvd_status tsvd_create(tsvd_ctx** out, int device, void* cuda_stream, const tsvd_opts* opts) {

@@ -144,6 +144,7 @@ struct SliceKnobs {
   int lanes;   // lanes per vector pair (4, 8 or 16)
   int ppg;     // vector pairs each lane group keeps in flight (1 or 2)
   int vform;   // 1: accumulate V and rebuild as W diag(d) V^H
+  int block;   // 1: block form (each block round on the Gram of the CTA's vectors)
 };
 
 struct SliceArgs {

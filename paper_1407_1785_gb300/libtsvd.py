@@ -35,6 +35,7 @@ EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_la
                     "tsvt_static", "tsvd_cgemm", "tsvd_measure_fp32_peak")
 OP_N, OP_T, OP_C = 0, 1, 2
 WARM_OFF, WARM_ON, WARM_AUTO = 0, 1, 2
+SLICE_AUTO, SLICE_PAIRWISE, SLICE_BLOCK = 0, 1, 2
 COMPRESS_GLOBAL, COMPRESS_TUBAL = 1, 2
 PROBLEM_COMPLETE, PROBLEM_RPCA = 1, 2
 
@@ -56,7 +57,8 @@ class Opts(ctypes.Structure):
                 ("autotune", ctypes.c_int), ("autotune_cache", ctypes.c_char_p),
                 ("use_graphs", ctypes.c_int), ("rsvt_oversample", ctypes.c_int),
                 ("rsvt_kmax", ctypes.c_int), ("rsvt_power", ctypes.c_int),
-                ("warm_start", ctypes.c_int), ("batch_persistent", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("batch_persistent", ctypes.c_int),
+                ("slice_form", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

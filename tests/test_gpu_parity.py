@@ -221,8 +221,8 @@ def test_graph_replay_matches_direct_launches(kind, tmp_path):
 def test_batched_uneven_problems_match_oracle(warm, persistent):
     """A batch of uneven tensors (completion and RPCA, 3-way and 4-way) in one call: every
     tensor matches the oracle's solve, with the warm-started Jacobi off, on for the
-    completions only (the default) or on for all, as one persistent launch per iteration
-    (the default) or as per-tensor stream branches; a second call replays the captured batch
+    completions only (the default) or on for all, as one persistent launch per iteration or
+    as per-tensor stream branches (the default); a second call replays the captured batch
     graph and gives the same bits."""
     from paper_1407_1785_gb300 import libtsvd
     warm_start = {"off": libtsvd.WARM_OFF, "auto": libtsvd.WARM_AUTO, "on": libtsvd.WARM_ON}[warm]
