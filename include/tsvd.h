@@ -143,6 +143,11 @@ typedef struct tsvd_opts {
                          its rotations on the Gram matrix of the CTA's vectors, then applies
                          their product to the vectors: the same rotations, fewer passes over
                          the vectors) */
+  int rsvt_small_fp64; /* mixed form: 1 runs the k x k CholeskyQR2 factorisations (k <= 112)
+                         and the Rayleigh-Ritz eigen-solve of the projected Gram (k <= 80) in
+                         FP64; 0 (default) in FP32 with the Cholesky pivots in double-single
+                         arithmetic (FP32 pairs).  The Grams themselves are FP32-level
+                         products either way. */
 } tsvd_opts;
 
 enum { TSVD_SLICE_AUTO = 0, TSVD_SLICE_PAIRWISE = 1, TSVD_SLICE_BLOCK = 2 };

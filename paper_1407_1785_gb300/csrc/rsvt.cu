@@ -495,6 +495,303 @@ __global__ void __launch_bounds__(1024) eig_svt_kernel(float2* G, float2* T, flo
   }
 }
 
+
+// ---- FP64 variants of the two k x k solves (RsvtArgs::small_fp64): the same algorithms as
+// cholqr_factor_kernel and eig_svt_kernel with the factorisation and the eigen-solve carried
+// in FP64 (the Grams arrive in FP32 from the products; the factors T and the rotations W go
+// back in FP32).  GB300's FP64 rate is a small fraction of its FP32 rate, so these are the
+// reference for the FP32 / double-single defaults (their accuracy and time are compared by
+// the tests and the benchmark).
+__global__ void __launch_bounds__(1024) cholqr_factor_fp64_kernel(const float2* G, float2* T,
+                                                                 const int* slices, int k,
+                                                                 int ldg, int64_t gs, float tol,
+                                                                 RsvtStat* rstat,
+                                                                 const int* kdev) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (kdev) k = *kdev;
+  const int s = slices[blockIdx.x];
+  const int ldS = k + 1;
+  double2* S = reinterpret_cast<double2*>(smem_raw);
+  double* piv = reinterpret_cast<double*>(S + (size_t)k * ldS);
+  double* dsc = piv + k;
+  double2* xd = reinterpret_cast<double2*>(dsc + k);
+  int* okc = reinterpret_cast<int*>(xd + k);
+  __shared__ double s_dmax;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tx = tid & 31, ty = tid >> 5;
+  const float2* Gp = G + (size_t)s * gs;
+  float2* Tp = T + (size_t)s * gs;
+  for (int i = tid; i < k; i += nthr) {
+    const double g = (double)Gp[i + (size_t)i * ldg].x;
+    dsc[i] = g > 0.0 ? sqrt(g) : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int i = 0; i < k; ++i) m = fmax(m, dsc[i]);
+    s_dmax = m;
+  }
+  __syncthreads();
+  const double dmin = 1e-30 * s_dmax;
+  for (int i = tid; i < k; i += nthr) {
+    const bool zero = !(dsc[i] > dmin) || s_dmax == 0.0;
+    piv[i] = zero ? 0.0 : 1.0;
+    if (zero) dsc[i] = 1.0;
+    xd[i] = make_double2(1.0, 0.0);
+  }
+  __syncthreads();
+  for (int r = ty; r < k; r += 32)
+    for (int c = tx; c < k; c += 32) {
+      double2 v = make_double2(0.0, 0.0);
+      if (r <= c && piv[r] != 0.0 && piv[c] != 0.0) {
+        const float2 g = Gp[r + (size_t)c * ldg];
+        const double inv = 1.0 / (dsc[r] * dsc[c]);
+        v = make_double2((double)g.x * inv, (double)g.y * inv);
+      }
+      S[(size_t)r * ldS + c] = v;
+    }
+  __syncthreads();
+  {
+    int far = 0;
+    for (int r = ty; r < k; r += 32)
+      for (int c = r + 1 + tx; c < k; c += 32) {
+        const double2 v = S[(size_t)r * ldS + c];
+        far |= fabs(v.x) + fabs(v.y) > 1e-6;
+      }
+    for (int r = tid; r < k; r += nthr) far |= piv[r] == 0.0;
+    if (__syncthreads_or(far) == 0) {
+      for (int c = ty; c < k; c += 32)
+        for (int i = tx; i < k; i += 32)
+          Tp[i + (size_t)c * ldg] = i == c ? make_float2((float)(1.0 / dsc[i]), 0.f)
+                                           : make_float2(0.f, 0.f);
+      return;
+    }
+  }
+  __shared__ double s_rjj, s_irjj;
+  __shared__ int s_ok;
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      const double pj = piv[j];
+      const bool ok = pj > (double)tol;
+      const double r = ok ? sqrt(pj) : 1.0;
+      s_ok = ok ? 1 : 0;
+      s_rjj = r;
+      s_irjj = ok ? 1.0 / r : 0.0;
+    }
+    __syncthreads();
+    const bool okj = s_ok != 0;
+    const double rjj = s_rjj, irjj = s_irjj;
+    for (int l = j + 1 + tid; l < k; l += nthr) {
+      const double2 v = S[(size_t)j * ldS + l];
+      S[(size_t)j * ldS + l] = make_double2(v.x * irjj, v.y * irjj);
+    }
+    for (int i = tid; i < j; i += nthr) {
+      const double2 v = S[(size_t)j * ldS + i];
+      S[(size_t)j * ldS + i] = make_double2(v.x * irjj, v.y * irjj);
+    }
+    if (tid == 0) {
+      S[(size_t)j * ldS + j] = make_double2(rjj, 0.0);
+      const double2 v = xd[j];
+      xd[j] = make_double2(v.x * irjj, v.y * irjj);
+      okc[j] = okj ? 1 : 0;
+    }
+    __syncthreads();
+    if (okj) {
+      for (int l = j + 1 + ty; l < k; l += 32) {
+        const double2 a = S[(size_t)j * ldS + l];
+        for (int l2 = l + tx; l2 < k; l2 += 32) {
+          const double2 b = S[(size_t)j * ldS + l2];
+          double2 v = S[(size_t)l * ldS + l2];
+          v.x -= a.x * b.x + a.y * b.y;
+          v.y -= a.x * b.y - a.y * b.x;
+          S[(size_t)l * ldS + l2] = v;
+        }
+        if (tx == 0) piv[l] -= a.x * a.x + a.y * a.y;
+        for (int i = tx; i <= j; i += 32) {
+          const double2 xj = i == j ? xd[j] : S[(size_t)j * ldS + i];
+          double2 v = S[(size_t)l * ldS + i];
+          v.x -= a.x * xj.x - a.y * xj.y;
+          v.y -= a.x * xj.y + a.y * xj.x;
+          S[(size_t)l * ldS + i] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int c = ty; c < k; c += 32)
+    for (int i = tx; i < k; i += 32) {
+      double2 v = make_double2(0.0, 0.0);
+      if (okc[c] && i <= c) {
+        v = i == c ? xd[c] : S[(size_t)c * ldS + i];
+        v.x /= dsc[i];
+        v.y /= dsc[i];
+      }
+      Tp[i + (size_t)c * ldg] = make_float2((float)v.x, (float)v.y);
+    }
+  if (rstat && tid == 0) {
+    int nd = 0;
+    for (int c = 0; c < k; ++c) nd += okc[c] ? 0 : 1;
+    if (nd) atomicAdd(&rstat->drops, nd);
+  }
+}
+
+// Widest sketch whose FP64 Gram and rotations fit one CTA's shared memory.
+constexpr int eig_fp64_max_k() { return 80; }
+
+__global__ void __launch_bounds__(1024) eig_svt_fp64_kernel(float2* G, float2* T, float* sig,
+                                                            const int* slices, int k, int ldg,
+                                                            int64_t gs, int64_t sig_stride,
+                                                            float tau, float tol, int max_sweeps,
+                                                            SliceStat* stat, SweepAccum* acc,
+                                                            const int* kdev) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (kdev) k = *kdev;
+  const int s = slices[blockIdx.x];
+  const int ldh = k + 1;
+  double2* H = reinterpret_cast<double2*>(smem_raw);
+  double2* W = H + (size_t)k * ldh;
+  double* rot = reinterpret_cast<double*>(W + (size_t)k * ldh);   // 4 per pair
+  int2* prs = reinterpret_cast<int2*>(rot + 4 * ((k + 1) / 2));
+  __shared__ int s_flags;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+  float2* Gp = G + (size_t)s * gs;
+  float2* Tp = T + (size_t)s * gs;
+  for (int c = warp; c < k; c += nwarps)
+    for (int m = lane; m < k; m += 32) {
+      const float2 g = Gp[m + (size_t)c * ldg];
+      H[m + (size_t)c * ldh] = make_double2(g.x, g.y);
+      W[m + (size_t)c * ldh] = make_double2(m == c ? 1.0 : 0.0, 0.0);
+    }
+  const int kp = k + (k & 1);
+  const int npair = kp / 2;
+  const double tol2 = (double)tol * (double)tol;
+  const double big2 = (double)tol / (2.0 * (double)k);
+  int sweeps = 0, converged = 0;
+  __syncthreads();
+  for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
+    if (tid == 0) s_flags = 0;
+    __syncthreads();
+    for (int r = 0; r < kp - 1; ++r) {
+      if (tid < npair) {
+        int p, q;
+        circle_pair(r, tid, kp, p, q);
+        double cm = 0.0, kr = 0.0, ki = 0.0, on = 0.0;
+        if (p < k && q < k) {
+          const double al = fmax(H[p + (size_t)p * ldh].x, 0.0);
+          const double be = fmax(H[q + (size_t)q * ldh].x, 0.0);
+          const double2 c = H[p + (size_t)q * ldh];
+          const double c2 = c.x * c.x + c.y * c.y;
+          const double ab = al * be;
+          if (c2 > tol2 * ab && c2 > 0.0) {
+            // the rotation of the one-sided form, in FP64: t = sign(zeta) / (|zeta| +
+            // sqrt(1 + zeta^2)), sn = t / r, cs - 1 = -t sn / (1 + r), r = sqrt(1 + t^2)
+            const double g = sqrt(c2);
+            const double zeta = (be - al) / (2.0 * g);
+            double t = 1.0 / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            t = zeta >= 0.0 ? t : -t;
+            if (t != 0.0) {
+              const double rr = sqrt(1.0 + t * t);
+              const double sn = t / rr;
+              cm = -(t * sn) / (1.0 + rr);
+              kr = sn * (c.x / g);
+              ki = sn * (c.y / g);
+              on = 1.0;
+              atomicOr(&s_flags, c2 > big2 * ab ? 3 : 1);
+            }
+          }
+        }
+        rot[4 * tid + 0] = cm;
+        rot[4 * tid + 1] = kr;
+        rot[4 * tid + 2] = ki;
+        rot[4 * tid + 3] = on;
+        prs[tid] = make_int2(p, q);
+      }
+      __syncthreads();
+      // columns of H and W: x <- x + cm x - conj(k) y,  y <- y + cm y + k x
+      for (int i = warp; i < npair; i += nwarps) {
+        if (rot[4 * i + 3] == 0.0) continue;
+        const double cm = rot[4 * i], kr = rot[4 * i + 1], ki = rot[4 * i + 2];
+        const int2 pq = prs[i];
+        for (int m = lane; m < k; m += 32) {
+#pragma unroll
+          for (int mat = 0; mat < 2; ++mat) {
+            double2* X = mat == 0 ? H : W;
+            double2& x = X[m + (size_t)pq.x * ldh];
+            double2& y = X[m + (size_t)pq.y * ldh];
+            const double2 xv = x, yv = y;
+            x = make_double2(xv.x + cm * xv.x - (kr * yv.x + ki * yv.y),
+                             xv.y + cm * xv.y - (kr * yv.y - ki * yv.x));
+            y = make_double2(yv.x + cm * yv.x + (kr * xv.x - ki * xv.y),
+                             yv.y + cm * yv.y + (kr * xv.y + ki * xv.x));
+          }
+        }
+      }
+      __syncthreads();
+      // rows of H: row_p <- row_p + cm row_p - k row_q,  row_q <- row_q + cm row_q + conj(k) row_p
+      for (int i = warp; i < npair; i += nwarps) {
+        if (rot[4 * i + 3] == 0.0) continue;
+        const double cm = rot[4 * i], kr = rot[4 * i + 1], ki = rot[4 * i + 2];
+        const int2 pq = prs[i];
+        for (int m = lane; m < k; m += 32) {
+          double2& x = H[pq.x + (size_t)m * ldh];
+          double2& y = H[pq.y + (size_t)m * ldh];
+          const double2 xv = x, yv = y;
+          x = make_double2(xv.x + cm * xv.x - (kr * yv.x - ki * yv.y),
+                           xv.y + cm * xv.y - (kr * yv.y + ki * yv.x));
+          y = make_double2(yv.x + cm * yv.x + (kr * xv.x + ki * xv.y),
+                           yv.y + cm * yv.y + (kr * xv.y - ki * xv.x));
+        }
+      }
+      __syncthreads();
+    }
+    const int fl = s_flags;
+    ++sweeps;
+    if (!(fl & 1) || !(fl & 2)) converged = 1;
+    __syncthreads();
+  }
+  __shared__ int s_rank;
+  __shared__ double s_nuc;
+  if (tid == 0) {
+    int rank = 0;
+    double nuc = 0.0;
+    for (int v = 0; v < k; ++v) {
+      const double sv = sqrt(fmax(H[v + (size_t)v * ldh].x, 0.0));
+      sig[(size_t)s * sig_stride + v] = (float)sv;
+      nuc += sv;
+      rank += sv > (double)tau ? 1 : 0;
+    }
+    s_rank = rank;
+    s_nuc = nuc;
+  }
+  for (int v = warp; v < k; v += nwarps) {
+    const double sv = sqrt(fmax(H[v + (size_t)v * ldh].x, 0.0));
+    const double f = sv > (double)tau ? (sv - (double)tau) / sv : 0.0;
+    for (int m = lane; m < k; m += 32) {
+      const double2 w = W[m + (size_t)v * ldh];
+      Tp[m + (size_t)v * ldg] = make_float2((float)w.x, (float)w.y);
+      Gp[m + (size_t)v * ldg] = make_float2((float)(w.x * f), (float)(w.y * f));
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (stat) {
+      SliceStat st;
+      st.rank = s_rank;
+      st.sweeps = sweeps;
+      st.converged = converged;
+      st.pad = 0;
+      st.nuc = s_nuc;
+      stat[s] = st;
+    }
+    if (acc) {
+      atomicAdd(&acc->total_sweeps, (unsigned long long)sweeps);
+      if (!converged) atomicAdd(&acc->nonconverged, 1ull);
+      atomicMax(&acc->max_sweeps, sweeps);
+    }
+  }
+}
+
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
@@ -583,6 +880,16 @@ constexpr int eig_max_k() { return 112; }
 
 size_t eig_smem(int k) {
   return 2 * (size_t)k * (k + 1) * sizeof(float2) + (size_t)((k + 1) / 2) * (sizeof(float4) + sizeof(int2));
+}
+
+size_t eig_fp64_smem(int k) {
+  return 2 * (size_t)k * (k + 1) * sizeof(double2) +
+         (size_t)((k + 1) / 2) * (4 * sizeof(double) + sizeof(int2));
+}
+
+size_t cholqr_fp64_smem(int k) {
+  return (size_t)k * (k + 1) * sizeof(double2) + 2 * (size_t)k * sizeof(double) +
+         (size_t)k * sizeof(double2) + (size_t)k * sizeof(int);
 }
 
 size_t cholqr_smem(int k) {
@@ -675,6 +982,13 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
     e = cudaFuncSetAttribute(eig_svt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)eig_smem(eig_max_k()));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(cholqr_factor_fp64_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cholqr_fp64_smem(eig_max_k()));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(eig_svt_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)eig_fp64_smem(eig_fp64_max_k()));
+    if (e != cudaSuccess) return e;
     attr_set = true;
   }
   // stage boundaries for the caller's timing (power-step-free calls only)
@@ -711,8 +1025,12 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
                            1, 1, 0),
                        orth_engine, st);
       if (e != cudaSuccess) return e;
-      cholqr_factor_kernel<<<ns, 1024, csm, st>>>(a.G, a.T, idx, k, kmax, gs, a.chol_tol,
-                                                 a.rstat, a.kdev);
+      if (a.small_fp64 && k <= eig_max_k())   // (wider: the FP32 factorisation)
+        cholqr_factor_fp64_kernel<<<ns, 1024, cholqr_fp64_smem(k), st>>>(
+            a.G, a.T, idx, k, kmax, gs, a.chol_tol, a.rstat, a.kdev);
+      else
+        cholqr_factor_kernel<<<ns, 1024, csm, st>>>(a.G, a.T, idx, k, kmax, gs, a.chol_tol,
+                                                   a.rstat, a.kdev);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       e = launch_cgemm(dyn(gemm(mw, k, k, ns, mat(src, idx, ys, 1, mw),
                                 mat(a.T, idx, gs, 1, kmax), mat(dst, idx, ys, 1, mw)),
@@ -737,8 +1055,14 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
                          1, 1, 0),
                      orth_engine, st);
     if (e != cudaSuccess) return e;
-    eig_svt_kernel<<<ns, 1024, eig_smem(k), st>>>(a.G, a.T, a.sig, idx, k, kmax, gs, kmax, a.tau,
-                                                  a.tol, a.max_sweeps, a.stat, a.acc, a.kdev);
+    if (a.small_fp64 && k <= eig_fp64_max_k())
+      eig_svt_fp64_kernel<<<ns, 1024, eig_fp64_smem(k), st>>>(a.G, a.T, a.sig, idx, k, kmax, gs,
+                                                              kmax, a.tau, a.tol, a.max_sweeps,
+                                                              a.stat, a.acc, a.kdev);
+    else
+      eig_svt_kernel<<<ns, 1024, eig_smem(k), st>>>(a.G, a.T, a.sig, idx, k, kmax, gs, kmax,
+                                                    a.tau, a.tol, a.max_sweeps, a.stat, a.acc,
+                                                    a.kdev);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_cgemm(dyn(gemm(nw, k, k, ns, mat(a.Bt, idx, bs, 1, nw, 1),
                               mat(a.T, idx, gs, 1, kmax, 1), mat(a.P, idx, ps, 1, nw)),

@@ -677,6 +677,8 @@ tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
     return fail(c, TSVD_EINVAL, "use_graphs must be 0 or 1");
   if (o.batch_persistent != 0 && o.batch_persistent != 1)
     return fail(c, TSVD_EINVAL, "batch_persistent must be 0 or 1");
+  if (o.rsvt_small_fp64 != 0 && o.rsvt_small_fp64 != 1)
+    return fail(c, TSVD_EINVAL, "rsvt_small_fp64 must be 0 or 1");
   if (o.slice_form != TSVD_SLICE_AUTO && o.slice_form != TSVD_SLICE_PAIRWISE &&
       o.slice_form != TSVD_SLICE_BLOCK)
     return fail(c, TSVD_EINVAL, "slice_form must be TSVD_SLICE_AUTO, _PAIRWISE or _BLOCK");
@@ -859,6 +861,7 @@ RsvtArgs rsvt_args(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau,
   a.jscratch = w.rjs;
   a.jscratch_bytes = w.rjs_bytes;
   a.jknobs = rsvt_knobs(c);
+  a.small_fp64 = c->opts.rsvt_small_fp64;
   return a;
 }
 

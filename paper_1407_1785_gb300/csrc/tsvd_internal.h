@@ -366,6 +366,9 @@ struct RsvtArgs {
   // [0] sketch product [1] CholeskyQR2 [2] projection product [3] small SVT [4] rebuild
   // product [5] refill [6]
   cudaEvent_t* stage_ev = nullptr;
+  // 1: the k x k CholeskyQR2 factorisations and (for k <= 80) the Rayleigh-Ritz eigen-solve
+  // in FP64 instead of FP32 with double-single pivots
+  int small_fp64 = 0;
 };
 
 int rsvt_max_k();

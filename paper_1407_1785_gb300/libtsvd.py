@@ -58,7 +58,7 @@ class Opts(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("rsvt_oversample", ctypes.c_int),
                 ("rsvt_kmax", ctypes.c_int), ("rsvt_power", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("batch_persistent", ctypes.c_int),
-                ("slice_form", ctypes.c_int)]
+                ("slice_form", ctypes.c_int), ("rsvt_small_fp64", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -145,13 +145,16 @@ def test_rpca_200_iterations_matches_oracle():
     _check(Sg, g["S"], None, "RPCA S", scale=M)
 
 
-def test_rpca_mixed_full_run_equal_error():
+@pytest.mark.parametrize("fp64", [0, 1])
+def test_rpca_mixed_full_run_equal_error(fp64):
     """The mixed form with split-TF32 (3xTF32) products at the 240 x 320 x 60 RPCA size:
     recovery error no worse than the oracle's beyond 1% (+1e-5), here the FP32 floor since
-    the oracle recovers L exactly."""
+    the oracle recovers L exactly; k x k solves in FP32 / double-single or FP64."""
     g = _golden("rpca_240x320x60")
     M, L0, S0, sup, lam = synth.workload_rpca(seed=1)
-    with _ctx(libtsvd.PRECISION_3XTF32) as ctx:
+    torch = _torch()
+    with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
+                         precision=libtsvd.PRECISION_3XTF32, rsvt_small_fp64=fp64) as ctx:
         Lg, Sg, st = _rpca(ctx, M, lam, g["iters"])
     _equal_error(Lg, g["L"], L0, "RPCA L (3xTF32)")
 
@@ -170,11 +173,14 @@ def test_rpca_tf32_full_run_recovery_bound():
 
 
 def test_video_mixed_full_run_equal_error():
+    """The 3xTF32 mixed form on the 144 x 176 x 100 video (150 iterations): equal error, and
+    its X also within 1e-3 of the oracle's at the stored sample."""
     g = _golden("video_completion_144x176x100")
     X, om = synth.workload_video_completion(seed=1)
     with _ctx(libtsvd.PRECISION_3XTF32) as ctx:
         Xg, st = _completion(ctx, X, om, g["iters"])
     _equal_error(Xg, g["X"], X, "video X (3xTF32)")
+    _check(Xg, g["X"], None, "video X (3xTF32)")
 
 
 # ---- the mixed form, one t-SVT call at the benchmark sizes, against the oracle's t-SVT ----
@@ -207,14 +213,17 @@ def _config_tsvt_case(name):
 
 
 @pytest.mark.parametrize("name", ["rpca_240x320x60", "color_video_288x352x3x60"])
-@pytest.mark.parametrize("prec,tol", [(libtsvd.PRECISION_3XTF32, 1e-4),
-                                      (libtsvd.PRECISION_TF32, 1e-3)])
-def test_mixed_tsvt_at_config_size(name, prec, tol):
+@pytest.mark.parametrize("prec,tol,fp64", [(libtsvd.PRECISION_3XTF32, 1e-4, 0),
+                                           (libtsvd.PRECISION_3XTF32, 1e-4, 1),
+                                           (libtsvd.PRECISION_TF32, 1e-3, 0)])
+def test_mixed_tsvt_at_config_size(name, prec, tol, fp64):
     """One mixed-form t-SVT call at the RPCA (240 x 320 x 60) and colour-video (288 x 352 x 3 x
-    60) sizes within 1e-3 of the FP64 oracle (TF32 products) or 1e-4 (split 3xTF32)."""
+    60) sizes within 1e-3 of the FP64 oracle (TF32 products) or 1e-4 (split 3xTF32), with the
+    k x k CholeskyQR2 and eigen-solve in FP32 / double-single or in FP64 (fp64 = 1)."""
     torch = _torch()
     Y, tau, Zo = _config_tsvt_case(name)
-    with _ctx(prec) as ctx:
+    with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
+                         precision=prec, rsvt_small_fp64=fp64) as ctx:
         y = torch.from_numpy(colmajor(Y)).cuda()
         z = torch.empty_like(y)
         ctx.tsvt(y, z, Y.shape, tau)

@@ -65,9 +65,10 @@ def check_tsvt(ctx, Y, tau):
     floor = 1e-3 * np.linalg.norm(Y32.astype(np.float64).ravel())
     err = relerr(Zg, Zo, floor=floor)
     assert err <= TSVT_TOL, f"t-SVT relative error {err:.3e}"
-    # the TNN sums every singular value, including thousands at the FP32 floor, each with an
-    # absolute error of order eps_32 * ||Yhat_k||_2, so the sum is compared at 1e-4
-    assert abs(tnng - tnno) <= 1e-4 * max(tnno, 1e-30)
+    # the TNN (sum of every Fourier slice's singular values) at 1e-5: measured 4.9e-7 on the
+    # 144 x 176 x 100 video and 4.7e-6 on the 240 x 320 x 60 RPCA input (each singular value
+    # carries the Jacobi's FP32 rounding, ~eps_32 sqrt(sweeps) relative)
+    assert abs(tnng - tnno) <= 1e-5 * max(tnno, 1e-30)
     # multi-rank: exact wherever no singular value sits within 1e-4 sigma_max of tau
     sv = slice_singular_values(Y32)
     smax = max(s.max() for s in sv.values()) if sv else 0.0
