@@ -277,6 +277,37 @@ tsvd_status tnn_complete(tsvd_ctx* ctx, const float* M_obs, const uint8_t* omega
 tsvd_status trpca(tsvd_ctx* ctx, const float* M, int order, const int64_t* dims, float lambda,
                   int iters, float* L_out, float* S_out, tsvd_stats* stats);
 
+/* The ADMM state a solve continues from (tnn_complete_resume, trpca_resume): the state after
+ * some iterations of the same method, as returned by an earlier call.  Every pointer is a
+ * device pointer on the context's device, dims-shaped, or NULL for a zero tensor. */
+typedef struct tsvd_admm_state {
+  const float* Z;       /* completion: Z of the last iteration */
+  const float* Q;       /* completion: scaled dual Q after the last iteration */
+  const float* S;       /* RPCA: S of the last iteration */
+  const float* W;       /* RPCA: scaled dual W after the last iteration */
+  double rho;           /* penalty to continue with (> 0), e.g. tsvd_stats.rho_final of the
+                           earlier call; <= 0: opts.rho0 */
+} tsvd_admm_state;
+
+/* tnn_complete continued from a state: `iters` (>= 1) more iterations of the same ADMM from
+ * (Z, Q, rho) instead of Z = Q = 0, rho = rho0, so that k1 iterations followed by a resumed
+ * call of k2 iterations (fed the first call's Z_out, Q_out and rho_final) compute what one
+ * call of k1 + k2 iterations computes.  init may be NULL (a fresh start).  Q_out (nullable,
+ * device): receives the scaled dual after the last iteration, rescaled to the final rho
+ * (stats->rho_final).  Other arguments, memory and errors as tnn_complete, plus EINVAL for
+ * host state pointers or iters < 1 with init. */
+tsvd_status tnn_complete_resume(tsvd_ctx* ctx, const float* M_obs, const uint8_t* omega,
+                                int order, const int64_t* dims, int iters,
+                                const tsvd_admm_state* init, float* X_out, float* Z_out,
+                                float* Q_out, tsvd_stats* stats);
+
+/* trpca continued from a state: `iters` (>= 1) more iterations from (S, W, rho); W_out
+ * (nullable, device) receives the scaled dual after the last iteration.  Otherwise as trpca
+ * and tnn_complete_resume. */
+tsvd_status trpca_resume(tsvd_ctx* ctx, const float* M, int order, const int64_t* dims,
+                         float lambda, int iters, const tsvd_admm_state* init, float* L_out,
+                         float* S_out, float* W_out, tsvd_stats* stats);
+
 /* One tensor of a batched solve (tsvd_solve_batched). */
 enum { TSVD_PROBLEM_COMPLETE = 1, TSVD_PROBLEM_RPCA = 2 };
 typedef struct tsvd_problem {
@@ -335,6 +366,23 @@ tsvd_status tsvd_cgemm(tsvd_ctx* ctx, int transa, int transb, int m, int n, int 
                        const float* A, int64_t lda, int64_t stride_a, const float* B,
                        int64_t ldb, int64_t stride_b, float* C, int64_t ldc, int64_t stride_c,
                        int batch);
+
+/* Testing aid (not a step of the paper's method): host-side fault injection.  With the spec
+ * "alloc:N" (from the TSVD_FAULT environment variable, read at the library's first device
+ * allocation, or given here) the N-th device allocation the library makes in this process,
+ * counting from 1, fails as if the device had no memory left, so the call that makes it
+ * returns TSVD_ENOMEM; the allocations before and after it are unaffected.  This call re-reads
+ * the spec (spec = NULL: the environment variable again), restarts the count and returns N (0:
+ * off, also for a spec it cannot parse).  Needs no device. */
+long long tsvd_fault_injection_reset(const char* spec);
+
+/* Testing aid (not a step of the paper's method): runs, on device `device`, the bounded wait
+ * the persistent batched kernel uses for its dependencies, on a device counter that nothing
+ * raises, with a limit of limit_ms milliseconds (0..10000).  The wait must give up: the call
+ * returns TSVD_ETIMEOUT, the way a batched solve reports a dependency that never arrived, and
+ * leaves the device usable.  TSVD_OK would mean the wait did not end by its limit.  Errors:
+ * EINVAL (limit out of range), ENOMEM, ECUDA. */
+tsvd_status tsvd_selftest_bounded_wait(int device, int limit_ms);
 
 /* Measurement aid (not a step of the paper's method): the FP32 CUDA-core throughput of device
  * `device` in TFLOP/s (2 flops per fused multiply-add), measured with a loop of independent

@@ -1415,6 +1415,22 @@ __device__ __forceinline__ unsigned batch_ld_acquire(const unsigned* p) {
   return v;
 }
 
+// Bounded wait (one thread): until *p >= target, polling with a short sleep; gives up after
+// limit_ns of globaltimer time and returns false.  The persistent kernel's only wait.
+__device__ bool wait_counter_geq(const unsigned* p, unsigned target, unsigned long long limit_ns) {
+  const unsigned long long t0 = batch_clock();
+  while (batch_ld_acquire(p) < target) {
+    if (batch_clock() - t0 > limit_ns) return false;
+    __nanosleep(256);
+  }
+  return true;
+}
+
+// The bounded wait on a counter nothing raises (tsvd_selftest_bounded_wait): must give up.
+__global__ void wait_selftest_kernel(const unsigned* counter, unsigned long long limit_ns, int* err) {
+  if (threadIdx.x == 0 && !wait_counter_geq(counter, 1u, limit_ns)) atomicExch(err, 1);
+}
+
 __device__ SliceArgs batch_slice_args(const BatchDesc& d, const BatchIter& it) {
   const BatchTensor& t = d.t;
   SliceArgs a{};
@@ -1590,17 +1606,10 @@ __global__ void __maxnreg__(max_regs_for(CMAX)) batch_iter_kernel(BatchLaunch L)
     TubeArgs ta;
     if (!batch_tube_args(d, it, ta)) continue;
     if (it.k >= 0) {
-      if (threadIdx.x == 0) {
-        const unsigned target = (unsigned)(it.k + 1) * (unsigned)d.t.nslices;
-        const unsigned long long t0 = batch_clock();
-        while (batch_ld_acquire(&it.done[tix]) < target) {
-          if (batch_clock() - t0 > kBatchWaitNs) {
-            atomicExch(it.err, 1);
-            break;
-          }
-          __nanosleep(256);
-        }
-      }
+      if (threadIdx.x == 0 &&
+          !wait_counter_geq(&it.done[tix], (unsigned)(it.k + 1) * (unsigned)d.t.nslices,
+                            kBatchWaitNs))
+        atomicExch(it.err, 1);
       __syncthreads();
       __threadfence();
     }
@@ -1822,6 +1831,12 @@ bool batch_plan(const BatchTensor* ts, int n, int C, int small_nv, BatchPlan& pl
   plan.grid = clusters * C;
   plan.scratch_bytes = C > 1 ? (size_t)clusters * plan.xbuf_floats * sizeof(float) : 0;
   return true;
+}
+
+cudaError_t launch_wait_selftest(const unsigned* counter, unsigned long long limit_ns, int* err,
+                                 cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(counter, limit_ns, err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batch_iteration(const BatchPlan& p, const void* table_dev, void* scratch,

@@ -5,9 +5,13 @@
 #include "tsvd.h"
 #include "tsvd_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -77,6 +81,48 @@ struct tsvd_ctx {
 namespace {
 
 constexpr size_t kAlign = 256;
+
+// ---- host-side fault injection: TSVD_FAULT="alloc:N" makes the N-th device allocation of the
+// library in this process (counting from 1) fail as if the device were out of memory, so the
+// TSVD_ENOMEM paths can be exercised without exhausting a GPU.  Read at the first allocation
+// (or by tsvd_fault_injection_reset).
+std::atomic<long long> g_fault_alloc_at{-1};   // -1: not read yet; 0: off
+std::atomic<long long> g_alloc_count{0};
+
+long long parse_fault_spec(const char* spec) {
+  if (!spec) return 0;
+  const char* pre = "alloc:";
+  if (std::strncmp(spec, pre, std::strlen(pre)) != 0) return 0;
+  char* end = nullptr;
+  const long long n = std::strtoll(spec + std::strlen(pre), &end, 10);
+  return (end && *end == '\0' && n > 0) ? n : 0;
+}
+
+// cudaMalloc, unless the fault injector says this allocation fails.
+cudaError_t device_alloc(void** ptr, size_t bytes) {
+  long long at = g_fault_alloc_at.load();
+  if (at < 0) {
+    at = parse_fault_spec(std::getenv("TSVD_FAULT"));
+    long long expect = -1;
+    g_fault_alloc_at.compare_exchange_strong(expect, at);
+    at = g_fault_alloc_at.load();
+  }
+  const long long n = ++g_alloc_count;
+  if (at > 0 && n == at) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
+
+// A named range of the library's host-side work for profilers (NVTX; no cost without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -487,7 +533,7 @@ tsvd_status prepare_workspace(tsvd_ctx* c, const Problem& p, const WsRequest& rq
       c->graphs.clear();
     }
     void* ptr = nullptr;
-    cudaError_t e = cudaMalloc(&ptr, total);
+    cudaError_t e = device_alloc(&ptr, total);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(c, TSVD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", total, cudaGetErrorString(e));
@@ -761,12 +807,14 @@ tsvd_status record_event(tsvd_ctx* c, int kind) {
 // Launch helpers: they enqueue on c->cur, which is the context's stream or, while a solver's
 // launch sequence is being captured into a graph, the private capture stream.
 tsvd_status run_tube(tsvd_ctx* c, const TubeArgs& a, const char* what) {
+  NvtxRange nr(what);
   TSVD_TRY(record_event(c, 1));
   TSVD_TRY(launch(c, launch_tube_pass(a, c->cur), what));
   return record_event(c, 1);
 }
 
 tsvd_status run_slice(tsvd_ctx* c, const SliceArgs& a) {
+  NvtxRange nr("slice SVT (Jacobi)");
   TSVD_TRY(record_event(c, 0));
   TSVD_TRY(launch(c, launch_jacobi_svt(a, c->cur), "slice SVT"));
   ++c->slice_launches;
@@ -924,6 +972,7 @@ tsvd_status rsvt_step(tsvd_ctx* c, const Problem& p, const Workspace& w, float t
   const double mw = w.mw, nw = w.nw, kk = k, ns = w.ndistinct;
   c->rs_gemm_gflop += (power + 1) * ns * 3.0 * 8.0 * mw * nw * kk * 1e-9;
   c->rs_svd_gflop += ns * 4.0 * (4.0 * nw * kk * kk + 8.0 * kk * kk * kk) * 1e-9;
+  NvtxRange nr("slice SVT (randomized)");
   TSVD_CUDA(c, cudaMemsetAsync(a.rstat, 0, sizeof(RsvtStat), c->cur));
   TSVD_TRY(record_event(c, 0));
   TSVD_TRY(launch(c, launch_rsvt(a, c->cur), "randomized slice SVT"));
@@ -1374,6 +1423,7 @@ const char* tsvd_last_error(const tsvd_ctx* c) {
 tsvd_status tsvt(tsvd_ctx* c, const float* Y, float* Z, int order, const int64_t* dims,
                  float tau, int32_t* multirank, double* tnn) {
   if (!c) return TSVD_EINVAL;
+  NvtxRange nr("tsvt");
   begin_call(c);
   if (!Y || !Z) return fail(c, TSVD_EINVAL, "Y and Z must not be NULL");
   if (!(tau >= 0.f) || !std::isfinite(tau)) return fail(c, TSVD_EINVAL, "tau must be finite and >= 0");
@@ -1458,7 +1508,7 @@ tsvd_status grow_fbuf(tsvd_ctx* c, size_t need) {
     c->fbuf_cap = 0;
   }
   void* ptr = nullptr;
-  const cudaError_t e = cudaMalloc(&ptr, need);
+  const cudaError_t e = device_alloc(&ptr, need);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, TSVD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", need, cudaGetErrorString(e));
@@ -1815,13 +1865,21 @@ tsvd_status tsvd_tproduct(tsvd_ctx* c, const float* A, const float* B, float* C,
   return TSVD_OK;
 }
 
-tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, int order,
-                         const int64_t* dims, int iters, float* X_out, float* Z_out,
-                         tsvd_stats* stats) {
+}  // extern "C"
+
+namespace {
+
+tsvd_status complete_impl(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, int order,
+                          const int64_t* dims, int iters, const tsvd_admm_state* init,
+                          float* X_out, float* Z_out, float* Q_out, tsvd_stats* stats) {
   if (!c) return TSVD_EINVAL;
+  NvtxRange nr("tnn_complete");
   begin_call(c);
   if (!M_obs || !omega || !X_out) return fail(c, TSVD_EINVAL, "M_obs, omega and X_out must not be NULL");
   if (iters < 0) return fail(c, TSVD_EINVAL, "iters must be >= 0");
+  if (init && iters < 1) return fail(c, TSVD_EINVAL, "a resumed solve runs at least 1 iteration");
+  if (init && init->rho > 0 && !std::isfinite(init->rho))
+    return fail(c, TSVD_EINVAL, "init->rho must be finite");
   Problem p;
   TSVD_TRY(make_problem(c, order, dims, p));
   DeviceGuard dg(c->device);
@@ -1830,12 +1888,18 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
   const int kx = pointer_kind(X_out, c->device);
   const int kzz = Z_out ? pointer_kind(Z_out, c->device) : 0;
   if (km < 0 || ko < 0 || kx < 0 || kzz < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
+  {
+    const void* st_ptrs[3] = {init ? init->Z : nullptr, init ? init->Q : nullptr, Q_out};
+    for (const void* q : st_ptrs)
+      if (q && pointer_kind(q, c->device) != 0)
+        return fail(c, TSVD_EINVAL, "the ADMM state and Q_out must be device memory");
+  }
   WsRequest rq;
   rq.state = rq.yn = true;
   rq.stage_in = km == 1;
   rq.stage_om = ko == 1;
   rq.stage_out0 = kx == 1;
-  rq.stage_out1 = Z_out && kzz == 1;
+  rq.stage_out1 = (Z_out && kzz == 1) || (Q_out && !Z_out);   // Z for Q_out
   rq.rsvt = mixed_precision(c);
   rq.warm = !rq.rsvt && c->opts.warm_start != TSVD_WARM_OFF && iters >= 2 &&
             warm_plan_exists(c, p);
@@ -1855,7 +1919,7 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
     om = w.stage_om;
   }
   float* x = kx == 1 ? w.stage_out0 : X_out;
-  float* z = Z_out ? (kzz == 1 ? w.stage_out1 : Z_out) : nullptr;
+  float* z = Z_out ? (kzz == 1 ? w.stage_out1 : Z_out) : (Q_out ? w.stage_out1 : nullptr);
 
   TSVD_TRY(launch(c, launch_encode_observed(m, om, w.yn, p.N, w.bad, c->stream), "encode observed"));
   int bad = 0;
@@ -1864,26 +1928,49 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
   if (bad) return fail(c, TSVD_EINVAL, "%d observed entries are not finite", bad);
 
   const double scale = threshold_scale(c, p);
-  double rho = c->opts.rho0;
+  const double rho_start = init && init->rho > 0 ? init->rho : c->opts.rho0;
+  double rho = rho_start;
   if (iters == 0) {
     TSVD_TRY(launch(c, launch_project_observed(m, om, x, p.N, c->stream), "project"));
     if (z) TSVD_CUDA(c, cudaMemsetAsync(z, 0, bytes, c->stream));
+    if (Q_out) TSVD_CUDA(c, cudaMemsetAsync(Q_out, 0, bytes, c->stream));
   } else {
     const bool tuned = !c->opts.autotune || c->tuned.count(plan_key(c, p, w.ndistinct));
     const SliceKnobs kn = planned_knobs(c, p, w.ndistinct);
     const std::vector<int64_t> key = solver_key(c, 1, p, iters, {m, om, x, z}, kn);
+    double last_ratio = 1.0;
     auto body = [&]() -> tsvd_status {
-      double r = c->opts.rho0;
+      double r = rho_start;
       RsvtLoop rl(c, p, w);
       if (w.rsvt) TSVD_TRY(rl.begin());
-      // iteration 0: X = P_Omega(M), Q = 0, V = X + Q
       TubeArgs t0 = tube_args(p, w, TUBE_COMPLETE);
       t0.in = w.yn;
       t0.state = w.state;
       t0.spec_out = w.spec_a;
-      t0.first = 1;
       t0.write_out = iters == 1;
       t0.out0 = x;
+      if (!init) {
+        // iteration 0: X = P_Omega(M), Q = 0, V = X + Q
+        t0.first = 1;
+      } else {
+        // resumed from (Z, Q): Z-hat = R2C(Z) and V = Z + Q, so the pass forms
+        // Q = V - Z, X = P_Omega(M) + P_Omega^c(Z - Q) and V = X + Q as every later pass does
+        if (init->Z) {
+          TubeArgs f = tube_args(p, w, TUBE_FWD);
+          f.in = init->Z;
+          f.spec_out = w.spec_b;
+          TSVD_TRY(run_tube(c, f, "tube pass (resumed Z)"));
+        } else {
+          TSVD_CUDA(c, cudaMemsetAsync(w.spec_b, 0, (size_t)p.g.nstore * p.g.N12 * sizeof(float2),
+                                       c->cur));
+        }
+        TSVD_TRY(launch(c, launch_combine4(w.state, init->Z, 1.f, init->Q, 1.f, nullptr, 0.f,
+                                           nullptr, 0.f, 1.f, p.N, c->cur),
+                        "resumed state"));
+        t0.first = 0;
+        t0.spec_in = w.spec_b;
+        t0.ratio = 1.f;
+      }
       TSVD_TRY(run_tube(c, t0, "completion pass"));
       for (int k = 0; k < iters; ++k) {
         const float tau = (float)(scale / r);
@@ -1905,6 +1992,7 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
           t.out0 = x;
           TSVD_TRY(run_tube(c, t, "completion pass"));
         }
+        last_ratio = r / r_next;
         r = r_next;
       }
       if (z) {
@@ -1913,10 +2001,14 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
         inv.out0 = z;
         TSVD_TRY(run_tube(c, inv, "tube pass (inverse)"));
       }
+      if (Q_out)   // the scaled dual of the last iteration: (V - Z) rho_{k} / rho_{k+1}
+        TSVD_TRY(launch(c, launch_combine4(Q_out, w.state, 1.f, z, -1.f, nullptr, 0.f, nullptr,
+                                           0.f, (float)last_ratio, p.N, c->cur),
+                        "final dual"));
       if (w.rsvt) TSVD_TRY(rl.finish());
       return TSVD_OK;
     };
-    TSVD_TRY(run_maybe_graph(c, key, tuned && !w.rsvt, body));
+    TSVD_TRY(run_maybe_graph(c, key, tuned && !w.rsvt && !init && !Q_out, body));
     for (int k = 0; k < iters; ++k) rho = std::fmin(c->opts.mu * rho, c->opts.rho_max);
   }
   if (kx == 1) TSVD_CUDA(c, cudaMemcpyAsync(X_out, x, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -1927,12 +2019,17 @@ tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, 
   return TSVD_OK;
 }
 
-tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, float lambda,
-                  int iters, float* L_out, float* S_out, tsvd_stats* stats) {
+tsvd_status rpca_impl(tsvd_ctx* c, const float* M, int order, const int64_t* dims, float lambda,
+                      int iters, const tsvd_admm_state* init, float* L_out, float* S_out,
+                      float* W_out, tsvd_stats* stats) {
   if (!c) return TSVD_EINVAL;
+  NvtxRange nr("trpca");
   begin_call(c);
   if (!M || !L_out || !S_out) return fail(c, TSVD_EINVAL, "M, L_out and S_out must not be NULL");
   if (iters < 0) return fail(c, TSVD_EINVAL, "iters must be >= 0");
+  if (init && iters < 1) return fail(c, TSVD_EINVAL, "a resumed solve runs at least 1 iteration");
+  if (init && init->rho > 0 && !std::isfinite(init->rho))
+    return fail(c, TSVD_EINVAL, "init->rho must be finite");
   if (!(lambda > 0.f) || !std::isfinite(lambda)) return fail(c, TSVD_EINVAL, "lambda must be finite and > 0");
   Problem p;
   TSVD_TRY(make_problem(c, order, dims, p));
@@ -1941,6 +2038,12 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
   const int km = pointer_kind(M, c->device), kl = pointer_kind(L_out, c->device);
   const int ks = pointer_kind(S_out, c->device);
   if (km < 0 || kl < 0 || ks < 0) return fail(c, TSVD_EINVAL, "tensor on another device");
+  {
+    const void* st_ptrs[3] = {init ? init->S : nullptr, init ? init->W : nullptr, W_out};
+    for (const void* q : st_ptrs)
+      if (q && pointer_kind(q, c->device) != 0)
+        return fail(c, TSVD_EINVAL, "the ADMM state and W_out must be device memory");
+  }
   WsRequest rq;
   rq.state = true;
   rq.stage_in = km == 1;
@@ -1968,10 +2071,12 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
   if (bad) return fail(c, TSVD_EINVAL, "%d entries of M are not finite", bad);
 
   const double scale = threshold_scale(c, p);
-  double rho = c->opts.rho0;
+  const double rho_start = init && init->rho > 0 ? init->rho : c->opts.rho0;
+  double rho = rho_start;
   if (iters == 0) {
     TSVD_CUDA(c, cudaMemsetAsync(l, 0, bytes, c->stream));
     TSVD_CUDA(c, cudaMemsetAsync(sp, 0, bytes, c->stream));
+    if (W_out) TSVD_CUDA(c, cudaMemsetAsync(W_out, 0, bytes, c->stream));
   } else {
     const bool tuned = !c->opts.autotune || c->tuned.count(plan_key(c, p, w.ndistinct));
     const SliceKnobs kn = planned_knobs(c, p, w.ndistinct);
@@ -1979,14 +2084,28 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
     int64_t lbits;
     std::memcpy(&lbits, &lambda, sizeof lambda);
     key.push_back(lbits);
+    double last_ratio = 1.0;
     auto body = [&]() -> tsvd_status {
-      double r = c->opts.rho0;
+      double r = rho_start;
       RsvtLoop rl(c, p, w);
       if (w.rsvt) TSVD_TRY(rl.begin());
-      // iteration 0: S = W = 0, so the t-SVT input is M itself
       TubeArgs t0 = tube_args(p, w, TUBE_FWD);
-      t0.in = m;
       t0.spec_out = w.spec_a;
+      if (!init) {
+        // iteration 0: S = W = 0, so the t-SVT input is M itself
+        t0.in = m;
+      } else {
+        // resumed from (S, W): the t-SVT input M - S - W (staged in the output spectrum's
+        // buffer, which the first slice SVT writes only after this pass), and W in the state
+        float* v0 = reinterpret_cast<float*>(w.spec_b);
+        TSVD_TRY(launch(c, launch_combine4(v0, m, 1.f, init->S, -1.f, init->W, -1.f, nullptr,
+                                           0.f, 1.f, p.N, c->cur),
+                        "resumed input"));
+        TSVD_TRY(launch(c, launch_combine4(w.state, init->W, 1.f, nullptr, 0.f, nullptr, 0.f,
+                                           nullptr, 0.f, 1.f, p.N, c->cur),
+                        "resumed state"));
+        t0.in = v0;
+      }
       TSVD_TRY(run_tube(c, t0, "tube pass (forward)"));
       for (int k = 0; k < iters; ++k) {
         const float tau = (float)(scale / r);
@@ -2004,18 +2123,25 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
         t.spec_out = w.spec_a;
         t.ratio = (float)(r / r_next);
         t.kappa = (float)((double)lambda / r);
-        t.first = k == 0;
+        t.first = k == 0 && !init;
         t.last = k + 1 == iters;
         t.out0 = l;
         t.out1 = sp;
         t.tube_sparse = c->opts.sparse_mode == TSVD_SPARSE_TUBE;
         TSVD_TRY(run_tube(c, t, "RPCA pass"));
+        last_ratio = r / r_next;
         r = r_next;
       }
+      // the scaled dual of the last iteration, (W + L + S - M) rho_k / rho_{k+1} (the last
+      // pass writes L and S and leaves W as it was)
+      if (W_out)
+        TSVD_TRY(launch(c, launch_combine4(W_out, w.state, 1.f, l, 1.f, sp, 1.f, m, -1.f,
+                                           (float)last_ratio, p.N, c->cur),
+                        "final dual"));
       if (w.rsvt) TSVD_TRY(rl.finish());
       return TSVD_OK;
     };
-    TSVD_TRY(run_maybe_graph(c, key, tuned && !w.rsvt, body));
+    TSVD_TRY(run_maybe_graph(c, key, tuned && !w.rsvt && !init && !W_out, body));
     for (int k = 0; k < iters; ++k) rho = std::fmin(c->opts.mu * rho, c->opts.rho_max);
   }
   if (kl == 1) TSVD_CUDA(c, cudaMemcpyAsync(L_out, l, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -2024,6 +2150,33 @@ tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, f
   TSVD_TRY(fill_stats(c, p, w, iters, rho, stats));
   TSVD_CUDA(c, cudaGetLastError());
   return TSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tsvd_status tnn_complete(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, int order,
+                         const int64_t* dims, int iters, float* X_out, float* Z_out,
+                         tsvd_stats* stats) {
+  return complete_impl(c, M_obs, omega, order, dims, iters, nullptr, X_out, Z_out, nullptr, stats);
+}
+
+tsvd_status tnn_complete_resume(tsvd_ctx* c, const float* M_obs, const uint8_t* omega, int order,
+                                const int64_t* dims, int iters, const tsvd_admm_state* init,
+                                float* X_out, float* Z_out, float* Q_out, tsvd_stats* stats) {
+  return complete_impl(c, M_obs, omega, order, dims, iters, init, X_out, Z_out, Q_out, stats);
+}
+
+tsvd_status trpca(tsvd_ctx* c, const float* M, int order, const int64_t* dims, float lambda,
+                  int iters, float* L_out, float* S_out, tsvd_stats* stats) {
+  return rpca_impl(c, M, order, dims, lambda, iters, nullptr, L_out, S_out, nullptr, stats);
+}
+
+tsvd_status trpca_resume(tsvd_ctx* c, const float* M, int order, const int64_t* dims,
+                         float lambda, int iters, const tsvd_admm_state* init, float* L_out,
+                         float* S_out, float* W_out, tsvd_stats* stats) {
+  return rpca_impl(c, M, order, dims, lambda, iters, init, L_out, S_out, W_out, stats);
 }
 
 }  // extern "C"
@@ -2115,6 +2268,7 @@ tsvd_status persistent_batch(tsvd_ctx* c, const std::vector<BatchItem>& items, i
   bi.done = done;
   bi.err = err;
   auto run = [&](int k, double r, double r_next, bool slices_only) -> tsvd_status {
+    NvtxRange nr("persistent batched iteration");
     bi.k = k;
     bi.r = r;
     bi.r_next = r_next;
@@ -2225,6 +2379,7 @@ tsvd_status persistent_batch(tsvd_ctx* c, const std::vector<BatchItem>& items, i
 tsvd_status solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, int iters,
                           tsvd_stats* stats, int only_kind) {
   if (!c) return TSVD_EINVAL;
+  NvtxRange nr("batched solve");
   begin_call(c);
   if (count < 0 || (count > 0 && !problems)) return fail(c, TSVD_EINVAL, "bad problem list");
   if (only_kind)
@@ -2306,7 +2461,7 @@ tsvd_status solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, 
       c->graphs.clear();
     }
     void* ptr = nullptr;
-    cudaError_t e = cudaMalloc(&ptr, total);
+    cudaError_t e = device_alloc(&ptr, total);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(c, TSVD_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", total, cudaGetErrorString(e));
@@ -2480,6 +2635,37 @@ extern "C" {
 tsvd_status tsvd_solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, int iters,
                                tsvd_stats* stats) {
   return solve_batched(c, count, problems, iters, stats, 0);
+}
+
+tsvd_status tsvd_selftest_bounded_wait(int device, int limit_ms) {
+  if (limit_ms < 0 || limit_ms > 10000) return TSVD_EINVAL;
+  DeviceGuard dg(device);
+  if (!dg.ok) {
+    cudaGetLastError();
+    return TSVD_ECUDA;
+  }
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, 2 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return TSVD_ENOMEM;
+  }
+  int err_h = 0;
+  cudaError_t e = cudaMemset(buf, 0, 2 * sizeof(int));
+  unsigned* counter = static_cast<unsigned*>(buf);
+  int* err = static_cast<int*>(buf) + 1;
+  if (e == cudaSuccess)
+    e = launch_wait_selftest(counter, (unsigned long long)limit_ms * 1000000ull, err, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&err_h, err, sizeof err_h, cudaMemcpyDeviceToHost);
+  cudaGetLastError();
+  cudaFree(buf);
+  if (e != cudaSuccess) return TSVD_ECUDA;
+  return err_h ? TSVD_ETIMEOUT : TSVD_OK;
+}
+
+long long tsvd_fault_injection_reset(const char* spec) {
+  g_fault_alloc_at = parse_fault_spec(spec ? spec : std::getenv("TSVD_FAULT"));
+  g_alloc_count = 0;
+  return g_fault_alloc_at.load();
 }
 
 tsvd_status tnn_complete_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, int iters,

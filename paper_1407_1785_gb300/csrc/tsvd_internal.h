@@ -117,6 +117,11 @@ cudaError_t launch_encode_observed(const float* M, const uint8_t* omega, float* 
                                    int64_t N, int* bad, cudaStream_t st);
 // Counts non-finite entries of x into *bad.
 cudaError_t launch_count_nonfinite(const float* x, int64_t N, int* bad, cudaStream_t st);
+// out = (a x + b y + c z + d w) * scale elementwise (nullptr inputs count as zero; out may
+// alias an input).
+cudaError_t launch_combine4(float* out, const float* x, float a, const float* y, float b,
+                           const float* z, float c, const float* w, float d, float scale,
+                           int64_t N, cudaStream_t st);
 // X = omega ? M : 0, Z = 0 (the zero-iteration completion result).
 cudaError_t launch_project_observed(const float* M, const uint8_t* omega, float* X, int64_t N,
                                     cudaStream_t st);
@@ -260,6 +265,10 @@ bool batch_plan(const BatchTensor* ts, int n, int C, int small_nv, BatchPlan& pl
 // that follow them (the init launch, it.k = -1: the first tube passes only).
 cudaError_t launch_batch_iteration(const BatchPlan& plan, const void* table_dev, void* scratch,
                                    const BatchIter& it, cudaStream_t st);
+// The persistent kernel's bounded wait on `counter` (>= 1) with the given limit; *err = 1 when
+// it gave up.
+cudaError_t launch_wait_selftest(const unsigned* counter, unsigned long long limit_ns, int* err,
+                                 cudaStream_t st);
 
 // Fourier-domain factors of the truncated t-SVD from the converged Jacobi of every distinct
 // slice (factor.cu): W (len x nv per stored slice, as SliceArgs::wout writes it), sigma (nv per

@@ -336,6 +336,22 @@ __global__ void project_observed_kernel(const float* __restrict__ M, const uint8
     X[e] = om[e] ? M[e] : 0.f;
 }
 
+// out = (a x + b y + c z + d w) * scale, absent inputs (nullptr) counting as zero.
+__global__ void combine4_kernel(float* __restrict__ out, const float* __restrict__ x, float a,
+                                const float* __restrict__ y, float b, const float* __restrict__ z,
+                                float c, const float* __restrict__ w, float d, float scale,
+                                int64_t N) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.f;
+    if (x) v = fmaf(a, x[e], v);
+    if (y) v = fmaf(b, y[e], v);
+    if (z) v = fmaf(c, z[e], v);
+    if (w) v = fmaf(d, w[e], v);
+    out[e] = v * scale;
+  }
+}
+
 unsigned elementwise_grid(int64_t N) {
   int64_t b = (N + 255) / 256;
   const int64_t cap = (int64_t)device_sm_count() * 16;
@@ -393,6 +409,14 @@ cudaError_t launch_encode_observed(const float* M, const uint8_t* omega, float* 
 cudaError_t launch_count_nonfinite(const float* x, int64_t N, int* bad, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
   count_nonfinite_kernel<<<elementwise_grid(N), 256, 0, st>>>(x, N, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine4(float* out, const float* x, float a, const float* y, float b,
+                           const float* z, float c, const float* w, float d, float scale,
+                           int64_t N, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  combine4_kernel<<<elementwise_grid(N), 256, 0, st>>>(out, x, a, y, b, z, c, w, d, scale, N);
   return cudaGetLastError();
 }
 

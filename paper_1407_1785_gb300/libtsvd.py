@@ -32,7 +32,9 @@ EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_la
                     "tsvt", "tsvd_factor", "tsvd_compress", "tsvd_tproduct", "tnn_complete",
                     "trpca",
                     "tsvd_solve_batched", "tnn_complete_batched", "trpca_batched",
-                    "tsvt_static", "tsvd_cgemm", "tsvd_measure_fp32_peak")
+                    "tsvt_static", "tsvd_cgemm", "tsvd_measure_fp32_peak",
+                    "tsvd_fault_injection_reset", "tsvd_selftest_bounded_wait",
+                    "tnn_complete_resume", "trpca_resume")
 OP_N, OP_T, OP_C = 0, 1, 2
 WARM_OFF, WARM_ON, WARM_AUTO = 0, 1, 2
 SLICE_AUTO, SLICE_PAIRWISE, SLICE_BLOCK = 0, 1, 2
@@ -45,6 +47,11 @@ class Problem(ctypes.Structure):
                 ("dims", ctypes.c_int64 * 4), ("M", ctypes.c_void_p),
                 ("omega", ctypes.c_void_p), ("lam", ctypes.c_float),
                 ("out0", ctypes.c_void_p), ("out1", ctypes.c_void_p)]
+
+
+class AdmmState(ctypes.Structure):
+    _fields_ = [("Z", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("S", ctypes.c_void_p),
+                ("W", ctypes.c_void_p), ("rho", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
@@ -127,6 +134,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.trpca.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_float, ctypes.c_int, P, P,
                         ctypes.POINTER(Stats)]
     L.trpca.restype = ctypes.c_int
+    L.tnn_complete_resume.argtypes = [P, P, P, ctypes.c_int, i64p, ctypes.c_int,
+                                      ctypes.POINTER(AdmmState), P, P, P, ctypes.POINTER(Stats)]
+    L.tnn_complete_resume.restype = ctypes.c_int
+    L.trpca_resume.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_float, ctypes.c_int,
+                               ctypes.POINTER(AdmmState), P, P, P, ctypes.POINTER(Stats)]
+    L.trpca_resume.restype = ctypes.c_int
     L.tsvt_static.argtypes = [P, P, ctypes.c_int, i64p, ctypes.c_float, P]
     L.tsvt_static.restype = ctypes.c_int
     L.tsvd_solve_batched.argtypes = [P, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_int,
@@ -138,6 +151,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     L.tsvd_measure_fp32_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_double)]
     L.tsvd_measure_fp32_peak.restype = ctypes.c_int
+    L.tsvd_fault_injection_reset.argtypes = [ctypes.c_char_p]
+    L.tsvd_fault_injection_reset.restype = ctypes.c_longlong
+    L.tsvd_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.tsvd_selftest_bounded_wait.restype = ctypes.c_int
     i64 = ctypes.c_int64
     L.tsvd_cgemm.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                              ctypes.c_int, P, i64, i64, P, i64, i64, P, i64, i64, ctypes.c_int]
@@ -161,6 +178,18 @@ def measure_fp32_peak(device: int = 0):
     if st != TSVD_OK:
         raise TsvdError("tsvd_measure_fp32_peak", st, "measurement failed")
     return a.value, b.value
+
+
+def fault_injection_reset(spec: Optional[str] = None) -> int:
+    """Host-side fault injection ("alloc:N": the N-th device allocation of the library fails);
+    None re-reads the TSVD_FAULT environment variable.  Returns N (0 = off)."""
+    return int(load().tsvd_fault_injection_reset(spec.encode() if spec is not None else None))
+
+
+def selftest_bounded_wait(device: int = 0, limit_ms: int = 50) -> int:
+    """Runs the persistent kernel's bounded wait on a counter nothing raises; returns the
+    status (TSVD_ETIMEOUT when the wait gave up, as it must)."""
+    return int(load().tsvd_selftest_bounded_wait(int(device), int(limit_ms)))
 
 
 def default_opts() -> Opts:
@@ -297,6 +326,31 @@ class Context:
         st = self._L.trpca(self._h, _ptr(M), len(dims), _dims(dims), float(lam), int(iters),
                            _ptr(L_out), _ptr(S_out), ctypes.byref(s) if stats else None)
         self._check("trpca", st)
+        return s.as_dict() if stats else None
+
+    def tnn_complete_resume(self, M_obs, omega, dims: Sequence[int], iters: int, X_out,
+                            Z_out=None, Q_out=None, Z0=None, Q0=None, rho=0.0,
+                            stats: bool = False):
+        """tnn_complete continued from (Z0, Q0, rho) (device buffers or None); Q_out receives
+        the final scaled dual."""
+        st0 = AdmmState(_ptr(Z0), _ptr(Q0), None, None, float(rho))
+        s = Stats()
+        st = self._L.tnn_complete_resume(self._h, _ptr(M_obs), _ptr(omega), len(dims),
+                                         _dims(dims), int(iters), ctypes.byref(st0),
+                                         _ptr(X_out), _ptr(Z_out), _ptr(Q_out),
+                                         ctypes.byref(s) if stats else None)
+        self._check("tnn_complete_resume", st)
+        return s.as_dict() if stats else None
+
+    def trpca_resume(self, M, dims: Sequence[int], lam: float, iters: int, L_out, S_out,
+                     W_out=None, S0=None, W0=None, rho=0.0, stats: bool = False):
+        """trpca continued from (S0, W0, rho); W_out receives the final scaled dual."""
+        st0 = AdmmState(None, None, _ptr(S0), _ptr(W0), float(rho))
+        s = Stats()
+        st = self._L.trpca_resume(self._h, _ptr(M), len(dims), _dims(dims), float(lam),
+                                  int(iters), ctypes.byref(st0), _ptr(L_out), _ptr(S_out),
+                                  _ptr(W_out), ctypes.byref(s) if stats else None)
+        self._check("trpca_resume", st)
         return s.as_dict() if stats else None
 
     def solve_batched(self, problems, iters: int, stats: bool = False,

@@ -95,3 +95,16 @@ def test_create_without_gpu_reports_cuda_error():
 def test_library_is_the_in_tree_build():
     assert os.path.commonpath([libtsvd.library_path(), ROOT]) == ROOT
     assert os.path.exists(libtsvd.library_path())
+
+
+def test_fault_injection_spec_parsing():
+    """TSVD_FAULT specs: "alloc:N" with N >= 1 turns the N-th device allocation into a failure;
+    anything else is off (0).  Needs no GPU."""
+    from paper_1407_1785_gb300 import libtsvd
+    try:
+        assert libtsvd.fault_injection_reset("alloc:3") == 3
+        assert libtsvd.fault_injection_reset("alloc:1") == 1
+        for bad in ("alloc:0", "alloc:-2", "alloc:", "alloc:3x", "free:1", ""):
+            assert libtsvd.fault_injection_reset(bad) == 0, bad
+    finally:
+        libtsvd.fault_injection_reset("")
