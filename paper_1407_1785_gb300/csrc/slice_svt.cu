@@ -1588,7 +1588,9 @@ __global__ void __maxnreg__(max_regs_for(CMAX)) batch_iter_kernel(BatchLaunch L)
     }
     if (it.slices_only) return;
   }
-  // 3. tube tiles (threads TILE_THREADS and up skip the tile work)
+  // 3. tube tiles (threads TILE_THREADS and up skip the tile work); the tile tables are
+  // rebuilt only when the tensor changes
+  int last_tix = -1;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(&it.ctr[2], 1);
     __syncthreads();
@@ -1615,12 +1617,14 @@ __global__ void __maxnreg__(max_regs_for(CMAX)) batch_iter_kernel(BatchLaunch L)
     }
     if (threadIdx.x < TILE_THREADS) {
       const int64_t t0 = (int64_t)(item - L.tile_start[lo]) * TT;
+      const bool build = tix != last_tix;
       switch (d.rm) {
-        case 2: tube_tile_body<2>(ta, t0, smem_raw); break;
-        case 4: tube_tile_body<4>(ta, t0, smem_raw); break;
-        default: tube_tile_body<8>(ta, t0, smem_raw); break;
+        case 2: tube_tile_body<2>(ta, t0, smem_raw, build); break;
+        case 4: tube_tile_body<4>(ta, t0, smem_raw, build); break;
+        default: tube_tile_body<8>(ta, t0, smem_raw, build); break;
       }
     }
+    last_tix = tix;
   }
 }
 

@@ -19,6 +19,8 @@
 #include "tsvd_internal.h"
 #include "tube_tile.cuh"
 
+#include <algorithm>
+
 namespace tsvd {
 namespace {
 
@@ -271,10 +273,12 @@ __global__ void __launch_bounds__(TB) tube_pass_kernel(TubeArgs a) {
   }
 }
 
+// Persistent over tiles: a CTA builds the tables once and takes tiles blockIdx.x, + gridDim.x, ...
 template <int RM>
-__global__ void __launch_bounds__(TILE_THREADS) tube_tile_kernel(TubeArgs a) {
+__global__ void __launch_bounds__(TILE_THREADS) tube_tile_kernel(TubeArgs a, int64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  tube_tile_body<RM>(a, (int64_t)blockIdx.x * TT, smem_raw);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    tube_tile_body<RM>(a, tile * TT, smem_raw, tile == (int64_t)blockIdx.x);
 }
 
 template <int RM>
@@ -283,9 +287,17 @@ cudaError_t launch_tile(const TubeArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(tube_tile_kernel<RM>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t grid = (a.g.N12 + TT - 1) / TT;
-  if (grid > 0x7fffffff) return cudaErrorInvalidValue;
-  tube_tile_kernel<RM><<<(unsigned)grid, TILE_THREADS, smem, st>>>(a);
+  const int64_t ntiles = (a.g.N12 + TT - 1) / TT;
+  // a persistent grid: the CTAs that fit on the device at once (or fewer tiles)
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tube_tile_kernel<RM>, TILE_THREADS,
+                                                    smem);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)per_sm * device_sm_count());
+  tube_tile_kernel<RM><<<(unsigned)grid, TILE_THREADS, smem, st>>>(a, ntiles);
   return cudaGetLastError();
 }
 

@@ -9,25 +9,27 @@ namespace tsvd {
 namespace {
 
 // ---------------------------------------------------------------------------------------------
-// Tile form (used whenever the shape fits): one CTA of 256 threads per tile of TT = 32
-// consecutive tubes.  Global accesses are rows of 32 consecutive tubes (128 B real, 256 B
-// complex).  The tile lives in shared memory as
-//   zt[jf*nh + jh][t]          the real tube entries,
-//   yt[jf*2hh + 2kh + c][t]    the half spectrum as (re, im) rows, c = 0, 1,
-// and the half-mode DFTs of the tile are two small real matrix products against one shared
-// matrix Fr[jh][2kh + c] = (cos, -sin)(2 pi kh jh / nh):
-//   forward  (R2C)   yt = Fr^T zt   per jf block (M = 2hh rows, K = nh);
-//   inverse  (C2R)   zt = Fr  (w . yt) per jf block (M = nh rows, K = 2hh), where the weights
-//                    w_kh = c_kh / (nf nh) (c = 1 at kh = 0 and nh/2, else 2) are applied when
-//                    the spectrum is loaded.
-// Blocks of zt are nh4 = nh rounded up to 4 rows, blocks of yt and the rows of Fr q4 = 2hh
-// rounded up to 8 (Fr has nh4 rows), all padding zero, so the products run over K in steps
-// of 4 with 128-bit loads: the forward reads Fr rows r..r+RM-1 of one k at once, the inverse
-// 4 k of one row.  256 threads = 8 groups of 4 tubes x 32 groups of RM consecutive rows; a
-// thread accumulates RM rows x 4 tubes with packed FP32x2 FMAs (two tubes per register pair).
-// The full-mode DFT of the 4-way case (length nf <= 8) runs in registers per (kh, tube).
-// The fused ADMM steps are those of the thread-per-tube form above, on the tile in shared
-// memory.
+// Tile form (used whenever the shape fits): a CTA runs tiles of TT = 32 consecutive tubes with
+// TILE_THREADS = 256 threads.  Global accesses are rows of 32 consecutive tubes (128 B real,
+// 256 B complex).  The tile lives in shared memory as
+//   zt[jf][jh][t]            the real tube entries (blocks of znb rows),
+//   yt[jf][c][kh][t]         the half spectrum, real rows (c = 0) then imaginary rows (c = 1),
+//                            blocks of q2 rows each,
+// and the half-mode DFT of length nh uses the real input's symmetry.  With KR = nh/2 + 1 (rounded
+// down) cosine rows and KI = nh - KR sine rows of one matrix
+//   F[r][kh] = cos(2 pi r kh / nh) for r < KR,   F[r][kh] = -sin(2 pi r kh / nh) for r >= KR,
+// the forward (R2C) first folds every pair of a tube, (x_j, x_nh-j) <- (x_j + x_nh-j,
+// x_nh-j - x_j), and then Re X[kh] = sum_{r < KR} F[r][kh] x'_r and Im X[kh] = sum_{r >= KR}
+// F[r][kh] x'_r; the inverse (C2R) forms A_r = sum_kh F[r][kh] w Re X[kh] for r < KR and
+// B_r = sum_kh F[r][kh] w Im X[kh] for r >= KR (B_r = sum w Im X sin(2 pi (nh - r) kh / nh))
+// and unfolds (x_j, x_nh-j) = (A_j - B_nh-j, A_j + B_nh-j).  Each transform is thus two small
+// real matrix products of about nh/2 x nh/2 per tube (half the multiply-adds of the full
+// cos/sin matrix), computed by tile_product on blocks zero-padded to multiples of 4, two tubes
+// per packed FP32x2 FMA.  The weights w_kh = c_kh / (nf nh) (c = 1 at kh = 0 and nh/2, else 2)
+// are applied when the spectrum is loaded.  The full-mode DFT of the 4-way case (length nf <=
+// 8) runs in registers per (kh, tube).  The tables depend only on the tube geometry: a CTA
+// builds them once and then takes tile after tile.  The fused ADMM steps are those of the
+// thread-per-tube form above, on the tile in shared memory.
 constexpr int TT = 32;
 constexpr int TILE_THREADS = 256;
 constexpr int NF_MAX = 8;
@@ -39,41 +41,96 @@ __device__ __forceinline__ void tile_sync() {
 }
 
 struct TileSmem {
-  float* fr;     // [nh][ldq]
-  float* zt;     // [nf*nh][TT]
-  float* yt;     // [nf*2hh][TT]
+  float* fre;    // [kr4][ldf]  cos rows r < KR, zero-padded
+  float* fim;    // [ki4][ldf]  -sin rows r >= KR, zero-padded
+  float* zt;     // [nf][znb][TT]
+  float* yt;     // [nf][2 q2][TT]
   float* nrm;    // [RS][TT] partial tube norms (RPCA tube mode)
-  int ldq;
+  int ldf, kr, ki, znb, q2;
 };
 
-__host__ __device__ inline int tile_nh4(const TubeGeom& g) { return (g.nh + 3) & ~3; }
-// q4 a multiple of 8: a row group r0 = RM rg < q4 (RM = 2, 4, 8) then ends inside the row
-__host__ __device__ inline int tile_q4(const TubeGeom& g) { return (2 * g.hh + 7) & ~7; }
-__host__ __device__ inline int tile_ldq(const TubeGeom& g) { return tile_q4(g); }
+__host__ __device__ inline int tile_kr(const TubeGeom& g) { return g.nh / 2 + 1; }
+__host__ __device__ inline int tile_ki(const TubeGeom& g) { return g.nh - tile_kr(g); }
+__host__ __device__ inline int tile_round4(int x) { return (x + 3) & ~3; }
+// table row length: hh rounded up to 8 (an RM-row group of the forward product reads inside it)
+__host__ __device__ inline int tile_ldf(const TubeGeom& g) { return (g.hh + 7) & ~7; }
+// zt block rows: the sine product reads KI rounded up to 4 rows from row KR, up to row nh + 2
+__host__ __device__ inline int tile_znb(const TubeGeom& g) { return tile_round4(g.nh + 3); }
+__host__ __device__ inline int tile_q2(const TubeGeom& g) { return tile_round4(g.hh); }
 
-// Floats of the Fr matrix (a multiple of 16: the tiles after it stay 16-byte aligned).
-__host__ __device__ inline size_t tile_fr_floats(const TubeGeom& g) {
-  return (size_t)tile_nh4(g) * tile_q4(g);
+__host__ __device__ inline size_t tile_table_floats(const TubeGeom& g) {
+  const int ki4 = tile_round4(tile_ki(g) > 0 ? tile_ki(g) : 1);
+  return (size_t)(tile_round4(tile_kr(g)) + ki4) * tile_ldf(g);
 }
 
 __host__ __device__ inline size_t tile_smem_bytes(const TubeGeom& g) {
-  return (tile_fr_floats(g) + (size_t)g.nf * tile_nh4(g) * TT + (size_t)g.nf * tile_q4(g) * TT +
-          (size_t)(TILE_THREADS / TT) * TT) * sizeof(float);
+  return (tile_table_floats(g) + (size_t)g.nf * tile_znb(g) * TT +
+          (size_t)g.nf * 2 * tile_q2(g) * TT + (size_t)(TILE_THREADS / TT) * TT) *
+         sizeof(float);
+}
+
+__device__ __forceinline__ TileSmem tile_carve(unsigned char* raw, const TubeGeom& g) {
+  TileSmem s;
+  s.ldf = tile_ldf(g);
+  s.kr = tile_kr(g);
+  s.ki = tile_ki(g);
+  s.znb = tile_znb(g);
+  s.q2 = tile_q2(g);
+  s.fre = reinterpret_cast<float*>(raw);
+  s.fim = s.fre + (size_t)tile_round4(s.kr) * s.ldf;
+  s.zt = s.fre + tile_table_floats(g);
+  s.yt = s.zt + (size_t)g.nf * s.znb * TT;
+  s.nrm = s.yt + (size_t)g.nf * 2 * s.q2 * TT;
+  return s;
+}
+
+// The tables F (from the twiddle table, exact at the quarter points: the index r kh mod nh is
+// stepped by r) and the zero padding of the zt and yt blocks, which the tile steps never write.
+__device__ void tile_build(const TileSmem& s, const TubeGeom& g, const float2* __restrict__ twid_h) {
+  const int nh = g.nh, hh = g.hh, ldf = s.ldf;
+  const int rows = tile_round4(s.kr) + tile_round4(s.ki > 0 ? s.ki : 1);
+  for (int r = threadIdx.x; r < rows; r += TILE_THREADS) {
+    const bool cosrow = r < tile_round4(s.kr);
+    const int jr = cosrow ? r : s.kr + (r - tile_round4(s.kr));   // the DFT index of the row
+    const bool live = cosrow ? r < s.kr : jr < nh;
+    float* row = s.fre + (size_t)r * ldf;   // fim follows fre directly
+    int m = 0;
+    for (int kh = 0; kh < ldf; ++kh) {
+      float v = 0.f;
+      if (live && kh < hh) {
+        const float2 w = twid_h[m];
+        v = cosrow ? w.x : -w.y;
+      }
+      row[kh] = v;
+      m += jr;
+      while (m >= nh) m -= nh;
+    }
+  }
+  for (int f = 0; f < g.nf; ++f) {
+    for (int idx = threadIdx.x; idx < (s.znb - nh) * TT; idx += TILE_THREADS)
+      s.zt[((size_t)f * s.znb + nh) * TT + idx] = 0.f;
+    for (int c = 0; c < 2; ++c)
+      for (int idx = threadIdx.x; idx < (s.q2 - hh) * TT; idx += TILE_THREADS)
+        s.yt[((size_t)f * 2 * s.q2 + (size_t)c * s.q2 + hh) * TT + idx] = 0.f;
+  }
 }
 
 __device__ __forceinline__ float2 ffma2s(float a, float2 b, float2 c) {
   return __ffma2_rn(make_float2(a, a), b, c);
 }
 
-// out[r][t] = sum_{k < K} A(r, k) B[k][t] for r < M and the 32 tubes of the tile; K is a
+// out[r][t] = sum_{k < K} A(r, k) B[k][t] for r < M <= 16 RM and the 32 tubes of the tile; K is a
 // multiple of 4 (B rows and A entries past the true extent are zero).  FWD: A(r, k) =
 // fr[k * ldq + r]; otherwise A(r, k) = fr[r * ldq + k].  Rows past Fr's extent (rext: ldq for
 // FWD, the row count otherwise) read a clamped, in-bounds position once and are not stored.
+// Row groups rg0 .. rg0 + 15 of the 32 take part (rows (rg - rg0) RM ..), so two products run
+// side by side on the two halves of the tile's threads.
 template <int RM, bool FWD>
 __device__ __forceinline__ void tile_product(const float* __restrict__ fr, int ldq, int rext,
                                              const float* __restrict__ b, float* __restrict__ out,
-                                             int M, int K) {
-  const int tg = threadIdx.x & 7, rg = threadIdx.x >> 3;
+                                             int M, int K, int rg0) {
+  const int tg = threadIdx.x & 7, rg = (threadIdx.x >> 3) - rg0;
+  if (rg < 0 || rg >= 16) return;
   const int r0 = rg * RM;
   float2 acc[RM][2];
 #pragma unroll
@@ -142,13 +199,13 @@ __device__ __forceinline__ void tile_product(const float* __restrict__ fr, int l
 // sign +1 (inverse, no scaling) or -1 (forward).
 __device__ void tile_full_dft(const TileSmem& s, const TubeGeom& g, const float2* __restrict__ twf,
                               float sign, const float2* __restrict__ fm) {
-  const int nf = g.nf, hh = g.hh, q4 = tile_q4(g);
+  const int nf = g.nf, hh = g.hh, q2 = s.q2;
   for (int idx = threadIdx.x; idx < hh * TT; idx += TILE_THREADS) {
     const int kh = idx / TT, t = idx % TT;
     float2 x[NF_MAX], y[NF_MAX];
     for (int f = 0; f < nf; ++f) {
-      const size_t row = (size_t)f * q4 + 2 * kh;
-      x[f] = make_float2(s.yt[row * TT + t], s.yt[(row + 1) * TT + t]);
+      const size_t row = (size_t)f * 2 * q2 + kh;
+      x[f] = make_float2(s.yt[row * TT + t], s.yt[(row + q2) * TT + t]);
     }
     for (int o = 0; o < nf; ++o) {
       float ar = 0.f, ai = 0.f;
@@ -164,10 +221,24 @@ __device__ void tile_full_dft(const TileSmem& s, const TubeGeom& g, const float2
       y[o] = make_float2(ar, ai);
     }
     for (int f = 0; f < nf; ++f) {
-      const size_t row = (size_t)f * q4 + 2 * kh;
+      const size_t row = (size_t)f * 2 * q2 + kh;
       s.yt[row * TT + t] = y[f].x;
-      s.yt[(row + 1) * TT + t] = y[f].y;
+      s.yt[(row + q2) * TT + t] = y[f].y;
     }
+  }
+}
+
+// (x_j, x_nh-j) <- (x_j + x_nh-j, x_nh-j - x_j) (forward) or (x_j - x_nh-j, x_j + x_nh-j)
+// (inverse) for j = 1 .. KI on every zt block.
+__device__ void tile_fold(const TileSmem& s, const TubeGeom& g, bool forward) {
+  const int nh = g.nh, ki = s.ki;
+  for (int idx = threadIdx.x; idx < g.nf * ki * TT; idx += TILE_THREADS) {
+    const int t = idx % TT, q = idx / TT;
+    const int j = 1 + q % ki, f = q / ki;
+    float* z = s.zt + (size_t)f * s.znb * TT + t;
+    const float a = z[(size_t)j * TT], b = z[(size_t)(nh - j) * TT];
+    z[(size_t)j * TT] = forward ? a + b : a - b;
+    z[(size_t)(nh - j) * TT] = forward ? b - a : a + b;
   }
 }
 
@@ -179,21 +250,41 @@ __device__ void tile_inverse(const TileSmem& s, const TubeGeom& g, const float2*
     tile_full_dft(s, g, twf, 1.f, fm);
     tile_sync();
   }
-  const int nh4 = tile_nh4(g), q4 = tile_q4(g);
-  for (int f = 0; f < g.nf; ++f)
-    tile_product<RM, false>(s.fr, s.ldq, nh4, s.yt + (size_t)f * q4 * TT,
-                            s.zt + (size_t)f * nh4 * TT, g.nh, q4);
+  for (int f = 0; f < g.nf; ++f) {
+    float* z = s.zt + (size_t)f * s.znb * TT;
+    const float* y = s.yt + (size_t)f * 2 * s.q2 * TT;
+    tile_product<RM, false>(s.fre, s.ldf, s.kr, y, z, s.kr, s.q2, 0);
+    if (s.ki > 0)
+      tile_product<RM, false>(s.fim, s.ldf, s.ki, y + (size_t)s.q2 * TT, z + (size_t)s.kr * TT,
+                              s.ki, s.q2, 16);
+  }
   tile_sync();
+  if (s.ki > 0) {
+    tile_fold(s, g, false);
+    tile_sync();
+  }
 }
 
 // Real tile -> spectrum tile.
 template <int RM>
 __device__ void tile_forward(const TileSmem& s, const TubeGeom& g, const float2* twf,
                              const float2* fm) {
-  const int nh4 = tile_nh4(g), q4 = tile_q4(g);
-  for (int f = 0; f < g.nf; ++f)
-    tile_product<RM, true>(s.fr, s.ldq, s.ldq, s.zt + (size_t)f * nh4 * TT,
-                           s.yt + (size_t)f * q4 * TT, 2 * g.hh, nh4);
+  if (s.ki > 0) {
+    tile_fold(s, g, true);
+    tile_sync();
+  }
+  for (int f = 0; f < g.nf; ++f) {
+    const float* z = s.zt + (size_t)f * s.znb * TT;
+    float* y = s.yt + (size_t)f * 2 * s.q2 * TT;
+    tile_product<RM, true>(s.fre, s.ldf, s.ldf, z, y, g.hh, tile_round4(s.kr), 0);
+    if (s.ki > 0) {
+      tile_product<RM, true>(s.fim, s.ldf, s.ldf, z + (size_t)s.kr * TT, y + (size_t)s.q2 * TT,
+                             g.hh, tile_round4(s.ki), 16);
+    } else if (threadIdx.x >= TILE_THREADS / 2) {
+      for (int idx = threadIdx.x - TILE_THREADS / 2; idx < g.hh * TT; idx += TILE_THREADS / 2)
+        y[(size_t)s.q2 * TT + idx] = 0.f;
+    }
+  }
   tile_sync();
   if (g.nf > 1) {
     tile_full_dft(s, g, twf, -1.f, fm);
@@ -206,10 +297,10 @@ __device__ void tile_forward(const TileSmem& s, const TubeGeom& g, const float2*
 __device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
                                    const float2* __restrict__ spec, int64_t t0,
                                    const int* __restrict__ fp) {
-  const int nf = g.nf, nh = g.nh, hh = g.hh, q4 = tile_q4(g);
+  const int nf = g.nf, nh = g.nh, hh = g.hh, q2 = s.q2;
   const float inv = 1.f / (float)(nf * nh);
   const int total = nf * hh * TT;
-  constexpr int U = 4;   // loads a thread keeps in flight (see the element loops)
+  constexpr int U = 8;   // loads a thread keeps in flight (see the element loops)
   const int t = threadIdx.x % TT;   // TILE_THREADS is a multiple of TT
   const bool live = t0 + t < g.N12;
   for (int base = threadIdx.x; base < total; base += U * TILE_THREADS) {
@@ -241,63 +332,39 @@ __device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
       const int kf = q % nf, kh = q / nf;
       const bool selfcol = (kh == 0) || (2 * kh == nh);
       const float w = (selfcol ? 1.f : 2.f) * inv;
-      const size_t row = (size_t)kf * q4 + 2 * kh;
+      const size_t row = (size_t)kf * 2 * q2 + kh;
       s.yt[row * TT + t] = v[u].x * w;
-      s.yt[(row + 1) * TT + t] = v[u].y * w;
+      s.yt[(row + q2) * TT + t] = v[u].y * w;
     }
   }
 }
 
 __device__ void tile_store_spectrum(const TileSmem& s, const TubeGeom& g, float2* __restrict__ spec,
                                     int64_t t0) {
-  const int nf = g.nf, hh = g.hh, q4 = tile_q4(g);
+  const int nf = g.nf, hh = g.hh, q2 = s.q2;
   for (int idx = threadIdx.x; idx < nf * hh * TT; idx += TILE_THREADS) {
     const int q = idx / TT, t = idx % TT;
     if (t0 + t >= g.N12) continue;
     const int kf = q % nf, kh = q / nf;
-    const size_t row = (size_t)kf * q4 + 2 * kh;
-    spec[(size_t)q * g.N12 + t0 + t] = make_float2(s.yt[row * TT + t], s.yt[(row + 1) * TT + t]);
+    const size_t row = (size_t)kf * 2 * q2 + kh;
+    spec[(size_t)q * g.N12 + t0 + t] = make_float2(s.yt[row * TT + t], s.yt[(row + q2) * TT + t]);
   }
 }
 
 // One tile of TT tubes starting at tube t0, run by threads 0 .. TILE_THREADS - 1 of the CTA
-// (their barrier is tile_sync); smem_raw holds tile_smem_bytes(a.g) bytes.
+// (their barrier is tile_sync); smem_raw holds tile_smem_bytes(a.g) bytes.  build: (re)build
+// the tables and paddings (the first tile of a CTA, or one of another geometry); a CTA that
+// keeps the geometry passes false for its later tiles.
 template <int RM>
-__device__ void tube_tile_body(const TubeArgs& a, int64_t t0, unsigned char* smem_raw) {
+__device__ void tube_tile_body(const TubeArgs& a, int64_t t0, unsigned char* smem_raw,
+                               bool build = true) {
   const TubeGeom g = a.g;
-  TileSmem s;
-  s.ldq = tile_ldq(g);
-  s.fr = reinterpret_cast<float*>(smem_raw);
-  const int nh4 = tile_nh4(g), q4 = tile_q4(g);
-  s.zt = s.fr + tile_fr_floats(g);
-  s.yt = s.zt + (size_t)g.nf * nh4 * TT;
-  s.nrm = s.yt + (size_t)g.nf * q4 * TT;
+  const TileSmem s = tile_carve(smem_raw, g);
   const int tid = threadIdx.x;
-  const int nh = g.nh, hh = g.hh, nreal = g.nf * g.nh;
+  const int nreal = g.nf * g.nh;
   const int64_t N12 = g.N12;
-  // Fr[jh][2kh + c] from the twiddle table (exact at the quarter points), one row per thread
-  // with the index jh kh mod nh stepped by jh; zero past nh rows and 2hh columns
-  for (int jh = tid; jh < nh4; jh += TILE_THREADS) {
-    float2* row = reinterpret_cast<float2*>(s.fr + (size_t)jh * s.ldq);
-    int m = 0;
-    for (int kh = 0; kh < q4 / 2; ++kh) {
-      float2 v = make_float2(0.f, 0.f);
-      if (jh < nh && kh < hh) {
-        const float2 w = a.twid_h[m];
-        v = make_float2(w.x, -w.y);
-      }
-      row[kh] = v;
-      m += jh;
-      if (m >= nh) m -= nh;
-    }
-  }
-  // zero the padding rows of the zt and yt blocks (never written below)
-  for (int f = 0; f < g.nf; ++f) {
-    for (int idx = tid; idx < (nh4 - nh) * TT; idx += TILE_THREADS)
-      s.zt[((size_t)f * nh4 + nh) * TT + idx] = 0.f;
-    for (int idx = tid; idx < (q4 - 2 * hh) * TT; idx += TILE_THREADS)
-      s.yt[((size_t)f * q4 + 2 * hh) * TT + idx] = 0.f;
-  }
+  tile_sync();   // the previous tile of this CTA is done with the shared memory
+  if (build) tile_build(s, g, a.twid_h);
   const bool need_inv = a.mode == TUBE_INV || a.mode == TUBE_RPCA ||
                         (a.mode == TUBE_COMPLETE && !a.first);
   if (need_inv) tile_load_spectrum(s, g, a.spec_in, t0, a.fpart);
@@ -305,16 +372,17 @@ __device__ void tube_tile_body(const TubeArgs& a, int64_t t0, unsigned char* sme
   if (need_inv) tile_inverse<RM>(s, g, a.twid_f, a.fmat);
 
   // element (j, t) of the tile; t = tid % TT is fixed per thread (TILE_THREADS % TT == 0).
-  // Tube offset j = jf + nf*jh of the tensor (mode 3 fastest) is tile row jf*nh4 + jh.
+  // Tube offset j = jf + nf*jh of the tensor (mode 3 fastest) is tile row jf*znb + jh.
   const int t = tid % TT;
   const int nf = g.nf;
-  auto zrow = [&](int j) -> size_t { return ((size_t)(j % nf) * nh4 + j / nf) * TT + t; };
+  const int znb = s.znb;
+  auto zrow = [&](int j) -> size_t { return ((size_t)(j % nf) * znb + j / nf) * TT + t; };
   const bool live = t0 + t < N12;
   // rows j0, j0 + RS, ... of a thread are processed U at a time: the U rows' global loads are
   // issued together before any of their stores (restrict pointers), so each thread keeps U
   // loads in flight instead of one
   constexpr int RS = TILE_THREADS / TT;
-  constexpr int U = 4;
+  constexpr int U = 8;
   const float* __restrict__ in = a.in;
   float* __restrict__ state = a.state;
   float* __restrict__ out0 = a.out0;
@@ -466,12 +534,12 @@ __device__ void tube_tile_body(const TubeArgs& a, int64_t t0, unsigned char* sme
   tile_store_spectrum(s, g, a.spec_out, t0);
 }
 
-// The tile form handles nf <= NF_MAX, 2 hh <= 256 (RM <= 8) and a tile that fits in shared
+// The tile form handles nf <= NF_MAX, hh <= 128 (RM <= 8) and a tile that fits in shared
 // memory.
 inline int tile_rm(const TubeGeom& g) {
-  const int m = 2 * g.hh > g.nh ? 2 * g.hh : g.nh;
-  if (g.nf > NF_MAX || m > 256 || tile_smem_bytes(g) > 200 * 1024) return 0;
-  return m <= 64 ? 2 : m <= 128 ? 4 : 8;
+  // 16 row groups of RM rows cover the hh output rows of each forward product
+  if (g.nf > NF_MAX || g.hh > 128 || tile_smem_bytes(g) > 200 * 1024) return 0;
+  return g.hh <= 32 ? 2 : g.hh <= 64 ? 4 : 8;
 }
 
 }  // namespace
