@@ -268,3 +268,25 @@ def test_batch_64_uneven_100_iterations_matches_oracle(persistent):
         else:
             _check(out0, gt["L"], it["truth"], f"tensor {b} L")
             _check(_host(q["out1"], it["dims"]), gt["S"], None, f"tensor {b} S", scale=it["M"])
+
+
+def test_color_video_150_iterations_matches_oracle():
+    """The 288 x 352 x 3 x 60 colour video (DFT along modes 3 and 4, 93 stored / 91 distinct
+    Fourier slices), 150 iterations of the plain form against the oracle's solve."""
+    g = _golden("color_video_completion_288x352x3x60")
+    X, om = synth.workload_color_video(seed=1)
+    with _ctx() as ctx:
+        Xg, st = _completion(ctx, X, om, g["iters"])
+    assert st["nonconverged"] == 0
+    _check(Xg, g["X"], X, "colour video X")
+
+
+def test_color_video_mixed_full_run_equal_error():
+    """The 3xTF32 mixed form on the colour video: equal error against the oracle, and X within
+    1e-3 of the oracle's at the stored sample."""
+    g = _golden("color_video_completion_288x352x3x60")
+    X, om = synth.workload_color_video(seed=1)
+    with _ctx(libtsvd.PRECISION_3XTF32) as ctx:
+        Xg, st = _completion(ctx, X, om, g["iters"])
+    _equal_error(Xg, g["X"], X, "colour video X (3xTF32)")
+    _check(Xg, g["X"], None, "colour video X (3xTF32)")
