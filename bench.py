@@ -101,7 +101,7 @@ TRAFFIC = {"source": "paper_1407_1785_gb300/csrc/slice_svt.cu",
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batch")
@@ -111,6 +111,9 @@ def parse_args():
                     "workload's count)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=0)
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel directly instead of replaying captured CUDA "
+                         "graphs (for kernel-by-kernel profilers)")
     ap.add_argument("--no-color", action="store_true",
                     help="batch workload: skip the colour-video lines reported alongside")
     return ap.parse_args()
@@ -284,10 +287,17 @@ def build_workload(name, seed):
     raise ValueError(name)
 
 
+NO_GRAPHS = False
+
+
 def ctx_options(wl):
-    """Context options a workload needs besides precision (the tube-wise sparse term)."""
+    """Context options a workload needs besides precision (the tube-wise sparse term), and
+    graphs off under --no-graphs."""
     from paper_1407_1785_gb300 import libtsvd
-    return {"sparse_mode": libtsvd.SPARSE_TUBE} if wl.get("tube") else {}
+    opts = {"sparse_mode": libtsvd.SPARSE_TUBE} if wl.get("tube") else {}
+    if NO_GRAPHS:
+        opts["use_graphs"] = 0
+    return opts
 
 
 def to_device(wl):
@@ -1030,7 +1040,9 @@ def run_compress(args):
 
 
 def main():
+    global NO_GRAPHS
     args = parse_args()
+    NO_GRAPHS = args.no_graphs
     if args.workload == "compress" and args.impl != "reference":
         return run_compress(args)
     if args.workload in ("factor", "compress"):
