@@ -117,16 +117,20 @@ typedef struct tsvd_opts {
   int rsvt_power;     /* mixed form, tsvt() only: extra power steps from a random start
                          (ADMM solves start each iteration from the previous basis);
                          default 2 */
-  int warm_start;     /* plain form, tnn_complete / trpca: TSVD_WARM_ON starts each slice's
+  int warm_start;     /* plain form, tnn_complete / trpca: a warm start begins each slice's
                          Jacobi SVD from the previous iteration's right singular vectors V
                          (the slice is pre-rotated to B V and the rotations accumulate into V,
                          the V form), with a cold start every 64 iterations; the rebuild
                          still projects B itself (U form), so the result is the same SVT,
                          reached in fewer sweeps.  TSVD_WARM_OFF: every SVD starts from B.
-                         TSVD_WARM_AUTO (default): on for tnn_complete, off for trpca, whose
-                         sparse residual changes the small singular vectors at every
-                         iteration, so a warm start saves fewer sweeps than the V form's
-                         extra rotations cost. */
+                         TSVD_WARM_ON / TSVD_WARM_AUTO (default): warm wherever the slice
+                         shape has a V-form plan (AUTO is ON; it stays a separate value so
+                         that a later policy can refine it).  Measured on the completion and
+                         RPCA workloads, warm solves take 2.5-3x fewer sweeps than cold ones,
+                         which more than pays for the V form's nv extra entries per vector:
+                         with the SVT stopping test (jacobi_stop) the directions of the
+                         FP32-noise tail, which change at every iteration of an RPCA solve,
+                         no longer cost rotations. */
   int batch_persistent; /* plain form, batched solves: 1 runs each ADMM iteration of the whole
                          batch as one persistent kernel launch that takes the slice SVTs of all
                          tensors (largest first) and then their tube passes from device work
@@ -148,9 +152,24 @@ typedef struct tsvd_opts {
                          FP64; 0 (default) in FP32 with the Cholesky pivots in double-single
                          arithmetic (FP32 pairs).  The Grams themselves are FP32-level
                          products either way. */
+  int jacobi_stop;    /* plain-form Jacobi stopping test of the slice SVTs (tsvt, the ADMM
+                         solves; tsvd_factor / tsvd_compress always use RELATIVE).
+                         TSVD_STOP_RELATIVE: a vector pair (x, y) is orthogonal once
+                         |x^H y| <= tol ||x|| ||y||, which orders even the tiniest singular
+                         directions to full relative accuracy.  TSVD_STOP_SVT (default): also
+                         once |x^H y| <= tol min(||x||, ||y||) ||B||_F / nv, i.e. once what
+                         the pair still moves in the rebuilt slice D_tau(B) (about
+                         |x^H y| / min(||x||, ||y||)) is below tol ||B||_F / nv (B the slice,
+                         nv = min(n1, n2)), so that all pairs stopped this way together move
+                         D_tau(B) by about tol ||B||_F at most.  This never rotates more than
+                         RELATIVE, stays within its worst-case error per pair, and stops
+                         rotating pairs of directions far below the slice's energy -- the
+                         FP32-noise tail of a nearly low-rank slice, which RELATIVE would
+                         orthogonalise to 1e-6 for nothing. */
 } tsvd_opts;
 
 enum { TSVD_SLICE_AUTO = 0, TSVD_SLICE_PAIRWISE = 1, TSVD_SLICE_BLOCK = 2 };
+enum { TSVD_STOP_SVT = 0, TSVD_STOP_RELATIVE = 1 };
 
 /* Counters of one ADMM solve (host struct). */
 typedef struct tsvd_stats {
@@ -326,10 +345,10 @@ typedef struct tsvd_problem {
  * context's options (one rho schedule for all).  With a mixed precision each tensor's sketch
  * width is chosen on the device after every iteration (same rule as the single-tensor
  * solvers, widths up to 112), so the whole batch is still captured into one graph.  In the
- * plain form each tensor follows warm_start as the single-tensor solvers do (TSVD_WARM_AUTO:
- * the completion tensors warm start, the RPCA tensors do not).  All pointers must be device
- * memory on the context's device.  Each tensor's iterations form an independent chain of kernels (its own
- * slice-SVT plan); the chains of all tensors are issued on parallel stream branches and, with
+ * plain form each tensor follows warm_start as the single-tensor solvers do.  All pointers
+ * must be device memory on the context's device.  Each tensor's iterations form an
+ * independent chain of kernels (its own slice-SVT plan); the chains of all tensors are issued
+ * on parallel stream branches and, with
  * use_graphs, captured once into one CUDA graph that later calls with the same problems
  * replay, so the tensors overlap on the GPU.  Plans come from the context's autotune cache
  * for shapes tuned earlier, else from the planner (no tuning inside a batch).  stats

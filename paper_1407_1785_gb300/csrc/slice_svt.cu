@@ -172,14 +172,16 @@ __device__ __forceinline__ void group_sum_n(float (&v)[K]) {
 }
 
 // The rotation of a vector pair from its 2 x 2 Gram entries al = ||x||^2, be = ||y||^2 and
-// x^H y = cr + i ci: 0 when the pair is orthogonal to the tolerance (|x^H y|^2 <= tol2 al be)
-// or the angle rounds to 0, else 1, or 3 when |cos|^2 = |x^H y|^2 / (al be) > big2; with
-// cm = cs - 1 and k = kr + i ki = sn e^{i phi} (see jacobi_pairs for the arithmetic).
+// x^H y = cr + i ci: 0 when the pair is orthogonal to the tolerance (|x^H y|^2 <= tol2 al be,
+// or |x^H y|^2 <= floor2 min(al, be): see svt_slice) or the angle rounds to 0, else 1, or 3
+// when |cos|^2 = |x^H y|^2 / (al be) > big2; with cm = cs - 1 and k = kr + i ki =
+// sn e^{i phi} (see jacobi_pairs for the arithmetic).
 __device__ __forceinline__ int pair_rotation(float al, float be, float cr, float ci, float tol2,
-                                             float big2, float& cm, float& kr, float& ki) {
+                                             float floor2, float big2, float& cm, float& kr,
+                                             float& ki) {
   const float c2 = cr * cr + ci * ci;
   const float ab = al * be;
-  if (!(c2 > tol2 * ab)) return 0;
+  if (!(c2 > tol2 * ab) || !(c2 > floor2 * fminf(al, be))) return 0;
   // ~ 1 / |x^H y| (the exact form below the normal range, where the approximation is not
   // defined: only vectors of norm ~1e-14 get there)
   const float inv_g = c2 >= 1e-30f ? rsqrtf(c2) : 1.f / sqrtf(c2);
@@ -241,7 +243,7 @@ template <int G, int CPL, int NP>
 __device__ __forceinline__ int jacobi_pairs(float* __restrict__ Wr, float* __restrict__ Wi,
                                             int rowp, int nchunkv, const int (&p)[NP],
                                             const int (&q)[NP], const bool (&real)[NP],
-                                            int gl, float tol2, float big2) {
+                                            int gl, float tol2, float floor2, float big2) {
   float4 xr[NP][CPL], xi[NP][CPL], yr[NP][CPL], yi[NP][CPL];
   float2 acc[NP][8];
 #pragma unroll
@@ -320,7 +322,7 @@ __device__ __forceinline__ int jacobi_pairs(float* __restrict__ Wr, float* __res
     if (!real[i]) continue;
     float cm, kr, ki;
     const int fl = pair_rotation(red[4 * i + 0], red[4 * i + 1], red[4 * i + 2], red[4 * i + 3],
-                                 tol2, big2, cm, kr, ki);
+                                 tol2, floor2, big2, cm, kr, ki);
     if (!fl) continue;
     const float2 CM = f2(cm, cm), KR = f2(kr, kr), KI = f2(ki, ki), NKR = f2(-kr, -kr),
                  NKI = f2(-ki, -ki);
@@ -458,6 +460,7 @@ struct SliceShared {
   int flag[2];
   int rank;
   double nuc;
+  float energy;   // this CTA's part of ||B||_F^2
 };
 
 // The vectors of blocks bx (local slot 0) and by (slot 1) of the pre-rotated slice, computed
@@ -668,7 +671,7 @@ __device__ void block_gram(const float* __restrict__ Xr, const float* __restrict
 // slot from the current G, then the column updates of G and W, then the row updates of G.
 // Returns the rotation flags of the slots this thread computed (see pair_rotation).
 __device__ int block_inner(const BlockSmem& b, const SliceShape& sh, int r, int bx, int by,
-                           float tol2, float big2) {
+                           float tol2, float floor2, float big2) {
   const int bs = sh.bs, nl = 2 * bs, nlp = b.nlp;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int nlr = r == 0 ? nl - 1 : bs;
@@ -683,8 +686,8 @@ __device__ int block_inner(const BlockSmem& b, const SliceShape& sh, int r, int 
       int fl = 0;
       if (gp < sh.nv && gq < sh.nv)
         fl = pair_rotation(b.gr[(size_t)pp * nlp + pp], b.gr[(size_t)qq * nlp + qq],
-                           b.gr[(size_t)pp * nlp + qq], b.gi[(size_t)pp * nlp + qq], tol2, big2,
-                           cm, kr, ki);
+                           b.gr[(size_t)pp * nlp + qq], b.gi[(size_t)pp * nlp + qq], tol2,
+                           floor2, big2, cm, kr, ki);
       flags |= fl;
       b.prm[slot] = make_float4(cm, kr, ki, fl ? 1.f : 0.f);
       b.idx[slot] = make_int2(pp, qq);
@@ -840,6 +843,36 @@ __device__ void svt_slice(const SliceArgs& a, const SliceShape& sh, int so, int 
   // each pair's cosine by at most ~big^2 per rotation touching it (2 nv of them), so after
   // the sweep every cosine is below 2 nv big^2 = tol and the checking sweep is skipped.
   const float big2 = a.tol / (2.f * (float)sh.nv);
+  // SVT stopping test (a.abs_stop): left unrotated, a pair with |x^H y| = g moves the rebuilt
+  // slice by about g / min(||x||, ||y||) (the rebuild projects B on the kept normalised
+  // vectors), so a pair also stops once that is below tol ||B||_F / nv:
+  // g^2 <= floor2 min(||x||^2, ||y||^2).  The nv (nv - 1) / 2 pairs stopped this way then move
+  // D_tau(B) by at most about tol ||B||_F / sqrt(2) together (summed in quadrature), whatever
+  // nv is, and each stays within the relative test's worst case per pair, tol times the
+  // largest vector norm (||B||_F / nv <= sigma_max / sqrt(nv)).  ||B||_F^2 (invariant under the
+  // rotations) is summed per vector in a fixed order, so the test is deterministic.
+  float floor2 = 0.f;
+  if (a.abs_stop) {
+    for (int v = warp; v < nl; v += nwarps) {
+      const float* wr = Wr + (size_t)v * rowp;
+      const float* wi = Wi + (size_t)v * rowp;
+      float e2 = 0.f;
+      for (int e = lane; e < len; e += 32) e2 += wr[e] * wr[e] + wi[e] * wi[e];
+      e2 = group_sum<32>(e2);
+      if (lane == 0) sig[v] = e2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float e2 = 0.f;
+      for (int v = 0; v < nl; ++v) e2 += sig[v];
+      ss.energy = e2;
+    }
+    if (C > 1) cluster.sync();
+    else __syncthreads();
+    float total = 0.f;
+    for (int c = 0; c < C; ++c) total += C > 1 ? *cluster.map_shared_rank(&ss.energy, c) : ss.energy;
+    floor2 = tol2 * (total / ((float)sh.nv * (float)sh.nv));
+  }
   const int trips = (bs + ngroups - 1) / ngroups;
   const size_t slotf = (size_t)bs * rowp;    // floats of one plane of one block
   int sweeps = 0, converged = 0, par = 0;
@@ -852,7 +885,7 @@ __device__ void svt_slice(const SliceArgs& a, const SliceShape& sh, int so, int 
       if (sh.block) {
         block_gram(Wr, Wi, rowp, (len + 3) / 4, nl, bsm);
         __syncthreads();
-        rotated |= block_inner(bsm, sh, r, bx, by, tol2, big2);
+        rotated |= block_inner(bsm, sh, r, bx, by, tol2, floor2, big2);
         block_update(Wr, Wi, rowp, rowp / 4, nl, bsm);
         __syncthreads();
       }
@@ -881,7 +914,7 @@ __device__ void svt_slice(const SliceArgs& a, const SliceShape& sh, int so, int 
           // every lane of the warp takes part in the shuffles when any group has work
           if (!__ballot_sync(0xffffffffu, any_real)) continue;
           rotated |= jacobi_pairs<G, CPL, NP>(Wr, Wi, rowp, nchunkv, p, q, real, gl, tol2,
-                                              big2);
+                                              floor2, big2);
         }
         __syncthreads();
       }
@@ -1446,6 +1479,7 @@ __device__ SliceArgs batch_slice_args(const BatchDesc& d, const BatchIter& it) {
   a.max_sweeps = it.max_sweeps;
   a.stat = t.stat;
   a.acc = t.acc;
+  a.abs_stop = it.abs_stop;
   if (t.warm) {
     // V form from the previous iteration's V (cold every kWarmColdEvery iterations), rebuilt
     // in the U form from B itself

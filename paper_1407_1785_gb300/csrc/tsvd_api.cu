@@ -628,6 +628,7 @@ SliceArgs slice_args(tsvd_ctx* c, const Problem& p, const Workspace& w, float ta
   s.scratch = w.jscratch;
   s.scratch_bytes = w.jscratch_bytes;
   s.knobs = planned_knobs(c, p, w.ndistinct);
+  s.abs_stop = c->opts.jacobi_stop == TSVD_STOP_SVT ? 1 : 0;
   return s;
 }
 
@@ -725,6 +726,8 @@ tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
     return fail(c, TSVD_EINVAL, "batch_persistent must be 0 or 1");
   if (o.rsvt_small_fp64 != 0 && o.rsvt_small_fp64 != 1)
     return fail(c, TSVD_EINVAL, "rsvt_small_fp64 must be 0 or 1");
+  if (o.jacobi_stop != TSVD_STOP_SVT && o.jacobi_stop != TSVD_STOP_RELATIVE)
+    return fail(c, TSVD_EINVAL, "jacobi_stop must be TSVD_STOP_SVT or TSVD_STOP_RELATIVE");
   if (o.slice_form != TSVD_SLICE_AUTO && o.slice_form != TSVD_SLICE_PAIRWISE &&
       o.slice_form != TSVD_SLICE_BLOCK)
     return fail(c, TSVD_EINVAL, "slice_form must be TSVD_SLICE_AUTO, _PAIRWISE or _BLOCK");
@@ -1065,6 +1068,7 @@ tsvd_status run_maybe_graph(tsvd_ctx* c, const std::vector<int64_t>& key, bool c
     c->cur = c->stream;
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (ec != cudaSuccess) cudaGetLastError();   // not left behind for a later launch check
     if (st != TSVD_OK) {
       if (graph) cudaGraphDestroy(graph);
       return st;
@@ -1197,10 +1201,9 @@ size_t carve_item(tsvd_ctx* c, BatchItem& it, char* base, int iters, bool persis
   const size_t real = (size_t)it.p.N * sizeof(float);
   const bool complete = it.src->kind == TSVD_PROBLEM_COMPLETE;
   const bool mixed = mixed_precision(c);
-  // the warm start as in the single-tensor solves (TSVD_WARM_AUTO: completion only)
+  // the warm start as in the single-tensor solves
   const int ws = c->opts.warm_start;
-  it.warm = !mixed && iters >= 2 && ws != TSVD_WARM_OFF && (complete || ws == TSVD_WARM_ON) &&
-            warm_plan_exists(c, it.p);
+  it.warm = !mixed && iters >= 2 && ws != TSVD_WARM_OFF && warm_plan_exists(c, it.p);
   it.kn = planned_knobs(c, it.p, it.w.ndistinct, it.warm ? 1 : vform_of(c));
   // (the persistent batched kernel keeps one exchange buffer per cluster instead)
   const size_t jbytes = mixed || persistent ? 0
@@ -1365,6 +1368,7 @@ void tsvd_default_opts(tsvd_opts* o) {
   o->rsvt_power = 2;
   o->warm_start = TSVD_WARM_AUTO;
   o->batch_persistent = 0;
+  o->jacobi_stop = TSVD_STOP_SVT;
 }
 
 tsvd_status tsvd_create(tsvd_ctx** out, int device, void* cuda_stream, const tsvd_opts* opts) {
@@ -1567,6 +1571,7 @@ tsvd_status factor_slices(tsvd_ctx* c, const float* Y, int order, const int64_t*
   sa.sig_stride = fw.nv;
   sa.vout = fw.J;
   sa.vstride = (int64_t)fw.nv * fw.nv;
+  sa.abs_stop = 0;   // a factorisation keeps every direction: the relative test alone
   return run_slice(c, sa);
 }
 
@@ -2050,7 +2055,7 @@ tsvd_status rpca_impl(tsvd_ctx* c, const float* M, int order, const int64_t* dim
   rq.stage_out0 = kl == 1;
   rq.stage_out1 = ks == 1;
   rq.rsvt = mixed_precision(c);
-  rq.warm = !rq.rsvt && c->opts.warm_start == TSVD_WARM_ON && iters >= 2 &&
+  rq.warm = !rq.rsvt && c->opts.warm_start != TSVD_WARM_OFF && iters >= 2 &&
             warm_plan_exists(c, p);
   // the plans (and the scratch sized for them) are those of the V form when warm
   c->vform_now = rq.warm;
@@ -2265,6 +2270,7 @@ tsvd_status persistent_batch(tsvd_ctx* c, const std::vector<BatchItem>& items, i
   bi.iters = iters;
   bi.tol = c->opts.jacobi_tol;
   bi.max_sweeps = c->opts.max_sweeps;
+  bi.abs_stop = c->opts.jacobi_stop == TSVD_STOP_SVT ? 1 : 0;
   bi.done = done;
   bi.err = err;
   auto run = [&](int k, double r, double r_next, bool slices_only) -> tsvd_status {
@@ -2442,6 +2448,17 @@ tsvd_status solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, 
     offs[(size_t)i] = total;
     total += carve_item(c, items[(size_t)i], nullptr, iters, persist);
   }
+  // a forced slice plan (ctas_per_slice, lanes_per_pair) that some tensor's slices do not fit
+  // is refused here, before anything is enqueued on the branches
+  if (!mixed_precision(c) && !persist && iters > 0)
+    for (int i = 0; i < count; ++i) {
+      const BatchItem& it = items[(size_t)i];
+      if (!jacobi_svt_plan_ok((int)it.p.n1, (int)it.p.n2, it.w.ndistinct, it.kn))
+        return fail(c, TSVD_EUNSUPPORTED,
+                    "problem %d: no slice SVT plan for %lld x %lld slices with %d CTAs per slice "
+                    "and %d lanes per pair",
+                    i, (long long)it.p.n1, (long long)it.p.n2, it.kn.ctas, it.kn.lanes);
+    }
   const size_t bad_off = total;
   total += align_up((size_t)count * sizeof(int));
   const size_t table_off = total;
@@ -2575,20 +2592,22 @@ tsvd_status solve_batched(tsvd_ctx* c, int count, const tsvd_problem* problems, 
       TSVD_CUDA(c, cudaEventRecord(c->fork, base));
       for (int b = 0; b < nbr; ++b) TSVD_CUDA(c, cudaStreamWaitEvent(c->branches[(size_t)b], c->fork, 0));
       // the costliest tensors are issued first on their branches
+      tsvd_status st = TSVD_OK;
       for (int i : order) {
         c->cur = c->branches[(size_t)branch_of[(size_t)i]];
-        const tsvd_status st = enqueue_item(c, items[(size_t)i], iters);
-        if (st != TSVD_OK) {
-          c->cur = base;
-          return st;
-        }
-      }
-      for (int b = 0; b < nbr; ++b) {
-        TSVD_CUDA(c, cudaEventRecord(c->joins[(size_t)b], c->branches[(size_t)b]));
-        TSVD_CUDA(c, cudaStreamWaitEvent(base, c->joins[(size_t)b], 0));
+        st = enqueue_item(c, items[(size_t)i], iters);
+        if (st != TSVD_OK) break;
       }
       c->cur = base;
-      return TSVD_OK;
+      // every branch joins the issuing stream even after a failed enqueue, so that no work
+      // is left outside the stream order (or unjoined in a capture)
+      for (int b = 0; b < nbr; ++b) {
+        const cudaError_t e1 = cudaEventRecord(c->joins[(size_t)b], c->branches[(size_t)b]);
+        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(base, c->joins[(size_t)b], 0) : e1;
+        if (e2 != cudaSuccess && st == TSVD_OK)
+          st = fail(c, TSVD_ECUDA, "branch join: %s", cudaGetErrorString(e2));
+      }
+      return st;
     };
     TSVD_TRY(run_maybe_graph(c, key, true, body));
   }

@@ -192,6 +192,9 @@ struct SliceArgs {
   // V form with vin: the kernel forms the pre-rotated vectors B V (columns) or V^T B (rows)
   // from ahat = B and vin itself while loading them (no separate pre-rotated input)
   int prerot = 0;
+  // 1: the SVT stopping test -- a pair also counts as orthogonal once
+  // |x^H y|^2 <= tol^2 (||B||_F^2 / nv^2) min(||x||^2, ||y||^2); 0: the relative test alone
+  int abs_stop = 0;
 };
 
 // Returns cudaErrorInvalidValue when a slice does not fit the kernel's shared memory.
@@ -206,7 +209,7 @@ struct BatchTensor {
   int kind;                 // TSVD_PROBLEM_COMPLETE (1) or TSVD_PROBLEM_RPCA (2)
   int n1, n2;
   int nslices;              // distinct stored slices (the `slices` list)
-  int warm;                 // plain V-form warm start (completion tensors)
+  int warm;                 // plain V-form warm start
   double scale;             // threshold scale: tau = scale / rho
   float lambda;             // RPCA
   int tube_sparse;          // RPCA: eq. sparse2 shrink
@@ -252,6 +255,7 @@ struct BatchIter {
   unsigned* done;           // per tensor: slice SVTs finished (monotonic over the solve)
   int* err;                 // set to 1 when a bounded wait gave up
   int slices_only = 0;      // skip the tube passes (plan timing)
+  int abs_stop = 1;         // SliceArgs::abs_stop of the slice SVTs
 };
 
 // Iterations between cold starts of the warm-started plain Jacobi (V reset to I).

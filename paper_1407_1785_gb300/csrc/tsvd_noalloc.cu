@@ -180,6 +180,7 @@ extern "C" tsvd_status tsvt_static(const float* Y, float* Z, int order, const in
   tsvd_default_opts(&o);
   s.tol = o.jacobi_tol;
   s.max_sweeps = o.max_sweeps;
+  s.abs_stop = o.jacobi_stop == TSVD_STOP_SVT ? 1 : 0;
   s.stat = nullptr;
   s.acc = nullptr;
   s.scratch = jsc ? b + 2 * spec + tw + lst : nullptr;

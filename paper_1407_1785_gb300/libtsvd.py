@@ -38,6 +38,7 @@ EXPORTED_SYMBOLS = ("tsvd_default_opts", "tsvd_create", "tsvd_destroy", "tsvd_la
 OP_N, OP_T, OP_C = 0, 1, 2
 WARM_OFF, WARM_ON, WARM_AUTO = 0, 1, 2
 SLICE_AUTO, SLICE_PAIRWISE, SLICE_BLOCK = 0, 1, 2
+STOP_SVT, STOP_RELATIVE = 0, 1
 COMPRESS_GLOBAL, COMPRESS_TUBAL = 1, 2
 PROBLEM_COMPLETE, PROBLEM_RPCA = 1, 2
 
@@ -65,7 +66,8 @@ class Opts(ctypes.Structure):
                 ("use_graphs", ctypes.c_int), ("rsvt_oversample", ctypes.c_int),
                 ("rsvt_kmax", ctypes.c_int), ("rsvt_power", ctypes.c_int),
                 ("warm_start", ctypes.c_int), ("batch_persistent", ctypes.c_int),
-                ("slice_form", ctypes.c_int), ("rsvt_small_fp64", ctypes.c_int)]
+                ("slice_form", ctypes.c_int), ("rsvt_small_fp64", ctypes.c_int),
+                ("jacobi_stop", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -75,3 +75,13 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["higher_is_better"] is True and d["n_gpus"] == 1
+
+
+def test_equal_error_verdict():
+    """Per tensor: within 1% (+1e-5) of the plain form's recovery error, or both at or below
+    the FP32 floor 1e-4 of an exact recovery; the worst tensor and the misses are reported."""
+    v = bench.equal_error_verdict([0.101, 4.8e-5, 0.2, 2e-4], [0.1, 3.5e-5, 0.1, 1e-4])
+    assert v["missing"] == [2, 3] and v["tensors_meeting"] == 2 and not v["equal_error"]
+    assert v["worst_tensor"] == 2 and abs(v["worst_ratio"] - 2.0) < 1e-12
+    assert bench.equal_error_verdict([0.0505], [0.05])["equal_error"]
+    assert not bench.equal_error_verdict([0.0506], [0.05])["equal_error"]

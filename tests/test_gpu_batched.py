@@ -105,3 +105,27 @@ def test_measured_fp32_peak_is_plausible():
     bound = sms * 128 * 2 * 2.2e9 / 1e12
     for v in (fma, fma2):
         assert 0.1 * bound < v < 2.0 * bound
+
+
+def test_forced_plan_a_tensor_cannot_take_fails_cleanly():
+    """A forced ctas_per_slice = 2 cannot hold a 288 x 352 complex slice (two CTAs' shared
+    memory is far below the slice's 811 KB): the batched call refuses it with EUNSUPPORTED
+    naming the tensor before anything is enqueued, and neither that context (on tensors that
+    do fit) nor a fresh one inherits an error from it."""
+    torch = _torch()
+    iters = 3
+    probs, refs = _completion_problems([((30, 41, 8), 3, 0.5), ((288, 352, 4), 5, 0.5),
+                                        ((24, 20, 6), 2, 0.5)], iters, seed0=360)
+    stream = torch.cuda.current_stream().cuda_stream
+    with libtsvd.Context(device=0, stream=stream, ctas_per_slice=2) as ctx:
+        st, _ = ctx.raw_solve_batched(probs, iters, entry="tnn_complete_batched")
+        assert st == libtsvd.TSVD_EUNSUPPORTED
+        assert "problem 1" in ctx.last_error()
+        small = [probs[0], probs[2]]
+        ctx.tnn_complete_batched(small, iters)
+        for q, Xo in zip(small, [refs[0], refs[2]]):
+            assert relerr(host(q["out0"], q["dims"]), Xo, floor=1e-6) <= ADMM_TOL
+    with libtsvd.Context(device=0, stream=stream) as ctx:
+        ctx.tnn_complete_batched(probs, iters)
+        for q, Xo in zip(probs, refs):
+            assert relerr(host(q["out0"], q["dims"]), Xo, floor=1e-6) <= ADMM_TOL
