@@ -92,7 +92,9 @@ typedef struct tsvd_opts {
   int timing;         /* 1: time every kernel launch with CUDA events on the context's stream
                          and report the totals in tsvd_stats; default 0 */
   int ctas_per_slice; /* CTAs (one thread-block cluster) per Fourier slice SVD: 1, 2, 4 or 8;
-                         0 (default) = chosen from the slice shape and count */
+                         TSVD_CTAS_FEWEST (-1): the fewest that hold the slice (for launches
+                         that share the GPU, e.g. many tensors at once); 0 (default) = chosen
+                         from the slice shape and count as if the launch had the GPU alone */
   int accumulate_v;   /* 1: also rotate V during the Jacobi sweeps and rebuild each slice as
                          W diag((s - tau)/s) V^H instead of U diag((s - tau)/s) U^H A;
                          default 0 */
@@ -170,6 +172,7 @@ typedef struct tsvd_opts {
 
 enum { TSVD_SLICE_AUTO = 0, TSVD_SLICE_PAIRWISE = 1, TSVD_SLICE_BLOCK = 2 };
 enum { TSVD_STOP_SVT = 0, TSVD_STOP_RELATIVE = 1 };
+enum { TSVD_CTAS_FEWEST = -1 };
 
 /* Counters of one ADMM solve (host struct). */
 typedef struct tsvd_stats {

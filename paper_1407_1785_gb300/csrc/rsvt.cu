@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(1024) eig_svt_kernel(float2* G, float2* T, flo
                                                        int64_t gs, int64_t sig_stride,
                                                        float tau, float tol, int max_sweeps,
                                                        SliceStat* stat, SweepAccum* acc,
-                                                       const int* kdev) {
+                                                       const int* kdev, int abs_stop) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (kdev) k = *kdev;
   const int s = slices[blockIdx.x];
@@ -366,7 +366,18 @@ __global__ void __launch_bounds__(1024) eig_svt_kernel(float2* G, float2* T, flo
   const float tol2 = tol * tol;
   const float big2 = tol / (2.f * (float)k);
   int sweeps = 0, converged = 0;
+  __shared__ float s_floor2;
   __syncthreads();
+  // the SVT stopping test of the one-sided kernel (abs_stop): a pair also stops once
+  // |H_pq|^2 <= tol^2 (trace(H) / k^2) min(H_pp, H_qq); trace(H) = ||Bt||_F^2 is invariant
+  // under the rotations and summed in a fixed order
+  if (tid == 0) {
+    float tr = 0.f;
+    for (int m = 0; m < k; ++m) tr += fmaxf(H[m + (size_t)m * ldh].x, 0.f);
+    s_floor2 = abs_stop ? tol2 * (tr / ((float)k * (float)k)) : 0.f;
+  }
+  __syncthreads();
+  const float floor2 = s_floor2;
   for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
     if (tid == 0) s_flags = 0;
     __syncthreads();
@@ -384,7 +395,7 @@ __global__ void __launch_bounds__(1024) eig_svt_kernel(float2* G, float2* T, flo
           const float2 c = H[p + (size_t)q * ldh];   // H_pq = col_p^H col_q
           const float c2 = c.x * c.x + c.y * c.y;
           const float ab = al * be;
-          if (c2 > tol2 * ab) {
+          if (c2 > tol2 * ab && c2 > floor2 * fminf(al, be)) {
             const float inv_g = c2 >= 1e-30f ? rsqrtf(c2) : 1.f / sqrtf(c2);
             const float zeta = (be - al) * (0.5f * inv_g);
             const float az = fabsf(zeta);
@@ -643,7 +654,7 @@ __global__ void __launch_bounds__(1024) eig_svt_fp64_kernel(float2* G, float2* T
                                                             int64_t gs, int64_t sig_stride,
                                                             float tau, float tol, int max_sweeps,
                                                             SliceStat* stat, SweepAccum* acc,
-                                                            const int* kdev) {
+                                                            const int* kdev, int abs_stop) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (kdev) k = *kdev;
   const int s = slices[blockIdx.x];
@@ -668,7 +679,16 @@ __global__ void __launch_bounds__(1024) eig_svt_fp64_kernel(float2* G, float2* T
   const double tol2 = (double)tol * (double)tol;
   const double big2 = (double)tol / (2.0 * (double)k);
   int sweeps = 0, converged = 0;
+  __shared__ double s_floor2;
   __syncthreads();
+  // the SVT stopping test (abs_stop), as in eig_svt_kernel
+  if (tid == 0) {
+    double tr = 0.0;
+    for (int m = 0; m < k; ++m) tr += fmax(H[m + (size_t)m * ldh].x, 0.0);
+    s_floor2 = abs_stop ? tol2 * (tr / ((double)k * (double)k)) : 0.0;
+  }
+  __syncthreads();
+  const double floor2 = s_floor2;
   for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
     if (tid == 0) s_flags = 0;
     __syncthreads();
@@ -683,7 +703,7 @@ __global__ void __launch_bounds__(1024) eig_svt_fp64_kernel(float2* G, float2* T
           const double2 c = H[p + (size_t)q * ldh];
           const double c2 = c.x * c.x + c.y * c.y;
           const double ab = al * be;
-          if (c2 > tol2 * ab && c2 > 0.0) {
+          if (c2 > tol2 * ab && c2 > floor2 * fmin(al, be) && c2 > 0.0) {
             // the rotation of the one-sided form, in FP64: t = sign(zeta) / (|zeta| +
             // sqrt(1 + zeta^2)), sn = t / r, cs - 1 = -t sn / (1 + r), r = sqrt(1 + t^2)
             const double g = sqrt(c2);
@@ -1058,11 +1078,11 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
     if (a.small_fp64 && k <= eig_fp64_max_k())
       eig_svt_fp64_kernel<<<ns, 1024, eig_fp64_smem(k), st>>>(a.G, a.T, a.sig, idx, k, kmax, gs,
                                                               kmax, a.tau, a.tol, a.max_sweeps,
-                                                              a.stat, a.acc, a.kdev);
+                                                              a.stat, a.acc, a.kdev, a.abs_stop);
     else
       eig_svt_kernel<<<ns, 1024, eig_smem(k), st>>>(a.G, a.T, a.sig, idx, k, kmax, gs, kmax,
                                                     a.tau, a.tol, a.max_sweeps, a.stat, a.acc,
-                                                    a.kdev);
+                                                    a.kdev, a.abs_stop);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_cgemm(dyn(gemm(nw, k, k, ns, mat(a.Bt, idx, bs, 1, nw, 1),
                               mat(a.T, idx, gs, 1, kmax, 1), mat(a.P, idx, ps, 1, nw)),
@@ -1099,6 +1119,7 @@ cudaError_t launch_rsvt(const RsvtArgs& a, cudaStream_t st) {
   j.N12 = bs;
   j.tau = a.tau;
   j.tol = a.tol;
+  j.abs_stop = a.abs_stop;
   j.max_sweeps = a.max_sweeps;
   j.stat = a.stat;
   j.acc = a.acc;

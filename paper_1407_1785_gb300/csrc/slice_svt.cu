@@ -1321,12 +1321,21 @@ bool plan_with_ctas(int n1, int n2, int C, const SliceKnobs& k, SliceShape& sh, 
 }
 
 // CTAs per slice: the fewest waves of one CTA per SM, weighted by the work of one CTA
-// (1/C), without blocks thinner than kMinBlock vectors; the smallest C on ties.
+// (1/C), without blocks thinner than kMinBlock vectors; the smallest C on ties.  k.ctas = -1:
+// the fewest CTAs that hold the slice (for launches that share the GPU with others).
 bool plan_slice(int n1, int n2, int nslices, const SliceKnobs& k, SliceShape& sh,
                 size_t& smem) {
   const int nv = n1 < n2 ? n1 : n2;
-  const int force = k.ctas;
   const int cands[4] = {1, 2, 4, 8};
+  if (k.ctas == -1) {
+    SliceKnobs k1 = k;
+    for (int C : cands) {
+      k1.ctas = C;
+      if (plan_with_ctas(n1, n2, C, k1, sh, smem)) return true;
+    }
+    return false;
+  }
+  const int force = k.ctas;
   double best = 1e300;
   bool found = false;
   for (int C : cands) {

@@ -712,8 +712,8 @@ tsvd_status check_opts(tsvd_ctx* c, const tsvd_opts& o) {
   if (!(o.jacobi_tol > 0) || !std::isfinite(o.jacobi_tol))
     return fail(c, TSVD_EINVAL, "jacobi_tol must be positive");
   if (o.ctas_per_slice != 0 && o.ctas_per_slice != 1 && o.ctas_per_slice != 2 &&
-      o.ctas_per_slice != 4 && o.ctas_per_slice != 8)
-    return fail(c, TSVD_EINVAL, "ctas_per_slice must be 0, 1, 2, 4 or 8");
+      o.ctas_per_slice != 4 && o.ctas_per_slice != 8 && o.ctas_per_slice != TSVD_CTAS_FEWEST)
+    return fail(c, TSVD_EINVAL, "ctas_per_slice must be 0, 1, 2, 4, 8 or TSVD_CTAS_FEWEST");
   if (o.accumulate_v != 0 && o.accumulate_v != 1)
     return fail(c, TSVD_EINVAL, "accumulate_v must be 0 or 1");
   if (o.lanes_per_pair != 0 && o.lanes_per_pair != 4 && o.lanes_per_pair != 8 &&
@@ -913,6 +913,7 @@ RsvtArgs rsvt_args(tsvd_ctx* c, const Problem& p, const Workspace& w, float tau,
   a.jscratch_bytes = w.rjs_bytes;
   a.jknobs = rsvt_knobs(c);
   a.small_fp64 = c->opts.rsvt_small_fp64;
+  a.abs_stop = c->opts.jacobi_stop == TSVD_STOP_SVT ? 1 : 0;
   return a;
 }
 

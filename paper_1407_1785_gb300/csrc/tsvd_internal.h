@@ -382,6 +382,8 @@ struct RsvtArgs {
   // 1: the k x k CholeskyQR2 factorisations and (for k <= 80) the Rayleigh-Ritz eigen-solve
   // in FP64 instead of FP32 with double-single pivots
   int small_fp64 = 0;
+  // 1: the small SVTs use the SVT stopping test (SliceArgs::abs_stop)
+  int abs_stop = 0;
 };
 
 int rsvt_max_k();

@@ -39,6 +39,7 @@ OP_N, OP_T, OP_C = 0, 1, 2
 WARM_OFF, WARM_ON, WARM_AUTO = 0, 1, 2
 SLICE_AUTO, SLICE_PAIRWISE, SLICE_BLOCK = 0, 1, 2
 STOP_SVT, STOP_RELATIVE = 0, 1
+CTAS_FEWEST = -1
 COMPRESS_GLOBAL, COMPRESS_TUBAL = 1, 2
 PROBLEM_COMPLETE, PROBLEM_RPCA = 1, 2
 

@@ -75,7 +75,8 @@ def test_bad_options_rejected():
     assert L.tsvd_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == libtsvd.TSVD_EINVAL
     for field, bad in (("precision", 5), ("precision", -1), ("rsvt_oversample", -1),
                        ("rsvt_oversample", 65), ("rsvt_kmax", -3), ("rsvt_power", 9),
-                       ("warm_start", 3), ("warm_start", -1)):
+                       ("warm_start", 3), ("warm_start", -1), ("ctas_per_slice", 3),
+                       ("ctas_per_slice", -2), ("jacobi_stop", 2), ("jacobi_stop", -1)):
         o = libtsvd.default_opts()
         setattr(o, field, bad)
         assert L.tsvd_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == libtsvd.TSVD_EINVAL

@@ -129,3 +129,22 @@ def test_forced_plan_a_tensor_cannot_take_fails_cleanly():
         ctx.tnn_complete_batched(probs, iters)
         for q, Xo in zip(probs, refs):
             assert relerr(host(q["out0"], q["dims"]), Xo, floor=1e-6) <= ADMM_TOL
+
+
+def test_fewest_ctas_plan_matches_oracle():
+    """ctas_per_slice = CTAS_FEWEST (each slice on the fewest CTAs that hold it, for launches
+    that share the GPU): the batched solves still reach the oracle's iterates."""
+    torch = _torch()
+    iters = 20
+    probs, refs = _completion_problems([((64, 48, 7), 3, 0.5), ((120, 100, 4), 4, 0.5)], iters,
+                                       seed0=380)
+    rp, rrefs = _rpca_problems([((90, 70, 6), 2, 0.1)], iters, seed0=381)
+    with libtsvd.Context(device=0, stream=torch.cuda.current_stream().cuda_stream,
+                         ctas_per_slice=libtsvd.CTAS_FEWEST) as ctx:
+        st = ctx.solve_batched(probs + rp, iters, stats=True)
+    assert st["nonconverged"] == 0
+    for q, Xo in zip(probs, refs):
+        assert relerr(host(q["out0"], q["dims"]), Xo, floor=1e-6) <= ADMM_TOL
+    for q, ((Lo, So), nm) in zip(rp, rrefs):
+        assert relerr(host(q["out0"], q["dims"]), Lo, floor=1e-6) <= ADMM_TOL
+        assert relerr(host(q["out1"], q["dims"]), So, floor=1e-3 * nm) <= ADMM_TOL
