@@ -231,6 +231,8 @@ class Context:
         for k, v in opts.items():
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")
+            if isinstance(v, str):   # autotune_cache: a path
+                v = os.fsencode(v)
             setattr(o, k, v)
         h = ctypes.c_void_p()
         st = L.tsvd_create(ctypes.byref(h), int(device), ctypes.c_void_p(stream or 0),
