@@ -41,13 +41,34 @@ __device__ __forceinline__ void tile_sync() {
 }
 
 struct TileSmem {
-  float* fre;    // [kr4][ldf]  cos rows r < KR, zero-padded
-  float* fim;    // [ki4][ldf]  -sin rows r >= KR, zero-padded
+  float* fre;    // [kr4][ldf]  cos rows r < KR, zero-padded (product form)
+  float* fim;    // [ki4][ldf]  -sin rows r >= KR, zero-padded (product form)
+  float2* tw;    // [nh] (cos, sin)(2 pi m / nh) (FFT form)
   float* zt;     // [nf][znb][TT]
   float* yt;     // [nf][2 q2][TT]
   float* nrm;    // [RS][TT] partial tube norms (RPCA tube mode)
   int ldf, kr, ki, znb, q2;
+  bool fft;
 };
+
+// FFT form of the half-mode transform: for even nh >= kTileFftMinNh whose half length
+// M = nh / 2 has no prime factor above 5, the R2C of a tube packs it into the complex sequence
+// c_j = x_2j + i x_2j+1 of length M, transforms that with a mixed-radix Stockham FFT (radices
+// 4, 2, 3, 5) and splits the result into the M + 1 stored coefficients; the C2R runs the same
+// steps backwards.  Shorter tubes use the DFT products above, which measured faster there: the
+// products run two tubes per packed FMA from register-blocked rows, while the FFT's stages are
+// separated by barriers (128 x 128 slices: products 0.027 / 0.041 / 0.069 ms per tube pass at
+// nh = 60 / 100 / 128, FFT 0.045 / 0.046 / 0.059; at nh = 200 and 250 the FFT takes 0.086 and
+// 0.097 ms against 0.136 and 0.167).
+constexpr int kTileFftMinNh = 128;
+__host__ __device__ inline bool tile_fft_ok(const TubeGeom& g) {
+  if (g.nh < kTileFftMinNh || (g.nh & 1)) return false;
+  int m = g.nh / 2;
+  while (m % 2 == 0) m /= 2;
+  while (m % 3 == 0) m /= 3;
+  while (m % 5 == 0) m /= 5;
+  return m == 1;
+}
 
 __host__ __device__ inline int tile_kr(const TubeGeom& g) { return g.nh / 2 + 1; }
 __host__ __device__ inline int tile_ki(const TubeGeom& g) { return g.nh - tile_kr(g); }
@@ -59,6 +80,7 @@ __host__ __device__ inline int tile_znb(const TubeGeom& g) { return tile_round4(
 __host__ __device__ inline int tile_q2(const TubeGeom& g) { return tile_round4(g.hh); }
 
 __host__ __device__ inline size_t tile_table_floats(const TubeGeom& g) {
+  if (tile_fft_ok(g)) return (size_t)tile_round4(2 * g.nh);
   const int ki4 = tile_round4(tile_ki(g) > 0 ? tile_ki(g) : 1);
   return (size_t)(tile_round4(tile_kr(g)) + ki4) * tile_ldf(g);
 }
@@ -76,8 +98,10 @@ __device__ __forceinline__ TileSmem tile_carve(unsigned char* raw, const TubeGeo
   s.ki = tile_ki(g);
   s.znb = tile_znb(g);
   s.q2 = tile_q2(g);
+  s.fft = tile_fft_ok(g);
   s.fre = reinterpret_cast<float*>(raw);
   s.fim = s.fre + (size_t)tile_round4(s.kr) * s.ldf;
+  s.tw = reinterpret_cast<float2*>(raw);
   s.zt = s.fre + tile_table_floats(g);
   s.yt = s.zt + (size_t)g.nf * s.znb * TT;
   s.nrm = s.yt + (size_t)g.nf * 2 * s.q2 * TT;
@@ -88,6 +112,10 @@ __device__ __forceinline__ TileSmem tile_carve(unsigned char* raw, const TubeGeo
 // stepped by r) and the zero padding of the zt and yt blocks, which the tile steps never write.
 __device__ void tile_build(const TileSmem& s, const TubeGeom& g, const float2* __restrict__ twid_h) {
   const int nh = g.nh, hh = g.hh, ldf = s.ldf;
+  if (s.fft) {
+    for (int m = threadIdx.x; m < nh; m += TILE_THREADS) s.tw[m] = twid_h[m];
+    return;   // the FFT form reads no padding
+  }
   const int rows = tile_round4(s.kr) + tile_round4(s.ki > 0 ? s.ki : 1);
   for (int r = threadIdx.x; r < rows; r += TILE_THREADS) {
     const bool cosrow = r < tile_round4(s.kr);
@@ -242,6 +270,270 @@ __device__ void tile_fold(const TileSmem& s, const TubeGeom& g, bool forward) {
   }
 }
 
+// ---- FFT form
+// Each thread works on two adjacent tubes (t, t + 1) at once: a complex value of the pair is
+// CP{re, im} with re = (Re x_t, Re x_t+1), im = (Im x_t, Im x_t+1), so the arithmetic runs on
+// packed FP32x2 instructions and the shared-memory accesses are 8-byte rows of 16 lanes.
+struct CP {
+  float2 re, im;
+};
+__device__ __forceinline__ float2 f2s(float c) { return make_float2(c, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2s(-1.f), a); }
+__device__ __forceinline__ CP cpadd(CP a, CP b) { return CP{add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ CP cpsub(CP a, CP b) { return CP{sub2(a.re, b.re), sub2(a.im, b.im)}; }
+__device__ __forceinline__ CP cpscale(float c, CP a) {
+  return CP{__fmul2_rn(a.re, f2s(c)), __fmul2_rn(a.im, f2s(c))};
+}
+// a w for one complex number w = (wr, wi) shared by both tubes
+__device__ __forceinline__ CP cpmul(CP a, float wr, float wi) {
+  return CP{__ffma2_rn(a.re, f2s(wr), __fmul2_rn(a.im, f2s(-wi))),
+            __ffma2_rn(a.re, f2s(wi), __fmul2_rn(a.im, f2s(wr)))};
+}
+// i sg a for sg = +-1
+__device__ __forceinline__ CP cpimul(float sg, CP a) {
+  return CP{__fmul2_rn(a.im, f2s(-sg)), __fmul2_rn(a.re, f2s(sg))};
+}
+__device__ __forceinline__ CP cpconj(CP a) { return CP{a.re, __fmul2_rn(a.im, f2s(-1.f))}; }
+
+// A complex [M][TT] buffer of every mode-3 block f of the tile: real rows at re + f * fstride,
+// imaginary rows im rows further (row pitch TT); element (row, tube pair p) at 2 p.
+struct FftBuf {
+  float* re;
+  int fstride;
+  int im;
+  __device__ CP get(int f, int row, int p) const {
+    const float* q = re + (size_t)f * fstride + (size_t)row * TT + 2 * p;
+    return CP{*reinterpret_cast<const float2*>(q), *reinterpret_cast<const float2*>(q + (size_t)im * TT)};
+  }
+  __device__ void put(int f, int row, int p, CP v) const {
+    float* q = re + (size_t)f * fstride + (size_t)row * TT + 2 * p;
+    *reinterpret_cast<float2*>(q) = v.re;
+    *reinterpret_cast<float2*>(q + (size_t)im * TT) = v.im;
+  }
+};
+// The two buffers of the FFT form: A in the spectrum block (yt), B in the real block (zt).
+__device__ __forceinline__ FftBuf fft_buf_a(const TileSmem& s) {
+  return FftBuf{s.yt, 2 * s.q2 * TT, s.q2};
+}
+__device__ __forceinline__ FftBuf fft_buf_b(const TileSmem& s, int M) {
+  return FftBuf{s.zt, s.znb * TT, M};
+}
+
+constexpr int FFT_PAIRS = TT / 2;                       // tube pairs of a tile row
+constexpr int FFT_GROUPS = TILE_THREADS / FFT_PAIRS;    // rows a pass works on at once
+
+// v[m] <- sum_r v[r] e^{sg 2 pi i r m / R} (the small DFTs of the Stockham stages; radix 3 and 5
+// in the symmetric form, their constants read from the table).
+template <int R>
+__device__ __forceinline__ void fft_butterfly(CP (&v)[R], float sg, const float2* tw, int nh) {
+  static_assert(R == 2 || R == 3 || R == 4 || R == 5, "radix");
+  if constexpr (R == 2) {
+    const CP a = v[0], b = v[1];
+    v[0] = cpadd(a, b);
+    v[1] = cpsub(a, b);
+  } else if constexpr (R == 4) {
+    const CP s02 = cpadd(v[0], v[2]), d02 = cpsub(v[0], v[2]);
+    const CP s13 = cpadd(v[1], v[3]), d13 = cpimul(sg, cpsub(v[1], v[3]));
+    v[0] = cpadd(s02, s13);
+    v[2] = cpsub(s02, s13);
+    v[1] = cpadd(d02, d13);
+    v[3] = cpsub(d02, d13);
+  } else if constexpr (R == 3) {
+    const float s3 = tw[nh / 3].y;   // sin(2 pi / 3)
+    const CP t1 = cpadd(v[1], v[2]);
+    const CP t2 = cpsub(v[0], cpscale(0.5f, t1));
+    const CP t3 = cpimul(sg, cpscale(s3, cpsub(v[1], v[2])));
+    v[0] = cpadd(v[0], t1);
+    v[1] = cpadd(t2, t3);
+    v[2] = cpsub(t2, t3);
+  } else {
+    const float2 w1 = tw[nh / 5], w2 = tw[2 * (nh / 5)];   // (cos, sin)(2 pi / 5), (4 pi / 5)
+    const CP t1 = cpadd(v[1], v[4]), t2 = cpadd(v[2], v[3]);
+    const CP t3 = cpsub(v[1], v[4]), t4 = cpsub(v[2], v[3]);
+    const CP a1 = cpadd(v[0], cpadd(cpscale(w1.x, t1), cpscale(w2.x, t2)));
+    const CP a2 = cpadd(v[0], cpadd(cpscale(w2.x, t1), cpscale(w1.x, t2)));
+    const CP b1 = cpimul(sg, cpadd(cpscale(w1.y, t3), cpscale(w2.y, t4)));
+    const CP b2 = cpimul(sg, cpsub(cpscale(w2.y, t3), cpscale(w1.y, t4)));
+    v[0] = cpadd(v[0], cpadd(t1, t2));
+    v[1] = cpadd(a1, b1);
+    v[4] = cpsub(a1, b1);
+    v[2] = cpadd(a2, b2);
+    v[3] = cpsub(a2, b2);
+  }
+}
+
+// One Stockham stage of radix R on every block (in -> out): Ns is the product of the earlier
+// stages' radices; element j < M / R of the stage takes in[j + r M / R], turns entry r by
+// e^{sg 2 pi i r k / (Ns R)} (k = j mod Ns), runs the radix-R DFT and writes
+// out[(j / Ns) Ns R + k + m Ns] -- natural order after the last stage.  Thread (group g, pair
+// p) takes elements q = g, g + FFT_GROUPS, ... of the nf M / R of the tile (f = q / nb,
+// j = q mod nb), stepping f, j, j / Ns and j mod Ns without divisions.
+template <int R>
+__device__ void fft_stage(const FftBuf& in, const FftBuf& out, const float2* tw, int nh, int M,
+                          int nf, int Ns, float sg) {
+  const int nb = M / R;
+  const int p = threadIdx.x % FFT_PAIRS;
+  const int g = threadIdx.x / FFT_PAIRS;
+  const int step = nh / (Ns * R);
+  if (g >= nf * nb) return;
+  int f = g / nb, j = g % nb;
+  int jo = j / Ns, k = j % Ns;
+  const int dq = FFT_GROUPS / Ns, rq = FFT_GROUPS % Ns;
+  while (f < nf) {
+    CP v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in.get(f, j + r * nb, p);
+    if (k) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = tw[r * k * step];
+        v[r] = cpmul(v[r], w.x, sg * w.y);
+      }
+    }
+    fft_butterfly<R>(v, sg, tw, nh);
+    const int o = jo * Ns * R + k;
+#pragma unroll
+    for (int m = 0; m < R; ++m) out.put(f, o + m * Ns, p, v[m]);
+    // next element: j += FFT_GROUPS, carrying into f
+    j += FFT_GROUPS;
+    if (j < nb) {
+      jo += dq;
+      k += rq;
+      if (k >= Ns) {
+        k -= Ns;
+        ++jo;
+      }
+    } else {
+      while (j >= nb) {
+        j -= nb;
+        ++f;
+      }
+      jo = j / Ns;
+      k = j - jo * Ns;
+    }
+  }
+}
+
+// The radix of stage `stage` of a length-M transform (0 past the last stage): fours first,
+// then 2, 3, 5.
+__device__ __forceinline__ int fft_radix(int M, int stage) {
+  int n = 0;
+  for (int r = 4; r != 0; r = r == 4 ? 2 : r == 2 ? 3 : r == 3 ? 5 : 0) {
+    while (M % r == 0) {
+      if (n++ == stage) return r;
+      M /= r;
+    }
+  }
+  return 0;
+}
+__device__ __forceinline__ int fft_nstages(int M) {
+  int n = 0;
+  while (fft_radix(M, n)) ++n;
+  return n;
+}
+
+// The Stockham stages of a length-M transform from buffer `a` (ping-ponging with `b`); returns
+// true when the result ends in `b`.
+__device__ bool fft_run(const TileSmem& s, const FftBuf& a, const FftBuf& b, int nh, int M,
+                        int nf, float sg) {
+  int Ns = 1;
+  bool in_b = false;
+  for (int st = 0;; ++st) {
+    const int R = fft_radix(M, st);
+    if (!R) break;
+    const FftBuf& src = in_b ? b : a;
+    const FftBuf& dst = in_b ? a : b;
+    switch (R) {
+      case 4: fft_stage<4>(src, dst, s.tw, nh, M, nf, Ns, sg); break;
+      case 2: fft_stage<2>(src, dst, s.tw, nh, M, nf, Ns, sg); break;
+      case 3: fft_stage<3>(src, dst, s.tw, nh, M, nf, Ns, sg); break;
+      default: fft_stage<5>(src, dst, s.tw, nh, M, nf, Ns, sg); break;
+    }
+    tile_sync();
+    in_b = !in_b;
+    Ns *= R;
+  }
+  return in_b;
+}
+
+// Real tile (zt) -> spectrum tile (yt), FFT form: pack, transform, split
+// X_k = E_k + e^{-2 pi i k / nh} O_k with E_k = (C_k + conj C_M-k) / 2 and
+// O_k = (C_k - conj C_M-k) / 2i; one thread per pair (k, M - k), so the split may run in place.
+__device__ void tile_forward_fft(const TileSmem& s, const TubeGeom& g) {
+  const int nh = g.nh, M = nh / 2, nf = g.nf;
+  const int p = threadIdx.x % FFT_PAIRS;
+  const FftBuf A = fft_buf_a(s), B = fft_buf_b(s, M);
+  for (int f = 0; f < nf; ++f) {
+    const float* z = s.zt + (size_t)f * s.znb * TT + 2 * p;
+    for (int j = threadIdx.x / FFT_PAIRS; j < M; j += FFT_GROUPS)
+      A.put(f, j, p, CP{*reinterpret_cast<const float2*>(z + (size_t)(2 * j) * TT),
+                        *reinterpret_cast<const float2*>(z + (size_t)(2 * j + 1) * TT)});
+  }
+  tile_sync();
+  const FftBuf& C = fft_run(s, A, B, nh, M, nf, -1.f) ? B : A;
+  const int np = M / 2 + 1;
+  for (int f = 0; f < nf; ++f) {
+    for (int k = threadIdx.x / FFT_PAIRS; k < np; k += FFT_GROUPS) {
+      if (k == 0) {
+        const CP c0 = C.get(f, 0, p);
+        A.put(f, 0, p, CP{add2(c0.re, c0.im), f2s(0.f)});
+        A.put(f, M, p, CP{sub2(c0.re, c0.im), f2s(0.f)});
+        continue;
+      }
+      const int kk = M - k;
+      const CP ck = C.get(f, k, p), cm = C.get(f, kk, p);
+      const CP e = cpscale(0.5f, cpadd(ck, cpconj(cm)));
+      const CP o = cpimul(-1.f, cpscale(0.5f, cpsub(ck, cpconj(cm))));   // (ck - conj cm) / 2i
+      const float2 wk = s.tw[k];
+      A.put(f, k, p, cpadd(e, cpmul(o, wk.x, -wk.y)));
+      if (kk != k) {
+        const float2 wm = s.tw[kk];
+        A.put(f, kk, p, cpadd(cpconj(e), cpmul(cpconj(o), wm.x, -wm.y)));
+      }
+    }
+  }
+  tile_sync();
+}
+
+// Spectrum tile (yt, loaded with the uniform weight 1 / (nf nh)) -> real tile (zt), FFT form:
+// C_k = (X_k + conj X_M-k) + i e^{2 pi i k / nh} (X_k - conj X_M-k) for k < M, the inverse
+// transform, and x_2j = Re c_j, x_2j+1 = Im c_j.  The first step writes into B when the
+// transform has an odd number of stages, so that it ends in A.
+__device__ void tile_inverse_fft(const TileSmem& s, const TubeGeom& g) {
+  const int nh = g.nh, M = nh / 2, nf = g.nf;
+  const int p = threadIdx.x % FFT_PAIRS;
+  const FftBuf A = fft_buf_a(s), B = fft_buf_b(s, M);
+  const bool odd = fft_nstages(M) & 1;
+  const FftBuf& D = odd ? B : A;
+  const int np = M / 2 + 1;
+  for (int f = 0; f < nf; ++f) {
+    for (int k = threadIdx.x / FFT_PAIRS; k < np; k += FFT_GROUPS) {
+      const int kk = M - k;
+      CP xk = A.get(f, k, p), xm = A.get(f, kk, p);
+      if (k == 0) xk.im = xm.im = f2s(0.f);   // a C2R reads only the real parts of X_0, X_M
+      const float2 wk = s.tw[k];
+      D.put(f, k, p, cpadd(cpadd(xk, cpconj(xm)), cpimul(1.f, cpmul(cpsub(xk, cpconj(xm)), wk.x, wk.y))));
+      if (k != 0 && kk != k) {
+        const float2 wm = s.tw[kk];
+        D.put(f, kk, p,
+              cpadd(cpadd(xm, cpconj(xk)), cpimul(1.f, cpmul(cpsub(xm, cpconj(xk)), wm.x, wm.y))));
+      }
+    }
+  }
+  tile_sync();
+  fft_run(s, D, odd ? A : B, nh, M, nf, 1.f);   // ends in A by the choice of D
+  for (int f = 0; f < nf; ++f) {
+    float* z = s.zt + (size_t)f * s.znb * TT + 2 * p;
+    for (int j = threadIdx.x / FFT_PAIRS; j < M; j += FFT_GROUPS) {
+      const CP c = A.get(f, j, p);
+      *reinterpret_cast<float2*>(z + (size_t)(2 * j) * TT) = c.re;
+      *reinterpret_cast<float2*>(z + (size_t)(2 * j + 1) * TT) = c.im;
+    }
+  }
+  tile_sync();
+}
+
 // Spectrum tile (loaded, weighted) -> real tile.
 template <int RM>
 __device__ void tile_inverse(const TileSmem& s, const TubeGeom& g, const float2* twf,
@@ -249,6 +541,10 @@ __device__ void tile_inverse(const TileSmem& s, const TubeGeom& g, const float2*
   if (g.nf > 1) {
     tile_full_dft(s, g, twf, 1.f, fm);
     tile_sync();
+  }
+  if (s.fft) {
+    tile_inverse_fft(s, g);
+    return;
   }
   for (int f = 0; f < g.nf; ++f) {
     float* z = s.zt + (size_t)f * s.znb * TT;
@@ -265,10 +561,9 @@ __device__ void tile_inverse(const TileSmem& s, const TubeGeom& g, const float2*
   }
 }
 
-// Real tile -> spectrum tile.
+// Real tile -> spectrum tile, product form (before the mode-3 DFT).
 template <int RM>
-__device__ void tile_forward(const TileSmem& s, const TubeGeom& g, const float2* twf,
-                             const float2* fm) {
+__device__ void tile_forward_products(const TileSmem& s, const TubeGeom& g) {
   if (s.ki > 0) {
     tile_fold(s, g, true);
     tile_sync();
@@ -286,6 +581,17 @@ __device__ void tile_forward(const TileSmem& s, const TubeGeom& g, const float2*
     }
   }
   tile_sync();
+}
+
+// Real tile -> spectrum tile.
+template <int RM>
+__device__ void tile_forward(const TileSmem& s, const TubeGeom& g, const float2* twf,
+                             const float2* fm) {
+  if (s.fft) {
+    tile_forward_fft(s, g);
+  } else {
+    tile_forward_products<RM>(s, g);
+  }
   if (g.nf > 1) {
     tile_full_dft(s, g, twf, -1.f, fm);
     tile_sync();
@@ -293,7 +599,8 @@ __device__ void tile_forward(const TileSmem& s, const TubeGeom& g, const float2*
 }
 
 // Loads the stored spectrum of the tile (conjugate partners on the self-conjugate columns)
-// and applies the C2R weights c_kh / (nf nh).
+// and applies the C2R weights: c_kh / (nf nh) for the product form (c = 1 at kh = 0 and nh/2,
+// else 2), 1 / (nf nh) for the FFT form.
 __device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
                                    const float2* __restrict__ spec, int64_t t0,
                                    const int* __restrict__ fp) {
@@ -331,7 +638,7 @@ __device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
       const int q = idx / TT;
       const int kf = q % nf, kh = q / nf;
       const bool selfcol = (kh == 0) || (2 * kh == nh);
-      const float w = (selfcol ? 1.f : 2.f) * inv;
+      const float w = (selfcol || s.fft ? 1.f : 2.f) * inv;
       const size_t row = (size_t)kf * 2 * q2 + kh;
       s.yt[row * TT + t] = v[u].x * w;
       s.yt[(row + q2) * TT + t] = v[u].y * w;
