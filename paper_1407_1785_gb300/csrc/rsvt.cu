@@ -880,6 +880,10 @@ __global__ void __launch_bounds__(256) rsvt_refill_kernel(float2* P, const float
 // rank maximum restarts for the next call.
 __global__ void rsvt_next_k_kernel(RsvtStat* st, int oversample, int kmax) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double kc = st->k;   // the width this iteration ran with
+  st->ksum[0] += kc;
+  st->ksum[1] += kc * kc;
+  st->ksum[2] += kc * kc * kc;
   int kn = (st->rank_max + oversample + 7) / 8 * 8;
   kn = kn > st->k ? kn : st->k;
   kn = kn < kmax ? kn : kmax;
@@ -893,6 +897,7 @@ __global__ void rsvt_state_init_kernel(RsvtStat* st, int k0) {
   st->saturated = 0;
   st->drops = 0;
   st->k = k0;
+  st->ksum[0] = st->ksum[1] = st->ksum[2] = 0.0;
 }
 
 // Largest sketch width whose Gram and eigenvectors fit one CTA's shared memory.

@@ -337,6 +337,7 @@ struct RsvtStat {
   int saturated;   // slices whose whole sketch lay above that level
   int drops;       // columns dropped by the Cholesky factorisations
   int k;           // device-chosen sketch width (RsvtArgs::kdev mode)
+  double ksum[3];  // kdev mode: sums of k, k^2, k^3 over the iterations run (work accounting)
 };
 
 struct RsvtArgs {

@@ -70,3 +70,32 @@ def test_static_scratch_rejects_oversize_and_host_buffers():
     h = np.zeros(4 * 4 * 4, np.float32)
     assert libtsvd.tsvt_static(h, h, (4, 4, 4), 1.0) == libtsvd.TSVD_EINVAL
     assert libtsvd.tsvt_static(y, y, (2, 2, 2), -1.0) == libtsvd.TSVD_EINVAL
+
+
+def test_static_scratch_tsvt_is_capturable():
+    """After a first call outside capture (the scratch address lookup), tsvt_static can be
+    captured into a CUDA graph: its tables are written on the device from launch arguments,
+    so a replay reads no host memory; replays follow new contents of the input buffer."""
+    torch = pytest.importorskip("torch")
+    shape, tau = (40, 28, 12), 2.0
+    Y = synth.normal(25, 0, int(np.prod(shape))).reshape(shape, order="F").astype(np.float32)
+    y = torch.from_numpy(colmajor(Y)).cuda()
+    z = torch.empty_like(y)
+    assert libtsvd.tsvt_static(y, z, shape, tau, torch.cuda.current_stream().cuda_stream) == \
+        libtsvd.TSVD_OK
+    torch.cuda.synchronize()
+    Z1 = uncolmajor(z.cpu().numpy(), shape)
+    zg = torch.full_like(y, float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="thread_local"):
+        st = libtsvd.tsvt_static(y, zg, shape, tau, torch.cuda.current_stream().cuda_stream)
+    assert st == libtsvd.TSVD_OK
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(uncolmajor(zg.cpu().numpy(), shape), Z1)
+    y.mul_(3.0)
+    g.replay()
+    torch.cuda.synchronize()
+    Zo = oracle.tsvt(3.0 * Y.astype(np.float64), tau)
+    Zg = uncolmajor(zg.cpu().numpy(), shape)
+    assert relerr(Zg, Zo, floor=max(np.linalg.norm(Zo), 3e-3 * np.linalg.norm(Y))) <= TSVT_TOL
