@@ -223,8 +223,8 @@ def test_graph_replay_matches_direct_launches(kind, tmp_path):
 @pytest.mark.parametrize("warm", ["off", "auto", "on"])
 def test_batched_uneven_problems_match_oracle(warm, persistent):
     """A batch of uneven tensors (completion and RPCA, 3-way and 4-way) in one call: every
-    tensor matches the oracle's solve, with the warm-started Jacobi off, on for the
-    completions only (the default) or on for all, as one persistent launch per iteration or
+    tensor matches the oracle's solve, with the warm-started Jacobi off, AUTO (the default,
+    warm for every tensor) or ON, as one persistent launch per iteration or
     as per-tensor stream branches (the default); a second call replays the captured batch
     graph and gives the same bits."""
     from paper_1407_1785_gb300 import libtsvd
