@@ -91,6 +91,13 @@ def test_create_without_gpu_reports_cuda_error():
     h = ctypes.c_void_p()
     assert L.tsvd_create(ctypes.byref(h), 0, None, None) == libtsvd.TSVD_ECUDA
     assert not h.value
+    # valid non-default values pass the option checks and fail only at the device
+    for field, val in (("ctas_per_slice", libtsvd.CTAS_FEWEST), ("ctas_per_slice", 8),
+                       ("jacobi_stop", libtsvd.STOP_RELATIVE), ("warm_start", libtsvd.WARM_OFF)):
+        o = libtsvd.default_opts()
+        setattr(o, field, val)
+        assert L.tsvd_create(ctypes.byref(h), 0, None, ctypes.byref(o)) == libtsvd.TSVD_ECUDA
+        assert not h.value
 
 
 def test_library_is_the_in_tree_build():
