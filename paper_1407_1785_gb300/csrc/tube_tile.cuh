@@ -40,6 +40,18 @@ __device__ __forceinline__ void tile_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(TILE_THREADS) : "memory");
 }
 
+// j / nf for the mode-3 length nf <= NF_MAX without a division instruction: floor(j m / 2^16)
+// with m = ceil(2^16 / nf) is exact for j < 8192 (checked for every nf <= 8), and the tile
+// form's indices stay below nf nh <= 8 x 254 (tube offsets) and nf hh <= 8 x 128 (spectrum
+// rows).
+struct DivNf {
+  unsigned m;
+  int nf;
+  __device__ explicit DivNf(int n) : m((65536u + (unsigned)n - 1u) / (unsigned)n), nf(n) {}
+  __device__ __forceinline__ int div(int j) const { return (int)(((unsigned)j * m) >> 16); }
+  __device__ __forceinline__ int mod(int j) const { return j - div(j) * nf; }
+};
+
 struct TileSmem {
   float* fre;    // [kr4][ldf]  cos rows r < KR, zero-padded (product form)
   float* fim;    // [ki4][ldf]  -sin rows r >= KR, zero-padded (product form)
@@ -605,6 +617,7 @@ __device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
                                    const float2* __restrict__ spec, int64_t t0,
                                    const int* __restrict__ fp) {
   const int nf = g.nf, nh = g.nh, hh = g.hh, q2 = s.q2;
+  const DivNf dn(nf);
   const float inv = 1.f / (float)(nf * nh);
   const int total = nf * hh * TT;
   constexpr int U = 8;   // loads a thread keeps in flight (see the element loops)
@@ -618,9 +631,9 @@ __device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
       v[u] = make_float2(0.f, 0.f);
       if (idx < total && live) {
         const int q = idx / TT;
-        const int kf = q % nf, kh = q / nf;
+        const int kh = dn.div(q), kf = q - kh * nf;
         const bool selfcol = (kh == 0) || (2 * kh == nh);
-        const int pk = fp ? fp[kf] : (nf - kf) % nf;
+        const int pk = fp ? fp[kf] : (kf == 0 ? 0 : nf - kf);
         // L2-only loads: in the persistent batched kernel the spectrum was written by other
         // SMs earlier in the same launch
         if (selfcol && pk < kf) {
@@ -636,7 +649,7 @@ __device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
       const int idx = base + u * TILE_THREADS;
       if (idx >= total) continue;
       const int q = idx / TT;
-      const int kf = q % nf, kh = q / nf;
+      const int kh = dn.div(q), kf = q - kh * nf;
       const bool selfcol = (kh == 0) || (2 * kh == nh);
       const float w = (selfcol || s.fft ? 1.f : 2.f) * inv;
       const size_t row = (size_t)kf * 2 * q2 + kh;
@@ -649,10 +662,11 @@ __device__ void tile_load_spectrum(const TileSmem& s, const TubeGeom& g,
 __device__ void tile_store_spectrum(const TileSmem& s, const TubeGeom& g, float2* __restrict__ spec,
                                     int64_t t0) {
   const int nf = g.nf, hh = g.hh, q2 = s.q2;
+  const DivNf dn(nf);
   for (int idx = threadIdx.x; idx < nf * hh * TT; idx += TILE_THREADS) {
     const int q = idx / TT, t = idx % TT;
     if (t0 + t >= g.N12) continue;
-    const int kf = q % nf, kh = q / nf;
+    const int kh = dn.div(q), kf = q - kh * nf;
     const size_t row = (size_t)kf * 2 * q2 + kh;
     spec[(size_t)q * g.N12 + t0 + t] = make_float2(s.yt[row * TT + t], s.yt[(row + q2) * TT + t]);
   }
@@ -683,7 +697,11 @@ __device__ void tube_tile_body(const TubeArgs& a, int64_t t0, unsigned char* sme
   const int t = tid % TT;
   const int nf = g.nf;
   const int znb = s.znb;
-  auto zrow = [&](int j) -> size_t { return ((size_t)(j % nf) * znb + j / nf) * TT + t; };
+  const DivNf dn(nf);
+  auto zrow = [&](int j) -> size_t {
+    const int jh = dn.div(j);
+    return ((size_t)(j - jh * nf) * znb + jh) * TT + t;
+  };
   const bool live = t0 + t < N12;
   // rows j0, j0 + RS, ... of a thread are processed U at a time: the U rows' global loads are
   // issued together before any of their stores (restrict pointers), so each thread keeps U
