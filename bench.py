@@ -91,11 +91,26 @@ WORKLOADS = {
                        "completion / half RPCA, one batched call"),
 }
 
-# DRAM traffic of one jacobi_svt_kernel launch from an ncu capture of the video workload,
-# valid only for the kernel source it was taken on (see profiles/).
-TRAFFIC = {"source": "paper_1407_1785_gb300/csrc/slice_svt.cu",
-           "sha256": "21c090a1f89b98bb2d32052c08722cd18c9f1190226e1a8ca3914b9624739d58",
-           "bytes_per_launch": 21770240 + 9728512}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one tube-pass launch from an
+# ncu capture of the colour-video workload, valid only for the kernel sources it was taken on
+# (profiles/tube_tile_kernel_color_288x352x3x60.md); the slice SVT's traffic has no capture on
+# the current source, so its roofline reports none.
+TUBE_TRAFFIC = {"workload": "color",
+                "sources": {"paper_1407_1785_gb300/csrc/tube_tile.cuh":
+                            "0200a606ff6e438f8f86a5486581e4bdb0c500caa8365b9a944d2c87be1e8b8b",
+                            "paper_1407_1785_gb300/csrc/tube_pass.cu":
+                            "c8db9e21a8ca9b2ac2529373ff872fb62320ae3fa533fc2a30f6ed4348e14291"},
+                "bytes_per_launch": 219881472 + 106778624}
+
+
+def tube_traffic(workload):
+    """The captured tube-pass traffic per launch when it applies to this workload and source."""
+    if workload != TUBE_TRAFFIC["workload"]:
+        return None
+    for path, sha in TUBE_TRAFFIC["sources"].items():
+        if file_sha256(os.path.join(ROOT, path)) != sha:
+            return None
+    return TUBE_TRAFFIC["bytes_per_launch"]
 
 
 def parse_args():
@@ -755,13 +770,9 @@ def run_ours(args):
         flops = sum(jacobi_gvl_flops(it["dims"][0], it["dims"][1], half_slices(it["dims"]))
                     for it in items)
         achieved = flops / (slice_ms / 1000.0 / n_it) / 1e12
-        traffic = None
-        if (args.workload == "video" and
-                file_sha256(os.path.join(ROOT, TRAFFIC["source"])) == TRAFFIC["sha256"]):
-            traffic = TRAFFIC["bytes_per_launch"]
         roofline = {"bound": "alu", "kernel": "jacobi_svt_kernel", "achieved": achieved,
                     "peak": alu_peak(peaks), "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak(peaks), "traffic": traffic,
+                    "frac": achieved / alu_peak(peaks), "traffic": None,
                     "peak_source": peaks["fp32_source"],
                     "alg_flops_per_iteration": flops,
                     "avg_launch_ms": slice_ms / max(slice_launches, 1),
@@ -778,7 +789,8 @@ def run_ours(args):
                          "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                          "peak_source": ("MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks
                                          else "fallback"),
-                         "alg_bytes_per_iteration": t_bytes, "ms_per_iteration": tube_ms / n_it}
+                         "alg_bytes_per_iteration": t_bytes, "ms_per_iteration": tube_ms / n_it,
+                         "traffic": tube_traffic(args.workload)}
 
     mixed = None
     if prec == "fp32" and args.mixed not in ("none", "fp32"):

@@ -85,3 +85,17 @@ def test_equal_error_verdict():
     assert v["worst_tensor"] == 2 and abs(v["worst_ratio"] - 2.0) < 1e-12
     assert bench.equal_error_verdict([0.0505], [0.05])["equal_error"]
     assert not bench.equal_error_verdict([0.0506], [0.05])["equal_error"]
+
+
+def test_tube_traffic_matches_its_profile():
+    """The captured tube-pass traffic bench.py reports comes from the committed colour-video
+    profile: same kernel sources, and DRAM bytes equal to the profile's read + write."""
+    import re
+    with open(os.path.join(ROOT, "profiles", "tube_tile_kernel_color_288x352x3x60.md")) as f:
+        text = f.read()
+    for path, sha in bench.TUBE_TRAFFIC["sources"].items():
+        assert f"`{os.path.basename(path)}` sha256 `{sha}`" in text
+    mb = [float(x) for x in re.findall(r"`dram__bytes_(?:read|write)\.sum` \| ([0-9.]+) MB", text)]
+    assert len(mb) == 2
+    assert abs(sum(mb) * 1e6 - bench.TUBE_TRAFFIC["bytes_per_launch"]) < 0.1e6
+    assert bench.tube_traffic("video") is None
